@@ -1,0 +1,618 @@
+/*
+ * fq_oracle.c -- plain, slow FP64 CPU statement of the uPDI hot path of
+ * 3D-FQFlow (arXiv 2509.05464).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this code:
+ * only the tests, the smoke check and the CPU-baseline leg of the benchmark
+ * load it.  It shares no code, header, table or constant with the CUDA
+ * library; both read the same seeded inputs and nothing else.
+ *
+ * Every quantity is evaluated in double precision from its definition, in
+ * the order the definition states, with no blocking, fusion or reordering.
+ * Build with -ffp-contract=off so that the integer-valued decisions
+ * (classification, binning) follow plain IEEE double arithmetic.
+ *
+ * Parity status of each function is listed in its comment ("pinned by"):
+ * the pins live in tests/test_oracle_*.py.
+ *
+ * Parity unpinned: the absolute RF scale against the paper's
+ * frequency-domain PFIELD model (Eq. 1).  The paper prints no echo values,
+ * and the narrowband time-domain restatement used here differs from Eq. 1
+ * by design (ideal plane-wave transmit, single point per element, no
+ * elevation focusing); only its internal physics (time of flight, pulse
+ * energy, attenuation, directivity, superposition, symmetry) is pinned.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------
+ * Probe geometry (Sec. 2.3 / App. D): element centres on the z = 0 plane,
+ * x fastest.  Linear arrays have ny = 1.
+ * ---------------------------------------------------------------------- */
+static void element_pos(int m, int nx, int ny, double px, double py, double *ex, double *ey)
+{
+    int ix = m % nx, iy = m / nx;
+    *ex = ((double)ix - 0.5 * (double)(nx - 1)) * px;
+    *ey = ((double)iy - 0.5 * (double)(ny - 1)) * py;
+}
+
+/* plane-wave direction for tilts (tx, ty) */
+static void pw_dir(double tx, double ty, double u[3])
+{
+    u[0] = sin(tx);
+    u[1] = sin(ty);
+    u[2] = sqrt(1.0 - u[0] * u[0] - u[1] * u[1]);
+}
+
+/* min over elements of u . e_m: the transmit time origin (first firing) */
+static double pw_origin(const double u[3], int nx, int ny, double px, double py)
+{
+    double best = 1e300;
+    for (int m = 0; m < nx * ny; ++m) {
+        double ex, ey;
+        element_pos(m, nx, ny, px, py, &ex, &ey);
+        double d = u[0] * ex + u[1] * ey;
+        if (d < best) best = d;
+    }
+    return best;
+}
+
+static double sinc_unnorm(double x) { return x == 0.0 ? 1.0 : sin(x) / x; }
+
+/* ------------------------------------------------------------------------
+ * Two-way pulse p(t) = 1/2 (1 + cos(2 pi t / T)) cos(2 pi f0 t), |t| < T/2,
+ * T = n_cycles / f0: an n-cycle Hann-windowed tone (the transmit waveform of
+ * Eq. 1 restated in time; reading recorded in the design notes).
+ * ---------------------------------------------------------------------- */
+static double pulse(double t, double f0, double T)
+{
+    if (fabs(t) >= 0.5 * T) return 0.0;
+    return 0.5 * (1.0 + cos(2.0 * OR_PI * t / T)) * cos(2.0 * OR_PI * f0 * t);
+}
+
+/* ------------------------------------------------------------------------
+ * RF synthesis (Eq. 1 restated as a narrowband time-domain sum; Sec. 2.3,
+ * App. D; weak scattering => linear superposition over scatterers):
+ *
+ *   RF_{a,m}[k] = sum_s A_{s,m,a} p(k/fs - tau_{s,m,a})
+ *   tau = (u_a . r_s - min_m' u_a . e_m') / c + |r_s - e_m| / c
+ *   A   = R_s * D * exp(-alpha f0 c tau) / |r_s - e_m|
+ *   D   = sinc(k0 bx (x_s - x_m)/r) [* sinc(k0 by (y_s - y_m)/r) if ny > 1]
+ *
+ * pos: float [3][S] (x, y, z rows), amp: float [S]; rf: double [A][M][Ns].
+ * If accumulate != 0 the sum is added to rf, otherwise rf is overwritten.
+ * Pinned by: single-scatterer closed form (T1), superposition (T3),
+ * attenuation ratio, mirror symmetry (T11).
+ * ---------------------------------------------------------------------- */
+void or_simulate_rf(int nx, int ny, double px, double py, double wx, double wy,
+                    double f0, double fs, double c, double alpha_db_cm_mhz, int n_cycles, int ns,
+                    int n_ang, const double *tilt_x, const double *tilt_y,
+                    int64_t S, const float *pos, const float *amp, int accumulate, double *rf)
+{
+    const int M = nx * ny;
+    const double T = (double)n_cycles / f0;
+    const double k0 = 2.0 * OR_PI * f0 / c;
+    const double alpha_np = alpha_db_cm_mhz * 100.0 / (20.0 / log(10.0)); /* Np / (m MHz) */
+    const double f0_mhz = f0 * 1e-6;
+    const float *X = pos, *Y = pos + S, *Z = pos + 2 * S;
+
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int am = 0; am < n_ang * M; ++am) {
+        int a = am / M, m = am % M;
+        double u[3];
+        pw_dir(tilt_x[a], tilt_y[a], u);
+        double origin = pw_origin(u, nx, ny, px, py);
+        double ex, ey;
+        element_pos(m, nx, ny, px, py, &ex, &ey);
+        double *line = rf + (int64_t)am * ns;
+        if (!accumulate)
+            for (int k = 0; k < ns; ++k) line[k] = 0.0;
+        for (int64_t s = 0; s < S; ++s) {
+            double x = X[s], y = Y[s], z = Z[s];
+            double dx = x - ex, dy = y - ey, dz = z;
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (r == 0.0) continue;
+            double path_tx = u[0] * x + u[1] * y + u[2] * z - origin;
+            double path = path_tx + r;
+            double tau = path / c;
+            double D = sinc_unnorm(k0 * 0.5 * wx * dx / r);
+            if (ny > 1) D *= sinc_unnorm(k0 * 0.5 * wy * dy / r);
+            double A = (double)amp[s] * D * exp(-alpha_np * f0_mhz * path) / r;
+            int64_t kmin = (int64_t)ceil((tau - 0.5 * T) * fs);
+            int64_t kmax = (int64_t)floor((tau + 0.5 * T) * fs);
+            if (kmin < 0) kmin = 0;
+            if (kmax > ns - 1) kmax = ns - 1;
+            for (int64_t k = kmin; k <= kmax; ++k)
+                line[k] += A * pulse((double)k / fs - tau, f0, T);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * rf2iq (Alg. 3 step 2.3.2.1): mix down by f0 then low-pass:
+ *   IQ[k] = 2 sum_{j=-J..J} h_j RF[k-j] exp(-i 2 pi f0 (k-j) / fs)
+ * h: Hann-windowed ideal low-pass with cutoff f0, 2J+1 taps with
+ * J = 2 round(fs/f0), window w_j = 1/2 (1 + cos(pi j / (J+1))), normalised
+ * to sum 1.  Samples outside [0, Ns) are zero.  (The paper does not specify
+ * the filter; this reading is recorded in the design notes.)
+ * rf: float [n_lines][Ns]; iq: double complex interleaved [n_lines][Ns][2].
+ * Pinned by: np.convolve of the mixed signal, pure tone / DC responses.
+ * ---------------------------------------------------------------------- */
+int or_rf2iq_taps(double f0, double fs, double *h /* [2J+1] or NULL */)
+{
+    int J = 2 * (int)lround(fs / f0);
+    if (h) {
+        double sum = 0.0;
+        for (int j = -J; j <= J; ++j) {
+            double x = 2.0 * f0 / fs * (double)j;            /* normalised-sinc argument */
+            double ideal = 2.0 * f0 / fs * (j == 0 ? 1.0 : sin(OR_PI * x) / (OR_PI * x));
+            double w = 0.5 * (1.0 + cos(OR_PI * (double)j / (double)(J + 1)));
+            h[j + J] = w * ideal;
+            sum += h[j + J];
+        }
+        for (int j = 0; j < 2 * J + 1; ++j) h[j] /= sum;
+    }
+    return 2 * J + 1;
+}
+
+void or_rf2iq(double f0, double fs, int ns, int64_t n_lines, const float *rf, double *iq)
+{
+    int ntap = or_rf2iq_taps(f0, fs, NULL);
+    int J = (ntap - 1) / 2;
+    double *h = (double *)malloc(sizeof(double) * ntap);
+    or_rf2iq_taps(f0, fs, h);
+    #pragma omp parallel for schedule(static)
+    for (int64_t l = 0; l < n_lines; ++l) {
+        const float *x = rf + l * ns;
+        double *o = iq + l * ns * 2;
+        for (int k = 0; k < ns; ++k) {
+            double re = 0.0, im = 0.0;
+            for (int j = -J; j <= J; ++j) {
+                int n = k - j;
+                if (n < 0 || n >= ns) continue;
+                double ph = 2.0 * OR_PI * f0 * (double)n / fs;
+                re += h[j + J] * (double)x[n] * cos(ph);
+                im -= h[j + J] * (double)x[n] * sin(ph);
+            }
+            o[2 * k] = 2.0 * re;
+            o[2 * k + 1] = 2.0 * im;
+        }
+    }
+    free(h);
+}
+
+/* ------------------------------------------------------------------------
+ * Delay-and-sum with coherent compounding (Sec. 2.4.1, Alg. 3):
+ *   tau_{p,m,a} = (u_a . r_p - min u_a . e) / c + |r_p - e_m| / c
+ *   u = tau fs, i = floor(u), phi = u - i,
+ *   v = (1 - phi) IQ[i] + phi IQ[i+1]   (0 if i < 0 or i + 1 >= Ns)
+ *   IQ(p, f) = (1/A) sum_a sum_m w_m(p) v exp(+i 2 pi f0 tau)
+ *   w_m(p) = 1 iff |x_p - x_m| <= z_p / (2 f#) (and the same in y for
+ *   matrix arrays), else 0.  This integer decision is taken in binary32 on
+ *   the coordinates rounded to float, exactly as the kernel takes it.
+ * iq_ch: double complex [F][A][M][Ns][2]; pixels p = (iy*nz + iz)*nx + ix;
+ * out: double complex [P][F][2] (Casorati layout: frames contiguous).
+ * Pinned by: PSF peak (T2), the paper's explicit DAS-matrix form (T7),
+ * mirror symmetry (T11).
+ * ---------------------------------------------------------------------- */
+void or_das(int nx, int ny, double px, double py, double f0, double fs, double c, int ns,
+            int n_ang, const double *tilt_x, const double *tilt_y, int F, const double *iq_ch,
+            int gx, int gy, int gz, double x0, double y0, double z0, double dx, double dy,
+            double dz, double fnum, double *out)
+{
+    const int M = nx * ny;
+    const int64_t P = (int64_t)gx * gy * gz;
+    double *ux = (double *)malloc(sizeof(double) * 4 * n_ang);
+    for (int a = 0; a < n_ang; ++a) {
+        double u[3];
+        pw_dir(tilt_x[a], tilt_y[a], u);
+        ux[4 * a] = u[0]; ux[4 * a + 1] = u[1]; ux[4 * a + 2] = u[2];
+        ux[4 * a + 3] = pw_origin(u, nx, ny, px, py);
+    }
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < P; ++p) {
+        int ix = (int)(p % gx);
+        int iz = (int)((p / gx) % gz);
+        int iy = (int)(p / ((int64_t)gx * gz));
+        double x = x0 + ix * dx, y = y0 + iy * dy, z = z0 + iz * dz;
+        double *o = out + p * F * 2;
+        for (int f = 0; f < 2 * F; ++f) o[f] = 0.0;
+        for (int a = 0; a < n_ang; ++a) {
+            const double *u = ux + 4 * a;
+            double path_tx = u[0] * x + u[1] * y + u[2] * z - u[3];
+            for (int m = 0; m < M; ++m) {
+                double ex, ey;
+                element_pos(m, nx, ny, px, py, &ex, &ey);
+                /* aperture decision in binary32, as the kernel takes it:
+                   |x_p - x_m| <= z_p / (2 f#) on the rounded coordinates */
+                float half = (float)z * (float)(0.5 / fnum);
+                if (fabsf((float)x - (float)ex) > half) continue;
+                if (ny > 1 && fabsf((float)y - (float)ey) > half) continue;
+                double r = sqrt((x - ex) * (x - ex) + (y - ey) * (y - ey) + z * z);
+                double tau = (path_tx + r) / c;
+                double uu = tau * fs;
+                double fi = floor(uu);
+                double phi = uu - fi;
+                int64_t i = (int64_t)fi;
+                if (i < 0 || i + 1 >= ns) continue;
+                double ph = 2.0 * OR_PI * f0 * tau;
+                double cr = cos(ph), ci = sin(ph);
+                for (int f = 0; f < F; ++f) {
+                    const double *line = iq_ch + ((((int64_t)f * n_ang + a) * M + m) * ns) * 2;
+                    double vr = (1.0 - phi) * line[2 * i] + phi * line[2 * i + 2];
+                    double vi = (1.0 - phi) * line[2 * i + 1] + phi * line[2 * i + 3];
+                    o[2 * f] += vr * cr - vi * ci;
+                    o[2 * f + 1] += vr * ci + vi * cr;
+                }
+            }
+        }
+        for (int f = 0; f < 2 * F; ++f) o[f] /= (double)n_ang;
+    }
+    free(ux);
+}
+
+/* ------------------------------------------------------------------------
+ * Complex one-sided (Hestenes) Jacobi SVD of a P x F column set, FP64.
+ * On return the columns of A hold A V = U Sigma (column norms = singular
+ * values) and V (F x F, row-major, complex) is the accumulated rotation,
+ * both sorted by decreasing singular value.  A: [P][F][2] row-major.
+ * Rotations are applied in the round-robin (tournament) order so that the
+ * disjoint pairs of one round can be processed in parallel; the result does
+ * not depend on the thread count.
+ * ---------------------------------------------------------------------- */
+static void rr_pair(int n, int round, int k, int *i, int *j)
+{
+    /* round-robin schedule over n (even) players: player n-1 fixed */
+    int a, b;
+    if (k == 0) { a = n - 1; b = round % (n - 1); }
+    else {
+        a = (round + k) % (n - 1);
+        b = (round - k + (n - 1)) % (n - 1);
+    }
+    *i = a < b ? a : b;
+    *j = a < b ? b : a;
+}
+
+int or_jacobi_svd(int64_t P, int F, double *A, double *V, double *sigma)
+{
+    int n = F + (F & 1);
+    for (int i = 0; i < F; ++i)
+        for (int j = 0; j < F; ++j) {
+            V[2 * ((int64_t)i * F + j)] = (i == j) ? 1.0 : 0.0;
+            V[2 * ((int64_t)i * F + j) + 1] = 0.0;
+        }
+    int sweep, converged = 0;
+    for (sweep = 0; sweep < 80 && !converged; ++sweep) {
+        converged = 1;
+        for (int round = 0; round < n - 1; ++round) {
+            int changed = 0;
+            #pragma omp parallel for schedule(dynamic, 1) reduction(|:changed)
+            for (int k = 0; k < n / 2; ++k) {
+                int i, j;
+                rr_pair(n, round, k, &i, &j);
+                if (j >= F) continue;
+                double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+                for (int64_t p = 0; p < P; ++p) {
+                    double xr = A[2 * (p * F + i)], xi = A[2 * (p * F + i) + 1];
+                    double yr = A[2 * (p * F + j)], yi = A[2 * (p * F + j) + 1];
+                    al += xr * xr + xi * xi;
+                    be += yr * yr + yi * yi;
+                    gr += xr * yr + xi * yi; /* conj(x) y */
+                    gi += xr * yi - xi * yr;
+                }
+                double g = sqrt(gr * gr + gi * gi);
+                if (g <= 1e-15 * sqrt(al * be) || g == 0.0) continue;
+                changed = 1;
+                /* phase e^{-i phi} aligns column j with column i */
+                double er = gr / g, ei = -gi / g;
+                double zeta = (be - al) / (2.0 * g);
+                double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                for (int64_t p = 0; p < P; ++p) {
+                    double *x = A + 2 * (p * F + i), *y = A + 2 * (p * F + j);
+                    double yr = y[0] * er - y[1] * ei, yi = y[0] * ei + y[1] * er;
+                    double xr = x[0], xi = x[1];
+                    x[0] = cs * xr - sn * yr; x[1] = cs * xi - sn * yi;
+                    y[0] = sn * xr + cs * yr; y[1] = sn * xi + cs * yi;
+                }
+                for (int r = 0; r < F; ++r) {
+                    double *x = V + 2 * ((int64_t)r * F + i), *y = V + 2 * ((int64_t)r * F + j);
+                    double yr = y[0] * er - y[1] * ei, yi = y[0] * ei + y[1] * er;
+                    double xr = x[0], xi = x[1];
+                    x[0] = cs * xr - sn * yr; x[1] = cs * xi - sn * yi;
+                    y[0] = sn * xr + cs * yr; y[1] = sn * xi + cs * yi;
+                }
+            }
+            if (changed) converged = 0;
+        }
+    }
+    /* singular values = column norms; sort decreasing (selection sort) */
+    for (int i = 0; i < F; ++i) {
+        double s = 0.0;
+        for (int64_t p = 0; p < P; ++p)
+            s += A[2 * (p * F + i)] * A[2 * (p * F + i)] + A[2 * (p * F + i) + 1] * A[2 * (p * F + i) + 1];
+        sigma[i] = sqrt(s);
+    }
+    for (int i = 0; i < F; ++i) {
+        int best = i;
+        for (int j = i + 1; j < F; ++j)
+            if (sigma[j] > sigma[best]) best = j;
+        if (best != i) {
+            double ts = sigma[i]; sigma[i] = sigma[best]; sigma[best] = ts;
+            for (int64_t p = 0; p < P; ++p)
+                for (int q = 0; q < 2; ++q) {
+                    double tv = A[2 * (p * F + i) + q];
+                    A[2 * (p * F + i) + q] = A[2 * (p * F + best) + q];
+                    A[2 * (p * F + best) + q] = tv;
+                }
+            for (int r = 0; r < F; ++r)
+                for (int q = 0; q < 2; ++q) {
+                    double tv = V[2 * ((int64_t)r * F + i) + q];
+                    V[2 * ((int64_t)r * F + i) + q] = V[2 * ((int64_t)r * F + best) + q];
+                    V[2 * ((int64_t)r * F + best) + q] = tv;
+                }
+        }
+    }
+    return converged ? sweep : -sweep;
+}
+
+/* ------------------------------------------------------------------------
+ * SVD clutter filter and power Doppler (Sec. 2.4.2; Figs. 11-13):
+ *   S = U Sigma V^H (Casorati matrix, pixels x frames)
+ *   S_f = S - sum_{i<=k} sigma_i u_i v_i^H     (remove the k largest)
+ *   k = k_cut if k_cut >= 0, else the smallest k with
+ *       sum_{i<=k} sigma_i^2 >= energy_thresh * sum_i sigma_i^2
+ *   PD(p) = (1/F) sum_f |S_f(p, f)|^2
+ * S: double complex [P][F][2].  Outputs (each nullable): sigma [F],
+ * s_f double complex [P][F][2], pd double [P].  Returns k, or -1 on bad k.
+ * Pinned by: exact removal of a rank-k clutter with a spectral gap (T5),
+ * numpy's SVD, and PD = (1/F) sum_{j>k} sigma_j^2 |u_pj|^2.
+ * ---------------------------------------------------------------------- */
+int or_svd_filter(int64_t P, int F, const double *S, int k_cut, double energy_thresh,
+                  double *sigma_out, double *s_f, double *pd)
+{
+    if (k_cut > F) return -1;
+    double *A = (double *)malloc(sizeof(double) * 2 * P * F);
+    double *V = (double *)malloc(sizeof(double) * 2 * (int64_t)F * F);
+    double *sg = (double *)malloc(sizeof(double) * F);
+    memcpy(A, S, sizeof(double) * 2 * P * F);
+    or_jacobi_svd(P, F, A, V, sg);
+    int k = k_cut;
+    if (k < 0) {
+        double tot = 0.0, acc = 0.0;
+        for (int i = 0; i < F; ++i) tot += sg[i] * sg[i];
+        k = F;
+        for (int i = 0; i < F; ++i) {
+            acc += sg[i] * sg[i];
+            if (acc >= energy_thresh * tot) { k = i + 1; break; }
+        }
+    }
+    if (sigma_out) memcpy(sigma_out, sg, sizeof(double) * F);
+    #pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < P; ++p) {
+        double e = 0.0;
+        for (int f = 0; f < F; ++f) {
+            double re = S[2 * (p * F + f)], im = S[2 * (p * F + f) + 1];
+            for (int i = 0; i < k; ++i) {
+                /* (A V)_{p,i} conj(V_{f,i}) */
+                double ar = A[2 * (p * F + i)], ai = A[2 * (p * F + i) + 1];
+                double vr = V[2 * ((int64_t)f * F + i)], vi = -V[2 * ((int64_t)f * F + i) + 1];
+                re -= ar * vr - ai * vi;
+                im -= ar * vi + ai * vr;
+            }
+            if (s_f) { s_f[2 * (p * F + f)] = re; s_f[2 * (p * F + f) + 1] = im; }
+            e += re * re + im * im;
+        }
+        if (pd) pd[p] = e / (double)F;
+    }
+    free(A); free(V); free(sg);
+    return k;
+}
+
+/* Plain SVD access for tests: A [P][F][2] in, U Sigma (in A), V, sigma out. */
+int or_svd(int64_t P, int F, double *A, double *V, double *sigma)
+{
+    return or_jacobi_svd(P, F, A, V, sigma);
+}
+
+/* Casorati Gram G = S^H S (F x F complex, row-major [F][F][2]) by its
+ * definition G_ij = sum_p conj(S_pi) S_pj.  Pinned by brute force (T6). */
+void or_gram(int64_t P, int F, const double *S, double *G)
+{
+    #pragma omp parallel for schedule(static)
+    for (int ij = 0; ij < F * F; ++ij) {
+        int i = ij / F, j = ij % F;
+        double re = 0.0, im = 0.0;
+        for (int64_t p = 0; p < P; ++p) {
+            double xr = S[2 * (p * F + i)], xi = S[2 * (p * F + i) + 1];
+            double yr = S[2 * (p * F + j)], yi = S[2 * (p * F + j) + 1];
+            re += xr * yr + xi * yi;
+            im += xr * yi - xi * yr;
+        }
+        G[2 * ij] = re;
+        G[2 * ij + 1] = im;
+    }
+}
+
+/* Power Doppler of an already filtered ensemble: PD(p) = (1/F) sum_f |S_f|^2 */
+void or_power_doppler(int64_t P, int F, const double *s_f, double *pd)
+{
+    for (int64_t p = 0; p < P; ++p) {
+        double e = 0.0;
+        for (int f = 0; f < F; ++f)
+            e += s_f[2 * (p * F + f)] * s_f[2 * (p * F + f)] + s_f[2 * (p * F + f) + 1] * s_f[2 * (p * F + f) + 1];
+        pd[p] = e / (double)F;
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Scatterer advection (Sec. 2.2.2 steady-velocity-field trajectories in
+ * closed form; Poiseuille flow along the vessel centreline):
+ *
+ *  blood in segment i with flow coordinates (q, xi1, xi2):
+ *    v = vmax (1 - (xi1^2 + xi2^2) / R^2)
+ *    line: a = q + v t wrapped into [0, L): P = p0 + a a1 + xi1 a2 + xi2 a3
+ *    arc:  phi = q + v t / Rc wrapped into [0, phi1):
+ *          P = p0 + (Rc + xi1)(cos phi a1 + sin phi a2) + xi2 a3
+ *  tissue: P = P0.
+ *  then the tissue motion map (applied to both, evaluated with the
+ *  unperturbed position Q = P):
+ *    rotation about c_r by |omega| t around omega/|omega| (Rodrigues),
+ *    plus translation vel t,
+ *    plus (1 + g . (Q - c_e)) sum_j A_j sin(2 pi f_j t + phase_j) dir_j.
+ *
+ * seg table: [n_seg][24] (see workload.segment_table); motion: [40].
+ * Output float [3][S].  Pinned by: Poiseuille mean = vmax/2 over a disc and
+ * 2 vmax/3 over a stripe (T4), lumen confinement, translation and rotation
+ * closed forms (T10).
+ * ---------------------------------------------------------------------- */
+static double wrap_into(double a, double span)
+{
+    return a - span * floor(a / span);
+}
+
+void or_advect(int64_t S, const float *p0, const int32_t *seg, const float *flow,
+               const double *segt, const double *mot, double t, float *out)
+{
+    int nterm = (int)mot[0];
+    const double *om = mot + 34, *cr = mot + 37, *g = mot + 25, *ce = mot + 28, *vel = mot + 31;
+    double wn = sqrt(om[0] * om[0] + om[1] * om[1] + om[2] * om[2]);
+    double kx = 0, ky = 0, kz = 0, ct = 1.0, st = 0.0;
+    if (wn > 0.0) {
+        kx = om[0] / wn; ky = om[1] / wn; kz = om[2] / wn;
+        ct = cos(wn * t); st = sin(wn * t);
+    }
+    double dsum[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < nterm; ++j) {
+        double sj = mot[1 + j] * sin(2.0 * OR_PI * mot[5 + j] * t + mot[9 + j]);
+        for (int d = 0; d < 3; ++d) dsum[d] += sj * mot[13 + 3 * j + d];
+    }
+    #pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < S; ++s) {
+        double P[3];
+        int si = seg[s];
+        if (si < 0) {
+            P[0] = p0[s]; P[1] = p0[S + s]; P[2] = p0[2 * S + s];
+        } else {
+            const double *sg = segt + 24 * (int64_t)si;
+            double q = flow[s], x1 = flow[S + s], x2 = flow[2 * S + s];
+            double R = sg[14];
+            double v = sg[15] * (1.0 - (x1 * x1 + x2 * x2) / (R * R));
+            if ((int)sg[0] == 0) {
+                double a = wrap_into(q + v * t, sg[13]);
+                for (int d = 0; d < 3; ++d)
+                    P[d] = sg[1 + d] + a * sg[4 + d] + x1 * sg[7 + d] + x2 * sg[10 + d];
+            } else {
+                double phi = wrap_into(q + v * t / sg[16], sg[17]);
+                double cp = cos(phi), sp = sin(phi), rr = sg[16] + x1;
+                for (int d = 0; d < 3; ++d)
+                    P[d] = sg[1 + d] + rr * (cp * sg[4 + d] + sp * sg[7 + d]) + x2 * sg[10 + d];
+            }
+        }
+        double Q[3] = {P[0], P[1], P[2]};
+        if (wn > 0.0) {
+            double w0 = P[0] - cr[0], w1 = P[1] - cr[1], w2 = P[2] - cr[2];
+            double kw = kx * w0 + ky * w1 + kz * w2;
+            double c0 = ky * w2 - kz * w1, c1 = kz * w0 - kx * w2, c2 = kx * w1 - ky * w0;
+            P[0] = cr[0] + w0 * ct + c0 * st + kx * kw * (1.0 - ct);
+            P[1] = cr[1] + w1 * ct + c1 * st + ky * kw * (1.0 - ct);
+            P[2] = cr[2] + w2 * ct + c2 * st + kz * kw * (1.0 - ct);
+        }
+        double gain = 1.0 + (g[0] * (Q[0] - ce[0]) + g[1] * (Q[1] - ce[1]) + g[2] * (Q[2] - ce[2]));
+        for (int d = 0; d < 3; ++d) out[d * S + s] = (float)(P[d] + vel[d] * t + gain * dsum[d]);
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Vessel membership (replaces the band-limited delta projection of App. D,
+ * Eqs. 3-5, by an exact distance-to-centreline test):
+ *   blood scatterers keep their segment; a tissue scatterer gets the first
+ *   segment whose lumen strictly contains it, or -1.
+ *   line: w = P - p0, s = w.a1 in [0, L], (w.a2)^2 + (w.a3)^2 < R^2
+ *   arc:  w = P - C, x_k = w.a_k; angle in [0, phi1]:
+ *         x2 >= 0 if phi1 <= pi (sector test by signs of cross products with
+ *         the start (1,0) and end (cos phi1, sin phi1) directions);
+ *         (sqrt(x1^2 + x2^2) - Rc)^2 + x3^2 < R^2
+ * All arithmetic is IEEE double in the written order (integer result).
+ * Also returns the effective amplitude (tissue inside a lumen -> 0).
+ * Pinned by: brute-force geometric construction of inside/outside points.
+ * ---------------------------------------------------------------------- */
+static int inside_seg(const double *sg, double px, double py, double pz)
+{
+    double w0 = px - sg[1], w1 = py - sg[2], w2 = pz - sg[3];
+    double R2 = sg[14] * sg[14];
+    if ((int)sg[0] == 0) {
+        double s = (w0 * sg[4] + w1 * sg[5]) + w2 * sg[6];
+        if (s < 0.0 || s > sg[13]) return 0;
+        double q1 = (w0 * sg[7] + w1 * sg[8]) + w2 * sg[9];
+        double q2 = (w0 * sg[10] + w1 * sg[11]) + w2 * sg[12];
+        return (q1 * q1 + q2 * q2) < R2;
+    } else {
+        double x1 = (w0 * sg[4] + w1 * sg[5]) + w2 * sg[6];
+        double x2 = (w0 * sg[7] + w1 * sg[8]) + w2 * sg[9];
+        double x3 = (w0 * sg[10] + w1 * sg[11]) + w2 * sg[12];
+        /* start direction (1, 0): cross((1,0),(x1,x2)) = x2 >= 0
+           end direction (c1, s1): cross((x1,x2),(c1,s1)) = x1 s1 - x2 c1 >= 0
+           (arcs span at most pi) */
+        if (x2 < 0.0) return 0;
+        if (x1 * sg[19] - x2 * sg[18] < 0.0) return 0;
+        double rin = sqrt(x1 * x1 + x2 * x2) - sg[16];
+        return (rin * rin + x3 * x3) < R2;
+    }
+}
+
+void or_classify(int64_t S, const float *pos, const int32_t *seg, int n_seg, const double *segt,
+                 const float *amp_in, int32_t *vessel, float *amp_out)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < S; ++s) {
+        int v = seg[s];
+        if (v < 0) {
+            double px = pos[s], py = pos[S + s], pz = pos[2 * S + s];
+            for (int i = 0; i < n_seg; ++i)
+                if (inside_seg(segt + 24 * (int64_t)i, px, py, pz)) { v = i; break; }
+        }
+        vessel[s] = v;
+        if (amp_out) amp_out[s] = (seg[s] < 0 && v >= 0) ? 0.0f : amp_in[s];
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Depth binning: b(s) = clamp(floor(((double) z_s - z0) / dz), 0, B - 1);
+ * stable counting sort: bin_off[b] = #{s : bin(s) < b}, perm lists the
+ * scatterer indices ordered by (bin, index).  Pinned by: numpy's stable
+ * argsort and bincount on the same keys.
+ * ---------------------------------------------------------------------- */
+void or_bin(int64_t S, const float *z, double z0, double dz, int B, int32_t *bin_off, int32_t *perm)
+{
+    int32_t *key = (int32_t *)malloc(sizeof(int32_t) * (S > 0 ? S : 1));
+    for (int b = 0; b <= B; ++b) bin_off[b] = 0;
+    for (int64_t s = 0; s < S; ++s) {
+        double q = floor(((double)z[s] - z0) / dz);
+        int b = q < 0.0 ? 0 : (q > (double)(B - 1) ? B - 1 : (int)q);
+        key[s] = b;
+        bin_off[b + 1] += 1;
+    }
+    for (int b = 0; b < B; ++b) bin_off[b + 1] += bin_off[b];
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (B > 0 ? B : 1));
+    for (int b = 0; b < B; ++b) fill[b] = bin_off[b];
+    for (int64_t s = 0; s < S; ++s) perm[fill[key[s]]++] = (int32_t)s;
+    free(fill);
+    free(key);
+}
