@@ -1,0 +1,303 @@
+"""Benchmark of the uPDI hot path on GB300.
+
+One step = the whole path over one ensemble of the 2D compounded workload
+(128-element linear array, 5 plane waves, 2048 samples, 100k scatterers,
+200 frames, 256x256 pixels): vessel membership -> advection -> RF synthesis
+-> rf2iq + DAS compounding -> SVD clutter filter -> power Doppler.
+
+Prints one JSON line.  `value` is channel-samples/s of the whole step
+(F * A * M * Ns / step time), summed over ranks; `e2e` is the same metric
+through the public API with the scatterer inputs copied from pinned host
+memory and the power Doppler image copied back inside the timed region.
+`roofline` covers the dominant kernel (RF synthesis, FP32-ALU bound).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "channel-samples/s + DAS voxel-angle/s per GB300, % roofline, err vs FP64"
+UNIT = "channel-samples/s"
+# FP32 work of the model per (scatterer, element, transmit) pair, counted
+# from its plain definition: 17 for geometry and amplitude,
+# 10 per pulse tap, 2 * n_cycles * fs / (2 f0) taps on average.
+GEOM_FLOP_PER_PAIR = 17.0
+FLOP_PER_TAP = 10.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle --
+def oracle_step(w, n_frames):
+    """The oracle through the whole path on the first n_frames frames."""
+    import oracle
+    from paper_2509_05464_gb300 import workload as W
+    st, mt = W.segment_table(w), W.motion_table(w.motion)
+    t0 = time.perf_counter()
+    oracle.pipeline(w, st, mt, n_frames=n_frames, k_cut=min(w.k_cut, n_frames - 1))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(w, n_frames=6):
+    import oracle
+    dt = oracle_step(w, n_frames)
+    cs = n_frames * w.A * w.M * w.Ns
+    return {"value": cs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"whole path (advect, membership, RF, rf2iq, DAS, SVD filter, PD) on the first {n_frames} "
+                      f"of {w.n_frames} frames of the same workload, FP64, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    from paper_2509_05464_gb300 import workload as W
+    import oracle
+    if rank != 0:
+        return
+    w = W.config2(seed=2)
+    nf = 2
+    for _ in range(args.warmup):
+        oracle_step(w, nf)
+    times = [oracle_step(w, nf) for _ in range(args.steps)]
+    t = sum(times) / len(times)
+    cs = nf * w.A * w.M * w.Ns
+    v = cs / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sample_frames": nf},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": oracle.num_threads(),
+                             "sample": f"each step: the whole path on the first {nf} of {w.n_frames} frames"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours --
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2509_05464_gb300 import fq
+    from paper_2509_05464_gb300 import workload as W
+    from paper_2509_05464_gb300.pipeline import Pipeline
+
+    torch.cuda.set_device(local)
+    fq.lib()
+    w = W.config2(seed=2 + rank)  # an independent ensemble per rank (weak scaling)
+    pl = Pipeline(w)
+    pl.upload()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        pl.step()
+    torch.cuda.synchronize()
+    fq.fq_clutter_status(pl.ws_svd)
+
+    clk = ClockSampler(local)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    rf_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed events
+        ev[i][0].record(stream)
+        pl.classify()
+        pl.advect()
+        rf_ev[i][0].record(stream)
+        pl.simulate()
+        rf_ev[i][1].record(stream)
+        pl.beamform()
+        pl.clutter()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    rf_ms = [a.elapsed_time(b) for a, b in rf_ev]
+    ms = max_over_ranks(sum(step_ms) / len(step_ms))
+    rf_avg = sum(rf_ms) / len(rf_ms)
+
+    # end to end through the public API (pinned host in, PD out)
+    e2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        e2[i][0].record(stream)
+        pl.step_e2e()
+        e2[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2) / args.steps)
+    fq.fq_clutter_status(pl.ws_svd)
+
+    total_cs = sum_over_ranks(float(pl.channel_samples))
+    total_va = sum_over_ranks(float(pl.voxel_angles))
+    if rank != 0:
+        return
+    pk, src = peaks()
+    sm_for_peak = float(pk.get("sm_max_mhz", 2070.0))
+    peak = fp32_alu_peak_tflops(sm_for_peak)
+    p = w.probe
+    taps = p.n_cycles * p.fs / p.f0  # 2 * half-width
+    pairs = w.n_frames * w.A * w.M * w.S
+    flop = pairs * (GEOM_FLOP_PER_PAIR + FLOP_PER_TAP * taps)
+    achieved = flop / (rf_avg * 1e-3) / 1e12
+    cpu = cpu_baseline(w) if args.cpu_baseline else None
+    line = {
+        "metric": METRIC, "value": total_cs / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "frames": w.n_frames, "angles": w.A, "elements": w.M, "samples": w.Ns,
+                   "scatterers": w.S, "pixels": w.P, "parallelism": f"independent ensemble per GPU x{world}",
+                   "l2": "256 MiB buffer rewritten between timed steps, outside the timed events"},
+        "das_voxel_angle_per_s": total_va / (ms * 1e-3),
+        "kernel_ms": {"rf_synth": rf_avg, "step": ms},
+        "roofline": {"bound": "alu", "kernel": "rf_synth_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_for_peak:.0f} MHz ({src} max clock)",
+                     "work": f"{GEOM_FLOP_PER_PAIR:.0f} + {FLOP_PER_TAP:.0f} x {taps:.3f} taps FLOP per pair, "
+                             f"{pairs:.3e} pairs"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": total_cs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": pl.h2d_bytes,
+                "d2h_bytes_per_step": pl.d2h_bytes, "ms_per_step": e2e_ms},
+        "gpu_launches": pl.n_launches * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 0)
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

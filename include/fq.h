@@ -1,0 +1,333 @@
+/*
+ * fq.h -- C ABI of the GB300 (sm_103a) uPDI hot path of 3D-FQFlow
+ * (arXiv 2509.05464): scatterer advection, vessel membership, depth binning,
+ * pulse-echo RF synthesis, rf2iq, plane-wave delay-and-sum compounding, the
+ * SVD clutter filter and power Doppler.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Plain C types only.  "device" pointers are CUDA device (or managed)
+ *    memory owned by the caller; "host" pointers are ordinary host memory
+ *    read during the call only.  The library never allocates device memory:
+ *    scratch comes from a caller-provided workspace whose size the matching
+ *    *_workspace_size call returns (workspace pointers must be 256-byte
+ *    aligned).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *    only enqueues work on that stream and returns; outputs are valid once
+ *    the stream has reached that point.  Calls may be captured into CUDA
+ *    graphs unless stated otherwise.
+ *  - Inputs are never modified.  Outputs are fully overwritten unless a flag
+ *    says otherwise.
+ *  - Every call returns an fq_status.  On failure nothing has been enqueued
+ *    (argument errors) or the CUDA error is reported (FQ_ERR_CUDA);
+ *    fq_last_error() gives a message for the calling host thread.  No call
+ *    aborts, exits, throws or traps.
+ *  - Units are SI (m, s, Hz), angles in radians.
+ *  - Complex arrays are interleaved (re, im) pairs of the element type.
+ *  - Element m of a probe sits at x = (ix - (nx-1)/2) pitch_x,
+ *    y = (iy - (ny-1)/2) pitch_y, z = 0, with m = iy * nx + ix.
+ *    Linear arrays have ny = 1 (no elevation directivity).
+ *  - Pixel p of a grid sits at (x0 + ix dx, y0 + iy dy, z0 + iz dz) with
+ *    p = (iy * nz + iz) * nx + ix.
+ */
+#ifndef FQ_H
+#define FQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fq_status {
+    FQ_OK = 0,
+    FQ_ERR_INVALID_ARG = 1, /* null pointer, bad enum, negative size ... */
+    FQ_ERR_SHAPE = 2,       /* sizes out of the supported range */
+    FQ_ERR_ALIGN = 3,       /* pointer not aligned as documented */
+    FQ_ERR_WORKSPACE = 4,   /* workspace missing or too small */
+    FQ_ERR_CUDA = 5,        /* a CUDA runtime error (message has details) */
+    FQ_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out */
+    FQ_ERR_NUMERICAL = 7,   /* an iterative solver did not converge */
+    FQ_ERR_UNSUPPORTED = 8  /* valid request this build does not implement */
+} fq_status;
+
+typedef enum fq_dtype {
+    FQ_F32 = 0,  /* IEEE binary32 */
+    FQ_BF16 = 1, /* bfloat16 storage, FP32 arithmetic */
+    FQ_F16 = 2   /* binary16 storage, FP32 arithmetic */
+} fq_dtype;
+
+typedef enum fq_gram_mode {
+    FQ_GRAM_F32 = 0,  /* FP32 FMA Gram (CUDA cores) */
+    FQ_GRAM_TF32 = 1, /* TF32 operands on tcgen05 tensor cores, FP32 accumulate */
+    FQ_GRAM_BF16 = 2  /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
+} fq_gram_mode;
+
+enum { FQ_SEG_LINE = 0, FQ_SEG_ARC = 1 };
+enum { FQ_MAX_SEGMENTS = 128, FQ_MAX_ANGLES = 64, FQ_MAX_MOTION_TERMS = 4 };
+
+/* Transducer and medium (Sec. 2.3, App. D; Eq. 1 parameters).
+ * The two-way pulse is p(t) = 1/2 (1 + cos(2 pi t / T)) cos(2 pi f0 t) for
+ * |t| < T/2, T = n_cycles / f0. */
+typedef struct fq_probe {
+    int32_t nx, ny;             /* elements along x and y (ny = 1: linear) */
+    double pitch_x, pitch_y;    /* element pitch (m) */
+    double width_x, width_y;    /* element width (m); directivity half-width b = width/2 */
+    double f0;                  /* centre frequency (Hz) */
+    double fs;                  /* sampling frequency (Hz) */
+    double c;                   /* speed of sound (m/s) */
+    double alpha_db_cm_mhz;     /* amplitude attenuation (dB / cm / MHz) */
+    int32_t n_cycles;           /* pulse length in cycles */
+    int32_t n_samples;          /* samples per channel, Ns */
+} fq_probe;
+
+/* Plane-wave transmits: direction u = (sin tx, sin ty, sqrt(1 - sin^2 tx - sin^2 ty));
+ * time zero is when the first element fires. Arrays are host memory. */
+typedef struct fq_tx {
+    int32_t n_angles;           /* 1 .. FQ_MAX_ANGLES */
+    const double *tilt_x;       /* host [n_angles] */
+    const double *tilt_y;       /* host [n_angles] */
+} fq_tx;
+
+/* Reconstruction grid and receive aperture (f-number). */
+typedef struct fq_grid {
+    int32_t nx, ny, nz;
+    double x0, y0, z0;
+    double dx, dy, dz;
+    double fnumber;             /* element m is used for pixel p iff |x_p - x_m| <= z_p / (2 f#) */
+} fq_grid;
+
+/* One vessel piece with Poiseuille flow v(rho) = vmax (1 - rho^2 / radius^2).
+ * (a1, a2, a3) is a right-handed orthonormal frame.  line: p0 = start,
+ * a1 = axis, centreline p0 + s a1, s in [0, length).  arc: p0 = centre,
+ * centreline p0 + arc_radius (cos phi a1 + sin phi a2), phi in [0, phi1),
+ * phi1 <= pi, arc_end = (cos phi1, sin phi1). */
+typedef struct fq_segment {
+    int32_t kind;               /* FQ_SEG_LINE or FQ_SEG_ARC */
+    double p0[3];
+    double a1[3], a2[3], a3[3];
+    double length;              /* line only */
+    double radius;              /* lumen radius */
+    double vmax;                /* centreline speed (m/s) */
+    double arc_radius;          /* arc only */
+    double phi1;                /* arc only: angular span */
+    double arc_end[2];          /* arc only: (cos phi1, sin phi1) */
+} fq_segment;
+
+typedef struct fq_flow {
+    int32_t n_seg;              /* 0 .. FQ_MAX_SEGMENTS */
+    const fq_segment *seg;      /* host [n_seg] */
+} fq_flow;
+
+/* Tissue motion (Sec. 2.2.2, Sec. 3.2): rigid rotation by |omega| t about
+ * rot_center, translation vel t, and a periodic displacement
+ * (1 + g.(Q - elastic_center)) sum_j amp_j sin(2 pi freq_j t + phase_j) dir_j
+ * evaluated at the unperturbed position Q. */
+typedef struct fq_motion {
+    int32_t n_terms;            /* 0 .. FQ_MAX_MOTION_TERMS */
+    double amp[4], freq[4], phase[4];
+    double dir[4][3];
+    double elastic_grad[3];
+    double elastic_center[3];
+    double vel[3];
+    double omega[3];
+    double rot_center[3];
+} fq_motion;
+
+/* ------------------------------------------------------------------ */
+/* library information                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *fq_last_error(void);
+/* Static name of a status code. */
+const char *fq_status_string(fq_status s);
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int32_t fq_version(void);
+
+/* ------------------------------------------------------------------ */
+/* a1: scatterer advection                                              */
+/* ------------------------------------------------------------------ */
+
+/* Positions of S scatterers at the frame times t_f = t0 + f dt, f < n_frames
+ * (Sec. 2.2.2: trajectories of a steady velocity field, here in closed form;
+ * App. C: scatterers follow the local flow velocity).
+ *   blood (seg_id >= 0), flow coordinates (q, xi1, xi2):
+ *     v = vmax (1 - (xi1^2 + xi2^2) / R^2)
+ *     line: a = q + v t wrapped into [0, length), P = p0 + a a1 + xi1 a2 + xi2 a3
+ *     arc:  phi = q + v t / arc_radius wrapped into [0, phi1),
+ *           P = p0 + (arc_radius + xi1)(cos phi a1 + sin phi a2) + xi2 a3
+ *   tissue (seg_id = -1): P = p0.
+ * Then the tissue motion map is applied to every scatterer.
+ *   p0        device float [3][S]  initial positions (x row, y row, z row)
+ *   seg_id    device int32 [S]     segment index or -1
+ *   flow_coord device float [3][S] (q, xi1, xi2) rows, read for blood only
+ *   pos_out   device float [n_frames][3][S]
+ * Arithmetic is FP64 (wrap decisions bit-identical to IEEE double).
+ * Errors: FQ_ERR_INVALID_ARG (null pointer, S < 0, n_frames < 1, seg_id
+ * outside [-1, n_seg) is not checked on the device: such scatterers are
+ * treated as tissue), FQ_ERR_SHAPE (n_seg or n_terms above the maximum). */
+fq_status fq_advect_scatterers(const float *p0, const int32_t *seg_id, const float *flow_coord,
+                               int64_t S, const fq_flow *flow, const fq_motion *motion,
+                               double t0, double dt, int32_t n_frames, float *pos_out,
+                               void *stream);
+
+/* ------------------------------------------------------------------ */
+/* a2: vessel membership and depth binning                              */
+/* ------------------------------------------------------------------ */
+
+/* Vessel membership (App. D decides whether a scatterer lies inside a
+ * vessel; here by an exact distance-to-centreline test in IEEE double).
+ * vessel_out[s] = seg_id[s] for blood; for tissue the first segment whose
+ * lumen strictly contains pos[:, s], else -1.  amp_out (nullable) = amp_in
+ * with tissue scatterers inside a lumen set to 0.
+ *   pos device float [3][S]; seg_id, vessel_out device int32 [S];
+ *   amp_in, amp_out device float [S].
+ * The integer result is bit-identical to IEEE double evaluation. */
+fq_status fq_classify_scatterers(const float *pos, const int32_t *seg_id, int64_t S,
+                                 const fq_flow *flow, const float *amp_in, int32_t *vessel_out,
+                                 float *amp_out, void *stream);
+
+/* Depth bins b(s) = clamp(floor(((double) z_s - z0) / dz), 0, B - 1) and a
+ * stable counting sort: bin_off[b] = #{s : b(s) < b} (device int32 [B+1]),
+ * perm (device int32 [S]) = scatterer indices ordered by (bin, index).
+ * Bit-identical to IEEE double evaluation.  Needs a workspace of
+ * fq_bin_workspace_size bytes.  S < 2^31, 1 <= B <= 8192. */
+fq_status fq_bin_workspace_size(int64_t S, int32_t B, size_t *bytes);
+fq_status fq_bin_scatterers(const float *z, int64_t S, double z0, double dz, int32_t B,
+                            int32_t *bin_off, int32_t *perm, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* a3: pulse-echo RF synthesis                                          */
+/* ------------------------------------------------------------------ */
+
+/* RF channel data of n_frames frames (Eq. 1 restated as a narrowband
+ * time-domain sum under the weak-scattering assumption, App. D; Sec. 2.3):
+ *   RF[f][a][m][k] = base[a][m][k]
+ *       + sum_s A_{s,m,a} p(k / fs - tau_{s,m,a})
+ *   tau = ((u_a . r_s - min_m' u_a . e_m') + |r_s - e_m|) / c
+ *   A   = amp_s D exp(-alpha f0[MHz] c tau) / |r_s - e_m|,
+ *   alpha = alpha_db_cm_mhz * 100 / (20 / ln 10)  (Np / m / MHz)
+ *   D   = sinc(k0 b_x (x_s - x_m) / r) [* sinc(k0 b_y (y_s - y_m) / r) if ny > 1]
+ *   sinc(u) = sin(u) / u, k0 = 2 pi f0 / c.
+ * Samples outside [0, Ns) are dropped.  Alg. 1's static-tissue reuse is the
+ * `rf_base` term: pass the tissue RF of one frame (computed by an earlier
+ * call) and only the moving scatterers here.
+ *   pos     device float [n_frames][3][S]
+ *   amp     device float [S]
+ *   rf_base device float [A][M][Ns] or NULL
+ *   rf      device [n_frames][A][M][Ns] of out_dtype (FQ_F32 or FQ_BF16),
+ *           4-byte aligned
+ * Accumulation is FP32; delays use float-float (~48-bit) arithmetic.  The
+ * summation order over scatterers is not fixed, so the last bits may
+ * differ between runs.
+ * Errors: FQ_ERR_INVALID_ARG, FQ_ERR_SHAPE (Ns > 8192, n_angles outside
+ * [1, FQ_MAX_ANGLES], M > 65536), FQ_ERR_UNSUPPORTED (out_dtype FQ_F16). */
+fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, const float *pos,
+                         const float *amp, int64_t S, int32_t n_frames, const float *rf_base,
+                         int32_t out_dtype, void *rf, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* a4 + a5: rf2iq and delay-and-sum compounding                          */
+/* ------------------------------------------------------------------ */
+
+/* rf2iq (Alg. 3 step 2.3.2.1): IQ[k] = 2 sum_{j=-J..J} h_j RF[k-j]
+ * exp(-i 2 pi f0 (k-j) / fs), h = Hann-windowed ideal low-pass with cutoff
+ * f0, J = 2 round(fs/f0), w_j = (1 + cos(pi j / (J+1))) / 2, normalised to
+ * sum 1; RF outside [0, Ns) is 0.
+ *   rf      device [n_frames][n_lines][Ns] of rf_dtype (FQ_F32 / FQ_BF16)
+ *   iq_ch   device complex [n_lines][Ns][F_pad] of iq_dtype, frames
+ *           innermost, F_pad = fq_frame_pad(n_frames); padded frames are 0.
+ * n_lines = A * M.  J <= 32. */
+int32_t fq_frame_pad(int32_t n_frames);
+fq_status fq_rf2iq(const fq_probe *probe, int32_t n_lines, int32_t n_frames, const void *rf,
+                   int32_t rf_dtype, int32_t iq_dtype, void *iq_ch, void *stream);
+
+/* DAS with coherent compounding (Sec. 2.4.1, Alg. 3):
+ *   tau = ((u_a . r_p - min u_a . e) + |r_p - e_m|) / c,  u = tau fs,
+ *   i = floor(u), phi = u - i,
+ *   v = (1 - phi) IQ[i] + phi IQ[i+1]   (0 if i < 0 or i + 1 >= Ns)
+ *   iq[p][f] = (1/A) sum_a sum_m w_m(p) v exp(+i 2 pi f0 tau)
+ * w_m(p) = 1 iff |x_p - x_m| <= z_p / (2 f#) (and in y for matrix arrays),
+ * decided in binary32 on the coordinates rounded to float.
+ * Delays are computed once per (pixel, angle, element) and shared by all
+ * frames (the paper's precomputed-DAS-matrix idea, without the matrix).
+ *   iq_ch  device complex [A*M][Ns][F_pad] of ch_dtype (fq_rf2iq layout)
+ *   iq     device complex [P][n_frames] of iq_dtype (Casorati, frames
+ *          contiguous), 8-byte aligned.
+ * FP32 accumulation, float-float delays. */
+fq_status fq_das(const fq_probe *probe, const fq_tx *tx, const void *iq_ch, int32_t ch_dtype,
+                 int32_t n_frames, const fq_grid *grid, int32_t iq_dtype, void *iq, void *stream);
+
+/* rf2iq followed by DAS; the channel IQ lives in the workspace. */
+fq_status fq_beamform_das_workspace_size(const fq_probe *probe, const fq_tx *tx,
+                                         int32_t n_frames, int32_t ch_dtype, size_t *bytes);
+fq_status fq_beamform_das(const fq_probe *probe, const fq_tx *tx, const void *rf,
+                          int32_t rf_dtype, int32_t n_frames, const fq_grid *grid,
+                          int32_t ch_dtype, int32_t iq_dtype, void *iq, void *workspace,
+                          size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* a6 - a8: SVD clutter filter and power Doppler                        */
+/* ------------------------------------------------------------------ */
+
+/* Casorati Gram G = S^H S (Sec. 2.4.2: the SVD of S is obtained from the
+ * eigen-decomposition of its frames x frames Gram matrix).
+ *   S  device complex [P][F] of dtype
+ *   G  device float complex [F][F] (row-major, Hermitian, full matrix)
+ * gram_mode FQ_GRAM_F32 needs dtype FQ_F32 or FQ_BF16; FQ_GRAM_BF16 needs
+ * dtype FQ_BF16 and F a multiple of 32; FQ_GRAM_TF32 needs dtype FQ_F32.
+ * 2 <= F <= 512. */
+fq_status fq_gram_workspace_size(int64_t P, int32_t F, int32_t gram_mode, size_t *bytes);
+fq_status fq_casorati_gram(const void *S, int32_t dtype, int64_t P, int32_t F, int32_t gram_mode,
+                           float *G, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Eigen-decomposition of a Hermitian F x F matrix, G = V diag(lambda) V^H,
+ * lambda descending (= sigma^2 of S when G = S^H S).
+ *   G       device float complex [F][F]
+ *   eigvals device double [F]
+ *   V       device float complex [F][F], column j = eigenvector j
+ * Householder tridiagonalisation + implicit QL with Wilkinson shifts on one
+ * CTA (FP32).  FQ_ERR_NUMERICAL (reported through fq_clutter_status after
+ * the stream reaches the call) if QL needs more than 60 iterations for one
+ * eigenvalue; the outputs are then unspecified. */
+fq_status fq_eig_workspace_size(int32_t F, size_t *bytes);
+fq_status fq_hermitian_eig(const float *G, int32_t F, double *eigvals, float *V, void *workspace,
+                           size_t workspace_bytes, void *stream);
+
+/* SVD clutter filter + power Doppler (Sec. 2.4.2):
+ *   S_f = S - (S V_k) V_k^H   (the k largest singular components removed)
+ *   k   = k_cut if k_cut >= 0, else the smallest k with
+ *         sum_{i<k} lambda_i >= energy_thresh * sum_i lambda_i
+ *   pd[p] = (1/F) sum_f |S_f[p][f]|^2
+ *   iq       device complex [P][F] of dtype (FQ_F32 / FQ_BF16)
+ *   iq_f     device complex [P][F] of dtype, nullable (may equal iq)
+ *   pd       device float [P], nullable
+ *   eigvals  device double [F], nullable
+ *   k_used   device int32 [1], nullable
+ * k_cut > F -> FQ_ERR_INVALID_ARG; k == F -> S_f = 0.
+ * Everything stays on the device (k is decided on the device). */
+fq_status fq_clutter_svd_workspace_size(int64_t P, int32_t F, int32_t gram_mode, size_t *bytes);
+fq_status fq_clutter_svd(const void *iq, int32_t dtype, int64_t P, int32_t F, int32_t k_cut,
+                         double energy_thresh, int32_t gram_mode, void *iq_f, float *pd,
+                         double *eigvals, int32_t *k_used, void *workspace,
+                         size_t workspace_bytes, void *stream);
+
+/* Power Doppler of a filtered ensemble: pd[p] = (1/F) sum_f |iq_f[p][f]|^2
+ * (Sec. 2.4.2).  iq_f device complex [P][F] of dtype; pd device float [P]. */
+fq_status fq_power_doppler(const void *iq_f, int32_t dtype, int64_t P, int32_t F, float *pd,
+                           void *stream);
+
+/* Device-side status word of the solver calls that decide on the device
+ * (eigen-solver convergence).  Reads and clears the flag the last
+ * fq_hermitian_eig / fq_clutter_svd on this workspace wrote; synchronises
+ * `stream`. */
+fq_status fq_clutter_status(void *workspace, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FQ_H */

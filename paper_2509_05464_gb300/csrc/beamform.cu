@@ -1,0 +1,388 @@
+// beamform.cu -- a4 rf2iq and a5 plane-wave delay-and-sum compounding
+// (Sec. 2.4.1, Alg. 3).
+//
+// Layout: rf2iq writes the channel IQ frames-innermost, [A*M][Ns][F_pad]
+// complex, so that the DAS kernel, which computes each (pixel, transmit,
+// element) delay once and applies it to a chunk of FC frames, reads the two
+// interpolation samples of all FC frames as contiguous 128-byte vectors.
+// This is the paper's "delay matrix computed once, reused by every frame"
+// idea (Alg. 3 steps 2.2-2.3) without materialising the sparse matrix: the
+// delays live in registers for the duration of a frame chunk.
+//
+// Precision: delays, interpolation index and carrier phase are float-float;
+// the aperture decision is binary32 on coordinates rounded from IEEE double;
+// accumulation is FP32.
+#include <cmath>
+#include <cstring>
+
+#include "fq_internal.cuh"
+
+namespace {
+
+using fqi::ff;
+
+constexpr int kMaxHalfTaps = 32;
+constexpr int kFrameChunk = 16;  // frames per DAS thread and per rf2iq CTA (F_pad multiple)
+
+// ------------------------------------------------------------------ rf2iq --
+struct Rf2iqParams {
+    int L, F, Fp, ns, J;
+    fqi::df2 f0_over_fs;
+    float h[2 * kMaxHalfTaps + 1];
+};
+
+constexpr int kRfTile = 64;  // output samples per CTA
+
+template <typename InT, typename OutT>
+__global__ void __launch_bounds__(256) rf2iq_kernel(const Rf2iqParams p, const InT *__restrict__ rf,
+                                                    OutT *__restrict__ iq)
+{
+    extern __shared__ float2 mix[];  // [kFrameChunk][W]
+    const int l = blockIdx.y;
+    const int k0 = blockIdx.x * kRfTile;
+    const int f0 = blockIdx.z * kFrameChunk;
+    const int J = p.J;
+    const int W = kRfTile + 2 * J;
+    float2 *rot = mix + kFrameChunk * W;  // [W]: exp(-i 2 pi f0 n / fs)
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        int n = k0 - J + i;
+        // fractional carrier cycles (f0/fs) n in float-float, then sincospi
+        ff cyc = fqi::ff_mul_f(fqi::ff_load(p.f0_over_fs), (float)n);
+        float fr = fqi::ff_frac(cyc);
+        float sn, cs;
+        sincospif(2.0f * fr, &sn, &cs);
+        rot[i] = make_float2(cs, -sn);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kFrameChunk * W; i += blockDim.x) {
+        int fl = i / W, w = i - fl * W;
+        int n = k0 - J + w;
+        int f = f0 + fl;
+        float v = 0.0f;
+        if (n >= 0 && n < p.ns && f < p.F) v = fqi::load_f(rf, ((int64_t)f * p.L + l) * p.ns + n);
+        float2 r = rot[w];
+        mix[i] = make_float2(v * r.x, v * r.y);
+    }
+    __syncthreads();
+    // thread -> (frame fl = t % 16, sample kk = t / 16 + 16 q)
+    const int fl = threadIdx.x % kFrameChunk;
+    for (int kk = threadIdx.x / kFrameChunk; kk < kRfTile; kk += blockDim.x / kFrameChunk) {
+        int k = k0 + kk;
+        if (k >= p.ns) break;
+        // IQ[k] = 2 sum_{j=-J..J} h_j mix[k - j]; sample n sits at window index n - (k0 - J),
+        // so sample k - j is at kk + J - j
+        const float2 *src = mix + fl * W + kk + J;
+        float re = 0.0f, im = 0.0f;
+        for (int j = -J; j <= J; ++j) {
+            float2 m = src[-j];
+            float hj = p.h[j + J];
+            re = fmaf(hj, m.x, re);
+            im = fmaf(hj, m.y, im);
+        }
+        int f = f0 + fl;
+        if (f < p.Fp) fqi::store_c(iq, ((int64_t)l * p.ns + k) * p.Fp + f, make_float2(2.0f * re, 2.0f * im));
+    }
+}
+
+bool make_rf2iq_params(const fq_probe *probe, int L, int F, Rf2iqParams &p)
+{
+    std::memset(&p, 0, sizeof p);
+    p.L = L;
+    p.F = F;
+    p.Fp = fq_frame_pad(F);
+    p.ns = probe->n_samples;
+    int J = 2 * (int)std::lround(probe->fs / probe->f0);
+    if (J > kMaxHalfTaps || J < 0) return false;
+    p.J = J;
+    p.f0_over_fs = fqi::split_double(probe->f0 / probe->fs);
+    // Hann-windowed ideal low-pass, cutoff f0, normalised to unit DC gain
+    double h[2 * kMaxHalfTaps + 1];
+    double sum = 0.0;
+    const double fc = 2.0 * probe->f0 / probe->fs;  // cutoff in units of fs/2
+    for (int j = -J; j <= J; ++j) {
+        double ideal = (j == 0) ? fc : std::sin(M_PI * fc * j) / (M_PI * j);
+        double w = 0.5 * (1.0 + std::cos(M_PI * j / (J + 1.0)));
+        h[j + J] = w * ideal;
+        sum += h[j + J];
+    }
+    for (int j = 0; j < 2 * J + 1; ++j) p.h[j] = (float)(h[j] / sum);
+    return true;
+}
+
+template <typename InT, typename OutT>
+fq_status launch_rf2iq(const Rf2iqParams &p, const void *rf, void *iq, cudaStream_t st)
+{
+    int W = kRfTile + 2 * p.J;
+    size_t smem = sizeof(float2) * (size_t)(kFrameChunk + 1) * W;
+    dim3 grid((p.ns + kRfTile - 1) / kRfTile, p.L, p.Fp / kFrameChunk);
+    rf2iq_kernel<InT, OutT><<<grid, 256, smem, st>>>(p, (const InT *)rf, (OutT *)iq);
+    return fqi::launch_check("fq_rf2iq");
+}
+
+fq_status run_rf2iq(const fq_probe *probe, int L, int F, const void *rf, int rf_dtype, int iq_dtype, void *iq,
+                    cudaStream_t st)
+{
+    Rf2iqParams p;
+    FQ_REQUIRE(make_rf2iq_params(probe, L, F, p), FQ_ERR_SHAPE, "fq_rf2iq: 2 round(fs/f0) must be <= %d",
+               kMaxHalfTaps);
+    if (rf_dtype == FQ_F32 && iq_dtype == FQ_F32) return launch_rf2iq<float, float>(p, rf, iq, st);
+    if (rf_dtype == FQ_F32 && iq_dtype == FQ_BF16) return launch_rf2iq<float, __nv_bfloat16>(p, rf, iq, st);
+    if (rf_dtype == FQ_BF16 && iq_dtype == FQ_F32) return launch_rf2iq<__nv_bfloat16, float>(p, rf, iq, st);
+    if (rf_dtype == FQ_BF16 && iq_dtype == FQ_BF16)
+        return launch_rf2iq<__nv_bfloat16, __nv_bfloat16>(p, rf, iq, st);
+    return fqi::set_error(FQ_ERR_UNSUPPORTED, "fq_rf2iq: dtypes must be FQ_F32 or FQ_BF16");
+}
+
+// -------------------------------------------------------------------- DAS --
+struct DasParams {
+    fqi::ProbeFF pr;
+    double pitch_x, pitch_y;  // exact, for the binary32 aperture decision
+    int A, F, Fp;
+    int gx, gy, gz;
+    int64_t P;
+    double x0, y0, z0, dx, dy, dz;
+    float half_per_z;   // 1 / (2 f#)
+    float inv_A;
+    fqi::AngleFF ang[FQ_MAX_ANGLES];
+};
+
+constexpr int kDasThreads = 128;
+
+// 16 complex values of one channel sample for the frame chunk
+template <typename ChT>
+struct ChunkLoad;
+template <>
+struct ChunkLoad<float> {
+    static __device__ __forceinline__ void load(const float *base, float2 (&v)[kFrameChunk])
+    {
+        const float4 *q = reinterpret_cast<const float4 *>(base);
+#pragma unroll
+        for (int i = 0; i < kFrameChunk / 2; ++i) {
+            float4 t = __ldg(q + i);
+            v[2 * i] = make_float2(t.x, t.y);
+            v[2 * i + 1] = make_float2(t.z, t.w);
+        }
+    }
+};
+template <>
+struct ChunkLoad<__nv_bfloat16> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16 *base, float2 (&v)[kFrameChunk])
+    {
+        const uint4 *q = reinterpret_cast<const uint4 *>(base);
+#pragma unroll
+        for (int i = 0; i < kFrameChunk / 4; ++i) {
+            uint4 t = __ldg(q + i);
+            const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&t);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[4 * i + j] = __bfloat1622float2(b[j]);
+        }
+    }
+};
+
+template <typename ChT, typename OutT>
+__global__ void __launch_bounds__(kDasThreads) das_kernel(const DasParams p, const ChT *__restrict__ ch,
+                                                          OutT *__restrict__ iq)
+{
+    extern __shared__ float etab[];  // [6][M]: x as float, x hi, x lo, y float, y hi, y lo
+    const int M = p.pr.M;
+    float *exf = etab, *exh = etab + M, *exl = etab + 2 * M;
+    float *eyf = etab + 3 * M, *eyh = etab + 4 * M, *eyl = etab + 5 * M;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        int ix = m % p.pr.nx, iy = m / p.pr.nx;
+        double ex = __dmul_rn(__dsub_rn((double)ix, __dmul_rn(0.5, (double)(p.pr.nx - 1))), p.pitch_x);
+        double ey = __dmul_rn(__dsub_rn((double)iy, __dmul_rn(0.5, (double)(p.pr.ny - 1))), p.pitch_y);
+        fqi::df2 sx = fqi::split_double(ex), sy = fqi::split_double(ey);
+        exf[m] = (float)ex; exh[m] = sx.hi; exl[m] = sx.lo;
+        eyf[m] = (float)ey; eyh[m] = sy.hi; eyl[m] = sy.lo;
+    }
+    __syncthreads();
+
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int fbase = blockIdx.y * kFrameChunk;
+    const bool live = pix < p.P;
+    const int64_t pp = live ? pix : 0;
+    const int ix = (int)(pp % p.gx);
+    const int iz = (int)((pp / p.gx) % p.gz);
+    const int iy = (int)(pp / ((int64_t)p.gx * p.gz));
+    const double xd = __dadd_rn(p.x0, __dmul_rn((double)ix, p.dx));
+    const double yd = __dadd_rn(p.y0, __dmul_rn((double)iy, p.dy));
+    const double zd = __dadd_rn(p.z0, __dmul_rn((double)iz, p.dz));
+    const float xf = (float)xd, yf = (float)yd, zf = (float)zd;
+    const fqi::df2 xs = fqi::split_double(xd), ys = fqi::split_double(yd), zs = fqi::split_double(zd);
+    const ff X = {xs.hi, xs.lo}, Y = {ys.hi, ys.lo}, Z = {zs.hi, zs.lo};
+    const ff zz = fqi::ff_sqr(Z);
+    const float half = __fmul_rn(zf, p.half_per_z);
+    const bool matrix = p.pr.ny > 1;
+    const ff fs_c = fqi::ff_load(p.pr.fs_over_c);
+    const ff f0_fs = fqi::ff_load(p.pr.f0_over_fs);
+    const int ns = p.pr.ns;
+
+    float2 acc[kFrameChunk];
+#pragma unroll
+    for (int f = 0; f < kFrameChunk; ++f) acc[f] = make_float2(0.0f, 0.0f);
+
+    for (int a = 0; a < p.A; ++a) {
+        const fqi::AngleFF an = p.ang[a];
+        ff ptx = fqi::ff_add(fqi::ff_mul(fqi::ff_load(an.ux), X), fqi::ff_mul(fqi::ff_load(an.uy), Y));
+        ptx = fqi::ff_add(ptx, fqi::ff_mul(fqi::ff_load(an.uz), Z));
+        ptx = fqi::ff_add(ptx, fqi::ff_neg(fqi::ff_load(an.origin)));
+        const ChT *cha = ch + (int64_t)a * M * ns * p.Fp * 2;
+        for (int m = 0; m < M; ++m) {
+            bool on = live && fabsf(__fsub_rn(xf, exf[m])) <= half;
+            if (matrix) on = on && fabsf(__fsub_rn(yf, eyf[m])) <= half;
+            if (!__any_sync(0xffffffffu, on)) continue;
+            if (!on) continue;
+            ff dxx = fqi::ff_add(X, ff{-exh[m], -exl[m]});
+            ff r2 = fqi::ff_add(fqi::ff_sqr(dxx), zz);
+            if (matrix || yf != 0.0f) {
+                ff dyy = fqi::ff_add(Y, ff{-eyh[m], -eyl[m]});
+                r2 = fqi::ff_add(r2, fqi::ff_sqr(dyy));
+            }
+            const ff path = fqi::ff_add(ptx, fqi::ff_sqrt(r2));
+            const ff u = fqi::ff_mul(path, fs_c);
+            int i;
+            float phi;
+            fqi::ff_floor_frac(u, i, phi);
+            if (i < 0 || i + 1 >= ns) continue;
+            const float cyc = fqi::ff_frac(fqi::ff_mul(u, f0_fs));
+            float sn, cs;
+            sincospif(2.0f * cyc, &sn, &cs);
+            const ChT *b0 = cha + (((int64_t)m * ns + i) * p.Fp + fbase) * 2;
+            float2 v0[kFrameChunk], v1[kFrameChunk];
+            ChunkLoad<ChT>::load(b0, v0);
+            ChunkLoad<ChT>::load(b0 + (int64_t)p.Fp * 2, v1);
+#pragma unroll
+            for (int f = 0; f < kFrameChunk; ++f) {
+                float vr = fmaf(phi, v1[f].x - v0[f].x, v0[f].x);
+                float vi = fmaf(phi, v1[f].y - v0[f].y, v0[f].y);
+                acc[f].x = fmaf(vr, cs, fmaf(-vi, sn, acc[f].x));
+                acc[f].y = fmaf(vr, sn, fmaf(vi, cs, acc[f].y));
+            }
+        }
+    }
+    if (!live) return;
+    const int nf = min(kFrameChunk, p.F - fbase);
+    for (int f = 0; f < nf; ++f)
+        fqi::store_c(iq, pix * p.F + fbase + f, make_float2(acc[f].x * p.inv_A, acc[f].y * p.inv_A));
+}
+
+fq_status check_probe_tx(const fq_probe *probe, const fq_tx *tx, const char *who)
+{
+    FQ_REQUIRE(probe && tx, FQ_ERR_INVALID_ARG, "%s: null probe/tx", who);
+    FQ_REQUIRE(tx->n_angles >= 1 && tx->n_angles <= FQ_MAX_ANGLES && tx->tilt_x && tx->tilt_y, FQ_ERR_SHAPE,
+               "%s: n_angles must be in [1, %d]", who, FQ_MAX_ANGLES);
+    FQ_REQUIRE(probe->nx >= 1 && probe->ny >= 1 && (int64_t)probe->nx * probe->ny <= 4096, FQ_ERR_SHAPE,
+               "%s: element count must be in [1, 4096]", who);
+    FQ_REQUIRE(probe->n_samples >= 2 && probe->n_samples <= 65536, FQ_ERR_SHAPE, "%s: bad n_samples", who);
+    FQ_REQUIRE(probe->f0 > 0 && probe->fs > 0 && probe->c > 0, FQ_ERR_INVALID_ARG, "%s: f0, fs, c must be > 0",
+               who);
+    return FQ_OK;
+}
+
+template <typename ChT, typename OutT>
+fq_status launch_das(const DasParams &p, const void *ch, void *iq, cudaStream_t st)
+{
+    size_t smem = sizeof(float) * 6 * (size_t)p.pr.M;
+    auto kern = das_kernel<ChT, OutT>;
+    if (smem > 48 * 1024) {
+        fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)smem), "fq_das: smem attribute");
+        if (s) return s;
+    }
+    dim3 grid((unsigned)((p.P + kDasThreads - 1) / kDasThreads), p.Fp / kFrameChunk);
+    kern<<<grid, kDasThreads, smem, st>>>(p, (const ChT *)ch, (OutT *)iq);
+    return fqi::launch_check("fq_das");
+}
+
+fq_status run_das(const fq_probe *probe, const fq_tx *tx, const void *ch, int ch_dtype, int F, const fq_grid *g,
+                  int iq_dtype, void *iq, cudaStream_t st)
+{
+    FQ_REQUIRE(g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1, FQ_ERR_SHAPE, "fq_das: bad grid");
+    FQ_REQUIRE(g->fnumber > 0.0, FQ_ERR_INVALID_ARG, "fq_das: fnumber must be > 0");
+    DasParams p;
+    std::memset(&p, 0, sizeof p);
+    fqi::make_probe_ff(probe, p.pr);
+    p.pitch_x = probe->pitch_x;
+    p.pitch_y = probe->pitch_y;
+    p.A = tx->n_angles;
+    p.F = F;
+    p.Fp = fq_frame_pad(F);
+    p.gx = g->nx; p.gy = g->ny; p.gz = g->nz;
+    p.P = (int64_t)g->nx * g->ny * g->nz;
+    p.x0 = g->x0; p.y0 = g->y0; p.z0 = g->z0;
+    p.dx = g->dx; p.dy = g->dy; p.dz = g->dz;
+    p.half_per_z = (float)(0.5 / g->fnumber);
+    p.inv_A = 1.0f / (float)p.A;
+    fqi::make_angles_ff(probe, tx, p.ang);
+    if (ch_dtype == FQ_F32 && iq_dtype == FQ_F32) return launch_das<float, float>(p, ch, iq, st);
+    if (ch_dtype == FQ_F32 && iq_dtype == FQ_BF16) return launch_das<float, __nv_bfloat16>(p, ch, iq, st);
+    if (ch_dtype == FQ_BF16 && iq_dtype == FQ_F32) return launch_das<__nv_bfloat16, float>(p, ch, iq, st);
+    if (ch_dtype == FQ_BF16 && iq_dtype == FQ_BF16) return launch_das<__nv_bfloat16, __nv_bfloat16>(p, ch, iq, st);
+    return fqi::set_error(FQ_ERR_UNSUPPORTED, "fq_das: dtypes must be FQ_F32 or FQ_BF16");
+}
+
+size_t elem_size(int dtype) { return dtype == FQ_F32 ? 4 : 2; }
+
+}  // namespace
+
+extern "C" {
+
+int32_t fq_frame_pad(int32_t n_frames)
+{
+    if (n_frames < 1) return 0;
+    return (n_frames + kFrameChunk - 1) / kFrameChunk * kFrameChunk;
+}
+
+fq_status fq_rf2iq(const fq_probe *probe, int32_t n_lines, int32_t n_frames, const void *rf, int32_t rf_dtype,
+                   int32_t iq_dtype, void *iq_ch, void *stream)
+{
+    FQ_REQUIRE(probe && rf && iq_ch, FQ_ERR_INVALID_ARG, "fq_rf2iq: null argument");
+    FQ_REQUIRE(n_lines >= 1 && n_lines <= 65535 * 64 && n_frames >= 1, FQ_ERR_SHAPE, "fq_rf2iq: bad sizes");
+    FQ_REQUIRE(n_lines <= 65535, FQ_ERR_SHAPE, "fq_rf2iq: at most 65535 lines");
+    FQ_REQUIRE(probe->n_samples >= 2 && probe->f0 > 0 && probe->fs > 0, FQ_ERR_INVALID_ARG, "fq_rf2iq: bad probe");
+    FQ_REQUIRE(fqi::aligned(iq_ch, 16), FQ_ERR_ALIGN, "fq_rf2iq: iq_ch must be 16-byte aligned");
+    return run_rf2iq(probe, n_lines, n_frames, rf, rf_dtype, iq_dtype, iq_ch, (cudaStream_t)stream);
+}
+
+fq_status fq_das(const fq_probe *probe, const fq_tx *tx, const void *iq_ch, int32_t ch_dtype, int32_t n_frames,
+                 const fq_grid *grid, int32_t iq_dtype, void *iq, void *stream)
+{
+    fq_status s = check_probe_tx(probe, tx, "fq_das");
+    if (s) return s;
+    FQ_REQUIRE(iq_ch && iq && n_frames >= 1, FQ_ERR_INVALID_ARG, "fq_das: null argument or n_frames < 1");
+    FQ_REQUIRE(fqi::aligned(iq_ch, 16) && fqi::aligned(iq, 8), FQ_ERR_ALIGN,
+               "fq_das: iq_ch must be 16-byte and iq 8-byte aligned");
+    return run_das(probe, tx, iq_ch, ch_dtype, n_frames, grid, iq_dtype, iq, (cudaStream_t)stream);
+}
+
+fq_status fq_beamform_das_workspace_size(const fq_probe *probe, const fq_tx *tx, int32_t n_frames, int32_t ch_dtype,
+                                         size_t *bytes)
+{
+    FQ_REQUIRE(probe && tx && bytes && n_frames >= 1, FQ_ERR_INVALID_ARG, "fq_beamform_das_workspace_size: bad args");
+    size_t n = (size_t)tx->n_angles * probe->nx * probe->ny * probe->n_samples * fq_frame_pad(n_frames) * 2;
+    *bytes = (n * elem_size(ch_dtype) + 255) & ~(size_t)255;
+    return FQ_OK;
+}
+
+fq_status fq_beamform_das(const fq_probe *probe, const fq_tx *tx, const void *rf, int32_t rf_dtype,
+                          int32_t n_frames, const fq_grid *grid, int32_t ch_dtype, int32_t iq_dtype, void *iq,
+                          void *workspace, size_t workspace_bytes, void *stream)
+{
+    fq_status s = check_probe_tx(probe, tx, "fq_beamform_das");
+    if (s) return s;
+    FQ_REQUIRE(rf && iq && n_frames >= 1, FQ_ERR_INVALID_ARG, "fq_beamform_das: null argument");
+    size_t need = 0;
+    fq_beamform_das_workspace_size(probe, tx, n_frames, ch_dtype, &need);
+    FQ_REQUIRE(workspace && workspace_bytes >= need, FQ_ERR_WORKSPACE, "fq_beamform_das: workspace needs %zu bytes",
+               need);
+    FQ_REQUIRE(fqi::aligned(workspace, 256) && fqi::aligned(iq, 8), FQ_ERR_ALIGN,
+               "fq_beamform_das: workspace must be 256-byte and iq 8-byte aligned");
+    int L = tx->n_angles * probe->nx * probe->ny;
+    FQ_REQUIRE(L <= 65535, FQ_ERR_SHAPE, "fq_beamform_das: at most 65535 channel lines");
+    cudaStream_t st = (cudaStream_t)stream;
+    s = run_rf2iq(probe, L, n_frames, rf, rf_dtype, ch_dtype, workspace, st);
+    if (s) return s;
+    return run_das(probe, tx, workspace, ch_dtype, n_frames, grid, iq_dtype, iq, st);
+}
+
+}  // extern "C"

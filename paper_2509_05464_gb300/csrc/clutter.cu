@@ -1,0 +1,702 @@
+// clutter.cu -- a6 Casorati Gram, a7 Hermitian eigen-decomposition and
+// energy cutoff, a8 clutter projection and power Doppler (Sec. 2.4.2).
+//
+// The SVD of the Casorati matrix S (pixels x frames) is obtained from the
+// eigen-decomposition of its frames x frames Gram matrix G = S^H S
+// (eigenvalues sigma^2, eigenvectors = right singular vectors).  Removing
+// the k largest components is S_f = S - (S V_k) V_k^H and the power Doppler
+// is the mean of |S_f|^2 over frames.  With k << F this is O(P F k) and
+// bound by the single read of S.
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+
+#include "fq_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------ workspace --
+struct ClutterLayout {
+    size_t status, G, part, V, Vt, lam, k, hv, tau, big, total;
+    int n_chunks;
+    int64_t chunk_len;
+};
+
+constexpr int kGramTile = 32;
+
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int gram_chunks(int64_t P, int F)
+{
+    int nt = (F + kGramTile - 1) / kGramTile;
+    int pairs = nt * (nt + 1) / 2;
+    int want = (4 * 152 + pairs - 1) / pairs;
+    int64_t max_chunks = (P + kGramTile - 1) / kGramTile;
+    if (want > max_chunks) want = (int)max_chunks;
+    if (want > 64) want = 64;
+    if (want < 1) want = 1;
+    return want;
+}
+
+bool eig_in_smem(int F) { return (size_t)F * (F + 1) / 2 * sizeof(float2) <= 190 * 1024; }
+
+ClutterLayout layout(int64_t P, int F)
+{
+    ClutterLayout L;
+    size_t o = 0;
+    L.status = o; o += 256;
+    L.G = o; o += al256(sizeof(float2) * F * F);
+    L.n_chunks = gram_chunks(P, F);
+    int64_t per = (P + L.n_chunks - 1) / L.n_chunks;
+    L.chunk_len = (per + kGramTile - 1) / kGramTile * kGramTile;
+    L.part = o; o += al256(sizeof(float2) * (size_t)L.n_chunks * F * F);
+    L.V = o; o += al256(sizeof(float2) * F * F);
+    L.Vt = o; o += al256(sizeof(float2) * F * F);
+    L.lam = o; o += al256(sizeof(double) * F);
+    L.k = o; o += 256;
+    L.hv = o; o += al256(sizeof(float2) * F * F);
+    L.tau = o; o += al256(sizeof(float) * F);
+    L.big = o; o += eig_in_smem(F) ? 0 : al256(sizeof(float2) * (size_t)F * (F + 1) / 2);
+    L.total = o;
+    return L;
+}
+
+size_t eig_only_bytes(int F)
+{
+    // status, hv, tau, Vt, k, big
+    size_t o = 256 + al256(sizeof(float2) * F * F) + al256(sizeof(float) * F) + al256(sizeof(float2) * F * F) + 256;
+    if (!eig_in_smem(F)) o += al256(sizeof(float2) * (size_t)F * (F + 1) / 2);
+    return o;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// ----------------------------------------------------------------- Gram --
+// Upper-triangular tiles (ti <= tj) of G over pixel chunks; each CTA: one
+// 32x32 complex tile over one chunk; 256 threads, 2x2 outputs each.
+template <typename T>
+__global__ void __launch_bounds__(256) gram_partial_kernel(const T *__restrict__ S, int64_t P, int F, int nt,
+                                                           int64_t chunk_len, float2 *__restrict__ part)
+{
+    __shared__ float2 As[kGramTile][kGramTile + 1];
+    __shared__ float2 Bs[kGramTile][kGramTile + 1];
+    // decode upper-triangular tile pair
+    int t = blockIdx.x, ti = 0;
+    while (t >= nt - ti) { t -= nt - ti; ++ti; }
+    const int tj = ti + t;
+    const int c = blockIdx.y;
+    const int64_t pbeg = (int64_t)c * chunk_len;
+    const int64_t pend = min(P, pbeg + chunk_len);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    float2 acc[2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
+    for (int64_t p0 = pbeg; p0 < pend; p0 += kGramTile) {
+        for (int i = threadIdx.x; i < kGramTile * kGramTile; i += 256) {
+            int pr = i / kGramTile, col = i % kGramTile;
+            int64_t p = p0 + pr;
+            int ci = ti * kGramTile + col, cj = tj * kGramTile + col;
+            float2 a = make_float2(0, 0), b = make_float2(0, 0);
+            if (p < pend) {
+                if (ci < F) a = fqi::load_c(S, p * F + ci);
+                if (cj < F) b = fqi::load_c(S, p * F + cj);
+            }
+            As[pr][col] = a;
+            Bs[pr][col] = b;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int pr = 0; pr < kGramTile; ++pr) {
+            float2 a0 = As[pr][2 * ty], a1 = As[pr][2 * ty + 1];
+            float2 b0 = Bs[pr][2 * tx], b1 = Bs[pr][2 * tx + 1];
+            // conj(a) b
+            acc[0][0].x += a0.x * b0.x + a0.y * b0.y; acc[0][0].y += a0.x * b0.y - a0.y * b0.x;
+            acc[0][1].x += a0.x * b1.x + a0.y * b1.y; acc[0][1].y += a0.x * b1.y - a0.y * b1.x;
+            acc[1][0].x += a1.x * b0.x + a1.y * b0.y; acc[1][0].y += a1.x * b0.y - a1.y * b0.x;
+            acc[1][1].x += a1.x * b1.x + a1.y * b1.y; acc[1][1].y += a1.x * b1.y - a1.y * b1.x;
+        }
+        __syncthreads();
+    }
+    float2 *out = part + (size_t)c * F * F;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            int i = ti * kGramTile + 2 * ty + a, j = tj * kGramTile + 2 * tx + b;
+            if (i < F && j < F) out[(size_t)i * F + j] = acc[a][b];
+        }
+}
+
+__global__ void gram_reduce_kernel(const float2 *__restrict__ part, int n_chunks, int F, float2 *__restrict__ G)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= F * F) return;
+    int i = idx / F, j = idx % F;
+    bool upper = (i / kGramTile) <= (j / kGramTile);
+    int src = upper ? idx : j * F + i;
+    float2 s = make_float2(0, 0);
+    for (int c = 0; c < n_chunks; ++c) {
+        float2 v = part[(size_t)c * F * F + src];
+        s.x += v.x;
+        s.y += v.y;
+    }
+    G[idx] = upper ? s : cconj(s);
+}
+
+// ------------------------------------------------------------ eigen (1 CTA) --
+constexpr int kEigThreads = 1024;
+
+__device__ __forceinline__ int pidx(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
+
+// block-wide sum of one float per thread
+__device__ float block_sum(float v, float *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        float x = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[32] = x;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// Householder tridiagonalisation of the Hermitian G (lower triangle used),
+// implicit QL with Wilkinson shifts on the real tridiagonal (after a
+// diagonal unitary scaling), eigenvalue sort and back-transformation.
+// Optional: the energy / fixed cutoff k.
+__global__ void __launch_bounds__(kEigThreads) eig_kernel(const float2 *__restrict__ G, int F, float2 *__restrict__ big,
+                                                          float2 *__restrict__ hv, float *__restrict__ tau_g,
+                                                          double *__restrict__ lam_out, float2 *__restrict__ V,
+                                                          float2 *__restrict__ Vt, int k_cut, double thresh,
+                                                          int *__restrict__ k_out, int *__restrict__ status)
+{
+    extern __shared__ float2 dyn[];
+    float2 *Ap = big ? big : dyn;                 // packed lower triangle, later Z (real, stride F+1)
+    float *Z = reinterpret_cast<float *>(Ap);
+    __shared__ float red[33];
+    __shared__ float d[512], e[512], rc[512], rs[512];
+    __shared__ float2 ec[512], vv[512], pv[512], delta[512];
+    __shared__ int perm[512];
+    __shared__ float s_tau;
+    __shared__ int s_m, s_nrot, s_done, s_fail;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+
+    for (int i = wid; i < F; i += nw)
+        for (int j = lane; j <= i; j += 32) Ap[pidx(i, j)] = G[(size_t)i * F + j];
+    __syncthreads();
+
+    // ---- tridiagonalisation
+    for (int k = 0; k + 2 < F; ++k) {
+        const int m = F - k - 1;  // length of the column below the diagonal
+        float part = 0.0f;
+        for (int i = tid; i < m; i += blockDim.x) {
+            float2 x = Ap[pidx(k + 1 + i, k)];
+            part += x.x * x.x + x.y * x.y;
+        }
+        float a2 = block_sum(part, red);
+        if (tid == 0) {
+            d[k] = Ap[pidx(k, k)].x;
+            float2 x0 = Ap[pidx(k + 1, k)];
+            float ax0 = sqrtf(x0.x * x0.x + x0.y * x0.y);
+            float alpha = sqrtf(a2);
+            if (alpha <= 1e-30f) {
+                s_tau = 0.0f;
+                ec[k] = make_float2(0, 0);
+                vv[0] = make_float2(0, 0);
+            } else {
+                float2 th = ax0 > 0.0f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.0f, 0.0f);
+                ec[k] = make_float2(-th.x * alpha, -th.y * alpha);   // beta = -theta alpha
+                vv[0] = make_float2(th.x * (ax0 + alpha), th.y * (ax0 + alpha));
+                s_tau = 1.0f / (alpha * (alpha + ax0));
+            }
+        }
+        __syncthreads();
+        const float tau = s_tau;
+        for (int i = 1 + tid; i < m; i += blockDim.x) vv[i] = tau != 0.0f ? Ap[pidx(k + 1 + i, k)] : make_float2(0, 0);
+        __syncthreads();
+        for (int i = tid; i < m; i += blockDim.x) hv[(size_t)k * F + k + 1 + i] = vv[i];
+        if (tid == 0) tau_g[k] = tau;
+        if (tau == 0.0f) {
+            __syncthreads();
+            continue;
+        }
+        // p = tau A22 v (warp per row)
+        for (int i = wid; i < m; i += nw) {
+            float2 s = make_float2(0, 0);
+            const int gi = k + 1 + i;
+            for (int j = lane; j < m; j += 32) {
+                const int gj = k + 1 + j;
+                float2 a = gj <= gi ? Ap[pidx(gi, gj)] : cconj(Ap[pidx(gj, gi)]);
+                float2 t = cmul(a, vv[j]);
+                s.x += t.x;
+                s.y += t.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            }
+            if (lane == 0) pv[i] = make_float2(tau * s.x, tau * s.y);
+        }
+        __syncthreads();
+        // K = tau / 2 * Re(v^H p)
+        float q = 0.0f;
+        for (int i = tid; i < m; i += blockDim.x) q += vv[i].x * pv[i].x + vv[i].y * pv[i].y;
+        float vhp = block_sum(q, red);
+        const float K = 0.5f * tau * vhp;
+        // w = p - K v (in place in pv)
+        for (int i = tid; i < m; i += blockDim.x) pv[i] = make_float2(pv[i].x - K * vv[i].x, pv[i].y - K * vv[i].y);
+        __syncthreads();
+        // A22 -= v w^H + w v^H (lower triangle)
+        for (int i = wid; i < m; i += nw) {
+            const float2 vi = vv[i], wi = pv[i];
+            for (int j = lane; j <= i; j += 32) {
+                float2 a = Ap[pidx(k + 1 + i, k + 1 + j)];
+                float2 t1 = cmul(vi, cconj(pv[j]));
+                float2 t2 = cmul(wi, cconj(vv[j]));
+                a.x -= t1.x + t2.x;
+                a.y -= t1.y + t2.y;
+                Ap[pidx(k + 1 + i, k + 1 + j)] = a;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (F >= 2) {
+            d[F - 2] = Ap[pidx(F - 2, F - 2)].x;
+            ec[F - 2] = Ap[pidx(F - 1, F - 2)];
+        }
+        d[F - 1] = Ap[pidx(F - 1, F - 1)].x;
+        // diagonal unitary scaling making the off-diagonal real and >= 0
+        delta[0] = make_float2(1.0f, 0.0f);
+        for (int k = 0; k + 1 < F; ++k) {
+            float2 x = ec[k];
+            float ax = sqrtf(x.x * x.x + x.y * x.y);
+            e[k] = ax;
+            delta[k + 1] = ax > 0.0f ? cmul(delta[k], make_float2(x.x / ax, x.y / ax)) : delta[k];
+        }
+        e[F - 1] = 0.0f;
+        s_fail = 0;
+    }
+    __syncthreads();
+    // Z = identity (stride F+1), reusing the packed-matrix storage
+    const int zs = F + 1;
+    for (int i = tid; i < F * zs; i += blockDim.x) Z[i] = ((i / zs) == (i % zs)) ? 1.0f : 0.0f;
+    __syncthreads();
+
+    // ---- implicit QL; thread 0 runs the scalar recurrence, everybody applies the rotations
+    float tnorm = 0.0f;
+    if (tid == 0) {
+        for (int i = 0; i < F; ++i) tnorm = fmaxf(tnorm, fabsf(d[i]) + fabsf(e[i]));
+    }
+    for (int l = 0; l < F; ++l) {
+        int iter = 0;
+        bool stop_all = false;
+        while (true) {
+            if (tid == 0) {
+                int m = l;
+                for (; m < F - 1; ++m) {
+                    float dd = fabsf(d[m]) + fabsf(d[m + 1]);
+                    if (fabsf(e[m]) <= FLT_EPSILON * dd || fabsf(e[m]) <= 1e-3f * FLT_EPSILON * tnorm) break;
+                }
+                s_done = (m == l);
+                s_nrot = 0;
+                if (m != l) {
+                    if (++iter > 60) {
+                        s_fail = 1;
+                        s_done = 1;
+                    } else {
+                        float g = (d[l + 1] - d[l]) / (2.0f * e[l]);
+                        float r = hypotf(g, 1.0f);
+                        g = d[m] - d[l] + e[l] / (g + copysignf(r, g));
+                        float s = 1.0f, c = 1.0f, p = 0.0f;
+                        bool early = false;
+                        int nrot = 0;
+                        for (int i = m - 1; i >= l; --i) {
+                            float f = s * e[i], b = c * e[i];
+                            r = hypotf(f, g);
+                            e[i + 1] = r;
+                            if (r == 0.0f) {
+                                d[i + 1] -= p;
+                                e[m] = 0.0f;
+                                early = true;
+                                break;
+                            }
+                            s = f / r;
+                            c = g / r;
+                            g = d[i + 1] - p;
+                            r = (d[i] - g) * s + 2.0f * c * b;
+                            p = s * r;
+                            d[i + 1] = g + p;
+                            g = c * r - b;
+                            rc[nrot] = c;
+                            rs[nrot] = s;
+                            ++nrot;
+                        }
+                        if (!early) {
+                            d[l] -= p;
+                            e[l] = g;
+                            e[m] = 0.0f;
+                        }
+                        s_nrot = nrot;
+                        s_m = m;
+                    }
+                }
+            }
+            __syncthreads();
+            // every thread reads the sweep description between the two barriers
+            const int done = s_done, nrot = s_nrot, mm = s_m, fail = s_fail;
+            if (!done) {
+                // rotation r acts on columns (i, i+1) with i = m - 1 - r
+                for (int row = tid; row < F; row += blockDim.x) {
+                    float *zr = Z + row * zs;
+                    for (int r = 0; r < nrot; ++r) {
+                        int i = mm - 1 - r;
+                        float c = rc[r], s = rs[r];
+                        float t = zr[i + 1];
+                        zr[i + 1] = s * zr[i] + c * t;
+                        zr[i] = c * zr[i] - s * t;
+                    }
+                }
+            }
+            __syncthreads();
+            if (done) {
+                stop_all = fail != 0;
+                break;
+            }
+        }
+        if (stop_all) break;
+    }
+    __syncthreads();
+    // ---- sort descending (rank by value, ties by index)
+    for (int i = tid; i < F; i += blockDim.x) {
+        float di = d[i];
+        int rank = 0;
+        for (int j = 0; j < F; ++j) {
+            float dj = d[j];
+            rank += (dj > di) || (dj == di && j < i);
+        }
+        perm[rank] = i;
+    }
+    __syncthreads();
+    for (int j = tid; j < F; j += blockDim.x) lam_out[j] = (double)d[perm[j]];
+    if (tid == 0) {
+        int k = k_cut;
+        if (k < 0) {
+            double tot = 0.0, acc = 0.0;
+            for (int j = 0; j < F; ++j) tot += fmax((double)d[perm[j]], 0.0);
+            k = F;
+            for (int j = 0; j < F; ++j) {
+                acc += fmax((double)d[perm[j]], 0.0);
+                if (acc >= thresh * tot) { k = j + 1; break; }
+            }
+        }
+        if (k_out) *k_out = k;
+        if (status && s_fail) *status = FQ_ERR_NUMERICAL;
+    }
+    // ---- back-transformation V[:, j] = H_0 ... H_{F-3} D Z[:, perm[j]] (warp per column)
+    for (int j = wid; j < F; j += nw) {
+        const int src = perm[j];
+        float2 y[16];  // F <= 512: 16 values per lane
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            int i = lane + 32 * q;
+            y[q] = i < F ? make_float2(delta[i].x * Z[i * zs + src], delta[i].y * Z[i * zs + src]) : make_float2(0, 0);
+        }
+        for (int k = F - 3; k >= 0; --k) {
+            const float t = tau_g[k];
+            if (t == 0.0f) continue;
+            const float2 *v = hv + (size_t)k * F;
+            float2 s = make_float2(0, 0);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                int i = lane + 32 * q;
+                if (i > k && i < F) {
+                    float2 vi = v[i];
+                    s.x += vi.x * y[q].x + vi.y * y[q].y;  // conj(v) y
+                    s.y += vi.x * y[q].y - vi.y * y[q].x;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            }
+            s.x *= t;
+            s.y *= t;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                int i = lane + 32 * q;
+                if (i > k && i < F) {
+                    float2 u = cmul(v[i], s);
+                    y[q].x -= u.x;
+                    y[q].y -= u.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            int i = lane + 32 * q;
+            if (i < F) {
+                if (V) V[(size_t)i * F + j] = y[q];
+                Vt[(size_t)j * F + i] = y[q];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------ projection + power Doppler --
+// One warp per pixel: y_j = sum_f S[f] V[f][j] for j < k, then
+// S_f = S - sum_j y_j conj(V[:, j]) and pd = mean |S_f|^2.
+template <typename T>
+__global__ void __launch_bounds__(256) project_pd_kernel(const T *__restrict__ S, int64_t P, int F,
+                                                         const float2 *__restrict__ Vt, const int *__restrict__ k_ptr,
+                                                         T *__restrict__ S_f, float *__restrict__ pd)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int k = min(*k_ptr, F);
+    const float invF = 1.0f / (float)F;
+    for (int64_t p = warp0; p < P; p += nwarps) {
+        float2 s[16], sf[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            int f = lane + 32 * q;
+            s[q] = f < F ? fqi::load_c(S, p * F + f) : make_float2(0, 0);
+            sf[q] = s[q];
+        }
+        if (k >= F) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) sf[q] = make_float2(0, 0);
+        } else {
+            for (int j = 0; j < k; ++j) {
+                const float2 *vj = Vt + (size_t)j * F;
+                float2 y = make_float2(0, 0);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    int f = lane + 32 * q;
+                    if (f < F) {
+                        float2 t = cmul(s[q], vj[f]);
+                        y.x += t.x;
+                        y.y += t.y;
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    y.x += __shfl_xor_sync(0xffffffffu, y.x, o);
+                    y.y += __shfl_xor_sync(0xffffffffu, y.y, o);
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    int f = lane + 32 * q;
+                    if (f < F) {
+                        float2 t = cmul(y, cconj(vj[f]));
+                        sf[q].x -= t.x;
+                        sf[q].y -= t.y;
+                    }
+                }
+            }
+        }
+        float e = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            int f = lane + 32 * q;
+            if (f < F) {
+                e += sf[q].x * sf[q].x + sf[q].y * sf[q].y;
+                if (S_f) fqi::store_c(S_f, p * F + f, sf[q]);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (pd && lane == 0) pd[p] = e * invF;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) power_doppler_kernel(const T *__restrict__ S, int64_t P, int F,
+                                                            float *__restrict__ pd)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp0; p < P; p += nwarps) {
+        float e = 0.0f;
+        for (int f = lane; f < F; f += 32) {
+            float2 v = fqi::load_c(S, p * F + f);
+            e += v.x * v.x + v.y * v.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (lane == 0) pd[p] = e / (float)F;
+    }
+}
+
+// ------------------------------------------------------------- launchers --
+template <typename T>
+fq_status launch_gram(const void *S, int64_t P, int F, const ClutterLayout &L, char *ws, float2 *G, cudaStream_t st)
+{
+    int nt = (F + kGramTile - 1) / kGramTile;
+    int pairs = nt * (nt + 1) / 2;
+    float2 *part = (float2 *)(ws + L.part);
+    dim3 grid(pairs, L.n_chunks);
+    gram_partial_kernel<T><<<grid, 256, 0, st>>>((const T *)S, P, F, nt, L.chunk_len, part);
+    gram_reduce_kernel<<<(F * F + 255) / 256, 256, 0, st>>>(part, L.n_chunks, F, G);
+    return fqi::launch_check("fq_casorati_gram");
+}
+
+fq_status launch_eig(const float2 *G, int F, float2 *big, float2 *hv, float *tau, double *lam, float2 *V, float2 *Vt,
+                     int k_cut, double thresh, int *k_out, int *status, cudaStream_t st)
+{
+    size_t smem = big ? 0 : sizeof(float2) * (size_t)F * (F + 1) / 2;
+    if (smem > 48 * 1024) {
+        fq_status s = fqi::cuda_check(cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)smem), "eig: smem attribute");
+        if (s) return s;
+    }
+    eig_kernel<<<1, kEigThreads, smem, st>>>(G, F, big, hv, tau, lam, V, Vt, k_cut, thresh, k_out, status);
+    return fqi::launch_check("fq_hermitian_eig");
+}
+
+int pd_blocks(int64_t P)
+{
+    int64_t b = (P + 7) / 8;
+    return (int)(b < 152 * 16 ? b : 152 * 16);
+}
+
+}  // namespace
+
+extern "C" {
+
+fq_status fq_gram_workspace_size(int64_t P, int32_t F, int32_t gram_mode, size_t *bytes)
+{
+    FQ_REQUIRE(bytes && P >= 1 && F >= 2 && F <= 512, FQ_ERR_INVALID_ARG, "fq_gram_workspace_size: bad arguments");
+    (void)gram_mode;
+    ClutterLayout L = layout(P, F);
+    *bytes = al256(sizeof(float2) * (size_t)L.n_chunks * F * F);
+    return FQ_OK;
+}
+
+fq_status fq_casorati_gram(const void *S, int32_t dtype, int64_t P, int32_t F, int32_t gram_mode, float *G,
+                           void *workspace, size_t workspace_bytes, void *stream)
+{
+    FQ_REQUIRE(S && G && P >= 1 && F >= 2 && F <= 512, FQ_ERR_INVALID_ARG, "fq_casorati_gram: bad arguments");
+    FQ_REQUIRE(gram_mode == FQ_GRAM_F32, FQ_ERR_UNSUPPORTED, "fq_casorati_gram: gram_mode %d not built", gram_mode);
+    FQ_REQUIRE(dtype == FQ_F32 || dtype == FQ_BF16, FQ_ERR_UNSUPPORTED, "fq_casorati_gram: dtype");
+    size_t need = 0;
+    fq_gram_workspace_size(P, F, gram_mode, &need);
+    FQ_REQUIRE(workspace && workspace_bytes >= need, FQ_ERR_WORKSPACE, "fq_casorati_gram: workspace needs %zu bytes",
+               need);
+    FQ_REQUIRE(fqi::aligned(workspace, 256) && fqi::aligned(S, 8) && fqi::aligned(G, 8), FQ_ERR_ALIGN,
+               "fq_casorati_gram: alignment");
+    ClutterLayout L = layout(P, F);
+    L.part = 0;  // the partials are the only workspace content here
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == FQ_F32) return launch_gram<float>(S, P, F, L, (char *)workspace, (float2 *)G, st);
+    return launch_gram<__nv_bfloat16>(S, P, F, L, (char *)workspace, (float2 *)G, st);
+}
+
+fq_status fq_eig_workspace_size(int32_t F, size_t *bytes)
+{
+    FQ_REQUIRE(bytes && F >= 1 && F <= 512, FQ_ERR_INVALID_ARG, "fq_eig_workspace_size: F must be in [1, 512]");
+    *bytes = eig_only_bytes(F);
+    return FQ_OK;
+}
+
+fq_status fq_hermitian_eig(const float *G, int32_t F, double *eigvals, float *V, void *workspace,
+                           size_t workspace_bytes, void *stream)
+{
+    FQ_REQUIRE(G && eigvals && V && F >= 1 && F <= 512, FQ_ERR_INVALID_ARG, "fq_hermitian_eig: bad arguments");
+    size_t need = eig_only_bytes(F);
+    FQ_REQUIRE(workspace && workspace_bytes >= need, FQ_ERR_WORKSPACE, "fq_hermitian_eig: workspace needs %zu bytes",
+               need);
+    FQ_REQUIRE(fqi::aligned(workspace, 256) && fqi::aligned(G, 8) && fqi::aligned(V, 8), FQ_ERR_ALIGN,
+               "fq_hermitian_eig: alignment");
+    char *ws = (char *)workspace;
+    size_t o = 256;
+    float2 *hv = (float2 *)(ws + o); o += al256(sizeof(float2) * F * F);
+    float *tau = (float *)(ws + o); o += al256(sizeof(float) * F);
+    float2 *Vt = (float2 *)(ws + o); o += al256(sizeof(float2) * F * F);
+    int *kk = (int *)(ws + o); o += 256;
+    float2 *big = eig_in_smem(F) ? nullptr : (float2 *)(ws + o);
+    cudaStream_t st = (cudaStream_t)stream;
+    fq_status s = fqi::cuda_check(cudaMemsetAsync(ws, 0, 256, st), "fq_hermitian_eig: status reset");
+    if (s) return s;
+    return launch_eig((const float2 *)G, F, big, hv, tau, eigvals, (float2 *)V, Vt, 0, 0.0, kk, (int *)ws, st);
+}
+
+fq_status fq_clutter_svd_workspace_size(int64_t P, int32_t F, int32_t gram_mode, size_t *bytes)
+{
+    FQ_REQUIRE(bytes && P >= 1 && F >= 2 && F <= 512, FQ_ERR_INVALID_ARG,
+               "fq_clutter_svd_workspace_size: bad arguments");
+    (void)gram_mode;
+    *bytes = layout(P, F).total;
+    return FQ_OK;
+}
+
+fq_status fq_clutter_svd(const void *iq, int32_t dtype, int64_t P, int32_t F, int32_t k_cut, double energy_thresh,
+                         int32_t gram_mode, void *iq_f, float *pd, double *eigvals, int32_t *k_used, void *workspace,
+                         size_t workspace_bytes, void *stream)
+{
+    FQ_REQUIRE(iq && P >= 1 && F >= 2 && F <= 512, FQ_ERR_INVALID_ARG, "fq_clutter_svd: bad arguments");
+    FQ_REQUIRE(k_cut <= F, FQ_ERR_INVALID_ARG, "fq_clutter_svd: k_cut %d > F %d", k_cut, F);
+    FQ_REQUIRE(k_cut >= 0 || (energy_thresh > 0.0 && energy_thresh <= 1.0), FQ_ERR_INVALID_ARG,
+               "fq_clutter_svd: energy_thresh must be in (0, 1] when k_cut < 0");
+    FQ_REQUIRE(dtype == FQ_F32 || dtype == FQ_BF16, FQ_ERR_UNSUPPORTED, "fq_clutter_svd: dtype");
+    FQ_REQUIRE(gram_mode == FQ_GRAM_F32, FQ_ERR_UNSUPPORTED, "fq_clutter_svd: gram_mode %d not built", gram_mode);
+    ClutterLayout L = layout(P, F);
+    FQ_REQUIRE(workspace && workspace_bytes >= L.total, FQ_ERR_WORKSPACE,
+               "fq_clutter_svd: workspace needs %zu bytes", L.total);
+    FQ_REQUIRE(fqi::aligned(workspace, 256) && fqi::aligned(iq, 8) && fqi::aligned(iq_f, 8), FQ_ERR_ALIGN,
+               "fq_clutter_svd: alignment");
+    char *ws = (char *)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+    fq_status s = fqi::cuda_check(cudaMemsetAsync(ws, 0, 256, st), "fq_clutter_svd: status reset");
+    if (s) return s;
+    float2 *G = (float2 *)(ws + L.G);
+    s = dtype == FQ_F32 ? launch_gram<float>(iq, P, F, L, ws, G, st) : launch_gram<__nv_bfloat16>(iq, P, F, L, ws, G, st);
+    if (s) return s;
+    double *lam = eigvals ? eigvals : (double *)(ws + L.lam);
+    int *kk = k_used ? (int *)k_used : (int *)(ws + L.k);
+    float2 *big = eig_in_smem(F) ? nullptr : (float2 *)(ws + L.big);
+    s = launch_eig(G, F, big, (float2 *)(ws + L.hv), (float *)(ws + L.tau), lam, (float2 *)(ws + L.V),
+                   (float2 *)(ws + L.Vt), k_cut, energy_thresh, kk, (int *)ws, st);
+    if (s) return s;
+    if (!iq_f && !pd) return FQ_OK;
+    if (dtype == FQ_F32)
+        project_pd_kernel<float><<<pd_blocks(P), 256, 0, st>>>((const float *)iq, P, F, (const float2 *)(ws + L.Vt), kk,
+                                                               (float *)iq_f, pd);
+    else
+        project_pd_kernel<__nv_bfloat16><<<pd_blocks(P), 256, 0, st>>>(
+            (const __nv_bfloat16 *)iq, P, F, (const float2 *)(ws + L.Vt), kk, (__nv_bfloat16 *)iq_f, pd);
+    return fqi::launch_check("fq_clutter_svd: projection");
+}
+
+fq_status fq_power_doppler(const void *iq_f, int32_t dtype, int64_t P, int32_t F, float *pd, void *stream)
+{
+    FQ_REQUIRE(iq_f && pd && P >= 1 && F >= 1, FQ_ERR_INVALID_ARG, "fq_power_doppler: bad arguments");
+    FQ_REQUIRE(fqi::aligned(iq_f, 8), FQ_ERR_ALIGN, "fq_power_doppler: iq_f must be 8-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == FQ_F32)
+        power_doppler_kernel<float><<<pd_blocks(P), 256, 0, st>>>((const float *)iq_f, P, F, pd);
+    else if (dtype == FQ_BF16)
+        power_doppler_kernel<__nv_bfloat16><<<pd_blocks(P), 256, 0, st>>>((const __nv_bfloat16 *)iq_f, P, F, pd);
+    else
+        return fqi::set_error(FQ_ERR_UNSUPPORTED, "fq_power_doppler: dtype");
+    return fqi::launch_check("fq_power_doppler");
+}
+
+fq_status fq_clutter_status(void *workspace, void *stream)
+{
+    FQ_REQUIRE(workspace, FQ_ERR_INVALID_ARG, "fq_clutter_status: null workspace");
+    cudaStream_t st = (cudaStream_t)stream;
+    int flag = 0;
+    fq_status s = fqi::cuda_check(cudaMemcpyAsync(&flag, workspace, sizeof(int), cudaMemcpyDeviceToHost, st),
+                                  "fq_clutter_status: read");
+    if (s) return s;
+    s = fqi::cuda_check(cudaStreamSynchronize(st), "fq_clutter_status: sync");
+    if (s) return s;
+    s = fqi::cuda_check(cudaMemsetAsync(workspace, 0, sizeof(int), st), "fq_clutter_status: clear");
+    if (s) return s;
+    if (flag) return fqi::set_error((fq_status)flag, "device solver reported %s", fq_status_string((fq_status)flag));
+    return FQ_OK;
+}
+
+}  // extern "C"

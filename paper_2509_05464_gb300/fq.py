@@ -1,0 +1,395 @@
+"""Thin Python binding of the C ABI in include/fq.h (ctypes).
+
+Argument marshalling only: every step runs in libfq's CUDA kernels.  Torch
+tensors supply device memory and the current CUDA stream.  Complex arrays
+are real tensors with a trailing dimension of 2 (re, im), float32 or
+bfloat16.  Descriptors come from the dataclasses of ``workload`` (or any
+object with the same attributes).
+
+The library is loaded on first use from ``_build/libfq.so``; if it is
+missing this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfq.so")
+
+FQ_F32, FQ_BF16, FQ_F16 = 0, 1, 2
+FQ_GRAM_F32, FQ_GRAM_TF32, FQ_GRAM_BF16 = 0, 1, 2
+STATUS = {0: "FQ_OK", 1: "FQ_ERR_INVALID_ARG", 2: "FQ_ERR_SHAPE", 3: "FQ_ERR_ALIGN", 4: "FQ_ERR_WORKSPACE",
+          5: "FQ_ERR_CUDA", 6: "FQ_ERR_TIMEOUT", 7: "FQ_ERR_NUMERICAL", 8: "FQ_ERR_UNSUPPORTED"}
+
+
+class FqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ---------------------------------------------------------------- structs --
+class Probe(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("pitch_x", C.c_double), ("pitch_y", C.c_double),
+                ("width_x", C.c_double), ("width_y", C.c_double), ("f0", C.c_double), ("fs", C.c_double),
+                ("c", C.c_double), ("alpha_db_cm_mhz", C.c_double), ("n_cycles", C.c_int32),
+                ("n_samples", C.c_int32)]
+
+
+class Tx(C.Structure):
+    _fields_ = [("n_angles", C.c_int32), ("tilt_x", C.POINTER(C.c_double)), ("tilt_y", C.POINTER(C.c_double))]
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("x0", C.c_double), ("y0", C.c_double),
+                ("z0", C.c_double), ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("fnumber", C.c_double)]
+
+
+class Segment(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("p0", C.c_double * 3), ("a1", C.c_double * 3), ("a2", C.c_double * 3),
+                ("a3", C.c_double * 3), ("length", C.c_double), ("radius", C.c_double), ("vmax", C.c_double),
+                ("arc_radius", C.c_double), ("phi1", C.c_double), ("arc_end", C.c_double * 2)]
+
+
+class Flow(C.Structure):
+    _fields_ = [("n_seg", C.c_int32), ("seg", C.POINTER(Segment))]
+
+
+class Motion(C.Structure):
+    _fields_ = [("n_terms", C.c_int32), ("amp", C.c_double * 4), ("freq", C.c_double * 4),
+                ("phase", C.c_double * 4), ("dir", (C.c_double * 3) * 4), ("elastic_grad", C.c_double * 3),
+                ("elastic_center", C.c_double * 3), ("vel", C.c_double * 3), ("omega", C.c_double * 3),
+                ("rot_center", C.c_double * 3)]
+
+
+# ------------------------------------------------------------------ loading --
+_lock = threading.Lock()
+_lib = None
+_P = C.c_void_p
+_I32 = C.c_int32
+_I64 = C.c_int64
+_D = C.c_double
+_SZ = C.c_size_t
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise FqError(-1, f"libfq.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                              "python -m paper_2509_05464_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        L.fq_last_error.restype = C.c_char_p
+        L.fq_status_string.restype = C.c_char_p
+        L.fq_status_string.argtypes = [C.c_int]
+        L.fq_version.restype = _I32
+        L.fq_frame_pad.restype = _I32
+        L.fq_frame_pad.argtypes = [_I32]
+        sig = {
+            "fq_advect_scatterers": [_P, _P, _P, _I64, C.POINTER(Flow), C.POINTER(Motion), _D, _D, _I32, _P, _P],
+            "fq_classify_scatterers": [_P, _P, _I64, C.POINTER(Flow), _P, _P, _P, _P],
+            "fq_bin_workspace_size": [_I64, _I32, C.POINTER(_SZ)],
+            "fq_bin_scatterers": [_P, _I64, _D, _D, _I32, _P, _P, _P, _SZ, _P],
+            "fq_simulate_rf": [C.POINTER(Probe), C.POINTER(Tx), _P, _P, _I64, _I32, _P, _I32, _P, _P],
+            "fq_rf2iq": [C.POINTER(Probe), _I32, _I32, _P, _I32, _I32, _P, _P],
+            "fq_das": [C.POINTER(Probe), C.POINTER(Tx), _P, _I32, _I32, C.POINTER(Grid), _I32, _P, _P],
+            "fq_beamform_das_workspace_size": [C.POINTER(Probe), C.POINTER(Tx), _I32, _I32, C.POINTER(_SZ)],
+            "fq_beamform_das": [C.POINTER(Probe), C.POINTER(Tx), _P, _I32, _I32, C.POINTER(Grid), _I32, _I32, _P,
+                                _P, _SZ, _P],
+            "fq_gram_workspace_size": [_I64, _I32, _I32, C.POINTER(_SZ)],
+            "fq_casorati_gram": [_P, _I32, _I64, _I32, _I32, _P, _P, _SZ, _P],
+            "fq_eig_workspace_size": [_I32, C.POINTER(_SZ)],
+            "fq_hermitian_eig": [_P, _I32, _P, _P, _P, _SZ, _P],
+            "fq_clutter_svd_workspace_size": [_I64, _I32, _I32, C.POINTER(_SZ)],
+            "fq_clutter_svd": [_P, _I32, _I64, _I32, _I32, _D, _I32, _P, _P, _P, _P, _P, _SZ, _P],
+            "fq_power_doppler": [_P, _I32, _I64, _I32, _P, _P],
+            "fq_clutter_status": [_P, _P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        _lib = L
+        return L
+
+
+def _check(status):
+    if status != 0:
+        raise FqError(status, lib().fq_last_error().decode())
+
+
+def version() -> int:
+    return lib().fq_version()
+
+
+def frame_pad(n_frames: int) -> int:
+    return lib().fq_frame_pad(int(n_frames))
+
+
+# ------------------------------------------------------------------ helpers --
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return FQ_F32
+    if t.dtype == torch.bfloat16:
+        return FQ_BF16
+    if t.dtype == torch.float16:
+        return FQ_F16
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _tdt(code: int):
+    return {FQ_F32: torch.float32, FQ_BF16: torch.bfloat16, FQ_F16: torch.float16}[code]
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_probe(p) -> Probe:
+    return Probe(int(p.nx), int(p.ny), p.pitch_x, p.pitch_y, p.width_x, p.width_y, p.f0, p.fs, p.c,
+                 p.alpha_db_cm_mhz, int(p.n_cycles), int(p.n_samples))
+
+
+class _TxHolder:
+    def __init__(self, tilt_x, tilt_y):
+        self.tx_arr = np.ascontiguousarray(tilt_x, np.float64)
+        self.ty_arr = np.ascontiguousarray(tilt_y, np.float64)
+        dp = C.POINTER(C.c_double)
+        self.st = Tx(int(self.tx_arr.shape[0]), self.tx_arr.ctypes.data_as(dp), self.ty_arr.ctypes.data_as(dp))
+
+
+def make_grid(g) -> Grid:
+    return Grid(int(g.nx), int(g.ny), int(g.nz), g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, g.fnumber)
+
+
+class _FlowHolder:
+    def __init__(self, segments):
+        n = len(segments)
+        self.arr = (Segment * max(n, 1))()
+        for i, s in enumerate(segments):
+            self.arr[i] = Segment(int(s.kind), (C.c_double * 3)(*s.p0), (C.c_double * 3)(*s.a1),
+                                  (C.c_double * 3)(*s.a2), (C.c_double * 3)(*s.a3), s.length, s.radius, s.vmax,
+                                  s.arc_radius, s.phi1, (C.c_double * 2)(*s.arc_end))
+        self.st = Flow(n, C.cast(self.arr, C.POINTER(Segment)))
+
+
+def make_motion(m) -> Motion:
+    mo = Motion()
+    n = m.n_terms
+    mo.n_terms = n
+    for j in range(n):
+        mo.amp[j] = m.amp[j]
+        mo.freq[j] = m.freq[j]
+        mo.phase[j] = m.phase[j]
+        for d in range(3):
+            mo.dir[j][d] = m.dir[j][d]
+    for name in ("elastic_grad", "elastic_center", "vel", "omega", "rot_center"):
+        arr = getattr(mo, name)
+        for d in range(3):
+            arr[d] = getattr(m, name)[d]
+    return mo
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A device byte buffer (256-byte aligned by the caching allocator)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+# ------------------------------------------------------------- entry points --
+def fq_advect_scatterers(p0, seg_id, flow_coord, segments, motion, t0, dt, n_frames, pos_out=None, stream=None):
+    S = seg_id.shape[0]
+    if pos_out is None:
+        pos_out = torch.empty((n_frames, 3, S), dtype=torch.float32, device=p0.device)
+    fh = _FlowHolder(segments)
+    mo = make_motion(motion)
+    _check(lib().fq_advect_scatterers(_ptr(p0), _ptr(seg_id), _ptr(flow_coord), S, C.byref(fh.st), C.byref(mo),
+                                      float(t0), float(dt), int(n_frames), _ptr(pos_out), _stream(stream)))
+    return pos_out
+
+
+def fq_classify_scatterers(pos, seg_id, segments, amp_in, vessel_out=None, amp_out=None, want_amp=True,
+                           stream=None):
+    S = seg_id.shape[0]
+    if vessel_out is None:
+        vessel_out = torch.empty(S, dtype=torch.int32, device=pos.device)
+    if amp_out is None and want_amp:
+        amp_out = torch.empty(S, dtype=torch.float32, device=pos.device)
+    fh = _FlowHolder(segments)
+    _check(lib().fq_classify_scatterers(_ptr(pos), _ptr(seg_id), S, C.byref(fh.st), _ptr(amp_in),
+                                        _ptr(vessel_out), _ptr(amp_out), _stream(stream)))
+    return vessel_out, amp_out
+
+
+def fq_bin_workspace_size(S, B):
+    n = _SZ(0)
+    _check(lib().fq_bin_workspace_size(int(S), int(B), C.byref(n)))
+    return n.value
+
+
+def fq_bin_scatterers(z, z0, dz, B, bin_off=None, perm=None, ws=None, stream=None):
+    S = z.shape[0]
+    dev = z.device
+    if bin_off is None:
+        bin_off = torch.empty(B + 1, dtype=torch.int32, device=dev)
+    if perm is None:
+        perm = torch.empty(max(S, 1), dtype=torch.int32, device=dev)
+    need = fq_bin_workspace_size(S, B)
+    if ws is None:
+        ws = workspace(need, dev)
+    _check(lib().fq_bin_scatterers(_ptr(z), S, float(z0), float(dz), int(B), _ptr(bin_off), _ptr(perm),
+                                   _ptr(ws), ws.numel(), _stream(stream)))
+    return bin_off, perm[:S]
+
+
+def fq_simulate_rf(probe, tilt_x, tilt_y, pos, amp, n_frames, rf_base=None, out_dtype=torch.float32, rf=None,
+                   stream=None):
+    S = amp.shape[0]
+    A = len(tilt_x)
+    M = probe.nx * probe.ny
+    if rf is None:
+        rf = torch.empty((n_frames, A, M, probe.n_samples), dtype=out_dtype, device=amp.device)
+    pr = make_probe(probe)
+    th = _TxHolder(tilt_x, tilt_y)
+    _check(lib().fq_simulate_rf(C.byref(pr), C.byref(th.st), _ptr(pos), _ptr(amp), S, int(n_frames),
+                                _ptr(rf_base), _dt(rf), _ptr(rf), _stream(stream)))
+    return rf
+
+
+def fq_rf2iq(probe, n_lines, n_frames, rf, iq_dtype=torch.float32, iq_ch=None, stream=None):
+    Fp = frame_pad(n_frames)
+    if iq_ch is None:
+        iq_ch = torch.empty((n_lines, probe.n_samples, Fp, 2), dtype=iq_dtype, device=rf.device)
+    pr = make_probe(probe)
+    _check(lib().fq_rf2iq(C.byref(pr), int(n_lines), int(n_frames), _ptr(rf), _dt(rf), _dt(iq_ch), _ptr(iq_ch),
+                          _stream(stream)))
+    return iq_ch
+
+
+def fq_das(probe, tilt_x, tilt_y, iq_ch, n_frames, grid, iq_dtype=torch.float32, iq=None, stream=None):
+    P = grid.nx * grid.ny * grid.nz
+    if iq is None:
+        iq = torch.empty((P, n_frames, 2), dtype=iq_dtype, device=iq_ch.device)
+    pr = make_probe(probe)
+    th = _TxHolder(tilt_x, tilt_y)
+    gr = make_grid(grid)
+    _check(lib().fq_das(C.byref(pr), C.byref(th.st), _ptr(iq_ch), _dt(iq_ch), int(n_frames), C.byref(gr),
+                        _dt(iq), _ptr(iq), _stream(stream)))
+    return iq
+
+
+def fq_beamform_das_workspace_size(probe, tilt_x, tilt_y, n_frames, ch_dtype=torch.float32):
+    pr = make_probe(probe)
+    th = _TxHolder(tilt_x, tilt_y)
+    n = _SZ(0)
+    code = FQ_F32 if ch_dtype == torch.float32 else FQ_BF16
+    _check(lib().fq_beamform_das_workspace_size(C.byref(pr), C.byref(th.st), int(n_frames), code, C.byref(n)))
+    return n.value
+
+
+def fq_beamform_das(probe, tilt_x, tilt_y, rf, n_frames, grid, ch_dtype=torch.float32, iq_dtype=torch.float32,
+                    iq=None, ws=None, stream=None):
+    P = grid.nx * grid.ny * grid.nz
+    if iq is None:
+        iq = torch.empty((P, n_frames, 2), dtype=iq_dtype, device=rf.device)
+    need = fq_beamform_das_workspace_size(probe, tilt_x, tilt_y, n_frames, ch_dtype)
+    if ws is None:
+        ws = workspace(need, rf.device)
+    pr = make_probe(probe)
+    th = _TxHolder(tilt_x, tilt_y)
+    gr = make_grid(grid)
+    code = FQ_F32 if ch_dtype == torch.float32 else FQ_BF16
+    _check(lib().fq_beamform_das(C.byref(pr), C.byref(th.st), _ptr(rf), _dt(rf), int(n_frames), C.byref(gr), code,
+                                 _dt(iq), _ptr(iq), _ptr(ws), ws.numel(), _stream(stream)))
+    return iq
+
+
+def fq_gram_workspace_size(P, F, gram_mode=FQ_GRAM_F32):
+    n = _SZ(0)
+    _check(lib().fq_gram_workspace_size(int(P), int(F), int(gram_mode), C.byref(n)))
+    return n.value
+
+
+def fq_casorati_gram(S, gram_mode=FQ_GRAM_F32, G=None, ws=None, stream=None):
+    P, F = S.shape[0], S.shape[1]
+    if G is None:
+        G = torch.empty((F, F, 2), dtype=torch.float32, device=S.device)
+    if ws is None:
+        ws = workspace(fq_gram_workspace_size(P, F, gram_mode), S.device)
+    _check(lib().fq_casorati_gram(_ptr(S), _dt(S), P, F, int(gram_mode), _ptr(G), _ptr(ws), ws.numel(),
+                                  _stream(stream)))
+    return G
+
+
+def fq_eig_workspace_size(F):
+    n = _SZ(0)
+    _check(lib().fq_eig_workspace_size(int(F), C.byref(n)))
+    return n.value
+
+
+def fq_hermitian_eig(G, eigvals=None, V=None, ws=None, stream=None):
+    F = G.shape[0]
+    if eigvals is None:
+        eigvals = torch.empty(F, dtype=torch.float64, device=G.device)
+    if V is None:
+        V = torch.empty((F, F, 2), dtype=torch.float32, device=G.device)
+    if ws is None:
+        ws = workspace(fq_eig_workspace_size(F), G.device)
+    _check(lib().fq_hermitian_eig(_ptr(G), F, _ptr(eigvals), _ptr(V), _ptr(ws), ws.numel(), _stream(stream)))
+    return eigvals, V, ws
+
+
+def fq_clutter_svd_workspace_size(P, F, gram_mode=FQ_GRAM_F32):
+    n = _SZ(0)
+    _check(lib().fq_clutter_svd_workspace_size(int(P), int(F), int(gram_mode), C.byref(n)))
+    return n.value
+
+
+def fq_clutter_svd(iq, k_cut=2, energy_thresh=0.9, gram_mode=FQ_GRAM_F32, want_iq_f=True, iq_f=None, pd=None,
+                   eigvals=None, k_used=None, ws=None, stream=None):
+    P, F = iq.shape[0], iq.shape[1]
+    dev = iq.device
+    if iq_f is None and want_iq_f:
+        iq_f = torch.empty_like(iq)
+    if pd is None:
+        pd = torch.empty(P, dtype=torch.float32, device=dev)
+    if eigvals is None:
+        eigvals = torch.empty(F, dtype=torch.float64, device=dev)
+    if k_used is None:
+        k_used = torch.empty(1, dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = workspace(fq_clutter_svd_workspace_size(P, F, gram_mode), dev)
+    _check(lib().fq_clutter_svd(_ptr(iq), _dt(iq), P, F, int(k_cut), float(energy_thresh), int(gram_mode),
+                                _ptr(iq_f), _ptr(pd), _ptr(eigvals), _ptr(k_used), _ptr(ws), ws.numel(),
+                                _stream(stream)))
+    return dict(iq_f=iq_f, pd=pd, eigvals=eigvals, k=k_used, ws=ws)
+
+
+def fq_power_doppler(iq_f, pd=None, stream=None):
+    P, F = iq_f.shape[0], iq_f.shape[1]
+    if pd is None:
+        pd = torch.empty(P, dtype=torch.float32, device=iq_f.device)
+    _check(lib().fq_power_doppler(_ptr(iq_f), _dt(iq_f), P, F, _ptr(pd), _stream(stream)))
+    return pd
+
+
+def fq_clutter_status(ws, stream=None):
+    _check(lib().fq_clutter_status(_ptr(ws), _stream(stream)))

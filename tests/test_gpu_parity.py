@@ -1,0 +1,331 @@
+"""CUDA path vs the FP64 oracle, element by element, on the same seeded
+inputs (through the C ABI).  Tolerances: integer / index work bit-exact;
+RF and IQ relative L2 <= 1e-5 in FP32, <= 1e-2 with BF16 storage; power
+Doppler relative L2 <= 1e-3; advected positions within 1 ulp of binary32."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_05464_gb300 import build as fqbuild
+from paper_2509_05464_gb300 import fq
+from paper_2509_05464_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+RF_TOL = 1e-5
+BF16_TOL = 1e-2
+PD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    fqbuild.build()
+    fq.lib()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.float().cpu().numpy() if t.dtype == torch.bfloat16 else t.cpu().numpy()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def tables(w):
+    return W.segment_table(w), W.motion_table(w.motion)
+
+
+# --------------------------------------------------------------- a1 advect --
+def _advect_cases():
+    w2 = W.config2(n_scat=20_000, n_frames=3)
+    w3 = W.config3(n_scat=20_000, n_frames=3)
+    w1 = W.config1()
+    w1.motion = W.Motion(vel=(3e-3, 3e-3, 3e-3), omega=(0.0, -0.2, 0.0), rot_center=(0.0, 0.0, 25e-3))
+    return [(w2, 0.0, 1e-3), (w3, 0.0, 1e-3), (w1, 0.0, 1e-3), (w2, 7.3, 0.25)]
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_advect_within_one_ulp(case):
+    w, t0, dt = _advect_cases()[case]
+    st, mt = tables(w)
+    F = w.n_frames
+    pos = host(fq.fq_advect_scatterers(dev(w.p0), dev(w.seg), dev(w.flow), w.segments, w.motion, t0, dt, F))
+    for f in range(F):
+        t = t0 + f * dt
+        want = oracle.advect(w.p0, w.seg, w.flow, st, mt, t)
+        ulp = np.spacing(np.abs(want).astype(np.float32))
+        diff = np.abs(pos[f].astype(np.float64) - want.astype(np.float64))
+        assert np.all(diff <= ulp), (f, float((diff / ulp).max()))
+        assert np.mean(diff == 0) > 0.999
+
+
+# --------------------------------------------------- a2 membership, binning --
+def _near_wall_points(w, rng, n=4000):
+    """points scattered within +-2% of the lumen walls of every segment"""
+    pts = []
+    for s in w.segments:
+        k = n // max(1, len(w.segments))
+        if s.kind == W.SEG_LINE:
+            a = rng.uniform(-0.02, 1.02, k) * s.length
+            r = s.radius * rng.uniform(0.98, 1.02, k)
+            th = rng.uniform(0, 2 * math.pi, k)
+            p = (np.array(s.p0)[:, None] + np.outer(s.a1, a) + np.outer(s.a2, r * np.cos(th))
+                 + np.outer(s.a3, r * np.sin(th)))
+        else:
+            ph = rng.uniform(-0.05, s.phi1 + 0.05, k)
+            r = s.radius * rng.uniform(0.98, 1.02, k)
+            th = rng.uniform(0, 2 * math.pi, k)
+            rr = s.arc_radius + r * np.cos(th)
+            p = (np.array(s.p0)[:, None] + np.outer(s.a1, rr * np.cos(ph)) + np.outer(s.a2, rr * np.sin(ph))
+                 + np.outer(s.a3, r * np.sin(th)))
+        pts.append(p)
+    return np.concatenate(pts, axis=1).astype(np.float32)
+
+
+@pytest.mark.parametrize("cfg", ["c2", "c3"])
+def test_classify_bit_exact(cfg):
+    w = W.config2(n_scat=30_000, n_frames=1) if cfg == "c2" else W.config3(n_scat=30_000, n_frames=1)
+    st, _ = tables(w)
+    rng = np.random.default_rng(4)
+    extra = _near_wall_points(w, rng)
+    pos = np.concatenate([w.p0, extra], axis=1)
+    seg = np.concatenate([w.seg, np.full(extra.shape[1], -1, np.int32)])
+    amp = np.concatenate([w.amp, rng.standard_normal(extra.shape[1]).astype(np.float32)])
+    # blood rows of p0 are zero; give them real positions (their t = 0 flow position)
+    pos[:, :w.S] = oracle.advect(w.p0, w.seg, w.flow, st, W.motion_table(W.Motion()), 0.0)
+    v_gpu, a_gpu = fq.fq_classify_scatterers(dev(pos), dev(seg), w.segments, dev(amp))
+    v_ref, a_ref = oracle.classify(pos, seg, st, len(w.segments), amp)
+    assert np.array_equal(host(v_gpu), v_ref)
+    assert np.array_equal(host(a_gpu), a_ref)
+    assert (v_ref[w.S:] >= 0).sum() > 100 and (v_ref[w.S:] < 0).sum() > 100
+
+
+@pytest.mark.parametrize("S,B", [(0, 5), (1, 1), (4095, 7), (4096, 230), (4097, 230), (100_003, 230), (50_000, 8192)])
+def test_bin_bit_exact(S, B):
+    rng = np.random.default_rng(S + B)
+    z0, dz = 0.5e-3, 0.1e-3
+    z = rng.uniform(-1e-3, z0 + dz * B * 1.1, S).astype(np.float32)
+    if S > 100:
+        z[:40] = z[40:80]
+        z[80] = np.float32(z0)
+        z[81] = np.float32(z0 + 3 * dz)
+    off_g, perm_g = fq.fq_bin_scatterers(dev(z) if S else torch.empty(0, device="cuda"), z0, dz, B)
+    off_r, perm_r = oracle.bin_scatterers(z, z0, dz, B)
+    assert np.array_equal(host(off_g), off_r)
+    assert np.array_equal(host(perm_g)[:S], perm_r)
+
+
+# ------------------------------------------------------------ a3 RF synthesis --
+def _positions(w, frames):
+    st, mt = tables(w)
+    return np.stack([oracle.advect(w.p0, w.seg, w.flow, st, mt, f / w.prf) for f in frames])
+
+
+def _rf_cases():
+    c1 = W.config1()
+    c2 = W.shrink(W.config2(n_scat=100_000, n_frames=2), max_scat=4000)
+    c3 = W.shrink(W.config3(n_scat=50_000, n_frames=1), max_scat=500)
+    return {"c1": (c1, [0, 5]), "c2": (c2, [0, 1]), "c3": (c3, [0])}
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c2", "c3"])
+def test_rf_parity_fp32(cfg):
+    w, frames = _rf_cases()[cfg]
+    pos = _positions(w, frames).astype(np.float32)
+    rf = host(fq.fq_simulate_rf(w.probe, w.tilt_x, w.tilt_y, dev(pos), dev(w.amp), len(frames)))
+    for i in range(len(frames)):
+        want = oracle.simulate_rf(w.probe, w.tilt_x, w.tilt_y, pos[i], w.amp)
+        err = rel_l2(rf[i], want)
+        assert err <= RF_TOL, (cfg, i, err)
+
+
+def test_rf_static_tissue_base_and_bf16():
+    """Alg. 1: RF_total = RF_tissue(frame 0) + RF_blood(frame f) through the
+    rf_base input; BF16 storage within 1e-2."""
+    w = W.config1()
+    nt = w.n_tissue
+    pos = _positions(w, [0, 3]).astype(np.float32)
+    pos_t = np.ascontiguousarray(pos[:1, :, :nt])
+    pos_b = np.ascontiguousarray(pos[:, :, nt:])
+    base = fq.fq_simulate_rf(w.probe, w.tilt_x, w.tilt_y, dev(pos_t), dev(w.amp[:nt]), 1)
+    rf = host(fq.fq_simulate_rf(w.probe, w.tilt_x, w.tilt_y, dev(pos_b), dev(w.amp[nt:]), 2, rf_base=base[0]))
+    for i in range(2):
+        want = oracle.simulate_rf(w.probe, w.tilt_x, w.tilt_y, pos_t[0], w.amp[:nt])
+        want = oracle.simulate_rf(w.probe, w.tilt_x, w.tilt_y, pos_b[i], w.amp[nt:], rf=want, accumulate=True)
+        assert rel_l2(rf[i], want) <= RF_TOL
+    rf16 = host(fq.fq_simulate_rf(w.probe, w.tilt_x, w.tilt_y, dev(pos), dev(w.amp), 2, out_dtype=torch.bfloat16))
+    want = oracle.simulate_rf(w.probe, w.tilt_x, w.tilt_y, pos[1], w.amp)
+    assert rel_l2(rf16[1], want) <= BF16_TOL
+
+
+def test_rf_edge_cases():
+    """no scatterers -> zeros; scatterers whose echo straddles the record
+    ends keep only the in-record samples."""
+    p = W.Probe(8, 1, 0.3e-3, 0.3e-3, 0.3e-3, 0.3e-3, 5e6, 20e6, 1540.0, 0.5, 2, 300)
+    z = torch.zeros((1, 3, 0), device="cuda")
+    rf = host(fq.fq_simulate_rf(p, [0.0], [0.0], z, torch.zeros(0, device="cuda"), 1))
+    assert not rf.any()
+    # depth 0.05 mm (echo at t ~ 0) and ~11.5 mm (echo around the last sample)
+    pos = np.array([[[0.1e-3, 0.0, -0.2e-3], [0.0, 0.0, 0.0], [0.05e-3, 11.53e-3, 11.6e-3]]], np.float32)
+    amp = np.array([1.0, -2.0, 0.5], np.float32)
+    rf = host(fq.fq_simulate_rf(p, [0.0], [0.0], dev(pos), dev(amp), 1))
+    want = oracle.simulate_rf(p, [0.0], [0.0], pos[0], amp)
+    assert np.abs(want[0, :, -3:]).max() > 0
+    assert rel_l2(rf[0], want) <= RF_TOL
+
+
+# --------------------------------------------------------- a4 rf2iq, a5 DAS --
+def test_rf2iq_parity():
+    p = W.Probe(4, 1, 0.1e-3, 0.1e-3, 0.1e-3, 0.1e-3, 15.6e6, 62.5e6, 1540.0, 0.5, 2, 1000)
+    rng = np.random.default_rng(0)
+    F, L = 3, 6
+    rf = rng.standard_normal((F, L, p.n_samples)).astype(np.float32)
+    iq = host(fq.fq_rf2iq(p, L, F, dev(rf)))  # [L][Ns][Fp][2]
+    want = oracle.rf2iq(p, rf)  # [F][L][Ns] complex
+    got = iq[:, :, :F, 0] + 1j * iq[:, :, :F, 1]  # [L][Ns][F]
+    want = want.transpose(1, 2, 0)
+    assert rel_l2(np.stack([got.real, got.imag]), np.stack([want.real, want.imag])) <= RF_TOL
+    assert not iq[:, :, F:].any()
+
+
+def _das_cases():
+    c1 = W.config1(n_frames=3)
+    c2 = W.shrink(W.config2(n_scat=100_000, n_frames=3), max_scat=3000, grid_div=4)
+    c3 = W.shrink(W.config3(n_scat=50_000, n_frames=2), max_scat=300, grid_div=8)
+    return {"c1": c1, "c2": c2, "c3": c3}
+
+
+def _oracle_rf(w, frames):
+    pos = _positions(w, frames).astype(np.float32)
+    return np.stack([oracle.simulate_rf(w.probe, w.tilt_x, w.tilt_y, pos[i], w.amp) for i in range(len(frames))]
+                    ).astype(np.float32)
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c2", "c3"])
+def test_beamform_parity_fp32(cfg):
+    w = _das_cases()[cfg]
+    F = w.n_frames
+    rf = _oracle_rf(w, range(F))
+    iq = host(fq.fq_beamform_das(w.probe, w.tilt_x, w.tilt_y, dev(rf), F, w.grid))
+    want = oracle.beamform(w.probe, w.tilt_x, w.tilt_y, rf, w.grid)
+    got = iq[..., 0] + 1j * iq[..., 1]
+    err = rel_l2(np.stack([got.real, got.imag]), np.stack([want.real, want.imag]))
+    assert err <= RF_TOL, (cfg, err)
+
+
+def test_beamform_bf16_storage():
+    w = _das_cases()["c2"]
+    F = w.n_frames
+    rf = _oracle_rf(w, range(F))
+    want = oracle.beamform(w.probe, w.tilt_x, w.tilt_y, rf, w.grid)
+    iq = host(fq.fq_beamform_das(w.probe, w.tilt_x, w.tilt_y, dev(rf).bfloat16(), F, w.grid,
+                                 ch_dtype=torch.bfloat16, iq_dtype=torch.bfloat16))
+    got = iq[..., 0] + 1j * iq[..., 1]
+    assert rel_l2(np.stack([got.real, got.imag]), np.stack([want.real, want.imag])) <= BF16_TOL
+
+
+# --------------------------------------------------- a6-a8 clutter filter --
+def _clutter(P, F, k, seed, gap=1e3):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((F, F)) + 1j * rng.standard_normal((F, F)))
+    Uc, _ = np.linalg.qr(rng.standard_normal((P, k)) + 1j * rng.standard_normal((P, k)))
+    L = (Uc * (gap * np.linspace(2.0, 1.0, k))) @ Q[:, :k].conj().T
+    B = (rng.standard_normal((P, F)) + 1j * rng.standard_normal((P, F))) * 0.3
+    return L + B
+
+
+def cdev(S):
+    return dev(np.stack([S.real, S.imag], axis=-1).astype(np.float32))
+
+
+def cplx(t):
+    a = host(t).astype(np.float64)
+    return a[..., 0] + 1j * a[..., 1]
+
+
+@pytest.mark.parametrize("P,F", [(3000, 10), (3001, 64), (2048, 200), (100, 2)])
+def test_gram_parity(P, F):
+    rng = np.random.default_rng(P * F)
+    S = (rng.standard_normal((P, F)) + 1j * rng.standard_normal((P, F))).astype(np.complex64).astype(np.complex128)
+    G = cplx(fq.fq_casorati_gram(cdev(S)))
+    want = oracle.gram(S)
+    assert np.abs(G - want).max() <= 1e-5 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("P,F,k", [(2000, 48, 3), (3000, 200, 2), (64, 8, 1), (50, 3, 1)])
+def test_eig_against_oracle_svd(P, F, k):
+    S = _clutter(P, F, k, seed=F).astype(np.complex64).astype(np.complex128)
+    G64 = oracle.gram(S)
+    lam, V, ws = fq.fq_hermitian_eig(cdev(G64))
+    fq.fq_clutter_status(ws)
+    lam, V = host(lam), cplx(V)
+    _, Vo, sg = oracle.svd(S)
+    lmax = sg[0] ** 2
+    assert np.abs(lam - sg ** 2).max() <= 2e-6 * lmax
+    assert np.all(np.diff(lam) <= 0)
+    assert np.abs(V.conj().T @ V - np.eye(F)).max() <= 1e-5
+    assert np.abs(G64 @ V - V * lam).max() <= 2e-6 * lmax
+    Pk = V[:, :k] @ V[:, :k].conj().T
+    Po = Vo[:, :k] @ Vo[:, :k].conj().T
+    assert np.abs(Pk - Po).max() <= 1e-5
+
+
+def test_eig_degenerate_inputs():
+    """rank-deficient (P < F) and a zero matrix: eigenvalues still match and
+    the eigenvectors stay orthonormal."""
+    rng = np.random.default_rng(3)
+    S = (rng.standard_normal((5, 24)) + 1j * rng.standard_normal((5, 24))).astype(np.complex64).astype(np.complex128)
+    G = oracle.gram(S)
+    lam, V, ws = fq.fq_hermitian_eig(cdev(G))
+    fq.fq_clutter_status(ws)
+    lam, V = host(lam), cplx(V)
+    want = np.sort(np.concatenate([np.linalg.svd(S, compute_uv=False) ** 2, np.zeros(19)]))[::-1]
+    assert np.abs(lam - want).max() <= 2e-6 * want[0]
+    assert np.abs(V.conj().T @ V - np.eye(24)).max() <= 1e-5
+    lam, V, ws = fq.fq_hermitian_eig(cdev(np.zeros((6, 6), complex)))
+    fq.fq_clutter_status(ws)
+    assert not host(lam).any()
+    assert np.abs(cplx(V).conj().T @ cplx(V) - np.eye(6)).max() <= 1e-6
+
+
+@pytest.mark.parametrize("k_cut", [3, 0, -1, 32])
+def test_clutter_svd_parity(k_cut):
+    S = _clutter(4096, 32, 3, seed=11).astype(np.complex64).astype(np.complex128)
+    r = fq.fq_clutter_svd(cdev(S), k_cut=k_cut, energy_thresh=0.9)
+    fq.fq_clutter_status(r["ws"])
+    S_f, pd, sg, k = oracle.svd_filter(S, k_cut=k_cut, energy_thresh=0.9)
+    assert int(host(r["k"])[0]) == k
+    assert np.abs(host(r["eigvals"]) - sg ** 2).max() <= 2e-6 * sg[0] ** 2
+    if k == 32:
+        assert not host(r["pd"]).any() and not host(r["iq_f"]).any()
+        return
+    assert rel_l2(host(r["pd"]), pd) <= PD_TOL
+    got = cplx(r["iq_f"])
+    assert rel_l2(np.stack([got.real, got.imag]), np.stack([S_f.real, S_f.imag])) <= PD_TOL
+
+
+def test_clutter_svd_bf16_input():
+    S = _clutter(2048, 32, 2, seed=5).astype(np.complex64).astype(np.complex128)
+    Sb = cdev(S).bfloat16()
+    Sq = cplx(Sb)  # the BF16-rounded input both sides see
+    r = fq.fq_clutter_svd(Sb, k_cut=2)
+    _, pd, _, _ = oracle.svd_filter(Sq, k_cut=2)
+    assert rel_l2(host(r["pd"]), pd) <= BF16_TOL
+
+
+def test_power_doppler_parity():
+    rng = np.random.default_rng(1)
+    S = rng.standard_normal((5000, 37)) + 1j * rng.standard_normal((5000, 37))
+    S = S.astype(np.complex64).astype(np.complex128)
+    pd = host(fq.fq_power_doppler(cdev(S)))
+    assert rel_l2(pd, oracle.power_doppler(S)) <= 1e-6

@@ -1,0 +1,116 @@
+"""The whole hot path end to end on the GPU against the oracle, and checks
+at the full size of the 2D compounded workload (the benchmark's launch
+configuration) on sampled outputs and on properties that hold at any size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_05464_gb300 import build as fqbuild
+from paper_2509_05464_gb300 import fq
+from paper_2509_05464_gb300 import workload as W
+from paper_2509_05464_gb300.pipeline import Pipeline
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    fqbuild.build()
+    fq.lib()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_pipeline_c1_end_to_end():
+    """2D plain method (static tissue, Alg. 1 reuse): power Doppler within
+    1e-3 of the oracle.  Advected positions agree to <= 1 ulp, so RF and IQ
+    stay at the 1e-5 level and the SVD step sets the error."""
+    w = W.config1()
+    st, mt = W.segment_table(w), W.motion_table(w.motion)
+    pl = Pipeline(w, keep_iq_f=True)
+    pd = pl.step_e2e().numpy().copy()
+    torch.cuda.synchronize()
+    fq.fq_clutter_status(pl.ws_svd)
+    ref = oracle.pipeline(w, st, mt)
+    iq = pl.iq.cpu().numpy()
+    S = iq[..., 0] + 1j * iq[..., 1]
+    assert rel_l2(np.stack([S.real, S.imag]), np.stack([ref["S"].real, ref["S"].imag])) <= 1e-4
+    assert int(pl.k_used.item()) == ref["k"] == 2
+    assert rel_l2(pd, ref["pd"]) <= 1e-3
+
+
+def test_pipeline_c3_small_end_to_end():
+    """3D volumetric shape (matrix probe, 9 tilts, vessel tree, rigid +
+    elastic motion, energy cutoff) on a reduced size."""
+    w = W.shrink(W.config3(n_scat=60_000, n_frames=6), max_scat=400, grid_div=8)
+    st, mt = W.segment_table(w), W.motion_table(w.motion)
+    pl = Pipeline(w)
+    pd = pl.step_e2e().numpy().copy()
+    ref = oracle.pipeline(w, st, mt)
+    assert int(pl.k_used.item()) == ref["k"]
+    assert rel_l2(pd, ref["pd"]) <= 1e-3
+
+
+@pytest.fixture(scope="module")
+def c2_full():
+    w = W.config2()
+    pl = Pipeline(w)
+    pl.upload()
+    pl.step()
+    torch.cuda.synchronize()
+    return w, pl
+
+
+def test_c2_full_rf_sampled(c2_full):
+    """Full 2D compounded workload: RF of frames 0 and 137, middle transmit,
+    every element, against the oracle on the same scatterers."""
+    w, pl = c2_full
+    st, mt = W.segment_table(w), W.motion_table(w.motion)
+    _, amp_eff = oracle.classify(w.p0, w.seg, st, len(w.segments), w.amp)
+    assert np.array_equal(pl.pops[0].amp_eff.cpu().numpy(), amp_eff)
+    for f in (0, 137):
+        pos = oracle.advect(w.p0, w.seg, w.flow, st, mt, f / w.prf)
+        want = oracle.simulate_rf(w.probe, w.tilt_x[2:3], w.tilt_y[2:3], pos, amp_eff)[0]
+        got = pl.rf[f, 2].cpu().numpy()
+        assert rel_l2(got, want) <= 1e-5
+
+
+def test_c2_full_das_sampled():
+    """Full 2D compounded geometry (128 elements, 5 angles, 256x256 grid) on
+    two frames of oracle RF: every 16th pixel row against the oracle."""
+    w = W.config2(n_frames=2)
+    st, mt = W.segment_table(w), W.motion_table(w.motion)
+    _, amp_eff = oracle.classify(w.p0, w.seg, st, len(w.segments), w.amp)
+    rf = np.stack([oracle.simulate_rf(w.probe, w.tilt_x, w.tilt_y,
+                                      oracle.advect(w.p0, w.seg, w.flow, st, mt, f / w.prf), amp_eff)
+                   for f in range(2)]).astype(np.float32)
+    iq = fq.fq_beamform_das(w.probe, w.tilt_x, w.tilt_y, torch.from_numpy(rf).cuda(), 2, w.grid).cpu().numpy()
+    g = w.grid
+    sub = W.Grid(g.nx, 1, g.nz // 16, g.x0, 0.0, g.z0, g.dx, 0.0, g.dz * 16, g.fnumber)
+    want = oracle.beamform(w.probe, w.tilt_x, w.tilt_y, rf, sub)
+    got = iq.reshape(g.nz, g.nx, 2, 2)[::16].reshape(-1, 2, 2)
+    got = got[..., 0] + 1j * got[..., 1]
+    assert rel_l2(np.stack([got.real, got.imag]), np.stack([want.real, want.imag])) <= 1e-5
+
+
+def test_c2_full_clutter_properties(c2_full):
+    """Properties of the full-size SVD filter: eigenvalues sum to ||S||_F^2,
+    PD >= 0, and sum_p PD_p = (1/F) sum_{j >= k} lambda_j."""
+    w, pl = c2_full
+    fq.fq_clutter_status(pl.ws_svd)
+    iq = pl.iq.double()
+    tot = float((iq ** 2).sum())
+    lam = pl.eigvals.cpu().numpy()
+    k = int(pl.k_used.item())
+    pd = pl.pd.double().cpu().numpy()
+    assert abs(lam.sum() - tot) <= 1e-4 * tot
+    assert np.all(np.diff(lam) <= 1e-6 * lam[0])
+    assert pd.min() >= 0
+    assert k == 2
+    want = lam[k:].sum() / w.n_frames
+    assert abs(pd.sum() - want) <= 1e-3 * want + 1e-6 * lam[0] / w.n_frames
