@@ -197,7 +197,7 @@ def run_ours(args, rank, world, local):
 
     torch.cuda.set_device(local)
     fq.lib()
-    w = W.config2(seed=2 + rank)  # an independent ensemble per rank (weak scaling)
+    w = W.config2(seed=2 + rank, n_frames=args.frames)  # an independent ensemble per rank (weak scaling)
     pl = Pipeline(w)
     pl.upload()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -210,28 +210,23 @@ def run_ours(args, rank, world, local):
 
     clk = ClockSampler(local)
     clk.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    rf_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stages = ("classify", "advect", "simulate", "beamform", "clutter")
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
     for i in range(args.steps):
         flush.zero_()  # L2 flush outside the timed events
         ev[i][0].record(stream)
-        pl.classify()
-        pl.advect()
-        rf_ev[i][0].record(stream)
-        pl.simulate()
-        rf_ev[i][1].record(stream)
-        pl.beamform()
-        pl.clutter()
-        ev[i][1].record(stream)
+        for j, name in enumerate(stages):
+            getattr(pl, name)()
+            ev[i][j + 1].record(stream)
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    rf_ms = [a.elapsed_time(b) for a, b in rf_ev]
+    step_ms = [e[0].elapsed_time(e[-1]) for e in ev]
+    stage_ms = {name: sum(e[j].elapsed_time(e[j + 1]) for e in ev) / args.steps for j, name in enumerate(stages)}
     ms = max_over_ranks(sum(step_ms) / len(step_ms))
-    rf_avg = sum(rf_ms) / len(rf_ms)
+    rf_avg = stage_ms["simulate"]
 
     # end to end through the public API (pinned host in, PD out)
     e2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -265,7 +260,7 @@ def run_ours(args, rank, world, local):
                    "scatterers": w.S, "pixels": w.P, "parallelism": f"independent ensemble per GPU x{world}",
                    "l2": "256 MiB buffer rewritten between timed steps, outside the timed events"},
         "das_voxel_angle_per_s": total_va / (ms * 1e-3),
-        "kernel_ms": {"rf_synth": rf_avg, "step": ms},
+        "stage_ms": stage_ms,
         "roofline": {"bound": "alu", "kernel": "rf_synth_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_for_peak:.0f} MHz ({src} max clock)",
@@ -287,6 +282,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
     rank, world, local = dist_init(args)

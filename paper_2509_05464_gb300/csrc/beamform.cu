@@ -42,8 +42,9 @@ __global__ void __launch_bounds__(256) rf2iq_kernel(const Rf2iqParams p, const I
     const int k0 = blockIdx.x * kRfTile;
     const int f0 = blockIdx.z * kFrameChunk;
     const int J = p.J;
-    const int W = kRfTile + 2 * J;
-    float2 *rot = mix + kFrameChunk * W;  // [W]: exp(-i 2 pi f0 n / fs)
+    const int W = kRfTile + 2 * J;      // window samples
+    const int WS = W | 1;               // odd row stride: the 16 frame rows fall in distinct banks
+    float2 *rot = mix + kFrameChunk * WS;  // [W]: exp(-i 2 pi f0 n / fs)
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         int n = k0 - J + i;
         // fractional carrier cycles (f0/fs) n in float-float, then sincospi
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256) rf2iq_kernel(const Rf2iqParams p, const I
         float v = 0.0f;
         if (n >= 0 && n < p.ns && f < p.F) v = fqi::load_f(rf, ((int64_t)f * p.L + l) * p.ns + n);
         float2 r = rot[w];
-        mix[i] = make_float2(v * r.x, v * r.y);
+        mix[fl * WS + w] = make_float2(v * r.x, v * r.y);
     }
     __syncthreads();
     // thread -> (frame fl = t % 16, sample kk = t / 16 + 16 q)
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(256) rf2iq_kernel(const Rf2iqParams p, const I
         if (k >= p.ns) break;
         // IQ[k] = 2 sum_{j=-J..J} h_j mix[k - j]; sample n sits at window index n - (k0 - J),
         // so sample k - j is at kk + J - j
-        const float2 *src = mix + fl * W + kk + J;
+        const float2 *src = mix + fl * WS + kk + J;
         float re = 0.0f, im = 0.0f;
         for (int j = -J; j <= J; ++j) {
             float2 m = src[-j];
@@ -113,7 +114,7 @@ template <typename InT, typename OutT>
 fq_status launch_rf2iq(const Rf2iqParams &p, const void *rf, void *iq, cudaStream_t st)
 {
     int W = kRfTile + 2 * p.J;
-    size_t smem = sizeof(float2) * (size_t)(kFrameChunk + 1) * W;
+    size_t smem = sizeof(float2) * ((size_t)kFrameChunk * (W | 1) + W);
     dim3 grid((p.ns + kRfTile - 1) / kRfTile, p.L, p.Fp / kFrameChunk);
     rf2iq_kernel<InT, OutT><<<grid, 256, smem, st>>>(p, (const InT *)rf, (OutT *)iq);
     return fqi::launch_check("fq_rf2iq");

@@ -179,12 +179,33 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const float2 *__restri
     __shared__ float d[512], e[512], rc[512], rs[512];
     __shared__ float2 ec[512], vv[512], pv[512], delta[512];
     __shared__ int perm[512];
-    __shared__ float s_tau;
+    __shared__ float s_tau, s_scale;
     __shared__ int s_m, s_nrot, s_done, s_fail;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
 
+    // scale to max |G_ij| <= 1 (eigenvectors unchanged, eigenvalues rescaled at the end)
+    float amax = 0.0f;
     for (int i = wid; i < F; i += nw)
-        for (int j = lane; j <= i; j += 32) Ap[pidx(i, j)] = G[(size_t)i * F + j];
+        for (int j = lane; j <= i; j += 32) {
+            float2 g = G[(size_t)i * F + j];
+            amax = fmaxf(amax, fmaxf(fabsf(g.x), fabsf(g.y)));
+        }
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) red[wid] = amax;
+    __syncthreads();
+    if (tid == 0) {
+        float mx = 0.0f;
+        for (int w = 0; w < nw; ++w) mx = fmaxf(mx, red[w]);
+        // a power of two, so that the scaling itself is exact
+        s_scale = mx > 0.0f ? exp2f(ceilf(log2f(mx))) : 1.0f;
+    }
+    __syncthreads();
+    const float gscale = s_scale, ginv = 1.0f / s_scale;
+    for (int i = wid; i < F; i += nw)
+        for (int j = lane; j <= i; j += 32) {
+            float2 g = G[(size_t)i * F + j];
+            Ap[pidx(i, j)] = make_float2(g.x * ginv, g.y * ginv);
+        }
     __syncthreads();
 
     // ---- tridiagonalisation
@@ -308,23 +329,30 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const float2 *__restri
                         s_done = 1;
                     } else {
                         float g = (d[l + 1] - d[l]) / (2.0f * e[l]);
-                        float r = hypotf(g, 1.0f);
+                        float r = sqrtf(fmaf(g, g, 1.0f));
                         g = d[m] - d[l] + e[l] / (g + copysignf(r, g));
                         float s = 1.0f, c = 1.0f, p = 0.0f;
                         bool early = false;
                         int nrot = 0;
                         for (int i = m - 1; i >= l; --i) {
                             float f = s * e[i], b = c * e[i];
-                            r = hypotf(f, g);
-                            e[i + 1] = r;
-                            if (r == 0.0f) {
+                            // r = |(f, g)| and 1/r from one reciprocal square root plus a
+                            // Newton step (the matrix is scaled to max |entry| = 1, so no
+                            // overflow is possible)
+                            const float q = fmaf(f, f, g * g);
+                            if (q == 0.0f) {
+                                e[i + 1] = 0.0f;
                                 d[i + 1] -= p;
                                 e[m] = 0.0f;
                                 early = true;
                                 break;
                             }
-                            s = f / r;
-                            c = g / r;
+                            float rr = rsqrtf(q);
+                            rr = rr * fmaf(-0.5f * q * rr, rr, 1.5f);
+                            r = q * rr;
+                            e[i + 1] = r;
+                            s = f * rr;
+                            c = g * rr;
                             g = d[i + 1] - p;
                             r = (d[i] - g) * s + 2.0f * c * b;
                             p = s * r;
@@ -380,7 +408,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const float2 *__restri
         perm[rank] = i;
     }
     __syncthreads();
-    for (int j = tid; j < F; j += blockDim.x) lam_out[j] = (double)d[perm[j]];
+    for (int j = tid; j < F; j += blockDim.x) lam_out[j] = (double)d[perm[j]] * (double)gscale;
     if (tid == 0) {
         int k = k_cut;
         if (k < 0) {

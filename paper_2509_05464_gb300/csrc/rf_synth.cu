@@ -4,21 +4,23 @@
 // Design (GB300): one CTA owns the complete RF record of E consecutive
 // receive elements for one (frame, transmit) pair and keeps it in shared
 // memory (E x Ns FP32).  Its threads stream every scatterer of the frame
-// once (coalesced structure-of-arrays loads, each thread one scatterer), and
-// for each of the E elements evaluate the delay, amplitude and the few
-// pulse taps that land in the record, accumulating them into the shared
-// record with shared-memory atomics.  Nothing is atomically added in global
-// memory: the record is written out once, coalesced, after the last
-// scatterer.  The per-scatterer transmit path and its loads are shared by
-// the E elements.
+// once (coalesced structure-of-arrays loads, one scatterer per thread), and
+// for each of the E elements evaluate the delay, amplitude and the pulse
+// taps that land in the record, adding them to the shared record with
+// shared-memory atomics.  Nothing is atomically added in global memory: the
+// record is written out once, coalesced, after the last scatterer.  The
+// per-scatterer transmit path and the position loads are shared by the E
+// elements.
 //
 // Precision: the delay u = tau fs (hundreds to thousands of samples) must
 // be known to ~1e-6 sample for the carrier phase, so the geometry
 // (distance, transmit path, u) runs in float-float; the pulse itself is
-// evaluated at the small offset j - frac(u), where binary32 suffices.  The
-// pulse taps come from two complex rotors (carrier and Hann window) advanced
-// by a fixed angle per sample.
+// evaluated at the small offset j - frac(u), where binary32 suffices: the
+// taps' Hann-phase cosines follow the Chebyshev recurrence
+// C_{j+1} = 2 cos(w) C_j - C_{j-1} from the first tap, and for the
+// two-cycle pulse the carrier is cos(2 theta) = 2 C^2 - 1 of the Hann phase.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "fq_internal.cuh"
@@ -27,6 +29,8 @@ namespace {
 
 using fqi::ff;
 
+constexpr int kMaxTaps = 64;  // pulse taps per (scatterer, element) pair the kernel supports
+
 struct RfParams {
     fqi::ProbeFF pr;
     int A;
@@ -34,22 +38,54 @@ struct RfParams {
     float kbx, kby;     // k0 * width / 2
     float att;          // attenuation per metre of two-way path (Np / m)
     float half_w;       // pulse half-support in samples: n_cycles fs / (2 f0)
-    float w_c, w_h;     // carrier / Hann phase per sample (rad)
-    float cwc, swc, cwh, swh;  // rotor steps
-    int ntap;           // taps that can overlap the support
+    float w_h;          // Hann phase per sample (rad): 2 pi f0 / (n_cycles fs)
+    float w_c;          // carrier phase per sample (rad): 2 pi f0 / fs
+    float two_cos_h, two_cos_c;  // Chebyshev recurrence factors 2 cos(w)
+    float cos_h, sin_h, cos_c, sin_c;
+    int jmin;           // smallest first-tap offset ceil(frac - half_w) over frac in [0, 1)
+    int ntap_max;       // floor(2 half_w) + 1
+    float tab_h[2][2];  // (cos, sin)(w_h * j) for j = jmin, jmin + 1
+    float tab_c[2][2];  // (cos, sin)(w_c * j) for j = jmin, jmin + 1
+    int two_cycle;      // n_cycles == 2: carrier = 2 C^2 - 1 of the Hann phase
     fqi::AngleFF ang[FQ_MAX_ANGLES];
 };
 
+constexpr float kPi = 3.14159265358979f;
+
+// sin(u) / u for |u| < 2 pi: one conditional turn brings the argument into
+// [-pi, pi] where the hardware sine is accurate to ~4e-7 absolute.
 __device__ __forceinline__ float sinc_f(float u)
 {
-    return fabsf(u) < 1e-4f ? 1.0f - u * u * (1.0f / 6.0f) : sinf(u) / u;
+    float v = u;
+    if (v > kPi) v -= 2.0f * kPi;
+    if (v < -kPi) v += 2.0f * kPi;
+    return fabsf(u) < 1e-3f ? fmaf(-u * u, 1.0f / 6.0f, 1.0f) : __fdividef(__sinf(v), u);
+}
+
+// (cos, sin) of w * (jlo - frac) as exp(i w jlo) exp(-i w frac): the
+// hardware sincos only ever sees |w frac| < w
+__device__ __forceinline__ void first_tap(float w, float frac, float tc0, float ts0, float tc1, float ts1, bool sel1,
+                                          float &c, float &s)
+{
+    float sf, cf;
+    __sincosf(w * frac, &sf, &cf);
+    const float tc = sel1 ? tc1 : tc0, ts = sel1 ? ts1 : ts0;
+    c = fmaf(cf, tc, sf * ts);
+    s = fmaf(ts, cf, -tc * sf);
+}
+
+// one pulse tap of the two-cycle pulse from the Hann-phase cosine C:
+// A (1 + C)/2 (2 C^2 - 1) = ((A C + A) C - A/2) C - A/2
+__device__ __forceinline__ float tap2(float A, float hA, float C)
+{
+    return fmaf(fmaf(fmaf(A, C, A), C, -hA), C, -hA);
 }
 
 template <int E, int NT, typename OutT>
-__global__ void __launch_bounds__(NT) rf_synth_kernel(const RfParams p, const float *__restrict__ pos,
-                                                      const float *__restrict__ amp,
-                                                      const float *__restrict__ rf_base,
-                                                      OutT *__restrict__ rf)
+__global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const float *__restrict__ pos,
+                                                         const float *__restrict__ amp,
+                                                         const float *__restrict__ rf_base,
+                                                         OutT *__restrict__ rf)
 {
     extern __shared__ float tile[];  // [E][Ns]
     __shared__ float ex_hi[E], ex_lo[E], ey_hi[E], ey_lo[E];
@@ -80,60 +116,118 @@ __global__ void __launch_bounds__(NT) rf_synth_kernel(const RfParams p, const fl
     const fqi::AngleFF an = p.ang[a];
     const ff ux = fqi::ff_load(an.ux), uy = fqi::ff_load(an.uy), uz = fqi::ff_load(an.uz);
     const ff org = fqi::ff_load(an.origin);
-    const ff fs_c = fqi::ff_load(p.pr.fs_over_c);
+    const float Kh = p.pr.fs_over_c.hi, Kl = p.pr.fs_over_c.lo;
     const bool matrix = p.pr.ny > 1;
     const int64_t S = p.S;
     const float *X = pos + (int64_t)f * 3 * S;
     const float *Y = X + S;
     const float *Z = Y + S;
+    const float half_w = p.half_w;
+    const int ntap_max = p.ntap_max;
+    const bool fast8 = p.two_cycle && ntap_max <= 9;  // the common pulse: at most 9 taps
+    const float thc0 = p.tab_h[0][0], ths0 = p.tab_h[0][1], thc1 = p.tab_h[1][0], ths1 = p.tab_h[1][1];
 
     for (int64_t s = threadIdx.x; s < S; s += NT) {
         const float R = amp[s];
         if (R == 0.0f) continue;
         const float x = X[s], y = Y[s], z = Z[s];
-        // transmit path u . r - min u . e (float-float)
+        // transmit path u . r - min u . e, float-float (once per scatterer)
         ff ptx = fqi::ff_add(fqi::ff_mul_f(ux, x), fqi::ff_mul_f(uy, y));
         ptx = fqi::ff_add(ptx, fqi::ff_mul_f(uz, z));
         ptx = fqi::ff_add(ptx, fqi::ff_neg(org));
         const ff zz = fqi::ff_two_prod(z, z);
+        const bool use_y = matrix || y != 0.0f;  // 2D workloads keep every scatterer at y = 0
 #pragma unroll 1
         for (int e = 0; e < ne; ++e) {
-            ff dx = fqi::ff_add_f(ff{-ex_hi[e], -ex_lo[e]}, x);
-            ff r2 = fqi::ff_add(fqi::ff_sqr(dx), zz);
-            ff dy = {0.0f, 0.0f};
-            if (matrix || y != 0.0f) {  // 2D workloads keep every scatterer at y = 0
-                dy = fqi::ff_add_f(ff{-ey_hi[e], -ey_lo[e]}, y);
-                r2 = fqi::ff_add(r2, fqi::ff_sqr(dy));
+            // dx = x - ex as an unnormalised pair (TwoSum of x and -ex_hi, plus -ex_lo)
+            const float exh = ex_hi[e];
+            const float dxh = __fsub_rn(x, exh);
+            const float bb = __fsub_rn(dxh, x);
+            const float dxl = __fsub_rn(__fadd_rn(__fsub_rn(x, __fsub_rn(dxh, bb)), __fsub_rn(-exh, bb)), ex_lo[e]);
+            // r^2 = dx^2 + z^2 (+ dy^2)
+            const float p2 = __fmul_rn(dxh, dxh);
+            float lo = __fmaf_rn(2.0f * dxh, dxl, __fmaf_rn(dxh, dxh, -p2));
+            ff r2 = fqi::ff_two_sum(p2, zz.hi);
+            lo = __fadd_rn(lo, zz.lo);
+            float dyh = 0.0f;
+            if (use_y) {
+                const float eyh = ey_hi[e];
+                dyh = __fsub_rn(y, eyh);
+                const float cc = __fsub_rn(dyh, y);
+                const float dyl = __fsub_rn(__fadd_rn(__fsub_rn(y, __fsub_rn(dyh, cc)), __fsub_rn(-eyh, cc)), ey_lo[e]);
+                const float q2 = __fmul_rn(dyh, dyh);
+                lo = __fadd_rn(lo, __fmaf_rn(2.0f * dyh, dyl, __fmaf_rn(dyh, dyh, -q2)));
+                ff t2 = fqi::ff_two_sum(r2.hi, q2);
+                r2.hi = t2.hi;
+                lo = __fadd_rn(lo, t2.lo);
             }
+            lo = __fadd_rn(lo, r2.lo);
+            r2 = fqi::ff_fast_two_sum(r2.hi, lo);
             if (r2.hi <= 0.0f) continue;
-            const ff r = fqi::ff_sqrt(r2);
-            const ff path = fqi::ff_add(ptx, r);
-            const ff u = fqi::ff_mul(path, fs_c);
-            int k0;
-            float frac;
-            fqi::ff_floor_frac(u, k0, frac);
-            const float inv_r = 1.0f / r.hi;
-            float D = sinc_f(p.kbx * dx.hi * inv_r);
-            if (matrix) D *= sinc_f(p.kby * dy.hi * inv_r);
-            const float Aa = R * D * __expf(-p.att * path.hi) * inv_r;
-            const int jlo = (int)ceilf(frac - p.half_w);
-            const float t0 = (float)jlo - frac;
-            float sc, cc, sh, ch;
-            sincosf(p.w_c * t0, &sc, &cc);
-            sincosf(p.w_h * t0, &sh, &ch);
-            float *line = tile + e * ns;
-            int k = k0 + jlo;
-#pragma unroll 4
-            for (int j = 0; j < p.ntap; ++j, ++k) {
-                const float t = t0 + (float)j;
-                if (fabsf(t) < p.half_w && k >= 0 && k < ns)
-                    atomicAdd(line + k, Aa * (0.5f + 0.5f * ch) * cc);
-                float nc = cc * p.cwc - sc * p.swc;
-                sc = sc * p.cwc + cc * p.swc;
-                cc = nc;
-                float nh = ch * p.cwh - sh * p.swh;
-                sh = sh * p.cwh + ch * p.swh;
-                ch = nh;
+            // r = sqrt(r^2) and 1/r from one reciprocal square root, plus a
+            // Newton correction to float-float accuracy
+            const float rs = rsqrtf(r2.hi);
+            const float r0 = __fmul_rn(r2.hi, rs);
+            const float rl = __fmul_rn(__fadd_rn(__fmaf_rn(-r0, r0, r2.hi), r2.lo), 0.5f * rs);
+            // path = ptx + r, u = path * fs / c = k0 + frac
+            ff path = fqi::ff_two_sum(ptx.hi, r0);
+            path.lo = __fadd_rn(path.lo, __fadd_rn(ptx.lo, rl));
+            const float uh = __fmul_rn(path.hi, Kh);
+            const float ul = __fmaf_rn(path.hi, Kl, __fmaf_rn(path.lo, Kh, __fmaf_rn(path.hi, Kh, -uh)));
+            float fl = floorf(uh);
+            float frac = __fadd_rn(__fsub_rn(uh, fl), ul);
+            if (frac < 0.0f) { frac += 1.0f; fl -= 1.0f; }
+            else if (frac >= 1.0f) { frac -= 1.0f; fl += 1.0f; }
+            // amplitude: reflectivity x directivity x attenuation / r
+            float D = sinc_f(p.kbx * dxh * rs);
+            if (matrix) D *= sinc_f(p.kby * dyh * rs);
+            const float Aa = R * D * __expf(-p.att * path.hi) * rs;
+            // taps j = jlo .. jlo + ntap - 1 with |j - frac| < half_w
+            const int jlo = (int)ceilf(frac - half_w);
+            const int ntap = (int)floorf(frac + half_w) - jlo + 1;
+            const int kst = (int)fl + jlo;
+            float ch, sh;
+            first_tap(p.w_h, frac, thc0, ths0, thc1, ths1, jlo != p.jmin, ch, sh);
+            float *line = tile + e * ns + kst;
+            const bool inside = kst >= 0 && kst + ntap <= ns;
+            if (fast8 && inside) {
+                // C_j = cos(w_h (jlo + j - frac)) by the Chebyshev recurrence
+                const float hA = 0.5f * Aa;
+                float c0 = ch, c1 = fmaf(ch, p.cos_h, -sh * p.sin_h);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    atomicAdd(line + j, tap2(Aa, hA, c0));
+                    const float c2 = fmaf(p.two_cos_h, c1, -c0);
+                    c0 = c1;
+                    c1 = c2;
+                }
+                if (ntap > 8) atomicAdd(line + 8, tap2(Aa, hA, c0));
+            } else if (p.two_cycle) {
+                const float hA = 0.5f * Aa;
+                float c0 = ch, c1 = fmaf(ch, p.cos_h, -sh * p.sin_h);
+                for (int j = 0; j < ntap; ++j) {
+                    const int k = kst + j;
+                    if (k >= 0 && k < ns) atomicAdd(line + j, tap2(Aa, hA, c0));
+                    const float c2 = fmaf(p.two_cos_h, c1, -c0);
+                    c0 = c1;
+                    c1 = c2;
+                }
+            } else {
+                float cc, sc;
+                first_tap(p.w_c, frac, p.tab_c[0][0], p.tab_c[0][1], p.tab_c[1][0], p.tab_c[1][1], jlo != p.jmin, cc,
+                          sc);
+                float h0 = ch, h1 = fmaf(ch, p.cos_h, -sh * p.sin_h);
+                float q0 = cc, q1 = fmaf(cc, p.cos_c, -sc * p.sin_c);
+                for (int j = 0; j < ntap; ++j) {
+                    const int k = kst + j;
+                    if (k >= 0 && k < ns) atomicAdd(line + j, Aa * fmaf(0.5f, h0, 0.5f) * q0);
+                    const float h2 = fmaf(p.two_cos_h, h1, -h0);
+                    h0 = h1;
+                    h1 = h2;
+                    const float q2 = fmaf(p.two_cos_c, q1, -q0);
+                    q0 = q1;
+                    q1 = q2;
+                }
             }
         }
     }
@@ -157,15 +251,35 @@ fq_status launch_rf(const RfParams &p, int F, const float *pos, const float *amp
     return fqi::launch_check("fq_simulate_rf");
 }
 
+// Elements per CTA (4 unless the record is too long); FQ_RF_ELEMS (4, 8 or
+// 16) overrides it for tuning.
+int rf_elems(int ns)
+{
+    static int forced = -1;
+    if (forced < 0) {
+        const char *env = std::getenv("FQ_RF_ELEMS");
+        int v = env ? std::atoi(env) : 0;
+        forced = (v == 4 || v == 8 || v == 16) ? v : 0;
+    }
+    const size_t line = sizeof(float) * (size_t)ns;
+    if (forced && forced * line <= 200 * 1024) return forced;
+    // 4 elements keep the tile small enough for 6+ CTAs (48 warps) per SM,
+    // which hides the shared-atomic latency better than more reuse of the
+    // per-scatterer work (measured on the 2D compounded workload)
+    if (4 * line <= 200 * 1024) return 4;
+    return 2;
+}
+
 template <typename OutT>
 fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *amp, const float *base,
                       OutT *rf, cudaStream_t st)
 {
-    const size_t line = sizeof(float) * (size_t)p.pr.ns;
-    const size_t budget = 200 * 1024;
-    if (8 * line <= budget) return launch_rf<8>(p, F, pos, amp, base, rf, st);
-    if (4 * line <= budget) return launch_rf<4>(p, F, pos, amp, base, rf, st);
-    return launch_rf<2>(p, F, pos, amp, base, rf, st);
+    switch (rf_elems(p.pr.ns)) {
+    case 16: return launch_rf<16>(p, F, pos, amp, base, rf, st);
+    case 8: return launch_rf<8>(p, F, pos, amp, base, rf, st);
+    case 4: return launch_rf<4>(p, F, pos, amp, base, rf, st);
+    default: return launch_rf<2>(p, F, pos, amp, base, rf, st);
+    }
 }
 
 }  // namespace
@@ -201,15 +315,28 @@ extern "C" fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, cons
     p.att = (float)(probe->alpha_db_cm_mhz * 100.0 / (20.0 / std::log(10.0)) * probe->f0 * 1e-6);
     const double hw = probe->n_cycles * probe->fs / (2.0 * probe->f0);
     p.half_w = (float)hw;
-    p.ntap = (int)std::floor(2.0 * hw) + 1;
+    p.ntap_max = (int)std::floor(2.0 * hw) + 1;
+    FQ_REQUIRE(p.ntap_max <= kMaxTaps, FQ_ERR_SHAPE,
+               "fq_simulate_rf: n_cycles * fs / f0 must be below %d samples", kMaxTaps - 1);
     const double wc = 2.0 * M_PI * probe->f0 / probe->fs;
     const double wh = wc / probe->n_cycles;
     p.w_c = (float)wc;
     p.w_h = (float)wh;
-    p.cwc = (float)std::cos(wc);
-    p.swc = (float)std::sin(wc);
-    p.cwh = (float)std::cos(wh);
-    p.swh = (float)std::sin(wh);
+    p.jmin = (int)std::ceil(0.0 - hw);  // frac in [0, 1): jlo in {jmin, jmin + 1}
+    for (int q = 0; q < 2; ++q) {
+        double j = p.jmin + q;
+        p.tab_h[q][0] = (float)std::cos(wh * j);
+        p.tab_h[q][1] = (float)std::sin(wh * j);
+        p.tab_c[q][0] = (float)std::cos(wc * j);
+        p.tab_c[q][1] = (float)std::sin(wc * j);
+    }
+    p.cos_h = (float)std::cos(wh);
+    p.sin_h = (float)std::sin(wh);
+    p.cos_c = (float)std::cos(wc);
+    p.sin_c = (float)std::sin(wc);
+    p.two_cos_h = (float)(2.0 * std::cos(wh));
+    p.two_cos_c = (float)(2.0 * std::cos(wc));
+    p.two_cycle = probe->n_cycles == 2;
     fqi::make_angles_ff(probe, tx, p.ang);
     cudaStream_t st = (cudaStream_t)stream;
     if (out_dtype == FQ_F32) return dispatch_rf(p, n_frames, pos, amp, rf_base, (float *)rf, st);

@@ -72,7 +72,9 @@ class Pipeline:
             p.upload()
 
     def download(self):
+        """Copy the power Doppler image to pinned host memory and wait for it."""
         self.h_pd.copy_(self.pd, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
         return self.h_pd
 
     # the steps --------------------------------------------------------------
