@@ -198,6 +198,8 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     fq.lib()
     w = W.config2(seed=2 + rank, n_frames=args.frames)  # an independent ensemble per rank (weak scaling)
+    if args.scatterers or args.grid_div:  # reduced cases for profiler captures only
+        w = W.shrink(w, max_scat=args.scatterers or None, grid_div=args.grid_div or None)
     pl = Pipeline(w)
     pl.upload()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -283,6 +285,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
+    ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
+    ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
     rank, world, local = dist_init(args)
