@@ -315,6 +315,34 @@ fq_status fq_clutter_svd(const void *iq, int32_t dtype, int64_t P, int32_t F, in
                          double *eigvals, int32_t *k_used, void *workspace,
                          size_t workspace_bytes, void *stream);
 
+/* No-allocation variant of fq_clutter_svd.  The paper has no counterpart:
+ * it serves callers that cannot hand the library a workspace.  Some hosts
+ * cannot call cudaMalloc, or create device buffers, at the point where they
+ * filter an ensemble: their device memory belongs to an allocator they
+ * cannot reach (for instance a framework's caching allocator seen through a
+ * plugin interface), or their acquisition loop forbids device allocation
+ * after start-up.  This call takes all its scratch from one array built
+ * into the library instead, and allocates nothing itself (no cudaMalloc,
+ * no cudaFree, no library routine that allocates).
+ *   - The array holds 12 MiB of device memory on every GPU that loads the
+ *     library, until the process exits.
+ *   - Limit: F <= 256 frames (any P).  Larger F returns FQ_ERR_SHAPE with
+ *     a message; use fq_clutter_svd with a workspace instead.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind: calls
+ *     whose work overlaps on the GPU (unordered streams, or several host
+ *     threads) race with each other and give wrong results.
+ *   - The eigen-solver convergence flag is kept in the array and is not
+ *     reported by this call.
+ * Arguments and results are those of fq_clutter_svd with gram_mode
+ * FQ_GRAM_F32 (iq_f, pd, eigvals, k_used nullable; everything stays on the
+ * device). */
+fq_status fq_clutter_svd_noalloc(const void *iq, int32_t dtype, int64_t P, int32_t F, int32_t k_cut,
+                                 double energy_thresh, void *iq_f, float *pd, double *eigvals, int32_t *k_used,
+                                 void *stream);
+
 /* Power Doppler of a filtered ensemble: pd[p] = (1/F) sum_f |iq_f[p][f]|^2
  * (Sec. 2.4.2).  iq_f device complex [P][F] of dtype; pd device float [P]. */
 fq_status fq_power_doppler(const void *iq_f, int32_t dtype, int64_t P, int32_t F, float *pd,

@@ -10,6 +10,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "fq_internal.cuh"
 
@@ -583,6 +584,63 @@ fq_status launch_eig(const float2 *G, int F, float2 *big, float2 *hv, float *tau
     return fqi::launch_check("fq_hermitian_eig");
 }
 
+// ---------------------------------------------------- no-allocation variant --
+// Scratch for fq_clutter_svd_noalloc: one fixed array per device that loads
+// the library.  Its host-side name is only a stand-in; kernels get the
+// device address that cudaGetSymbolAddress returns for the current device.
+constexpr size_t kNoallocBytes = (size_t)12 << 20;
+constexpr int kNoallocMaxF = 256;
+constexpr int kNoallocMaxChunks = 16;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// The workspace layout of the clutter filter with at most max_chunks Gram
+// partial sums (fewer pixel chunks, each longer), so that its size depends
+// on F only.
+ClutterLayout layout_capped(int64_t P, int F, int max_chunks)
+{
+    ClutterLayout L = layout(P, F);
+    if (L.n_chunks <= max_chunks) return L;
+    size_t o = 0;
+    L.status = o; o += 256;
+    L.G = o; o += al256(sizeof(float2) * F * F);
+    L.n_chunks = max_chunks;
+    int64_t per = (P + L.n_chunks - 1) / L.n_chunks;
+    L.chunk_len = (per + kGramTile - 1) / kGramTile * kGramTile;
+    L.part = o; o += al256(sizeof(float2) * (size_t)L.n_chunks * F * F);
+    L.V = o; o += al256(sizeof(float2) * F * F);
+    L.Vt = o; o += al256(sizeof(float2) * F * F);
+    L.lam = o; o += al256(sizeof(double) * F);
+    L.k = o; o += 256;
+    L.hv = o; o += al256(sizeof(float2) * F * F);
+    L.tau = o; o += al256(sizeof(float) * F);
+    L.big = o; o += eig_in_smem(F) ? 0 : al256(sizeof(float2) * (size_t)F * (F + 1) / 2);
+    L.total = o;
+    return L;
+}
+
+// Device address of the scratch array on the current device, looked up
+// once per device (with that device current) and cached.
+fq_status noalloc_scratch(char **out)
+{
+    constexpr int kMaxDevices = 64;
+    static void *addr[kMaxDevices] = {};
+    static std::mutex mu;
+    int dev = 0;
+    fq_status s = fqi::cuda_check(cudaGetDevice(&dev), "fq_clutter_svd_noalloc: cudaGetDevice");
+    if (s) return s;
+    FQ_REQUIRE(dev >= 0 && dev < kMaxDevices, FQ_ERR_UNSUPPORTED, "fq_clutter_svd_noalloc: device ordinal %d", dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        s = fqi::cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch),
+                            "fq_clutter_svd_noalloc: cudaGetSymbolAddress");
+        if (s) return s;
+        addr[dev] = p;
+    }
+    *out = (char *)addr[dev];
+    return FQ_OK;
+}
+
 int pd_blocks(int64_t P)
 {
     int64_t b = (P + 7) / 8;
@@ -725,6 +783,49 @@ fq_status fq_clutter_status(void *workspace, void *stream)
     if (s) return s;
     if (flag) return fqi::set_error((fq_status)flag, "device solver reported %s", fq_status_string((fq_status)flag));
     return FQ_OK;
+}
+
+
+fq_status fq_clutter_svd_noalloc(const void *iq, int32_t dtype, int64_t P, int32_t F, int32_t k_cut,
+                                 double energy_thresh, void *iq_f, float *pd, double *eigvals, int32_t *k_used,
+                                 void *stream)
+{
+    FQ_REQUIRE(iq && P >= 1 && F >= 2, FQ_ERR_INVALID_ARG, "fq_clutter_svd_noalloc: bad arguments");
+    FQ_REQUIRE(F <= kNoallocMaxF, FQ_ERR_SHAPE,
+               "fq_clutter_svd_noalloc: F = %d frames exceeds the built-in scratch limit of %d frames; "
+               "use fq_clutter_svd with a workspace", F, kNoallocMaxF);
+    FQ_REQUIRE(k_cut <= F, FQ_ERR_INVALID_ARG, "fq_clutter_svd_noalloc: k_cut %d > F %d", k_cut, F);
+    FQ_REQUIRE(k_cut >= 0 || (energy_thresh > 0.0 && energy_thresh <= 1.0), FQ_ERR_INVALID_ARG,
+               "fq_clutter_svd_noalloc: energy_thresh must be in (0, 1] when k_cut < 0");
+    FQ_REQUIRE(dtype == FQ_F32 || dtype == FQ_BF16, FQ_ERR_UNSUPPORTED, "fq_clutter_svd_noalloc: dtype");
+    FQ_REQUIRE(fqi::aligned(iq, 8) && fqi::aligned(iq_f, 8), FQ_ERR_ALIGN, "fq_clutter_svd_noalloc: alignment");
+    ClutterLayout L = layout_capped(P, F, kNoallocMaxChunks);
+    FQ_REQUIRE(L.total <= kNoallocBytes, FQ_ERR_SHAPE,
+               "fq_clutter_svd_noalloc: needs %zu scratch bytes, the built-in array has %zu", L.total, kNoallocBytes);
+    char *ws = nullptr;
+    fq_status s = noalloc_scratch(&ws);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the status word must start at zero; everything else is fully rewritten
+    s = fqi::cuda_check(cudaMemsetAsync(ws, 0, 256, st), "fq_clutter_svd_noalloc: status reset");
+    if (s) return s;
+    float2 *G = (float2 *)(ws + L.G);
+    s = dtype == FQ_F32 ? launch_gram<float>(iq, P, F, L, ws, G, st) : launch_gram<__nv_bfloat16>(iq, P, F, L, ws, G, st);
+    if (s) return s;
+    double *lam = eigvals ? eigvals : (double *)(ws + L.lam);
+    int *kk = k_used ? (int *)k_used : (int *)(ws + L.k);
+    float2 *big = eig_in_smem(F) ? nullptr : (float2 *)(ws + L.big);
+    s = launch_eig(G, F, big, (float2 *)(ws + L.hv), (float *)(ws + L.tau), lam, (float2 *)(ws + L.V),
+                   (float2 *)(ws + L.Vt), k_cut, energy_thresh, kk, (int *)ws, st);
+    if (s) return s;
+    if (!iq_f && !pd) return FQ_OK;
+    if (dtype == FQ_F32)
+        project_pd_kernel<float><<<pd_blocks(P), 256, 0, st>>>((const float *)iq, P, F, (const float2 *)(ws + L.Vt), kk,
+                                                               (float *)iq_f, pd);
+    else
+        project_pd_kernel<__nv_bfloat16><<<pd_blocks(P), 256, 0, st>>>(
+            (const __nv_bfloat16 *)iq, P, F, (const float2 *)(ws + L.Vt), kk, (__nv_bfloat16 *)iq_f, pd);
+    return fqi::launch_check("fq_clutter_svd_noalloc: projection");
 }
 
 }  // extern "C"

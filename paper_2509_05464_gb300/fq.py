@@ -111,6 +111,7 @@ def lib():
             "fq_clutter_svd_workspace_size": [_I64, _I32, _I32, C.POINTER(_SZ)],
             "fq_clutter_svd": [_P, _I32, _I64, _I32, _I32, _D, _I32, _P, _P, _P, _P, _P, _SZ, _P],
             "fq_power_doppler": [_P, _I32, _I64, _I32, _P, _P],
+            "fq_clutter_svd_noalloc": [_P, _I32, _I64, _I32, _I32, _D, _P, _P, _P, _P, _P],
             "fq_clutter_status": [_P, _P],
         }
         for name, args in sig.items():
@@ -393,3 +394,22 @@ def fq_power_doppler(iq_f, pd=None, stream=None):
 
 def fq_clutter_status(ws, stream=None):
     _check(lib().fq_clutter_status(_ptr(ws), _stream(stream)))
+
+
+def fq_clutter_svd_noalloc(iq, k_cut=2, energy_thresh=0.9, want_iq_f=True, iq_f=None, pd=None, eigvals=None,
+                           k_used=None, stream=None):
+    """fq_clutter_svd without a workspace: the library uses its built-in
+    scratch array (F <= 256; calls that overlap on the GPU race)."""
+    P, F = iq.shape[0], iq.shape[1]
+    dev = iq.device
+    if iq_f is None and want_iq_f:
+        iq_f = torch.empty_like(iq)
+    if pd is None:
+        pd = torch.empty(P, dtype=torch.float32, device=dev)
+    if eigvals is None:
+        eigvals = torch.empty(F, dtype=torch.float64, device=dev)
+    if k_used is None:
+        k_used = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(lib().fq_clutter_svd_noalloc(_ptr(iq), _dt(iq), P, F, int(k_cut), float(energy_thresh), _ptr(iq_f),
+                                        _ptr(pd), _ptr(eigvals), _ptr(k_used), _stream(stream)))
+    return dict(iq_f=iq_f, pd=pd, eigvals=eigvals, k=k_used)
