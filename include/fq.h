@@ -220,9 +220,11 @@ fq_status fq_bin_scatterers(const float *z, int64_t S, double z0, double dz, int
  *   rf_base device float [A][M][Ns] or NULL
  *   rf      device [n_frames][A][M][Ns] of out_dtype (FQ_F32 or FQ_BF16),
  *           4-byte aligned
- * Accumulation is FP32; delays use float-float (~48-bit) arithmetic.  The
- * summation order over scatterers is not fixed, so the last bits may
- * differ between runs.
+ * Delays use float-float (~48-bit) arithmetic.  Taps are accumulated in
+ * fixed point (resolution 2^-20 of the largest |amp| per unit RF, range
+ * 2^27 of it), so results are bit-reproducible; a single tap is clamped to
+ * 2^17 |amp|max, i.e. scatterers closer than ~8 um to an element centre
+ * (far inside the element's near field, outside the model) saturate.
  * Errors: FQ_ERR_INVALID_ARG, FQ_ERR_SHAPE (Ns > 8192, n_angles outside
  * [1, FQ_MAX_ANGLES], M > 65536), FQ_ERR_UNSUPPORTED (out_dtype FQ_F16). */
 fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, const float *pos,

@@ -3,14 +3,15 @@
 //
 // Design (GB300): one CTA owns the complete RF record of E consecutive
 // receive elements for one (frame, transmit) pair and keeps it in shared
-// memory (E x Ns FP32).  Its threads stream every scatterer of the frame
-// once (coalesced structure-of-arrays loads, one scatterer per thread), and
-// for each of the E elements evaluate the delay, amplitude and the pulse
-// taps that land in the record, adding them to the shared record with
-// shared-memory atomics.  Nothing is atomically added in global memory: the
-// record is written out once, coalesced, after the last scatterer.  The
-// per-scatterer transmit path and the position loads are shared by the E
-// elements.
+// memory.  Its threads stream every scatterer of the frame once (coalesced
+// structure-of-arrays loads, one scatterer per thread), and for each of the
+// E elements evaluate the delay, amplitude and the pulse taps that land in
+// the record.  Taps are accumulated in fixed point with native shared-memory
+// int32 atomics (hi/lo split, see add_fixed): on this GPU shared-memory FP32
+// atomic adds run as compare-and-swap loops and sustain ~3.7x fewer adds per
+// second than int32 ones.  Nothing is atomically added in global memory: the
+// record is converted back and written out once, coalesced, after the last
+// scatterer.  Integer sums make the RF bit-reproducible.
 //
 // Precision: the delay u = tau fs (hundreds to thousands of samples) must
 // be known to ~1e-6 sample for the carrier phase, so the geometry
@@ -81,21 +82,53 @@ __device__ __forceinline__ float tap2(float A, float hA, float C)
     return fmaf(fmaf(fmaf(A, C, A), C, -hA), C, -hA);
 }
 
+// Fixed-point accumulation.  A tap value v (in units of the largest
+// |amplitude|, i.e. scaled by g = 2^-ceil(log2 max|amp|)) is held as
+// V = v g 2^20 split into hi = rint(V / 2^16) and lo = V - 2^16 hi
+// (|lo| <= 2^15), each added with a native shared-memory int32 atomic.  The
+// sums are exact integers (order-independent, so the RF is bit-reproducible)
+// and the split keeps 47 bits of range: |sum| < 2^27 in scaled units,
+// resolution 2^-20.  Rounding to integers uses the 1.5 * 2^23 magic-number
+// trick (exact for |x| < 2^22).
+constexpr float kFixScale = 1048576.0f;          // 2^20
+constexpr float kMagic = 12582912.0f;            // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+constexpr float kTapClamp = 137438953472.0f;     // 2^37: |v g| <= 2^17 per tap
+
+__device__ __forceinline__ void add_fixed(int *hi, int *lo, int k, float V)
+{
+    V = fminf(fmaxf(V, -kTapClamp), kTapClamp);
+    const float ht = fmaf(V, 1.0f / 65536.0f, kMagic);
+    const float hb = ht - kMagic;                 // rint(V / 2^16) as a float
+    const float lf = fmaf(-hb, 65536.0f, V);      // exact remainder, |lf| <= 2^15
+    const float lt = lf + kMagic;
+    atomicAdd(hi + k, __float_as_int(ht) - kMagicBits);
+    atomicAdd(lo + k, __float_as_int(lt) - kMagicBits);
+}
+
 template <int E, int NT, typename OutT>
 __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const float *__restrict__ pos,
                                                          const float *__restrict__ amp,
                                                          const float *__restrict__ rf_base,
                                                          OutT *__restrict__ rf)
 {
-    extern __shared__ float tile[];  // [E][Ns]
+    extern __shared__ int tile[];  // hi [E][Ns] then lo [E][Ns]
     __shared__ float ex_hi[E], ex_lo[E], ey_hi[E], ey_lo[E];
+    __shared__ float s_red[NT / 32];
     const int ns = p.pr.ns;
     const int M = p.pr.M;
     const int m0 = blockIdx.x * E;
     const int a = blockIdx.y;
     const int f = blockIdx.z;
     const int ne = min(E, M - m0);
+    const int64_t S = p.S;
+    int *thi = tile, *tlo = tile + E * ns;
 
+    // the amplitude scale g (identical in every CTA): largest |amp| -> [0.5, 1)
+    float amax = 0.0f;
+    for (int64_t s = threadIdx.x; s < S; s += NT) amax = fmaxf(amax, fabsf(amp[s]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = amax;
     if (threadIdx.x < E) {
         int m = min(m0 + (int)threadIdx.x, M - 1);
         ff ex = fqi::elem_coord(m % p.pr.nx, p.pr.nx, p.pr.pitch_x);
@@ -105,11 +138,24 @@ __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const
         ey_hi[threadIdx.x] = ey.hi;
         ey_lo[threadIdx.x] = ey.lo;
     }
+    __syncthreads();
+    amax = 0.0f;
+    for (int w = 0; w < NT / 32; ++w) amax = fmaxf(amax, s_red[w]);
+    int gexp = 0;
+    if (amax > 0.0f) frexpf(amax, &gexp);                 // amax = mant * 2^gexp, mant in [0.5, 1)
+    const float g = ldexpf(1.0f, -gexp);                  // exact power of two
+    const float to_fix = g * kFixScale;
+
     for (int i = threadIdx.x; i < E * ns; i += NT) {
         int e = i / ns, k = i - e * ns;
         float v = 0.0f;
         if (rf_base && e < ne) v = rf_base[((int64_t)a * M + m0 + e) * ns + k];
-        tile[i] = v;
+        float V = fminf(fmaxf(v * to_fix, -kTapClamp), kTapClamp);
+        const float ht = fmaf(V, 1.0f / 65536.0f, kMagic);
+        const float hb = ht - kMagic;
+        const float lt = fmaf(-hb, 65536.0f, V) + kMagic;
+        thi[i] = __float_as_int(ht) - kMagicBits;
+        tlo[i] = __float_as_int(lt) - kMagicBits;
     }
     __syncthreads();
 
@@ -118,7 +164,6 @@ __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const
     const ff org = fqi::ff_load(an.origin);
     const float Kh = p.pr.fs_over_c.hi, Kl = p.pr.fs_over_c.lo;
     const bool matrix = p.pr.ny > 1;
-    const int64_t S = p.S;
     const float *X = pos + (int64_t)f * 3 * S;
     const float *Y = X + S;
     const float *Z = Y + S;
@@ -137,6 +182,7 @@ __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const
         ptx = fqi::ff_add(ptx, fqi::ff_neg(org));
         const ff zz = fqi::ff_two_prod(z, z);
         const bool use_y = matrix || y != 0.0f;  // 2D workloads keep every scatterer at y = 0
+        const float Rfix = R * to_fix;
 #pragma unroll 1
         for (int e = 0; e < ne; ++e) {
             // dx = x - ex as an unnormalised pair (TwoSum of x and -ex_hi, plus -ex_lo)
@@ -178,17 +224,17 @@ __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const
             float frac = __fadd_rn(__fsub_rn(uh, fl), ul);
             if (frac < 0.0f) { frac += 1.0f; fl -= 1.0f; }
             else if (frac >= 1.0f) { frac -= 1.0f; fl += 1.0f; }
-            // amplitude: reflectivity x directivity x attenuation / r
+            // amplitude (fixed-point units): reflectivity x directivity x attenuation / r
             float D = sinc_f(p.kbx * dxh * rs);
             if (matrix) D *= sinc_f(p.kby * dyh * rs);
-            const float Aa = R * D * __expf(-p.att * path.hi) * rs;
+            const float Aa = Rfix * D * __expf(-p.att * path.hi) * rs;
             // taps j = jlo .. jlo + ntap - 1 with |j - frac| < half_w
             const int jlo = (int)ceilf(frac - half_w);
             const int ntap = (int)floorf(frac + half_w) - jlo + 1;
             const int kst = (int)fl + jlo;
             float ch, sh;
             first_tap(p.w_h, frac, thc0, ths0, thc1, ths1, jlo != p.jmin, ch, sh);
-            float *line = tile + e * ns + kst;
+            int *lhi = thi + e * ns, *llo = tlo + e * ns;
             const bool inside = kst >= 0 && kst + ntap <= ns;
             if (fast8 && inside) {
                 // C_j = cos(w_h (jlo + j - frac)) by the Chebyshev recurrence
@@ -196,18 +242,18 @@ __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const
                 float c0 = ch, c1 = fmaf(ch, p.cos_h, -sh * p.sin_h);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    atomicAdd(line + j, tap2(Aa, hA, c0));
+                    add_fixed(lhi, llo, kst + j, tap2(Aa, hA, c0));
                     const float c2 = fmaf(p.two_cos_h, c1, -c0);
                     c0 = c1;
                     c1 = c2;
                 }
-                if (ntap > 8) atomicAdd(line + 8, tap2(Aa, hA, c0));
+                if (ntap > 8) add_fixed(lhi, llo, kst + 8, tap2(Aa, hA, c0));
             } else if (p.two_cycle) {
                 const float hA = 0.5f * Aa;
                 float c0 = ch, c1 = fmaf(ch, p.cos_h, -sh * p.sin_h);
                 for (int j = 0; j < ntap; ++j) {
                     const int k = kst + j;
-                    if (k >= 0 && k < ns) atomicAdd(line + j, tap2(Aa, hA, c0));
+                    if (k >= 0 && k < ns) add_fixed(lhi, llo, k, tap2(Aa, hA, c0));
                     const float c2 = fmaf(p.two_cos_h, c1, -c0);
                     c0 = c1;
                     c1 = c2;
@@ -220,7 +266,7 @@ __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const
                 float q0 = cc, q1 = fmaf(cc, p.cos_c, -sc * p.sin_c);
                 for (int j = 0; j < ntap; ++j) {
                     const int k = kst + j;
-                    if (k >= 0 && k < ns) atomicAdd(line + j, Aa * fmaf(0.5f, h0, 0.5f) * q0);
+                    if (k >= 0 && k < ns) add_fixed(lhi, llo, k, Aa * fmaf(0.5f, h0, 0.5f) * q0);
                     const float h2 = fmaf(p.two_cos_h, h1, -h0);
                     h0 = h1;
                     h1 = h2;
@@ -232,8 +278,10 @@ __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const
         }
     }
     __syncthreads();
+    const float from_fix = 1.0f / to_fix;  // exact power of two
     OutT *out = rf + (((int64_t)f * p.A + a) * M + m0) * ns;
-    for (int i = threadIdx.x; i < ne * ns; i += NT) fqi::store_f(out, i, tile[i]);
+    for (int i = threadIdx.x; i < ne * ns; i += NT)
+        fqi::store_f(out, i, fmaf((float)thi[i], 65536.0f, (float)tlo[i]) * from_fix);
 }
 
 template <int E, typename OutT>
@@ -241,7 +289,7 @@ fq_status launch_rf(const RfParams &p, int F, const float *pos, const float *amp
                     OutT *rf, cudaStream_t st)
 {
     constexpr int NT = 256;
-    size_t smem = sizeof(float) * (size_t)E * p.pr.ns;
+    size_t smem = 2 * sizeof(int) * (size_t)E * p.pr.ns;
     auto kern = rf_synth_kernel<E, NT, OutT>;
     fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                                   "fq_simulate_rf: smem attribute");
@@ -251,22 +299,21 @@ fq_status launch_rf(const RfParams &p, int F, const float *pos, const float *amp
     return fqi::launch_check("fq_simulate_rf");
 }
 
-// Elements per CTA (4 unless the record is too long); FQ_RF_ELEMS (4, 8 or
-// 16) overrides it for tuning.
+// Elements per CTA (2); FQ_RF_ELEMS (2, 4, 8 or 16) overrides it for tuning.
 int rf_elems(int ns)
 {
     static int forced = -1;
     if (forced < 0) {
         const char *env = std::getenv("FQ_RF_ELEMS");
         int v = env ? std::atoi(env) : 0;
-        forced = (v == 4 || v == 8 || v == 16) ? v : 0;
+        forced = (v == 2 || v == 4 || v == 8 || v == 16) ? v : 0;
     }
-    const size_t line = sizeof(float) * (size_t)ns;
+    const size_t line = 2 * sizeof(int) * (size_t)ns;  // hi and lo accumulators
     if (forced && forced * line <= 200 * 1024) return forced;
-    // 4 elements keep the tile small enough for 6+ CTAs (48 warps) per SM,
-    // which hides the shared-atomic latency better than more reuse of the
-    // per-scatterer work (measured on the 2D compounded workload)
-    if (4 * line <= 200 * 1024) return 4;
+    // 2 elements (32 KB at Ns = 2048) keep 4 CTAs per SM resident, which
+    // hides the latency of the accumulation better than more reuse of the
+    // per-scatterer work (measured on the 2D compounded workload: 115 ms
+    // for 2 elements, 121 ms for 4)
     return 2;
 }
 
