@@ -48,8 +48,9 @@ def peaks():
 
 
 def fp32_alu_peak_tflops(sm_mhz):
-    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2 (packed f32x2 FMA issues
+    # two lanes' worth per instruction on sm_103a) x clock
+    return 152 * 128 * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -200,7 +201,8 @@ def run_ours(args, rank, world, local):
     w = W.config2(seed=2 + rank, n_frames=args.frames)  # an independent ensemble per rank (weak scaling)
     if args.scatterers or args.grid_div:  # reduced cases for profiler captures only
         w = W.shrink(w, max_scat=args.scatterers or None, grid_div=args.grid_div or None)
-    pl = Pipeline(w)
+    gram_mode = {"f32": fq.FQ_GRAM_F32, "tf32": fq.FQ_GRAM_TF32, "bf16": fq.FQ_GRAM_BF16}[args.gram]
+    pl = Pipeline(w, gram_mode=gram_mode)
     pl.upload()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -259,13 +261,15 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "frames": w.n_frames, "angles": w.A, "elements": w.M, "samples": w.Ns,
-                   "scatterers": w.S, "pixels": w.P, "parallelism": f"independent ensemble per GPU x{world}",
+                   "scatterers": w.S, "pixels": w.P, "gram": args.gram,
+                   "parallelism": f"independent ensemble per GPU x{world}",
                    "l2": "256 MiB buffer rewritten between timed steps, outside the timed events"},
         "das_voxel_angle_per_s": total_va / (ms * 1e-3),
         "stage_ms": stage_ms,
         "roofline": {"bound": "alu", "kernel": "rf_synth_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_for_peak:.0f} MHz ({src} max clock)",
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
+                                    f"({src} max clock)",
                      "work": f"{GEOM_FLOP_PER_PAIR:.0f} + {FLOP_PER_TAP:.0f} x {taps:.3f} taps FLOP per pair, "
                              f"{pairs:.3e} pairs"},
         "cpu_baseline": cpu,
@@ -287,6 +291,8 @@ def main():
     ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
+    ap.add_argument("--gram", choices=["f32", "tf32", "bf16"], default="f32",
+                    help="Casorati Gram arithmetic: FP32 CUDA cores or TF32 / BF16 tensor cores")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
     rank, world, local = dist_init(args)

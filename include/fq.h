@@ -279,9 +279,17 @@ fq_status fq_beamform_das(const fq_probe *probe, const fq_tx *tx, const void *rf
  * eigen-decomposition of its frames x frames Gram matrix).
  *   S  device complex [P][F] of dtype
  *   G  device float complex [F][F] (row-major, Hermitian, full matrix)
- * gram_mode FQ_GRAM_F32 needs dtype FQ_F32 or FQ_BF16; FQ_GRAM_BF16 needs
- * dtype FQ_BF16 and F a multiple of 32; FQ_GRAM_TF32 needs dtype FQ_F32.
- * 2 <= F <= 512. */
+ * dtype FQ_F32 or FQ_BF16, any gram_mode, 2 <= F <= 512, P >= 1.
+ *   FQ_GRAM_F32   FP32 products and sums on the CUDA cores.
+ *   FQ_GRAM_BF16  tcgen05 tensor cores: S is rounded to BF16 (nearest even),
+ *                 products are exact, sums FP32 (G is the Gram of the
+ *                 rounded S up to FP32 accumulation).
+ *   FQ_GRAM_TF32  as BF16 with TF32 operands (10 mantissa bits, nearest,
+ *                 ties away from zero).
+ * The tensor-core modes keep their scratch (a 2F x P operand copy plus
+ * FP32 partial tiles) in the workspace and a status word in its first 256
+ * bytes: a device-side wait that runs out (bounded at ~2 s) sets it to
+ * FQ_ERR_TIMEOUT, readable with fq_clutter_status(workspace). */
 fq_status fq_gram_workspace_size(int64_t P, int32_t F, int32_t gram_mode, size_t *bytes);
 fq_status fq_casorati_gram(const void *S, int32_t dtype, int64_t P, int32_t F, int32_t gram_mode,
                            float *G, void *workspace, size_t workspace_bytes, void *stream);
@@ -310,6 +318,8 @@ fq_status fq_hermitian_eig(const float *G, int32_t F, double *eigvals, float *V,
  *   eigvals  device double [F], nullable
  *   k_used   device int32 [1], nullable
  * k_cut > F -> FQ_ERR_INVALID_ARG; k == F -> S_f = 0.
+ * gram_mode selects the Gram arithmetic as for fq_casorati_gram; the
+ * projection always reads iq in its own dtype.
  * Everything stays on the device (k is decided on the device). */
 fq_status fq_clutter_svd_workspace_size(int64_t P, int32_t F, int32_t gram_mode, size_t *bytes);
 fq_status fq_clutter_svd(const void *iq, int32_t dtype, int64_t P, int32_t F, int32_t k_cut,
@@ -350,9 +360,10 @@ fq_status fq_clutter_svd_noalloc(const void *iq, int32_t dtype, int64_t P, int32
 fq_status fq_power_doppler(const void *iq_f, int32_t dtype, int64_t P, int32_t F, float *pd,
                            void *stream);
 
-/* Device-side status word of the solver calls that decide on the device
- * (eigen-solver convergence).  Reads and clears the flag the last
- * fq_hermitian_eig / fq_clutter_svd on this workspace wrote; synchronises
+/* Device-side status word of the calls that decide on the device
+ * (eigen-solver convergence, a timed-out tensor-core wait).  Reads and
+ * clears the flag the last fq_hermitian_eig / fq_clutter_svd (or
+ * tensor-core fq_casorati_gram) on this workspace wrote; synchronises
  * `stream`. */
 fq_status fq_clutter_status(void *workspace, void *stream);
 

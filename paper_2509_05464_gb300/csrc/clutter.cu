@@ -18,12 +18,13 @@ namespace {
 
 // ------------------------------------------------------------ workspace --
 struct ClutterLayout {
-    size_t status, G, part, V, Vt, lam, k, hv, tau, big, total;
+    size_t status, G, part, V, Vt, lam, k, hv, tau, big, ii, tc, total;
     int n_chunks;
     int64_t chunk_len;
 };
 
 constexpr int kGramTile = 32;
+constexpr int kFastMaxK = 48;  // top-k eigenvectors by inverse iteration up to this k
 
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -41,16 +42,21 @@ int gram_chunks(int64_t P, int F)
 
 bool eig_in_smem(int F) { return (size_t)F * (F + 1) / 2 * sizeof(float2) <= 190 * 1024; }
 
-ClutterLayout layout(int64_t P, int F)
+// Operand bytes of the tensor-core Gram modes (0 = CUDA-core FP32 Gram).
+int tc_esz(int gram_mode) { return gram_mode == FQ_GRAM_BF16 ? 2 : (gram_mode == FQ_GRAM_TF32 ? 4 : 0); }
+
+ClutterLayout layout(int64_t P, int F, int gram_mode = FQ_GRAM_F32)
 {
     ClutterLayout L;
     size_t o = 0;
+    const int esz = tc_esz(gram_mode);
     L.status = o; o += 256;
     L.G = o; o += al256(sizeof(float2) * F * F);
     L.n_chunks = gram_chunks(P, F);
     int64_t per = (P + L.n_chunks - 1) / L.n_chunks;
     L.chunk_len = (per + kGramTile - 1) / kGramTile * kGramTile;
-    L.part = o; o += al256(sizeof(float2) * (size_t)L.n_chunks * F * F);
+    L.part = o; o += esz ? 0 : al256(sizeof(float2) * (size_t)L.n_chunks * F * F);
+    L.tc = o; o += esz ? fqi::gram_tc_workspace_bytes(P, F, esz) : 0;
     L.V = o; o += al256(sizeof(float2) * F * F);
     L.Vt = o; o += al256(sizeof(float2) * F * F);
     L.lam = o; o += al256(sizeof(double) * F);
@@ -58,6 +64,7 @@ ClutterLayout layout(int64_t P, int F)
     L.hv = o; o += al256(sizeof(float2) * F * F);
     L.tau = o; o += al256(sizeof(float) * F);
     L.big = o; o += eig_in_smem(F) ? 0 : al256(sizeof(float2) * (size_t)F * (F + 1) / 2);
+    L.ii = o; o += al256(sizeof(float) * 6 * (size_t)kFastMaxK * F);
     L.total = o;
     return L;
 }
@@ -163,6 +170,153 @@ __device__ float block_sum(float v, float *red)
     return red[32];
 }
 
+// V[:, j] = H_0 ... H_{F-3} D Z[:, perm[j]] for j < ncol (warp per column).
+__device__ void back_transform(int F, int ncol, const float *Z, int zs, const int *perm, const float2 *delta,
+                               const float2 *__restrict__ hv, const float *__restrict__ tau_g, float2 *__restrict__ V,
+                               float2 *__restrict__ Vt, int lane, int wid, int nw)
+{
+    for (int j = wid; j < ncol; j += nw) {
+        const int src = perm[j];
+        float2 y[16];  // F <= 512: 16 values per lane
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            int i = lane + 32 * q;
+            y[q] = i < F ? make_float2(delta[i].x * Z[i * zs + src], delta[i].y * Z[i * zs + src]) : make_float2(0, 0);
+        }
+        for (int k = F - 3; k >= 0; --k) {
+            const float t = tau_g[k];
+            if (t == 0.0f) continue;
+            const float2 *v = hv + (size_t)k * F;
+            float2 s = make_float2(0, 0);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                int i = lane + 32 * q;
+                if (i > k && i < F) {
+                    float2 vi = v[i];
+                    s.x += vi.x * y[q].x + vi.y * y[q].y;  // conj(v) y
+                    s.y += vi.x * y[q].y - vi.y * y[q].x;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            }
+            s.x *= t;
+            s.y *= t;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                int i = lane + 32 * q;
+                if (i > k && i < F) {
+                    float2 u = cmul(v[i], s);
+                    y[q].x -= u.x;
+                    y[q].y -= u.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            int i = lane + 32 * q;
+            if (i < F) {
+                if (V) V[(size_t)i * F + j] = y[q];
+                Vt[(size_t)j * F + i] = y[q];
+            }
+        }
+    }
+}
+
+// Number of eigenvalues of the real symmetric tridiagonal (d, e) below x
+// (Sturm count by the LDL^T pivot recurrence; tiny pivots are replaced by
+// -pivmin so that the count stays monotone).
+__device__ int sturm_below(const float *d, const float *e2, int n, float x, float pivmin)
+{
+    int cnt = 0;
+    float q = d[0] - x;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0f;
+    for (int i = 1; i < n; ++i) {
+        q = (d[i] - x) - e2[i - 1] / q;
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += q < 0.0f;
+    }
+    return cnt;
+}
+
+// The m-th smallest eigenvalue (0-based) by bisection on [lo, hi].
+__device__ float bisect_eig(const float *d, const float *e2, int n, int m, float lo, float hi, float pivmin)
+{
+    for (int it = 0; it < 80; ++it) {
+        const float mid = 0.5f * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_below(d, e2, n, mid, pivmin) >= m + 1) hi = mid;
+        else lo = mid;
+    }
+    return 0.5f * (lo + hi);
+}
+
+// One eigenvector of the real tridiagonal for eigenvalue sigma by inverse
+// iteration: Gaussian elimination with partial pivoting of T - sigma I
+// (kept in per-thread local arrays), three solves from a fixed pseudo-random
+// start, each normalised.  Writes column `col` of Z (row stride zs).
+__device__ void inverse_iteration(const float *d, const float *e, int n, float sigma, float tiny, int seed,
+                                  float *Z, int zs, int col, float *__restrict__ scr)
+{
+    // scratch (global workspace, 6 n floats): u0, u1, u2, multipliers, swaps, x
+    float *u0 = scr, *u1 = scr + n, *u2 = scr + 2 * n, *ml = scr + 3 * n, *sw = scr + 4 * n, *x = scr + 5 * n;
+    float p0 = d[0] - sigma, p1 = n > 1 ? e[0] : 0.0f, p2 = 0.0f;
+    for (int i = 0; i + 1 < n; ++i) {
+        const float c = e[i];                       // sub-diagonal of row i + 1
+        const float a1 = d[i + 1] - sigma;
+        const float b1 = (i + 2 < n) ? e[i + 1] : 0.0f;
+        if (fabsf(c) > fabsf(p0)) {
+            // pivot on row i + 1
+            const float mlt = p0 / c;
+            u0[i] = c; u1[i] = a1; u2[i] = b1; ml[i] = mlt; sw[i] = 1.0f;
+            p0 = p1 - mlt * a1;
+            p1 = p2 - mlt * b1;
+            p2 = 0.0f;
+        } else {
+            const float piv = fabsf(p0) < tiny ? (p0 < 0.0f ? -tiny : tiny) : p0;
+            const float mlt = c / piv;
+            u0[i] = piv; u1[i] = p1; u2[i] = p2; ml[i] = mlt; sw[i] = 0.0f;
+            p0 = a1 - mlt * p1;
+            p1 = b1 - mlt * p2;
+            p2 = 0.0f;
+        }
+    }
+    u0[n - 1] = fabsf(p0) < tiny ? (p0 < 0.0f ? -tiny : tiny) : p0;
+    u1[n - 1] = 0.0f;
+    u2[n - 1] = 0.0f;
+    unsigned h = 0x9E3779B9u * (unsigned)(seed + 1);
+    for (int i = 0; i < n; ++i) {
+        h = h * 1664525u + 1013904223u;
+        x[i] = 1.0f + 0.25f * ((float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f);
+    }
+    for (int it = 0; it < 3; ++it) {
+        // forward: apply the row swaps and multipliers to the right-hand side
+        for (int i = 0; i + 1 < n; ++i) {
+            if (sw[i] != 0.0f) {
+                const float t = x[i];
+                x[i] = x[i + 1];
+                x[i + 1] = t - ml[i] * x[i];
+            } else {
+                x[i + 1] -= ml[i] * x[i];
+            }
+        }
+        // back substitution
+        x[n - 1] = x[n - 1] / u0[n - 1];
+        if (n > 1) x[n - 2] = (x[n - 2] - u1[n - 2] * x[n - 1]) / u0[n - 2];
+        for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - u1[i] * x[i + 1] - u2[i] * x[i + 2]) / u0[i];
+        float mx = 0.0f;
+        for (int i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(x[i]));
+        const float inv = mx > 0.0f ? 1.0f / mx : 1.0f;
+        for (int i = 0; i < n; ++i) x[i] *= inv;
+    }
+    float s2 = 0.0f;
+    for (int i = 0; i < n; ++i) s2 += x[i] * x[i];
+    const float inv = rsqrtf(s2);
+    for (int i = 0; i < n; ++i) Z[i * zs + col] = x[i] * inv;
+}
+
 // Householder tridiagonalisation of the Hermitian G (lower triangle used),
 // implicit QL with Wilkinson shifts on the real tridiagonal (after a
 // diagonal unitary scaling), eigenvalue sort and back-transformation.
@@ -171,7 +325,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const float2 *__restri
                                                           float2 *__restrict__ hv, float *__restrict__ tau_g,
                                                           double *__restrict__ lam_out, float2 *__restrict__ V,
                                                           float2 *__restrict__ Vt, int k_cut, double thresh,
-                                                          int *__restrict__ k_out, int *__restrict__ status)
+                                                          int *__restrict__ k_out, int *__restrict__ status,
+                                                          int topk_only, float *__restrict__ ii_scr)
 {
     extern __shared__ float2 dyn[];
     float2 *Ap = big ? big : dyn;                 // packed lower triangle, later Z (real, stride F+1)
@@ -302,8 +457,85 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const float2 *__restri
         s_fail = 0;
     }
     __syncthreads();
-    // Z = identity (stride F+1), reusing the packed-matrix storage
     const int zs = F + 1;
+    if (topk_only) {
+        // ---- all eigenvalues by bisection (one thread each), top-k vectors by
+        // inverse iteration; the QL path below is the fallback for large k
+        __shared__ float e2[512], lamd[512];
+        __shared__ float s_lo, s_hi, s_piv, s_tnorm;
+        __shared__ int s_k;
+        for (int i = tid; i < F; i += blockDim.x) e2[i] = e[i] * e[i];
+        if (tid == 0) {
+            float lo = 1e30f, hi = -1e30f, tn = 0.0f;
+            for (int i = 0; i < F; ++i) {
+                const float r = (i > 0 ? e[i - 1] : 0.0f) + e[i];
+                lo = fminf(lo, d[i] - r);
+                hi = fmaxf(hi, d[i] + r);
+                tn = fmaxf(tn, fabsf(d[i]) + r);
+            }
+            const float pad = 4.0f * FLT_EPSILON * fmaxf(tn, 1e-30f);
+            s_lo = lo - pad;
+            s_hi = hi + pad;
+            s_tnorm = tn;
+            s_piv = fmaxf(1e-30f, FLT_MIN * 4.0f);
+        }
+        __syncthreads();
+        for (int j = tid; j < F; j += blockDim.x)
+            lamd[j] = bisect_eig(d, e2, F, F - 1 - j, s_lo, s_hi, s_piv);  // descending order
+        __syncthreads();
+        for (int j = tid; j < F; j += blockDim.x) lam_out[j] = (double)lamd[j] * (double)gscale;
+        if (tid == 0) {
+            int k = k_cut;
+            if (k < 0) {
+                double tot = 0.0, acc = 0.0;
+                for (int j = 0; j < F; ++j) tot += fmax((double)lamd[j], 0.0);
+                k = F;
+                for (int j = 0; j < F; ++j) {
+                    acc += fmax((double)lamd[j], 0.0);
+                    if (acc >= thresh * tot) { k = j + 1; break; }
+                }
+            }
+            if (k_out) *k_out = k;
+            s_k = k;
+        }
+        __syncthreads();
+        const int k = s_k;
+        if (k <= kFastMaxK && ii_scr) {
+            const float tiny = FLT_EPSILON * fmaxf(s_tnorm, 1e-30f);
+            for (int j = tid; j < k; j += blockDim.x)
+                inverse_iteration(d, e, F, lamd[j], tiny, j, Z, zs, j, ii_scr + (size_t)j * 6 * F);
+            __syncthreads();
+            // re-orthogonalise vectors of close eigenvalues (modified Gram-Schmidt, warp 0)
+            if (wid == 0) {
+                const float gap = 1e-3f * s_tnorm;
+                for (int j = 1; j < k; ++j) {
+                    bool any = false;
+                    for (int i = 0; i < j; ++i) {
+                        if (fabsf(lamd[i] - lamd[j]) > gap) continue;
+                        any = true;
+                        float dot = 0.0f;
+                        for (int r = lane; r < F; r += 32) dot += Z[r * zs + i] * Z[r * zs + j];
+                        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                        for (int r = lane; r < F; r += 32) Z[r * zs + j] -= dot * Z[r * zs + i];
+                        __syncwarp();
+                    }
+                    if (any) {
+                        float n2 = 0.0f;
+                        for (int r = lane; r < F; r += 32) n2 += Z[r * zs + j] * Z[r * zs + j];
+                        for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+                        const float inv = rsqrtf(n2);
+                        for (int r = lane; r < F; r += 32) Z[r * zs + j] *= inv;
+                        __syncwarp();
+                    }
+                }
+            }
+            for (int j = tid; j < F; j += blockDim.x) perm[j] = j;
+            __syncthreads();
+            back_transform(F, k, Z, zs, perm, delta, hv, tau_g, V, Vt, lane, wid, nw);
+            return;
+        }
+    }
+    // Z = identity (stride F+1), reusing the packed-matrix storage
     for (int i = tid; i < F * zs; i += blockDim.x) Z[i] = ((i / zs) == (i % zs)) ? 1.0f : 0.0f;
     __syncthreads();
 
@@ -424,54 +656,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const float2 *__restri
         if (k_out) *k_out = k;
         if (status && s_fail) *status = FQ_ERR_NUMERICAL;
     }
-    // ---- back-transformation V[:, j] = H_0 ... H_{F-3} D Z[:, perm[j]] (warp per column)
-    for (int j = wid; j < F; j += nw) {
-        const int src = perm[j];
-        float2 y[16];  // F <= 512: 16 values per lane
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            int i = lane + 32 * q;
-            y[q] = i < F ? make_float2(delta[i].x * Z[i * zs + src], delta[i].y * Z[i * zs + src]) : make_float2(0, 0);
-        }
-        for (int k = F - 3; k >= 0; --k) {
-            const float t = tau_g[k];
-            if (t == 0.0f) continue;
-            const float2 *v = hv + (size_t)k * F;
-            float2 s = make_float2(0, 0);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                int i = lane + 32 * q;
-                if (i > k && i < F) {
-                    float2 vi = v[i];
-                    s.x += vi.x * y[q].x + vi.y * y[q].y;  // conj(v) y
-                    s.y += vi.x * y[q].y - vi.y * y[q].x;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-                s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-            }
-            s.x *= t;
-            s.y *= t;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                int i = lane + 32 * q;
-                if (i > k && i < F) {
-                    float2 u = cmul(v[i], s);
-                    y[q].x -= u.x;
-                    y[q].y -= u.y;
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            int i = lane + 32 * q;
-            if (i < F) {
-                if (V) V[(size_t)i * F + j] = y[q];
-                Vt[(size_t)j * F + i] = y[q];
-            }
-        }
-    }
+    back_transform(F, F, Z, zs, perm, delta, hv, tau_g, V, Vt, lane, wid, nw);
 }
 
 // ------------------------------------------------ projection + power Doppler --
@@ -571,8 +756,19 @@ fq_status launch_gram(const void *S, int64_t P, int F, const ClutterLayout &L, c
     return fqi::launch_check("fq_casorati_gram");
 }
 
+// Gram of gram_mode into G; the tensor-core modes use the L.tc region and
+// report a timed-out wait through the status word at ws.
+fq_status gram_any(const void *S, int dtype, int64_t P, int F, int gram_mode, const ClutterLayout &L, char *ws,
+                   float2 *G, cudaStream_t st)
+{
+    const int esz = tc_esz(gram_mode);
+    if (esz) return fqi::gram_tc(S, dtype, P, F, esz, G, ws + L.tc, (int *)(ws + L.status), st);
+    return dtype == FQ_F32 ? launch_gram<float>(S, P, F, L, ws, G, st) : launch_gram<__nv_bfloat16>(S, P, F, L, ws, G, st);
+}
+
 fq_status launch_eig(const float2 *G, int F, float2 *big, float2 *hv, float *tau, double *lam, float2 *V, float2 *Vt,
-                     int k_cut, double thresh, int *k_out, int *status, cudaStream_t st)
+                     int k_cut, double thresh, int *k_out, int *status, cudaStream_t st, int topk_only = 0,
+                     float *ii_scr = nullptr)
 {
     size_t smem = big ? 0 : sizeof(float2) * (size_t)F * (F + 1) / 2;
     if (smem > 48 * 1024) {
@@ -580,7 +776,8 @@ fq_status launch_eig(const float2 *G, int F, float2 *big, float2 *hv, float *tau
                                                            (int)smem), "eig: smem attribute");
         if (s) return s;
     }
-    eig_kernel<<<1, kEigThreads, smem, st>>>(G, F, big, hv, tau, lam, V, Vt, k_cut, thresh, k_out, status);
+    eig_kernel<<<1, kEigThreads, smem, st>>>(G, F, big, hv, tau, lam, V, Vt, k_cut, thresh, k_out, status,
+                                             topk_only, ii_scr);
     return fqi::launch_check("fq_hermitian_eig");
 }
 
@@ -614,6 +811,8 @@ ClutterLayout layout_capped(int64_t P, int F, int max_chunks)
     L.hv = o; o += al256(sizeof(float2) * F * F);
     L.tau = o; o += al256(sizeof(float) * F);
     L.big = o; o += eig_in_smem(F) ? 0 : al256(sizeof(float2) * (size_t)F * (F + 1) / 2);
+    L.ii = o; o += al256(sizeof(float) * 6 * (size_t)kFastMaxK * F);
+    L.tc = o;
     L.total = o;
     return L;
 }
@@ -654,7 +853,13 @@ extern "C" {
 fq_status fq_gram_workspace_size(int64_t P, int32_t F, int32_t gram_mode, size_t *bytes)
 {
     FQ_REQUIRE(bytes && P >= 1 && F >= 2 && F <= 512, FQ_ERR_INVALID_ARG, "fq_gram_workspace_size: bad arguments");
-    (void)gram_mode;
+    FQ_REQUIRE(gram_mode >= FQ_GRAM_F32 && gram_mode <= FQ_GRAM_BF16, FQ_ERR_INVALID_ARG,
+               "fq_gram_workspace_size: gram_mode %d", gram_mode);
+    const int esz = tc_esz(gram_mode);
+    if (esz) {
+        *bytes = 256 + fqi::gram_tc_workspace_bytes(P, F, esz);  // status word + operands + partials
+        return FQ_OK;
+    }
     ClutterLayout L = layout(P, F);
     *bytes = al256(sizeof(float2) * (size_t)L.n_chunks * F * F);
     return FQ_OK;
@@ -664,7 +869,8 @@ fq_status fq_casorati_gram(const void *S, int32_t dtype, int64_t P, int32_t F, i
                            void *workspace, size_t workspace_bytes, void *stream)
 {
     FQ_REQUIRE(S && G && P >= 1 && F >= 2 && F <= 512, FQ_ERR_INVALID_ARG, "fq_casorati_gram: bad arguments");
-    FQ_REQUIRE(gram_mode == FQ_GRAM_F32, FQ_ERR_UNSUPPORTED, "fq_casorati_gram: gram_mode %d not built", gram_mode);
+    FQ_REQUIRE(gram_mode >= FQ_GRAM_F32 && gram_mode <= FQ_GRAM_BF16, FQ_ERR_INVALID_ARG,
+               "fq_casorati_gram: gram_mode %d", gram_mode);
     FQ_REQUIRE(dtype == FQ_F32 || dtype == FQ_BF16, FQ_ERR_UNSUPPORTED, "fq_casorati_gram: dtype");
     size_t need = 0;
     fq_gram_workspace_size(P, F, gram_mode, &need);
@@ -672,9 +878,15 @@ fq_status fq_casorati_gram(const void *S, int32_t dtype, int64_t P, int32_t F, i
                need);
     FQ_REQUIRE(fqi::aligned(workspace, 256) && fqi::aligned(S, 8) && fqi::aligned(G, 8), FQ_ERR_ALIGN,
                "fq_casorati_gram: alignment");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int esz = tc_esz(gram_mode);
+    if (esz) {
+        fq_status s = fqi::cuda_check(cudaMemsetAsync(workspace, 0, 256, st), "fq_casorati_gram: status reset");
+        if (s) return s;
+        return fqi::gram_tc(S, dtype, P, F, esz, (float2 *)G, (char *)workspace + 256, (int *)workspace, st);
+    }
     ClutterLayout L = layout(P, F);
     L.part = 0;  // the partials are the only workspace content here
-    cudaStream_t st = (cudaStream_t)stream;
     if (dtype == FQ_F32) return launch_gram<float>(S, P, F, L, (char *)workspace, (float2 *)G, st);
     return launch_gram<__nv_bfloat16>(S, P, F, L, (char *)workspace, (float2 *)G, st);
 }
@@ -712,8 +924,9 @@ fq_status fq_clutter_svd_workspace_size(int64_t P, int32_t F, int32_t gram_mode,
 {
     FQ_REQUIRE(bytes && P >= 1 && F >= 2 && F <= 512, FQ_ERR_INVALID_ARG,
                "fq_clutter_svd_workspace_size: bad arguments");
-    (void)gram_mode;
-    *bytes = layout(P, F).total;
+    FQ_REQUIRE(gram_mode >= FQ_GRAM_F32 && gram_mode <= FQ_GRAM_BF16, FQ_ERR_INVALID_ARG,
+               "fq_clutter_svd_workspace_size: gram_mode %d", gram_mode);
+    *bytes = layout(P, F, gram_mode).total;
     return FQ_OK;
 }
 
@@ -726,8 +939,9 @@ fq_status fq_clutter_svd(const void *iq, int32_t dtype, int64_t P, int32_t F, in
     FQ_REQUIRE(k_cut >= 0 || (energy_thresh > 0.0 && energy_thresh <= 1.0), FQ_ERR_INVALID_ARG,
                "fq_clutter_svd: energy_thresh must be in (0, 1] when k_cut < 0");
     FQ_REQUIRE(dtype == FQ_F32 || dtype == FQ_BF16, FQ_ERR_UNSUPPORTED, "fq_clutter_svd: dtype");
-    FQ_REQUIRE(gram_mode == FQ_GRAM_F32, FQ_ERR_UNSUPPORTED, "fq_clutter_svd: gram_mode %d not built", gram_mode);
-    ClutterLayout L = layout(P, F);
+    FQ_REQUIRE(gram_mode >= FQ_GRAM_F32 && gram_mode <= FQ_GRAM_BF16, FQ_ERR_INVALID_ARG,
+               "fq_clutter_svd: gram_mode %d", gram_mode);
+    ClutterLayout L = layout(P, F, gram_mode);
     FQ_REQUIRE(workspace && workspace_bytes >= L.total, FQ_ERR_WORKSPACE,
                "fq_clutter_svd: workspace needs %zu bytes", L.total);
     FQ_REQUIRE(fqi::aligned(workspace, 256) && fqi::aligned(iq, 8) && fqi::aligned(iq_f, 8), FQ_ERR_ALIGN,
@@ -737,13 +951,13 @@ fq_status fq_clutter_svd(const void *iq, int32_t dtype, int64_t P, int32_t F, in
     fq_status s = fqi::cuda_check(cudaMemsetAsync(ws, 0, 256, st), "fq_clutter_svd: status reset");
     if (s) return s;
     float2 *G = (float2 *)(ws + L.G);
-    s = dtype == FQ_F32 ? launch_gram<float>(iq, P, F, L, ws, G, st) : launch_gram<__nv_bfloat16>(iq, P, F, L, ws, G, st);
+    s = gram_any(iq, dtype, P, F, gram_mode, L, ws, G, st);
     if (s) return s;
     double *lam = eigvals ? eigvals : (double *)(ws + L.lam);
     int *kk = k_used ? (int *)k_used : (int *)(ws + L.k);
     float2 *big = eig_in_smem(F) ? nullptr : (float2 *)(ws + L.big);
     s = launch_eig(G, F, big, (float2 *)(ws + L.hv), (float *)(ws + L.tau), lam, (float2 *)(ws + L.V),
-                   (float2 *)(ws + L.Vt), k_cut, energy_thresh, kk, (int *)ws, st);
+                   (float2 *)(ws + L.Vt), k_cut, energy_thresh, kk, (int *)ws, st, 1, (float *)(ws + L.ii));
     if (s) return s;
     if (!iq_f && !pd) return FQ_OK;
     if (dtype == FQ_F32)
@@ -816,7 +1030,7 @@ fq_status fq_clutter_svd_noalloc(const void *iq, int32_t dtype, int64_t P, int32
     int *kk = k_used ? (int *)k_used : (int *)(ws + L.k);
     float2 *big = eig_in_smem(F) ? nullptr : (float2 *)(ws + L.big);
     s = launch_eig(G, F, big, (float2 *)(ws + L.hv), (float *)(ws + L.tau), lam, (float2 *)(ws + L.V),
-                   (float2 *)(ws + L.Vt), k_cut, energy_thresh, kk, (int *)ws, st);
+                   (float2 *)(ws + L.Vt), k_cut, energy_thresh, kk, (int *)ws, st, 1, (float *)(ws + L.ii));
     if (s) return s;
     if (!iq_f && !pd) return FQ_OK;
     if (dtype == FQ_F32)

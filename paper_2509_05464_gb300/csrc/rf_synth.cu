@@ -177,9 +177,7 @@ __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const
         if (R == 0.0f) continue;
         const float x = X[s], y = Y[s], z = Z[s];
         // transmit path u . r - min u . e, float-float (once per scatterer)
-        ff ptx = fqi::ff_add(fqi::ff_mul_f(ux, x), fqi::ff_mul_f(uy, y));
-        ptx = fqi::ff_add(ptx, fqi::ff_mul_f(uz, z));
-        ptx = fqi::ff_add(ptx, fqi::ff_neg(org));
+        const ff ptx = fqi::ff_dot3_minus(an.ux, an.uy, an.uz, an.origin, x, y, z);
         const ff zz = fqi::ff_two_prod(z, z);
         const bool use_y = matrix || y != 0.0f;  // 2D workloads keep every scatterer at y = 0
         const float Rfix = R * to_fix;
@@ -284,6 +282,254 @@ __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const
         fqi::store_f(out, i, fmaf((float)thi[i], 65536.0f, (float)tlo[i]) * from_fix);
 }
 
+// ---------------------------------------------------------------------------
+// Paired-element kernel for the two-cycle pulse (at most 9 taps): each thread
+// evaluates one scatterer for the CTA's two elements at once in packed
+// f32x2 arithmetic (float-float geometry, amplitude products, Chebyshev taps,
+// fixed-point split); hardware-function calls (rsqrt, sin, exp, sincos) stay
+// scalar.  Same results as rf_synth_kernel up to rounding of the FP32 parts.
+// ---------------------------------------------------------------------------
+using fqi::f2;
+
+__device__ __forceinline__ void add_fixed2(int *hi0, int *lo0, int *hi1, int *lo1, int k0, int k1, f2 V, bool on0,
+                                           bool on1)
+{
+    const f2 ht = fqi::f2_fma(V, fqi::f2_dup(1.0f / 65536.0f), fqi::f2_dup(kMagic));
+    const f2 hb = fqi::f2_sub(ht, fqi::f2_dup(kMagic));
+    const f2 lt = fqi::f2_add(fqi::f2_fma(fqi::f2_neg(hb), fqi::f2_dup(65536.0f), V), fqi::f2_dup(kMagic));
+    float h0, h1, l0, l1;
+    fqi::f2_split(ht, h0, h1);
+    fqi::f2_split(lt, l0, l1);
+    if (on0) {
+        atomicAdd(hi0 + k0, __float_as_int(h0) - kMagicBits);
+        atomicAdd(lo0 + k0, __float_as_int(l0) - kMagicBits);
+    }
+    if (on1) {
+        atomicAdd(hi1 + k1, __float_as_int(h1) - kMagicBits);
+        atomicAdd(lo1 + k1, __float_as_int(l1) - kMagicBits);
+    }
+}
+
+// the two-cycle tap value for the pair: ((A C + A) C - A/2) C - A/2
+__device__ __forceinline__ f2 tap2x2(f2 A, f2 hA, f2 C)
+{
+    const f2 nhA = fqi::f2_neg(hA);
+    return fqi::f2_fma(fqi::f2_fma(fqi::f2_fma(A, C, A), C, nhA), C, nhA);
+}
+
+template <int NT, int MINB, typename OutT>
+__global__ void __launch_bounds__(NT, MINB) rf_synth_pair_kernel(const RfParams p, const float *__restrict__ pos,
+                                                              const float *__restrict__ amp,
+                                                              const float *__restrict__ rf_base,
+                                                              OutT *__restrict__ rf)
+{
+    constexpr int E = 2;
+    extern __shared__ int tile[];  // hi [2][Ns] then lo [2][Ns]
+    __shared__ float s_red[NT / 32];
+    const int ns = p.pr.ns;
+    const int M = p.pr.M;
+    const int m0 = blockIdx.x * E;
+    const int a = blockIdx.y;
+    const int f = blockIdx.z;
+    const int ne = min(E, M - m0);
+    const int64_t S = p.S;
+    int *hi0 = tile, *hi1 = tile + ns, *lo0 = tile + 2 * ns, *lo1 = tile + 3 * ns;
+
+    float amax = 0.0f;
+    for (int64_t s = threadIdx.x; s < S; s += NT) amax = fmaxf(amax, fabsf(amp[s]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    amax = 0.0f;
+    for (int w = 0; w < NT / 32; ++w) amax = fmaxf(amax, s_red[w]);
+    int gexp = 0;
+    if (amax > 0.0f) frexpf(amax, &gexp);
+    const float g = ldexpf(1.0f, -gexp);
+    const float to_fix = g * kFixScale;
+
+    for (int i = threadIdx.x; i < E * ns; i += NT) {
+        int e = i / ns, k = i - e * ns;
+        float v = 0.0f;
+        if (rf_base && e < ne) v = rf_base[((int64_t)a * M + m0 + e) * ns + k];
+        float V = fminf(fmaxf(v * to_fix, -kTapClamp), kTapClamp);
+        const float ht = fmaf(V, 1.0f / 65536.0f, kMagic);
+        const float hb = ht - kMagic;
+        const float lt = fmaf(-hb, 65536.0f, V) + kMagic;
+        tile[e * ns + k] = __float_as_int(ht) - kMagicBits;
+        tile[(2 + e) * ns + k] = __float_as_int(lt) - kMagicBits;
+    }
+    __syncthreads();
+
+    // element centres (float-float) of the pair
+    const int m1c = min(m0 + 1, M - 1);
+    const ff ex0 = fqi::elem_coord(m0 % p.pr.nx, p.pr.nx, p.pr.pitch_x);
+    const ff ex1 = fqi::elem_coord(m1c % p.pr.nx, p.pr.nx, p.pr.pitch_x);
+    const ff ey0 = fqi::elem_coord(m0 / p.pr.nx, p.pr.ny, p.pr.pitch_y);
+    const ff ey1 = fqi::elem_coord(m1c / p.pr.nx, p.pr.ny, p.pr.pitch_y);
+    const f2 EXH = fqi::f2_make(ex0.hi, ex1.hi), EXL = fqi::f2_make(ex0.lo, ex1.lo);
+    const f2 EYH = fqi::f2_make(ey0.hi, ey1.hi), EYL = fqi::f2_make(ey0.lo, ey1.lo);
+    const f2 NEXH = fqi::f2_neg(EXH), NEYH = fqi::f2_neg(EYH);
+    const bool valid1 = ne > 1;
+
+    const fqi::AngleFF an = p.ang[a];
+    const ff ux = fqi::ff_load(an.ux), uy = fqi::ff_load(an.uy), uz = fqi::ff_load(an.uz);
+    const ff org = fqi::ff_load(an.origin);
+    const f2 KH = fqi::f2_dup(p.pr.fs_over_c.hi), KL = fqi::f2_dup(p.pr.fs_over_c.lo);
+    const f2 HALF = fqi::f2_dup(0.5f);
+    const bool matrix = p.pr.ny > 1;
+    const float *X = pos + (int64_t)f * 3 * S;
+    const float *Y = X + S;
+    const float *Z = Y + S;
+    const float half_w = p.half_w;
+    const float thc0 = p.tab_h[0][0], ths0 = p.tab_h[0][1], thc1 = p.tab_h[1][0], ths1 = p.tab_h[1][1];
+    const f2 COSH = fqi::f2_dup(p.cos_h), SINH = fqi::f2_dup(p.sin_h), TWOCOS = fqi::f2_dup(p.two_cos_h);
+
+    for (int64_t s = threadIdx.x; s < S; s += NT) {
+        const float R = amp[s];
+        if (R == 0.0f) continue;
+        const float x = X[s], y = Y[s], z = Z[s];
+        const ff ptx = fqi::ff_dot3_minus(an.ux, an.uy, an.uz, an.origin, x, y, z);
+        const ff zz = fqi::ff_two_prod(z, z);
+        // dx = x - ex for both elements (TwoSum plus the low word)
+        const f2 Xd = fqi::f2_dup(x);
+        const f2 dxh = fqi::f2_sub(Xd, EXH);
+        const f2 bb = fqi::f2_sub(dxh, Xd);
+        const f2 dxl = fqi::f2_sub(fqi::f2_add(fqi::f2_sub(Xd, fqi::f2_sub(dxh, bb)), fqi::f2_sub(NEXH, bb)), EXL);
+        // r^2 = dx^2 + z^2 (+ dy^2), float-float
+        const f2 p2 = fqi::f2_mul(dxh, dxh);
+        f2 lo = fqi::f2_fma(fqi::f2_add(dxh, dxh), dxl, fqi::f2_fma(dxh, dxh, fqi::f2_neg(p2)));
+        const f2 ZZH = fqi::f2_dup(zz.hi);
+        f2 sh2 = fqi::f2_add(p2, ZZH);
+        f2 b2 = fqi::f2_sub(sh2, p2);
+        f2 err = fqi::f2_add(fqi::f2_sub(p2, fqi::f2_sub(sh2, b2)), fqi::f2_sub(ZZH, b2));
+        lo = fqi::f2_add(lo, fqi::f2_dup(zz.lo));
+        f2 dyh = fqi::f2_dup(0.0f);
+        if (matrix || y != 0.0f) {
+            const f2 Yd = fqi::f2_dup(y);
+            dyh = fqi::f2_sub(Yd, EYH);
+            const f2 cy = fqi::f2_sub(dyh, Yd);
+            const f2 dyl = fqi::f2_sub(fqi::f2_add(fqi::f2_sub(Yd, fqi::f2_sub(dyh, cy)), fqi::f2_sub(NEYH, cy)), EYL);
+            const f2 q2 = fqi::f2_mul(dyh, dyh);
+            lo = fqi::f2_add(lo, fqi::f2_fma(fqi::f2_add(dyh, dyh), dyl, fqi::f2_fma(dyh, dyh, fqi::f2_neg(q2))));
+            const f2 t2 = fqi::f2_add(sh2, q2);
+            const f2 b3 = fqi::f2_sub(t2, sh2);
+            lo = fqi::f2_add(lo, fqi::f2_add(fqi::f2_sub(sh2, fqi::f2_sub(t2, b3)), fqi::f2_sub(q2, b3)));
+            sh2 = t2;
+        }
+        lo = fqi::f2_add(lo, err);
+        const f2 r2h = fqi::f2_add(sh2, lo);
+        const f2 r2l = fqi::f2_sub(lo, fqi::f2_sub(r2h, sh2));
+        float q0, q1;
+        fqi::f2_split(r2h, q0, q1);
+        const bool live0 = q0 > 0.0f;
+        const bool live1 = valid1 && q1 > 0.0f;
+        const f2 R2 = fqi::f2_make(live0 ? q0 : 1.0f, live1 ? q1 : 1.0f);
+        const f2 RS = fqi::f2_make(rsqrtf(fqi::f2_lo(R2)), rsqrtf(fqi::f2_hi(R2)));
+        // r = r0 + rl and 1/r from one reciprocal square root per element
+        const f2 r0 = fqi::f2_mul(R2, RS);
+        const f2 rl = fqi::f2_mul(fqi::f2_add(fqi::f2_fma(fqi::f2_neg(r0), r0, R2), r2l), fqi::f2_mul(HALF, RS));
+        // path = ptx + r, u = path fs / c
+        const f2 PH = fqi::f2_dup(ptx.hi);
+        const f2 sp = fqi::f2_add(PH, r0);
+        const f2 b4 = fqi::f2_sub(sp, PH);
+        const f2 pl = fqi::f2_add(fqi::f2_add(fqi::f2_sub(PH, fqi::f2_sub(sp, b4)), fqi::f2_sub(r0, b4)),
+                                  fqi::f2_add(fqi::f2_dup(ptx.lo), rl));
+        const f2 uh = fqi::f2_mul(sp, KH);
+        const f2 ul = fqi::f2_fma(sp, KL, fqi::f2_fma(pl, KH, fqi::f2_fma(sp, KH, fqi::f2_neg(uh))));
+        float uh0, uh1, ul0, ul1;
+        fqi::f2_split(uh, uh0, uh1);
+        fqi::f2_split(ul, ul0, ul1);
+        float fl0 = floorf(uh0), fl1 = floorf(uh1);
+        const f2 FR = fqi::f2_add(fqi::f2_sub(uh, fqi::f2_make(fl0, fl1)), ul);
+        float fr0, fr1;
+        fqi::f2_split(FR, fr0, fr1);
+        if (fr0 < 0.0f) { fr0 += 1.0f; fl0 -= 1.0f; } else if (fr0 >= 1.0f) { fr0 -= 1.0f; fl0 += 1.0f; }
+        if (fr1 < 0.0f) { fr1 += 1.0f; fl1 -= 1.0f; } else if (fr1 >= 1.0f) { fr1 -= 1.0f; fl1 += 1.0f; }
+        // amplitude in fixed-point units
+        float dxh0, dxh1, rs0, rs1, sp0, sp1;
+        fqi::f2_split(dxh, dxh0, dxh1);
+        fqi::f2_split(RS, rs0, rs1);
+        fqi::f2_split(sp, sp0, sp1);
+        float D0 = sinc_f(p.kbx * dxh0 * rs0), D1 = sinc_f(p.kbx * dxh1 * rs1);
+        if (matrix) {
+            float dy0, dy1;
+            fqi::f2_split(dyh, dy0, dy1);
+            D0 *= sinc_f(p.kby * dy0 * rs0);
+            D1 *= sinc_f(p.kby * dy1 * rs1);
+        }
+        const float Rfix = R * to_fix;
+        f2 A2 = fqi::f2_mul(fqi::f2_mul(fqi::f2_dup(Rfix), fqi::f2_make(D0, D1)),
+                            fqi::f2_mul(fqi::f2_make(__expf(-p.att * sp0), __expf(-p.att * sp1)), RS));
+        {  // one clamp per pair bounds every tap (|p| <= 1)
+            float a0_, a1_;
+            fqi::f2_split(A2, a0_, a1_);
+            a0_ = live0 ? fminf(fmaxf(a0_, -kTapClamp), kTapClamp) : 0.0f;
+            a1_ = live1 ? fminf(fmaxf(a1_, -kTapClamp), kTapClamp) : 0.0f;
+            A2 = fqi::f2_make(a0_, a1_);
+        }
+        const int jlo0 = (int)ceilf(fr0 - half_w), jlo1 = (int)ceilf(fr1 - half_w);
+        const int nt0 = (int)floorf(fr0 + half_w) - jlo0 + 1, nt1 = (int)floorf(fr1 + half_w) - jlo1 + 1;
+        const int k0 = (int)fl0 + jlo0, k1 = (int)fl1 + jlo1;
+        float ch0, sh0, ch1, sh1;
+        first_tap(p.w_h, fr0, thc0, ths0, thc1, ths1, jlo0 != p.jmin, ch0, sh0);
+        first_tap(p.w_h, fr1, thc0, ths0, thc1, ths1, jlo1 != p.jmin, ch1, sh1);
+        const f2 CH = fqi::f2_make(ch0, ch1), SH = fqi::f2_make(sh0, sh1);
+        f2 C0 = CH;
+        f2 C1 = fqi::f2_fma(CH, COSH, fqi::f2_neg(fqi::f2_mul(SH, SINH)));
+        const f2 hA = fqi::f2_mul(HALF, A2);
+        const bool in0 = live0 && k0 >= 0 && k0 + nt0 <= ns;
+        const bool in1 = live1 && k1 >= 0 && k1 + nt1 <= ns;
+        if ((in0 || !live0) && (in1 || !live1)) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                add_fixed2(hi0, lo0, hi1, lo1, k0 + j, k1 + j, tap2x2(A2, hA, C0), live0, live1);
+                const f2 C2 = fqi::f2_fma(TWOCOS, C1, fqi::f2_neg(C0));
+                C0 = C1;
+                C1 = C2;
+            }
+            if (nt0 > 8 || nt1 > 8)
+                add_fixed2(hi0, lo0, hi1, lo1, k0 + 8, k1 + 8, tap2x2(A2, hA, C0), live0 && nt0 > 8,
+                           live1 && nt1 > 8);
+        } else {
+            // an echo straddles a record end: per-tap bounds
+            for (int j = 0; j < 9; ++j) {
+                const int ka = k0 + j, kb = k1 + j;
+                const bool oa = live0 && j < nt0 && ka >= 0 && ka < ns;
+                const bool ob = live1 && j < nt1 && kb >= 0 && kb < ns;
+                add_fixed2(hi0, lo0, hi1, lo1, oa ? ka : 0, ob ? kb : 0, tap2x2(A2, hA, C0), oa, ob);
+                const f2 C2 = fqi::f2_fma(TWOCOS, C1, fqi::f2_neg(C0));
+                C0 = C1;
+                C1 = C2;
+            }
+        }
+    }
+    __syncthreads();
+    const float from_fix = 1.0f / to_fix;
+    OutT *out = rf + (((int64_t)f * p.A + a) * M + m0) * ns;
+    for (int i = threadIdx.x; i < ne * ns; i += NT)
+        fqi::store_f(out, i, fmaf((float)tile[i], 65536.0f, (float)tile[2 * ns + i]) * from_fix);
+}
+
+template <typename OutT>
+fq_status launch_rf_pair(const RfParams &p, int F, const float *pos, const float *amp, const float *base, OutT *rf,
+                         cudaStream_t st)
+{
+    constexpr int NT = 256;
+    size_t smem = 4 * sizeof(int) * (size_t)p.pr.ns;
+    static int minb = -1;
+    if (minb < 0) {
+        const char *env = std::getenv("FQ_RF_MINB");
+        minb = (env && env[0] == '2') ? 2 : 3;
+    }
+    auto kern = minb == 3 ? rf_synth_pair_kernel<NT, 3, OutT> : rf_synth_pair_kernel<NT, 2, OutT>;
+    fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                                  "fq_simulate_rf: smem attribute");
+    if (s) return s;
+    dim3 grid((p.pr.M + 1) / 2, p.A, F);
+    kern<<<grid, NT, smem, st>>>(p, pos, amp, base, rf);
+    return fqi::launch_check("fq_simulate_rf");
+}
+
 template <int E, typename OutT>
 fq_status launch_rf(const RfParams &p, int F, const float *pos, const float *amp, const float *base,
                     OutT *rf, cudaStream_t st)
@@ -321,6 +567,14 @@ template <typename OutT>
 fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *amp, const float *base,
                       OutT *rf, cudaStream_t st)
 {
+    static int scalar_only = -1;
+    if (scalar_only < 0) {
+        const char *env = std::getenv("FQ_RF_SCALAR");
+        scalar_only = env && env[0] == '1';
+    }
+    // the common pulse (two cycles, <= 9 taps) runs on the packed-pair kernel
+    if (!scalar_only && p.two_cycle && p.ntap_max <= 9 && 4 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
+        return launch_rf_pair(p, F, pos, amp, base, rf, st);
     switch (rf_elems(p.pr.ns)) {
     case 16: return launch_rf<16>(p, F, pos, amp, base, rf, st);
     case 8: return launch_rf<8>(p, F, pos, amp, base, rf, st);

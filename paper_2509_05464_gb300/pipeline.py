@@ -137,6 +137,8 @@ class Pipeline:
     @property
     def n_launches(self) -> int:
         """Kernels of libfq one step launches: classify and advect per
-        population, RF (1 or 2), rf2iq, DAS, Gram (2), eig, projection."""
+        population, RF (1 or 2), rf2iq, DAS, Gram (2 on the CUDA cores;
+        transpose, MMA and reduce on the tensor cores), eig, projection."""
         n = len(self.pops)
-        return n + n + (2 if self.static else 1) + 2 + 2 + 1 + 1
+        gram = 2 if self.gram_mode == fq.FQ_GRAM_F32 else 3
+        return n + n + (2 if self.static else 1) + 2 + gram + 1 + 1

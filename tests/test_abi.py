@@ -56,8 +56,17 @@ def test_argument_validation_without_gpu(libfq):
     assert libfq.fq_clutter_svd(C.c_void_p(256), 0, 100, 8, 9, 0.9, 0, None, None, None, None,
                                 C.c_void_p(256), n.value, None) == 1
     assert libfq.fq_bin_scatterers(None, 10, 0.0, 1e-4, 0, None, None, None, 0, None) == 2
-    assert libfq.fq_casorati_gram(C.c_void_p(256), 0, 100, 8, 1, C.c_void_p(256), C.c_void_p(256), 1 << 20,
-                                  None) == 8
+    # unknown gram_mode; the tensor-core modes size their own scratch
+    assert libfq.fq_casorati_gram(C.c_void_p(256), 0, 100, 8, 7, C.c_void_p(256), C.c_void_p(256), 1 << 20,
+                                  None) == 1
+    sizes = []
+    for mode in (0, 1, 2):
+        assert libfq.fq_gram_workspace_size(65536, 200, mode, C.byref(n)) == 0
+        sizes.append(n.value)
+    # BF16 operands take half the bytes of TF32 ones; 2F x P operand copy at least
+    assert sizes[2] >= 400 * 65536 * 2 and sizes[1] >= 400 * 65536 * 4 and sizes[1] > sizes[2]
+    assert libfq.fq_gram_workspace_size(65536, 200, 3, C.byref(n)) == 1
+    assert libfq.fq_clutter_svd_workspace_size(65536, 200, 2, C.byref(n)) == 0 and n.value > sizes[2]
 
 
 def test_binding_fails_loudly_without_library(monkeypatch):

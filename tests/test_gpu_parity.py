@@ -262,6 +262,80 @@ def test_gram_parity(P, F):
     assert np.abs(G - want).max() <= 1e-5 * np.abs(want).max()
 
 
+def _round_bf16(x):
+    """binary32 -> bfloat16, round to nearest even (as float64)."""
+    return torch.from_numpy(np.asarray(x, np.float32)).bfloat16().double().numpy()
+
+
+def _round_tf32(x):
+    """binary32 -> TF32 (10 explicit mantissa bits), round to nearest with
+    ties away from zero, as the operand conversion cvt.rna.tf32.f32 does."""
+    b = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x1000) & 0xFFFFE000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _round_c(S, mode):
+    r = _round_bf16 if mode == fq.FQ_GRAM_BF16 else _round_tf32
+    return r(S.real) + 1j * r(S.imag)
+
+
+def test_operand_rounding_helpers():
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -11), 1.0 + 2.0 ** -11 + 2.0 ** -20])
+    assert list(_round_bf16(x)) == [1.0, 1.0, 1.0 + 2.0 ** -6, -(1.0 + 2.0 ** -11) + 2.0 ** -11, 1.0]
+    assert list(_round_tf32(x)) == [1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -10),
+                                    1.0 + 2.0 ** -10]
+
+
+@pytest.mark.parametrize("mode", [2, 1], ids=["bf16", "tf32"])
+@pytest.mark.parametrize("P,F", [(3000, 10), (3001, 64), (2048, 200), (100, 2), (5000, 300), (64, 512),
+                                 (40000, 33)])
+def test_gram_tensor_core_parity(mode, P, F):
+    """tcgen05 Gram: the exact Gram of the operand-rounded input (products of
+    BF16 / TF32 operands are exact in FP32), up to FP32 accumulation."""
+    rng = np.random.default_rng(P * F + mode)
+    S = (rng.standard_normal((P, F)) + 1j * rng.standard_normal((P, F))).astype(np.complex64).astype(np.complex128)
+    ws = fq.workspace(fq.fq_gram_workspace_size(P, F, mode), torch.device("cuda"))
+    G = cplx(fq.fq_casorati_gram(cdev(S), gram_mode=mode, ws=ws))
+    fq.fq_clutter_status(ws)  # no timed-out wait
+    want = oracle.gram(_round_c(S, mode))
+    assert np.abs(G - want).max() <= 1e-5 * np.abs(want).max()
+    off = G - np.diag(np.diag(G))
+    assert np.array_equal(off, off.conj().T)  # lower triangle is the conjugate of the upper
+
+
+def test_gram_tensor_core_bf16_input():
+    rng = np.random.default_rng(77)
+    S = rng.standard_normal((5000, 96)) + 1j * rng.standard_normal((5000, 96))
+    Sb = cdev(S).bfloat16()
+    Sq = cplx(Sb)
+    for mode in (fq.FQ_GRAM_BF16, fq.FQ_GRAM_TF32):
+        G = cplx(fq.fq_casorati_gram(Sb, gram_mode=mode))
+        want = oracle.gram(Sq)
+        assert np.abs(G - want).max() <= 1e-5 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("mode", [2, 1], ids=["bf16", "tf32"])
+def test_clutter_svd_tensor_core_gram(mode):
+    """The whole filter with the tensor-core Gram on FP32 input.  Rounding
+    the Gram operand moves the clutter subspace; the tolerance adds to
+    PD_TOL four times the PD change that this rounding alone causes in exact
+    arithmetic (eigh of the FP64 Gram of the rounded input, FP64 projection
+    of the unrounded one)."""
+    k = 3
+    S = _clutter(4096, 32, k, seed=11).astype(np.complex64).astype(np.complex128)
+    r = fq.fq_clutter_svd(cdev(S), k_cut=k, gram_mode=mode)
+    fq.fq_clutter_status(r["ws"])
+    _, pd, sg, _ = oracle.svd_filter(S, k_cut=k)
+    _, Vq = np.linalg.eigh(oracle.gram(_round_c(S, mode)))
+    Vk = Vq[:, ::-1][:, :k]
+    pd_q = np.mean(np.abs(S - (S @ Vk) @ Vk.conj().T) ** 2, axis=1)
+    tol = PD_TOL + 4 * rel_l2(pd_q, pd)
+    assert rel_l2(host(r["pd"]), pd) <= tol
+    sq = np.linalg.svd(_round_c(S, mode), compute_uv=False)
+    assert np.abs(host(r["eigvals"]) - sq ** 2).max() <= 2e-6 * sq[0] ** 2
+
+
 @pytest.mark.parametrize("P,F,k", [(2000, 48, 3), (3000, 200, 2), (64, 8, 1), (50, 3, 1)])
 def test_eig_against_oracle_svd(P, F, k):
     S = _clutter(P, F, k, seed=F).astype(np.complex64).astype(np.complex128)
