@@ -147,23 +147,90 @@ def sum_over_ranks(x: float) -> float:
 
 
 # ---------------------------------------------------------------- oracle --
-def oracle_step(w, n_frames):
-    """The oracle through the whole path on the first n_frames frames."""
+def oracle_run(w, n_frames):
+    """The oracle through the whole path on the first n_frames frames:
+    (seconds, results)."""
     import oracle
     from paper_2509_05464_gb300 import workload as W
     st, mt = W.segment_table(w), W.motion_table(w.motion)
     t0 = time.perf_counter()
-    oracle.pipeline(w, st, mt, n_frames=n_frames, k_cut=min(w.k_cut, n_frames - 1))
-    return time.perf_counter() - t0
+    r = oracle.pipeline(w, st, mt, n_frames=n_frames, k_cut=min(w.k_cut, n_frames - 1))
+    return time.perf_counter() - t0, r
+
+
+def oracle_step(w, n_frames):
+    return oracle_run(w, n_frames)[0]
 
 
 def cpu_baseline(w, n_frames=6):
     import oracle
-    dt = oracle_step(w, n_frames)
+    dt, r = oracle_run(w, n_frames)
     cs = n_frames * w.A * w.M * w.Ns
     return {"value": cs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"whole path (advect, membership, RF, rf2iq, DAS, SVD filter, PD) on the first {n_frames} "
-                      f"of {w.n_frames} frames of the same workload, FP64, {dt:.1f} s"}
+                      f"of {w.n_frames} frames of the same workload, FP64, {dt:.1f} s"}, r
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# Precision variants of the path: (name, RF storage, channel IQ, Casorati, Gram)
+VARIANTS = [("f32", "float32", "float32", "float32", "f32"),
+            ("f32+tf32_gram", "float32", "float32", "float32", "tf32"),
+            ("f32+bf16_gram", "float32", "float32", "float32", "bf16"),
+            ("bf16", "bfloat16", "bfloat16", "bfloat16", "bf16")]
+
+
+def precision_variants(w, ref, n_ref, steps, warmup):
+    """Each variant on the full workload (device-timed step) and its error vs
+    the FP64 oracle: RF and Casorati IQ on the first n_ref frames of the full
+    run, PD of an n_ref-frame ensemble of the same workload."""
+    import dataclasses
+    import torch
+    from paper_2509_05464_gb300 import fq
+    from paper_2509_05464_gb300.pipeline import Pipeline
+    gmode = {"f32": fq.FQ_GRAM_F32, "tf32": fq.FQ_GRAM_TF32, "bf16": fq.FQ_GRAM_BF16}
+    w_small = dataclasses.replace(w, n_frames=n_ref, k_cut=min(w.k_cut, n_ref - 1))
+    S_ref = ref["S"]
+    out = []
+    stream = torch.cuda.current_stream()
+    for name, rf_t, ch_t, iq_t, gm in VARIANTS:
+        kw = dict(rf_dtype=getattr(torch, rf_t), ch_dtype=getattr(torch, ch_t), iq_dtype=getattr(torch, iq_t),
+                  gram_mode=gmode[gm])
+        pl = Pipeline(w, **kw)
+        pl.upload()
+        for _ in range(warmup):
+            pl.step()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(steps):
+            pl.step()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        fq.fq_clutter_status(pl.ws_svd)
+        ms = ev[0].elapsed_time(ev[1]) / steps
+        rf = pl.rf[:n_ref].float().cpu().numpy()
+        iq = pl.iq[:, :n_ref].float().cpu().numpy()
+        iq_c = iq[..., 0] + 1j * iq[..., 1]
+        del pl
+        ps = Pipeline(w_small, **kw)
+        ps.upload()
+        ps.step()
+        fq.fq_clutter_status(ps.ws_svd)
+        pd = ps.download().numpy().copy()
+        del ps
+        out.append({"variant": name, "rf": rf_t, "channel_iq": ch_t, "casorati": iq_t, "gram": gm,
+                    "ms_per_step": ms,
+                    "err_vs_fp64": {"rf_rel_l2": rel_l2(rf, ref["rf"]),
+                                    "iq_rel_l2": rel_l2(np.stack([iq_c.real, iq_c.imag]),
+                                                        np.stack([S_ref.real, S_ref.imag])),
+                                    "pd_rel_l2": rel_l2(pd, ref["pd"])}})
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args, rank, world):
@@ -243,6 +310,7 @@ def run_ours(args, rank, world, local):
     e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2) / args.steps)
     fq.fq_clutter_status(pl.ws_svd)
 
+    n_launches, h2d_bytes, d2h_bytes = pl.n_launches, pl.h2d_bytes, pl.d2h_bytes
     total_cs = sum_over_ranks(float(pl.channel_samples))
     total_va = sum_over_ranks(float(pl.voxel_angles))
     if rank != 0:
@@ -255,7 +323,12 @@ def run_ours(args, rank, world, local):
     pairs = w.n_frames * w.A * w.M * w.S
     flop = pairs * (GEOM_FLOP_PER_PAIR + FLOP_PER_TAP * taps)
     achieved = flop / (rf_avg * 1e-3) / 1e12
-    cpu = cpu_baseline(w) if args.cpu_baseline else None
+    cpu, ref = cpu_baseline(w) if args.cpu_baseline else (None, None)
+    variants = None
+    if ref is not None and args.variants:
+        del pl, flush
+        torch.cuda.empty_cache()
+        variants = precision_variants(w, ref, 6, steps=3, warmup=2)
     line = {
         "metric": METRIC, "value": total_cs / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -266,16 +339,18 @@ def run_ours(args, rank, world, local):
                    "l2": "256 MiB buffer rewritten between timed steps, outside the timed events"},
         "das_voxel_angle_per_s": total_va / (ms * 1e-3),
         "stage_ms": stage_ms,
-        "roofline": {"bound": "alu", "kernel": "rf_synth_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "alu", "kernel": "rf_synth_pair_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
                                     f"({src} max clock)",
                      "work": f"{GEOM_FLOP_PER_PAIR:.0f} + {FLOP_PER_TAP:.0f} x {taps:.3f} taps FLOP per pair, "
                              f"{pairs:.3e} pairs"},
         "cpu_baseline": cpu,
-        "e2e": {"value": total_cs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": pl.h2d_bytes,
-                "d2h_bytes_per_step": pl.d2h_bytes, "ms_per_step": e2e_ms},
-        "gpu_launches": pl.n_launches * args.steps,
+        "e2e": {"value": total_cs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
+                "d2h_bytes_per_step": d2h_bytes, "ms_per_step": e2e_ms},
+        "err_vs_fp64": variants[0]["err_vs_fp64"] if variants else None,
+        "precision_variants": variants,
+        "gpu_launches": n_launches * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -288,6 +363,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the precision variants (each is checked against the oracle)")
     ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
