@@ -367,6 +367,121 @@ fq_status fq_power_doppler(const void *iq_f, int32_t dtype, int64_t P, int32_t F
  * `stream`. */
 fq_status fq_clutter_status(void *workspace, void *stream);
 
+/* sizeof of the ABI's structs as this library was compiled, for bindings
+ * that check their own layouts: 0 fq_probe, 1 fq_tx, 2 fq_grid,
+ * 3 fq_segment, 4 fq_flow, 5 fq_motion, 6 fq_ensemble_desc,
+ * 7 fq_tile_choice; 0 for any other index.  The paper has no counterpart. */
+size_t fq_sizeof(int32_t which);
+
+/* ------------------------------------------------------------------ */
+/* a11: many uneven ensembles in one persistent kernel per stage        */
+/* ------------------------------------------------------------------ */
+/* The paper simulates its ensembles one after another and processes each
+ * in chunks (Alg. 2-3); a batch instead puts the work items of all its
+ * ensembles into one queue per stage.  One persistent kernel per stage
+ * takes items from that queue (an atomic counter), most expensive
+ * ensembles first, and runs the same tile code as the single-ensemble
+ * calls above, so every ensemble's result equals what fq_classify_scatterers
+ * -> fq_advect_scatterers -> fq_simulate_rf -> fq_beamform_das ->
+ * fq_clutter_svd (gram_mode FQ_GRAM_F32) give for it.  A stage's queue
+ * covers one wave of ensembles: the plan groups ensembles into waves whose
+ * scratch (positions, RF, channel IQ, Casorati matrix, clutter workspace)
+ * fits the arena budget and runs the waves in turn. */
+
+/* One ensemble: host descriptions read by fq_batch_plan, device pointers
+ * read by the kernels.  Requirements: two-cycle pulse with
+ * n_cycles fs / f0 <= 9 samples, n_samples <= 8192, 2 <= n_frames <= 512,
+ * element count <= 4096, S >= 1. */
+typedef struct fq_ensemble_desc {
+    fq_probe probe;
+    fq_tx tx;                   /* host arrays */
+    fq_grid grid;
+    fq_flow flow;               /* host segment array */
+    fq_motion motion;
+    int64_t S;                  /* scatterers */
+    int32_t n_frames;           /* F */
+    double t0, dt;              /* frame f is at time t0 + f dt */
+    int32_t k_cut;              /* as fq_clutter_svd */
+    double energy_thresh;
+    const float *p0;            /* device [3][S] */
+    const int32_t *seg_id;      /* device [S] */
+    const float *flow_coord;    /* device [3][S] */
+    const float *amp;           /* device [S] */
+    float *pd;                  /* device [P] output: power Doppler */
+    double *eigvals;            /* device [F] output, nullable */
+    int32_t *k_used;            /* device [1] output, nullable */
+} fq_ensemble_desc;
+
+typedef struct fq_batch fq_batch;  /* opaque plan (host memory) */
+typedef struct fq_graph fq_graph;  /* opaque captured batch */
+
+enum { FQ_OP_RF = 0, FQ_OP_DAS = 1 };
+
+/* A tile shape the autotuner chose for one stage.
+ *   FQ_OP_RF : choice = minimum resident CTAs per SM of the RF kernel
+ *              (2 or 3; sets its register budget)
+ *   FQ_OP_DAS: choice = threads per DAS CTA (64, 128 or 256) */
+typedef struct fq_tile_choice {
+    int32_t op;
+    int32_t choice;
+    int32_t n_tried;
+    int32_t tried[4];           /* the candidates, in the order timed */
+    float tried_ms[4];          /* their device times (ms) */
+    float ms;                   /* time of the chosen one */
+} fq_tile_choice;
+
+/* Plan a batch of n >= 1 ensembles (host only, no CUDA call).
+ *   rf_dtype, ch_dtype, iq_dtype  FQ_F32 / FQ_BF16 storage of the RF, the
+ *       channel IQ and the Casorati matrix
+ *   max_arena_bytes  budget for the arena; 0 = no budget (one wave).  An
+ *       ensemble that alone exceeds the budget gets a wave of its own.
+ *   *arena_bytes  receives the size of the arena fq_batch_launch needs
+ *       (256-byte aligned device memory the caller owns).
+ * Errors: FQ_ERR_INVALID_ARG / FQ_ERR_SHAPE / FQ_ERR_UNSUPPORTED naming
+ * the first bad ensemble. */
+fq_status fq_batch_plan(const fq_ensemble_desc *ens, int32_t n, int32_t rf_dtype, int32_t ch_dtype,
+                        int32_t iq_dtype, size_t max_arena_bytes, fq_batch **plan, size_t *arena_bytes);
+
+/* Plan facts: waves, and work items per stage (9 stages: classify, advect,
+ * RF, rf2iq, DAS, Gram, Gram reduce, eigen-solver, projection). */
+fq_status fq_batch_info(const fq_batch *plan, int32_t *n_waves, int64_t items[9]);
+
+/* Use a tile choice (from fq_autotune) for every wave of the plan. */
+fq_status fq_batch_set_tile(fq_batch *plan, const fq_tile_choice *choice);
+
+/* Enqueue the whole batch on `stream`: the plan's tables are copied into
+ * the arena (synchronously, the first time this arena is used with this
+ * plan), then per wave one persistent kernel per stage.  Outputs are valid
+ * once the stream reaches the end of the call.  The arena holds a status
+ * word per ensemble; fq_batch_status reads them. */
+fq_status fq_batch_launch(fq_batch *plan, void *arena, size_t arena_bytes, void *stream);
+
+/* Reads (and clears) every ensemble's device status word; synchronises the
+ * stream.  Returns the first non-OK status with the ensemble index in the
+ * message. */
+fq_status fq_batch_status(fq_batch *plan, void *arena, void *stream);
+
+void fq_batch_free(fq_batch *plan);
+
+/* Plan + launch + free in one call (arena sized by a previous plan). */
+fq_status fq_run_batched(const fq_ensemble_desc *ens, int32_t n, int32_t dtype, void *arena, size_t arena_bytes,
+                         void *stream);
+
+/* Capture a planned batch on this arena into a CUDA graph (the tables are
+ * uploaded first, outside the capture), and replay it.  The graph keeps
+ * the arena pointer and the descriptors' device pointers: they must stay
+ * valid while the graph is used.  Replays on one arena must not overlap. */
+fq_status fq_graph_capture(fq_batch *plan, void *arena, size_t arena_bytes, fq_graph **graph);
+fq_status fq_graph_launch(fq_graph *graph, void *stream);
+void fq_graph_free(fq_graph *graph);
+
+/* Autotuner: time every candidate tile shape of `op` on one ensemble (its
+ * batch of one, on this arena), keep the fastest.  Results are cached per
+ * (op, probe, frames, scatterers, grid) in the process; a cached answer is
+ * returned without timing (out->n_tried = 0).  Synchronises `stream`. */
+fq_status fq_autotune(int32_t op, const fq_ensemble_desc *ens, int32_t rf_dtype, void *arena, size_t arena_bytes,
+                      fq_tile_choice *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

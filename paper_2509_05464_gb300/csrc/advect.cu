@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "batch.cuh"
 #include "fq_internal.cuh"
 
 namespace {
@@ -85,6 +86,50 @@ __device__ void frame_constants(const MotionParams &mp, double t, FrameConst &fc
     }
 }
 
+// Position of scatterer s at the frame time of fc (written to o[d * S + s]).
+__device__ __forceinline__ void advect_point(const float *__restrict__ p0, const int32_t *__restrict__ seg,
+                                             const float *__restrict__ flow, int64_t S, int64_t s,
+                                             const SegTable &st, const MotionParams &mp, const FrameConst &fc,
+                                             float *__restrict__ o)
+{
+    const double t = fc.t;
+    double P[3];
+    int si = seg[s];
+    if (si < 0 || si >= st.n) {
+        P[0] = p0[s];
+        P[1] = p0[S + s];
+        P[2] = p0[2 * S + s];
+    } else {
+        const double *sg = st.t[si];
+        double q = flow[s], x1 = flow[S + s], x2 = flow[2 * S + s];
+        double R = sg[14];
+        double v = sg[15] * (1.0 - (x1 * x1 + x2 * x2) / (R * R));
+        if ((int)sg[0] == FQ_SEG_LINE) {
+            double a = wrap_into(q + v * t, sg[13]);
+            for (int d = 0; d < 3; ++d)
+                P[d] = sg[1 + d] + a * sg[4 + d] + x1 * sg[7 + d] + x2 * sg[10 + d];
+        } else {
+            double phi = wrap_into(q + v * t / sg[16], sg[17]);
+            double cp = cos(phi), sp = sin(phi), rr = sg[16] + x1;
+            for (int d = 0; d < 3; ++d)
+                P[d] = sg[1 + d] + rr * (cp * sg[4 + d] + sp * sg[7 + d]) + x2 * sg[10 + d];
+        }
+    }
+    double Q0 = P[0], Q1 = P[1], Q2 = P[2];
+    if (fc.wn > 0.0) {
+        const double *cr = mp.cr;
+        double w0 = P[0] - cr[0], w1 = P[1] - cr[1], w2 = P[2] - cr[2];
+        double kw = fc.kx * w0 + fc.ky * w1 + fc.kz * w2;
+        double c0 = fc.ky * w2 - fc.kz * w1, c1 = fc.kz * w0 - fc.kx * w2, c2 = fc.kx * w1 - fc.ky * w0;
+        double omc = 1.0 - fc.ct;
+        P[0] = cr[0] + w0 * fc.ct + c0 * fc.st + fc.kx * kw * omc;
+        P[1] = cr[1] + w1 * fc.ct + c1 * fc.st + fc.ky * kw * omc;
+        P[2] = cr[2] + w2 * fc.ct + c2 * fc.st + fc.kz * kw * omc;
+    }
+    double gain = 1.0 + (mp.g[0] * (Q0 - mp.ce[0]) + mp.g[1] * (Q1 - mp.ce[1]) + mp.g[2] * (Q2 - mp.ce[2]));
+    for (int d = 0; d < 3; ++d) o[d * S + s] = (float)(P[d] + mp.vel[d] * t + gain * fc.dsum[d]);
+}
+
 __global__ void advect_kernel(const float *__restrict__ p0, const int32_t *__restrict__ seg,
                               const float *__restrict__ flow, int64_t S, const SegTable st,
                               const MotionParams mp, double t0, double dt,
@@ -94,46 +139,10 @@ __global__ void advect_kernel(const float *__restrict__ p0, const int32_t *__res
     const int f = blockIdx.y;
     if (threadIdx.x == 0) frame_constants(mp, t0 + (double)f * dt, fc);
     __syncthreads();
-    const double t = fc.t;
     float *o = out + (int64_t)f * 3 * S;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        double P[3];
-        int si = seg[s];
-        if (si < 0 || si >= st.n) {
-            P[0] = p0[s];
-            P[1] = p0[S + s];
-            P[2] = p0[2 * S + s];
-        } else {
-            const double *sg = st.t[si];
-            double q = flow[s], x1 = flow[S + s], x2 = flow[2 * S + s];
-            double R = sg[14];
-            double v = sg[15] * (1.0 - (x1 * x1 + x2 * x2) / (R * R));
-            if ((int)sg[0] == FQ_SEG_LINE) {
-                double a = wrap_into(q + v * t, sg[13]);
-                for (int d = 0; d < 3; ++d)
-                    P[d] = sg[1 + d] + a * sg[4 + d] + x1 * sg[7 + d] + x2 * sg[10 + d];
-            } else {
-                double phi = wrap_into(q + v * t / sg[16], sg[17]);
-                double cp = cos(phi), sp = sin(phi), rr = sg[16] + x1;
-                for (int d = 0; d < 3; ++d)
-                    P[d] = sg[1 + d] + rr * (cp * sg[4 + d] + sp * sg[7 + d]) + x2 * sg[10 + d];
-            }
-        }
-        double Q0 = P[0], Q1 = P[1], Q2 = P[2];
-        if (fc.wn > 0.0) {
-            const double *cr = mp.cr;
-            double w0 = P[0] - cr[0], w1 = P[1] - cr[1], w2 = P[2] - cr[2];
-            double kw = fc.kx * w0 + fc.ky * w1 + fc.kz * w2;
-            double c0 = fc.ky * w2 - fc.kz * w1, c1 = fc.kz * w0 - fc.kx * w2, c2 = fc.kx * w1 - fc.ky * w0;
-            double omc = 1.0 - fc.ct;
-            P[0] = cr[0] + w0 * fc.ct + c0 * fc.st + fc.kx * kw * omc;
-            P[1] = cr[1] + w1 * fc.ct + c1 * fc.st + fc.ky * kw * omc;
-            P[2] = cr[2] + w2 * fc.ct + c2 * fc.st + fc.kz * kw * omc;
-        }
-        double gain = 1.0 + (mp.g[0] * (Q0 - mp.ce[0]) + mp.g[1] * (Q1 - mp.ce[1]) + mp.g[2] * (Q2 - mp.ce[2]));
-        for (int d = 0; d < 3; ++d) o[d * S + s] = (float)(P[d] + mp.vel[d] * t + gain * fc.dsum[d]);
-    }
+         s += (int64_t)gridDim.x * blockDim.x)
+        advect_point(p0, seg, flow, S, s, st, mp, fc, o);
 }
 
 // ------------------------------------------------------------ membership --
@@ -157,20 +166,89 @@ __device__ __forceinline__ bool inside_seg(const double *sg, double px, double p
     return (rin * rin + x3 * x3) < R2;
 }
 
+__device__ __forceinline__ void classify_point(const float *__restrict__ pos, const int32_t *__restrict__ seg,
+                                               int64_t S, int64_t s, const SegTable &st,
+                                               const float *__restrict__ amp_in, int32_t *__restrict__ vessel,
+                                               float *__restrict__ amp_out)
+{
+    int v = seg[s];
+    if (v < 0) {
+        double px = pos[s], py = pos[S + s], pz = pos[2 * S + s];
+        for (int i = 0; i < st.n; ++i)
+            if (inside_seg(st.t[i], px, py, pz)) { v = i; break; }
+    }
+    vessel[s] = v;
+    if (amp_out) amp_out[s] = (seg[s] < 0 && v >= 0) ? 0.0f : amp_in[s];
+}
+
 __global__ void classify_kernel(const float *__restrict__ pos, const int32_t *__restrict__ seg,
                                 int64_t S, const SegTable st, const float *__restrict__ amp_in,
                                 int32_t *__restrict__ vessel, float *__restrict__ amp_out)
 {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        int v = seg[s];
-        if (v < 0) {
-            double px = pos[s], py = pos[S + s], pz = pos[2 * S + s];
-            for (int i = 0; i < st.n; ++i)
-                if (inside_seg(st.t[i], px, py, pz)) { v = i; break; }
-        }
-        vessel[s] = v;
-        if (amp_out) amp_out[s] = (seg[s] < 0 && v >= 0) ? 0.0f : amp_in[s];
+         s += (int64_t)gridDim.x * blockDim.x)
+        classify_point(pos, seg, S, s, st, amp_in, vessel, amp_out);
+}
+
+// ----------------------------------------------------------- batched --
+// Items of fqb::kItemScat scatterers (classify: one item per chunk; advect:
+// one per (chunk, frame)).
+using fqb::kItemScat;
+constexpr int kBatchThreads = 256;
+
+__global__ void __launch_bounds__(kBatchThreads) classify_batched_kernel(const fqb::EnsDev *__restrict__ ens,
+                                                                         const fqb::StageQueue q)
+{
+    __shared__ int s_buf[2];
+    fqb::Item it;
+    while (fqb::next_item(q, ens, fqb::ST_CLASSIFY, s_buf, it)) {
+        const fqb::EnsDev &e = ens[it.e];
+        const SegTable &st = *reinterpret_cast<const SegTable *>(e.seg_table);
+        const int64_t beg = (int64_t)it.x * kItemScat;
+        const int64_t end = beg + kItemScat < e.S ? beg + kItemScat : e.S;
+        for (int64_t s = beg + threadIdx.x; s < end; s += blockDim.x)
+            classify_point(e.p0, e.seg, e.S, s, st, e.amp, e.vessel, e.amp_eff);
+    }
+}
+
+__global__ void __launch_bounds__(kBatchThreads) advect_batched_kernel(const fqb::EnsDev *__restrict__ ens,
+                                                                       const fqb::StageQueue q)
+{
+    __shared__ int s_buf[2];
+    __shared__ FrameConst fc;
+    fqb::Item it;
+    while (fqb::next_item(q, ens, fqb::ST_ADVECT, s_buf, it)) {
+        const fqb::EnsDev &e = ens[it.e];
+        const SegTable &st = *reinterpret_cast<const SegTable *>(e.seg_table);
+        const MotionParams &mp = *reinterpret_cast<const MotionParams *>(e.motion);
+        const int f = it.y;
+        if (threadIdx.x == 0) frame_constants(mp, e.t0 + (double)f * e.dt, fc);
+        __syncthreads();
+        float *o = e.pos + (int64_t)f * 3 * e.S;
+        const int64_t beg = (int64_t)it.x * kItemScat;
+        const int64_t end = beg + kItemScat < e.S ? beg + kItemScat : e.S;
+        for (int64_t s = beg + threadIdx.x; s < end; s += blockDim.x)
+            advect_point(e.p0, e.seg, e.flow, e.S, s, st, mp, fc, o);
+    }
+}
+
+void pack_motion(const fq_motion *motion, MotionParams &mp)
+{
+    std::memset(&mp, 0, sizeof mp);
+    if (!motion) return;
+    mp.n_terms = motion->n_terms;
+    for (int j = 0; j < 4; ++j) {
+        mp.amp[j] = motion->amp[j];
+        mp.freq[j] = motion->freq[j];
+        mp.phase[j] = motion->phase[j];
+        for (int d = 0; d < 3; ++d) mp.dir[j][d] = motion->dir[j][d];
+    }
+    for (int d = 0; d < 3; ++d) {
+        mp.g[d] = motion->elastic_grad[d];
+        mp.ce[d] = motion->elastic_center[d];
+        mp.vel[d] = motion->vel[d];
+        mp.omega[d] = motion->omega[d];
+        mp.cr[d] = motion->rot_center[d];
     }
 }
 
@@ -292,23 +370,7 @@ fq_status fq_advect_scatterers(const float *p0, const int32_t *seg_id, const flo
     SegTable local;
     pack_segments(flow, local);
     MotionParams mp;
-    std::memset(&mp, 0, sizeof mp);
-    if (motion) {
-        mp.n_terms = motion->n_terms;
-        for (int j = 0; j < 4; ++j) {
-            mp.amp[j] = motion->amp[j];
-            mp.freq[j] = motion->freq[j];
-            mp.phase[j] = motion->phase[j];
-            for (int d = 0; d < 3; ++d) mp.dir[j][d] = motion->dir[j][d];
-        }
-        for (int d = 0; d < 3; ++d) {
-            mp.g[d] = motion->elastic_grad[d];
-            mp.ce[d] = motion->elastic_center[d];
-            mp.vel[d] = motion->vel[d];
-            mp.omega[d] = motion->omega[d];
-            mp.cr[d] = motion->rot_center[d];
-        }
-    }
+    pack_motion(motion, mp);
     const int threads = 256;
     int64_t blocks = (S + threads - 1) / threads;
     if (blocks > 4096) blocks = 4096;
@@ -385,3 +447,26 @@ fq_status fq_bin_scatterers(const float *z, int64_t S, double z0, double dz, int
 }
 
 }  // extern "C"
+
+namespace fqi {
+
+size_t seg_table_bytes() { return (sizeof(SegTable) + 15) & ~(size_t)15; }
+size_t motion_bytes() { return (sizeof(MotionParams) + 15) & ~(size_t)15; }
+void build_seg_table(const fq_flow *flow, void *out) { pack_segments(flow, *reinterpret_cast<SegTable *>(out)); }
+void build_motion(const fq_motion *m, void *out) { pack_motion(m, *reinterpret_cast<MotionParams *>(out)); }
+
+fq_status batched_classify(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, cudaStream_t st)
+{
+    const int grid = fqb::persistent_grid(classify_batched_kernel, kBatchThreads, 0, items);
+    classify_batched_kernel<<<grid, kBatchThreads, 0, st>>>(ens, q);
+    return launch_check("batched classify");
+}
+
+fq_status batched_advect(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, cudaStream_t st)
+{
+    const int grid = fqb::persistent_grid(advect_batched_kernel, kBatchThreads, 0, items);
+    advect_batched_kernel<<<grid, kBatchThreads, 0, st>>>(ens, q);
+    return launch_check("batched advect");
+}
+
+}  // namespace fqi

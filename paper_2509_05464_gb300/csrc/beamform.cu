@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "batch.cuh"
 #include "fq_internal.cuh"
 
 namespace {
@@ -33,14 +34,16 @@ struct Rf2iqParams {
 
 constexpr int kRfTile = 64;  // output samples per CTA
 
+static_assert(kRfTile == fqb::kIqTile && kFrameChunk == fqb::kFrameChunkB, "batched item shapes");
+
+// One tile: output samples bx * 64 .. + 63 of channel line l, frames
+// 16 bz .. 16 bz + 15.  `mix` is the dynamic shared memory.
 template <typename InT, typename OutT>
-__global__ void __launch_bounds__(256) rf2iq_kernel(const Rf2iqParams p, const InT *__restrict__ rf,
-                                                    OutT *__restrict__ iq)
+__device__ __forceinline__ void rf2iq_tile(const Rf2iqParams &p, int bx, int l, int bz, const InT *__restrict__ rf,
+                                           OutT *__restrict__ iq, float2 *mix)
 {
-    extern __shared__ float2 mix[];  // [kFrameChunk][W]
-    const int l = blockIdx.y;
-    const int k0 = blockIdx.x * kRfTile;
-    const int f0 = blockIdx.z * kFrameChunk;
+    const int k0 = bx * kRfTile;
+    const int f0 = bz * kFrameChunk;
     const int J = p.J;
     const int W = kRfTile + 2 * J;      // window samples
     const int WS = W | 1;               // odd row stride: the 16 frame rows fall in distinct banks
@@ -82,6 +85,37 @@ __global__ void __launch_bounds__(256) rf2iq_kernel(const Rf2iqParams p, const I
         }
         int f = f0 + fl;
         if (f < p.Fp) fqi::store_c(iq, ((int64_t)l * p.ns + k) * p.Fp + f, make_float2(2.0f * re, 2.0f * im));
+    }
+}
+
+template <typename InT, typename OutT>
+__global__ void __launch_bounds__(256) rf2iq_kernel(const Rf2iqParams p, const InT *__restrict__ rf,
+                                                    OutT *__restrict__ iq)
+{
+    extern __shared__ float2 mix[];  // [kFrameChunk][W | 1] then the rotation row [W]
+    rf2iq_tile<InT, OutT>(p, blockIdx.x, blockIdx.y, blockIdx.z, rf, iq, mix);
+}
+
+constexpr int kIqParamBytes = (sizeof(Rf2iqParams) + 15) & ~15;
+
+template <typename InT, typename OutT>
+__global__ void __launch_bounds__(256) rf2iq_batched_kernel(const fqb::EnsDev *__restrict__ ens,
+                                                            const fqb::StageQueue q)
+{
+    extern __shared__ float2 mix[];
+    __shared__ __align__(16) unsigned char s_par[kIqParamBytes];
+    __shared__ int s_buf[2];
+    int cur = -1;
+    fqb::Item it;
+    while (fqb::next_item(q, ens, fqb::ST_RF2IQ, s_buf, it)) {
+        const fqb::EnsDev &e = ens[it.e];
+        if (it.e != cur) {
+            fqb::copy_block(s_par, e.iq_params, kIqParamBytes);
+            cur = it.e;
+            __syncthreads();
+        }
+        rf2iq_tile<InT, OutT>(*reinterpret_cast<const Rf2iqParams *>(s_par), it.x, it.y, it.z,
+                              (const InT *)e.rf, (OutT *)e.ch, mix);
     }
 }
 
@@ -180,11 +214,12 @@ struct ChunkLoad<__nv_bfloat16> {
     }
 };
 
+// One tile: pixels bx * blockDim.x .. + blockDim.x - 1, frames 16 by ..
+// 16 by + 15.  `etab` is the dynamic shared memory (6 M floats).
 template <typename ChT, typename OutT>
-__global__ void __launch_bounds__(kDasThreads) das_kernel(const DasParams p, const ChT *__restrict__ ch,
-                                                          OutT *__restrict__ iq)
+__device__ __forceinline__ void das_tile(const DasParams &p, int bx, int by, const ChT *__restrict__ ch,
+                                         OutT *__restrict__ iq, float *etab)
 {
-    extern __shared__ float etab[];  // [6][M]: x as float, x hi, x lo, y float, y hi, y lo
     const int M = p.pr.M;
     float *exf = etab, *exh = etab + M, *exl = etab + 2 * M;
     float *eyf = etab + 3 * M, *eyh = etab + 4 * M, *eyl = etab + 5 * M;
@@ -198,8 +233,8 @@ __global__ void __launch_bounds__(kDasThreads) das_kernel(const DasParams p, con
     }
     __syncthreads();
 
-    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int fbase = blockIdx.y * kFrameChunk;
+    const int64_t pix = (int64_t)bx * blockDim.x + threadIdx.x;
+    const int fbase = by * kFrameChunk;
     const bool live = pix < p.P;
     const int64_t pp = live ? pix : 0;
     const int ix = (int)(pp % p.gx);
@@ -267,6 +302,35 @@ __global__ void __launch_bounds__(kDasThreads) das_kernel(const DasParams p, con
         fqi::store_c(iq, pix * p.F + fbase + f, make_float2(acc[f].x * p.inv_A, acc[f].y * p.inv_A));
 }
 
+template <typename ChT, typename OutT, int NT>
+__global__ void __launch_bounds__(NT) das_kernel(const DasParams p, const ChT *__restrict__ ch, OutT *__restrict__ iq)
+{
+    extern __shared__ float etab[];  // [6][M]: x as float, x hi, x lo, y float, y hi, y lo
+    das_tile<ChT, OutT>(p, blockIdx.x, blockIdx.y, ch, iq, etab);
+}
+
+constexpr int kDasParamBytes = (sizeof(DasParams) + 15) & ~15;
+
+template <typename ChT, typename OutT, int NT>
+__global__ void __launch_bounds__(NT) das_batched_kernel(const fqb::EnsDev *__restrict__ ens, const fqb::StageQueue q)
+{
+    extern __shared__ float etab[];
+    __shared__ __align__(16) unsigned char s_par[kDasParamBytes];
+    __shared__ int s_buf[2];
+    int cur = -1;
+    fqb::Item it;
+    while (fqb::next_item(q, ens, fqb::ST_DAS, s_buf, it)) {
+        const fqb::EnsDev &e = ens[it.e];
+        if (it.e != cur) {
+            fqb::copy_block(s_par, e.das_params, kDasParamBytes);
+            cur = it.e;
+            __syncthreads();
+        }
+        das_tile<ChT, OutT>(*reinterpret_cast<const DasParams *>(s_par), it.x, it.y, (const ChT *)e.ch,
+                            (OutT *)e.iq, etab);
+    }
+}
+
 fq_status check_probe_tx(const fq_probe *probe, const fq_tx *tx, const char *who)
 {
     FQ_REQUIRE(probe && tx, FQ_ERR_INVALID_ARG, "%s: null probe/tx", who);
@@ -284,7 +348,7 @@ template <typename ChT, typename OutT>
 fq_status launch_das(const DasParams &p, const void *ch, void *iq, cudaStream_t st)
 {
     size_t smem = sizeof(float) * 6 * (size_t)p.pr.M;
-    auto kern = das_kernel<ChT, OutT>;
+    auto kern = das_kernel<ChT, OutT, kDasThreads>;
     if (smem > 48 * 1024) {
         fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                            (int)smem), "fq_das: smem attribute");
@@ -295,12 +359,8 @@ fq_status launch_das(const DasParams &p, const void *ch, void *iq, cudaStream_t 
     return fqi::launch_check("fq_das");
 }
 
-fq_status run_das(const fq_probe *probe, const fq_tx *tx, const void *ch, int ch_dtype, int F, const fq_grid *g,
-                  int iq_dtype, void *iq, cudaStream_t st)
+void make_das_params(const fq_probe *probe, const fq_tx *tx, int F, const fq_grid *g, DasParams &p)
 {
-    FQ_REQUIRE(g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1, FQ_ERR_SHAPE, "fq_das: bad grid");
-    FQ_REQUIRE(g->fnumber > 0.0, FQ_ERR_INVALID_ARG, "fq_das: fnumber must be > 0");
-    DasParams p;
     std::memset(&p, 0, sizeof p);
     fqi::make_probe_ff(probe, p.pr);
     p.pitch_x = probe->pitch_x;
@@ -315,6 +375,15 @@ fq_status run_das(const fq_probe *probe, const fq_tx *tx, const void *ch, int ch
     p.half_per_z = (float)(0.5 / g->fnumber);
     p.inv_A = 1.0f / (float)p.A;
     fqi::make_angles_ff(probe, tx, p.ang);
+}
+
+fq_status run_das(const fq_probe *probe, const fq_tx *tx, const void *ch, int ch_dtype, int F, const fq_grid *g,
+                  int iq_dtype, void *iq, cudaStream_t st)
+{
+    FQ_REQUIRE(g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1, FQ_ERR_SHAPE, "fq_das: bad grid");
+    FQ_REQUIRE(g->fnumber > 0.0, FQ_ERR_INVALID_ARG, "fq_das: fnumber must be > 0");
+    DasParams p;
+    make_das_params(probe, tx, F, g, p);
     if (ch_dtype == FQ_F32 && iq_dtype == FQ_F32) return launch_das<float, float>(p, ch, iq, st);
     if (ch_dtype == FQ_F32 && iq_dtype == FQ_BF16) return launch_das<float, __nv_bfloat16>(p, ch, iq, st);
     if (ch_dtype == FQ_BF16 && iq_dtype == FQ_F32) return launch_das<__nv_bfloat16, float>(p, ch, iq, st);
@@ -387,3 +456,79 @@ fq_status fq_beamform_das(const fq_probe *probe, const fq_tx *tx, const void *rf
 }
 
 }  // extern "C"
+
+namespace fqi {
+
+size_t iq_params_bytes() { return kIqParamBytes; }
+
+fq_status build_iq_params(const fq_probe *probe, int L, int F, void *out, int *J)
+{
+    std::memset(out, 0, kIqParamBytes);
+    Rf2iqParams &p = *reinterpret_cast<Rf2iqParams *>(out);
+    FQ_REQUIRE(make_rf2iq_params(probe, L, F, p), FQ_ERR_SHAPE, "batch: 2 round(fs/f0) must be <= %d",
+               kMaxHalfTaps);
+    *J = p.J;
+    return FQ_OK;
+}
+
+size_t das_params_bytes() { return kDasParamBytes; }
+
+fq_status build_das_params(const fq_probe *probe, const fq_tx *tx, int F, const fq_grid *g, void *out)
+{
+    std::memset(out, 0, kDasParamBytes);
+    make_das_params(probe, tx, F, g, *reinterpret_cast<DasParams *>(out));
+    return FQ_OK;
+}
+
+template <typename InT, typename OutT>
+fq_status launch_rf2iq_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int J_max,
+                               cudaStream_t st)
+{
+    const int W = kRfTile + 2 * J_max;
+    const size_t smem = sizeof(float2) * ((size_t)kFrameChunk * (W | 1) + W);
+    const int grid = fqb::persistent_grid(rf2iq_batched_kernel<InT, OutT>, 256, smem, items);
+    rf2iq_batched_kernel<InT, OutT><<<grid, 256, smem, st>>>(ens, q);
+    return launch_check("batched rf2iq");
+}
+
+fq_status batched_rf2iq(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, int ch_dtype,
+                        int J_max, cudaStream_t st)
+{
+    if (rf_dtype == FQ_F32 && ch_dtype == FQ_F32) return launch_rf2iq_batched<float, float>(ens, q, items, J_max, st);
+    if (rf_dtype == FQ_F32) return launch_rf2iq_batched<float, __nv_bfloat16>(ens, q, items, J_max, st);
+    if (ch_dtype == FQ_F32) return launch_rf2iq_batched<__nv_bfloat16, float>(ens, q, items, J_max, st);
+    return launch_rf2iq_batched<__nv_bfloat16, __nv_bfloat16>(ens, q, items, J_max, st);
+}
+
+template <typename ChT, typename OutT, int NT>
+fq_status launch_das_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int M_max, cudaStream_t st)
+{
+    const size_t smem = sizeof(float) * 6 * (size_t)M_max;
+    auto kern = das_batched_kernel<ChT, OutT, NT>;
+    fq_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                             "batched DAS: smem attribute");
+    if (s) return s;
+    const int grid = fqb::persistent_grid(kern, NT, smem, items);
+    kern<<<grid, NT, smem, st>>>(ens, q);
+    return launch_check("batched DAS");
+}
+
+template <typename ChT, typename OutT>
+fq_status das_by_threads(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int M_max, int threads,
+                         cudaStream_t st)
+{
+    if (threads == 64) return launch_das_batched<ChT, OutT, 64>(ens, q, items, M_max, st);
+    if (threads == 256) return launch_das_batched<ChT, OutT, 256>(ens, q, items, M_max, st);
+    return launch_das_batched<ChT, OutT, 128>(ens, q, items, M_max, st);
+}
+
+fq_status batched_das(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int ch_dtype, int iq_dtype,
+                      int M_max, int threads, cudaStream_t st)
+{
+    if (ch_dtype == FQ_F32 && iq_dtype == FQ_F32) return das_by_threads<float, float>(ens, q, items, M_max, threads, st);
+    if (ch_dtype == FQ_F32) return das_by_threads<float, __nv_bfloat16>(ens, q, items, M_max, threads, st);
+    if (iq_dtype == FQ_F32) return das_by_threads<__nv_bfloat16, float>(ens, q, items, M_max, threads, st);
+    return das_by_threads<__nv_bfloat16, __nv_bfloat16>(ens, q, items, M_max, threads, st);
+}
+
+}  // namespace fqi

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "batch.cuh"
 #include "fq_internal.cuh"
 
 namespace {
@@ -45,7 +46,7 @@ bool eig_in_smem(int F) { return (size_t)F * (F + 1) / 2 * sizeof(float2) <= 190
 // Operand bytes of the tensor-core Gram modes (0 = CUDA-core FP32 Gram).
 int tc_esz(int gram_mode) { return gram_mode == FQ_GRAM_BF16 ? 2 : (gram_mode == FQ_GRAM_TF32 ? 4 : 0); }
 
-ClutterLayout layout(int64_t P, int F, int gram_mode = FQ_GRAM_F32)
+ClutterLayout layout(int64_t P, int F, int gram_mode = FQ_GRAM_F32, bool force_big = false)
 {
     ClutterLayout L;
     size_t o = 0;
@@ -63,7 +64,7 @@ ClutterLayout layout(int64_t P, int F, int gram_mode = FQ_GRAM_F32)
     L.k = o; o += 256;
     L.hv = o; o += al256(sizeof(float2) * F * F);
     L.tau = o; o += al256(sizeof(float) * F);
-    L.big = o; o += eig_in_smem(F) ? 0 : al256(sizeof(float2) * (size_t)F * (F + 1) / 2);
+    L.big = o; o += (eig_in_smem(F) && !force_big) ? 0 : al256(sizeof(float2) * (size_t)F * (F + 1) / 2);
     L.ii = o; o += al256(sizeof(float) * 6 * (size_t)kFastMaxK * F);
     L.total = o;
     return L;
@@ -84,16 +85,14 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 // Upper-triangular tiles (ti <= tj) of G over pixel chunks; each CTA: one
 // 32x32 complex tile over one chunk; 256 threads, 2x2 outputs each.
 template <typename T>
-__global__ void __launch_bounds__(256) gram_partial_kernel(const T *__restrict__ S, int64_t P, int F, int nt,
-                                                           int64_t chunk_len, float2 *__restrict__ part)
+__device__ __forceinline__ void gram_tile(const T *__restrict__ S, int64_t P, int F, int nt, int64_t chunk_len,
+                                          float2 *__restrict__ part, int pair, int c,
+                                          float2 (*As)[kGramTile + 1], float2 (*Bs)[kGramTile + 1])
 {
-    __shared__ float2 As[kGramTile][kGramTile + 1];
-    __shared__ float2 Bs[kGramTile][kGramTile + 1];
     // decode upper-triangular tile pair
-    int t = blockIdx.x, ti = 0;
+    int t = pair, ti = 0;
     while (t >= nt - ti) { t -= nt - ti; ++ti; }
     const int tj = ti + t;
-    const int c = blockIdx.y;
     const int64_t pbeg = (int64_t)c * chunk_len;
     const int64_t pend = min(P, pbeg + chunk_len);
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -132,9 +131,18 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const T *__restrict__
         }
 }
 
-__global__ void gram_reduce_kernel(const float2 *__restrict__ part, int n_chunks, int F, float2 *__restrict__ G)
+template <typename T>
+__global__ void __launch_bounds__(256) gram_partial_kernel(const T *__restrict__ S, int64_t P, int F, int nt,
+                                                           int64_t chunk_len, float2 *__restrict__ part)
 {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float2 As[kGramTile][kGramTile + 1];
+    __shared__ float2 Bs[kGramTile][kGramTile + 1];
+    gram_tile<T>(S, P, F, nt, chunk_len, part, blockIdx.x, blockIdx.y, As, Bs);
+}
+
+__device__ __forceinline__ void gram_reduce_at(const float2 *__restrict__ part, int n_chunks, int F,
+                                               float2 *__restrict__ G, int idx)
+{
     if (idx >= F * F) return;
     int i = idx / F, j = idx % F;
     bool upper = (i / kGramTile) <= (j / kGramTile);
@@ -146,6 +154,11 @@ __global__ void gram_reduce_kernel(const float2 *__restrict__ part, int n_chunks
         s.y += v.y;
     }
     G[idx] = upper ? s : cconj(s);
+}
+
+__global__ void gram_reduce_kernel(const float2 *__restrict__ part, int n_chunks, int F, float2 *__restrict__ G)
+{
+    gram_reduce_at(part, n_chunks, F, G, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ------------------------------------------------------------ eigen (1 CTA) --
@@ -321,12 +334,12 @@ __device__ void inverse_iteration(const float *d, const float *e, int n, float s
 // implicit QL with Wilkinson shifts on the real tridiagonal (after a
 // diagonal unitary scaling), eigenvalue sort and back-transformation.
 // Optional: the energy / fixed cutoff k.
-__global__ void __launch_bounds__(kEigThreads) eig_kernel(const float2 *__restrict__ G, int F, float2 *__restrict__ big,
-                                                          float2 *__restrict__ hv, float *__restrict__ tau_g,
-                                                          double *__restrict__ lam_out, float2 *__restrict__ V,
-                                                          float2 *__restrict__ Vt, int k_cut, double thresh,
-                                                          int *__restrict__ k_out, int *__restrict__ status,
-                                                          int topk_only, float *__restrict__ ii_scr)
+__device__ __forceinline__ void eig_body(const float2 *__restrict__ G, int F, float2 *__restrict__ big,
+                                         float2 *__restrict__ hv, float *__restrict__ tau_g,
+                                         double *__restrict__ lam_out, float2 *__restrict__ V,
+                                         float2 *__restrict__ Vt, int k_cut, double thresh,
+                                         int *__restrict__ k_out, int *__restrict__ status,
+                                         int topk_only, float *__restrict__ ii_scr)
 {
     extern __shared__ float2 dyn[];
     float2 *Ap = big ? big : dyn;                 // packed lower triangle, later Z (real, stride F+1)
@@ -659,20 +672,37 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const float2 *__restri
     back_transform(F, F, Z, zs, perm, delta, hv, tau_g, V, Vt, lane, wid, nw);
 }
 
+__global__ void __launch_bounds__(kEigThreads) eig_kernel(const float2 *__restrict__ G, int F, float2 *__restrict__ big,
+                                                          float2 *__restrict__ hv, float *__restrict__ tau_g,
+                                                          double *__restrict__ lam_out, float2 *__restrict__ V,
+                                                          float2 *__restrict__ Vt, int k_cut, double thresh,
+                                                          int *__restrict__ k_out, int *__restrict__ status,
+                                                          int topk_only, float *__restrict__ ii_scr)
+{
+    eig_body(G, F, big, hv, tau_g, lam_out, V, Vt, k_cut, thresh, k_out, status, topk_only, ii_scr);
+}
+
+// One CTA per ensemble of a wave; the packed matrix always in the workspace.
+__global__ void __launch_bounds__(kEigThreads) eig_batched_kernel(const fqb::EnsDev *__restrict__ ens,
+                                                                  const int *__restrict__ members)
+{
+    const fqb::EnsDev &e = ens[members[blockIdx.x]];
+    char *ws = e.cws;
+    double *lam = e.eigvals ? e.eigvals : (double *)(ws + e.cl_lam);
+    int *kk = e.k_used ? e.k_used : (int *)(ws + e.cl_k);
+    eig_body((const float2 *)(ws + e.cl_G), e.F, (float2 *)(ws + e.cl_big), (float2 *)(ws + e.cl_hv),
+             (float *)(ws + e.cl_tau), lam, (float2 *)(ws + e.cl_V), (float2 *)(ws + e.cl_Vt), e.k_cut,
+             e.energy_thresh, kk, e.status, 1, (float *)(ws + e.cl_ii));
+}
+
 // ------------------------------------------------ projection + power Doppler --
 // One warp per pixel: y_j = sum_f S[f] V[f][j] for j < k, then
 // S_f = S - sum_j y_j conj(V[:, j]) and pd = mean |S_f|^2.
 template <typename T>
-__global__ void __launch_bounds__(256) project_pd_kernel(const T *__restrict__ S, int64_t P, int F,
-                                                         const float2 *__restrict__ Vt, const int *__restrict__ k_ptr,
-                                                         T *__restrict__ S_f, float *__restrict__ pd)
+__device__ __forceinline__ void project_pixel(const T *__restrict__ S, int64_t p, int F, const float2 *__restrict__ Vt,
+                                              int k, T *__restrict__ S_f, float *__restrict__ pd, float invF, int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int k = min(*k_ptr, F);
-    const float invF = 1.0f / (float)F;
-    for (int64_t p = warp0; p < P; p += nwarps) {
+    {
         float2 s[16], sf[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -722,6 +752,66 @@ __global__ void __launch_bounds__(256) project_pd_kernel(const T *__restrict__ S
         }
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
         if (pd && lane == 0) pd[p] = e * invF;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) project_pd_kernel(const T *__restrict__ S, int64_t P, int F,
+                                                         const float2 *__restrict__ Vt, const int *__restrict__ k_ptr,
+                                                         T *__restrict__ S_f, float *__restrict__ pd)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int k = min(*k_ptr, F);
+    const float invF = 1.0f / (float)F;
+    for (int64_t p = warp0; p < P; p += nwarps) project_pixel(S, p, F, Vt, k, S_f, pd, invF, lane);
+}
+
+// ------------------------------------------------------------- batched --
+template <typename T>
+__global__ void __launch_bounds__(256) gram_batched_kernel(const fqb::EnsDev *__restrict__ ens, const fqb::StageQueue q)
+{
+    __shared__ float2 As[kGramTile][kGramTile + 1];
+    __shared__ float2 Bs[kGramTile][kGramTile + 1];
+    __shared__ int s_buf[2];
+    fqb::Item it;
+    while (fqb::next_item(q, ens, fqb::ST_GRAM, s_buf, it)) {
+        const fqb::EnsDev &e = ens[it.e];
+        const int nt = (e.F + kGramTile - 1) / kGramTile;
+        gram_tile<T>((const T *)e.iq, e.P, e.F, nt, e.chunk_len, (float2 *)(e.cws + e.cl_part), it.x, it.y, As, Bs);
+    }
+}
+
+__global__ void __launch_bounds__(256) gram_reduce_batched_kernel(const fqb::EnsDev *__restrict__ ens,
+                                                                  const fqb::StageQueue q)
+{
+    __shared__ int s_buf[2];
+    fqb::Item it;
+    while (fqb::next_item(q, ens, fqb::ST_GRAM_REDUCE, s_buf, it)) {
+        const fqb::EnsDev &e = ens[it.e];
+        gram_reduce_at((const float2 *)(e.cws + e.cl_part), e.n_chunks, e.F, (float2 *)(e.cws + e.cl_G),
+                       it.x * 256 + threadIdx.x);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) project_batched_kernel(const fqb::EnsDev *__restrict__ ens,
+                                                              const fqb::StageQueue q)
+{
+    __shared__ int s_buf[2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    fqb::Item it;
+    while (fqb::next_item(q, ens, fqb::ST_PROJECT, s_buf, it)) {
+        const fqb::EnsDev &e = ens[it.e];
+        const int *kk = e.k_used ? e.k_used : (const int *)(e.cws + e.cl_k);
+        const int k = min(*kk, e.F);
+        const float invF = 1.0f / (float)e.F;
+        const int64_t beg = (int64_t)it.x * fqb::kItemPix;
+        const int64_t end = beg + fqb::kItemPix < e.P ? beg + fqb::kItemPix : e.P;
+        for (int64_t p = beg + wid; p < end; p += 8)
+            project_pixel((const T *)e.iq, p, e.F, (const float2 *)(e.cws + e.cl_Vt), k, (T *)nullptr, e.pd, invF,
+                          lane);
     }
 }
 
@@ -1043,3 +1133,52 @@ fq_status fq_clutter_svd_noalloc(const void *iq, int32_t dtype, int64_t P, int32
 }
 
 }  // extern "C"
+
+namespace fqi {
+
+void clutter_layout_batched(int64_t P, int F, size_t off[10], int *n_chunks, int64_t *chunk_len, size_t *total)
+{
+    const ClutterLayout L = layout(P, F, FQ_GRAM_F32, true);
+    const size_t o[10] = {L.G, L.part, L.V, L.Vt, L.lam, L.k, L.hv, L.tau, L.big, L.ii};
+    for (int i = 0; i < 10; ++i) off[i] = o[i];
+    *n_chunks = L.n_chunks;
+    *chunk_len = L.chunk_len;
+    *total = L.total;
+}
+
+fq_status batched_gram(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int iq_dtype, cudaStream_t st)
+{
+    if (iq_dtype == FQ_F32)
+        gram_batched_kernel<float><<<fqb::persistent_grid(gram_batched_kernel<float>, 256, 0, items), 256, 0, st>>>(
+            ens, q);
+    else
+        gram_batched_kernel<__nv_bfloat16>
+            <<<fqb::persistent_grid(gram_batched_kernel<__nv_bfloat16>, 256, 0, items), 256, 0, st>>>(ens, q);
+    return launch_check("batched Gram");
+}
+
+fq_status batched_gram_reduce(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, cudaStream_t st)
+{
+    gram_reduce_batched_kernel<<<fqb::persistent_grid(gram_reduce_batched_kernel, 256, 0, items), 256, 0, st>>>(ens,
+                                                                                                               q);
+    return launch_check("batched Gram reduce");
+}
+
+fq_status batched_eig(const fqb::EnsDev *ens, const int *members, int n, cudaStream_t st)
+{
+    eig_batched_kernel<<<n, kEigThreads, 0, st>>>(ens, members);
+    return launch_check("batched eig");
+}
+
+fq_status batched_project(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int iq_dtype, cudaStream_t st)
+{
+    if (iq_dtype == FQ_F32)
+        project_batched_kernel<float>
+            <<<fqb::persistent_grid(project_batched_kernel<float>, 256, 0, items), 256, 0, st>>>(ens, q);
+    else
+        project_batched_kernel<__nv_bfloat16>
+            <<<fqb::persistent_grid(project_batched_kernel<__nv_bfloat16>, 256, 0, items), 256, 0, st>>>(ens, q);
+    return launch_check("batched projection");
+}
+
+}  // namespace fqi

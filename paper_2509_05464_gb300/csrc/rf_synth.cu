@@ -24,6 +24,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "batch.cuh"
 #include "fq_internal.cuh"
 
 namespace {
@@ -317,20 +318,17 @@ __device__ __forceinline__ f2 tap2x2(f2 A, f2 hA, f2 C)
     return fqi::f2_fma(fqi::f2_fma(fqi::f2_fma(A, C, A), C, nhA), C, nhA);
 }
 
-template <int NT, int MINB, typename OutT>
-__global__ void __launch_bounds__(NT, MINB) rf_synth_pair_kernel(const RfParams p, const float *__restrict__ pos,
-                                                              const float *__restrict__ amp,
-                                                              const float *__restrict__ rf_base,
-                                                              OutT *__restrict__ rf)
+// One tile: elements 2 bx, 2 bx + 1 of transmit a, frame f.  `tile` is the
+// dynamic shared memory (4 Ns ints), `s_red` NT / 32 floats.
+template <int NT, typename OutT>
+__device__ __forceinline__ void rf_pair_tile(const RfParams &p, int bx, int a, int f, const float *__restrict__ pos,
+                                             const float *__restrict__ amp, const float *__restrict__ rf_base,
+                                             OutT *__restrict__ rf, int *tile, float *s_red)
 {
     constexpr int E = 2;
-    extern __shared__ int tile[];  // hi [2][Ns] then lo [2][Ns]
-    __shared__ float s_red[NT / 32];
     const int ns = p.pr.ns;
     const int M = p.pr.M;
-    const int m0 = blockIdx.x * E;
-    const int a = blockIdx.y;
-    const int f = blockIdx.z;
+    const int m0 = bx * E;
     const int ne = min(E, M - m0);
     const int64_t S = p.S;
     int *hi0 = tile, *hi1 = tile + ns, *lo0 = tile + 2 * ns, *lo1 = tile + 3 * ns;
@@ -510,6 +508,42 @@ __global__ void __launch_bounds__(NT, MINB) rf_synth_pair_kernel(const RfParams 
         fqi::store_f(out, i, fmaf((float)tile[i], 65536.0f, (float)tile[2 * ns + i]) * from_fix);
 }
 
+template <int NT, int MINB, typename OutT>
+__global__ void __launch_bounds__(NT, MINB) rf_synth_pair_kernel(const RfParams p, const float *__restrict__ pos,
+                                                              const float *__restrict__ amp,
+                                                              const float *__restrict__ rf_base,
+                                                              OutT *__restrict__ rf)
+{
+    extern __shared__ int tile[];  // hi [2][Ns] then lo [2][Ns]
+    __shared__ float s_red[NT / 32];
+    rf_pair_tile<NT, OutT>(p, blockIdx.x, blockIdx.y, blockIdx.z, pos, amp, rf_base, rf, tile, s_red);
+}
+
+// Persistent form over the RF items of many ensembles (no static-tissue base).
+constexpr int kRfParamBytes = (sizeof(RfParams) + 15) & ~15;
+
+template <int NT, int MINB, typename OutT>
+__global__ void __launch_bounds__(NT, MINB) rf_pair_batched_kernel(const fqb::EnsDev *__restrict__ ens,
+                                                                const fqb::StageQueue q)
+{
+    extern __shared__ int tile[];
+    __shared__ float s_red[NT / 32];
+    __shared__ __align__(16) unsigned char s_par[kRfParamBytes];
+    __shared__ int s_buf[2];
+    int cur = -1;
+    fqb::Item it;
+    while (fqb::next_item(q, ens, fqb::ST_RF, s_buf, it)) {
+        const fqb::EnsDev &e = ens[it.e];
+        if (it.e != cur) {
+            fqb::copy_block(s_par, e.rf_params, kRfParamBytes);
+            cur = it.e;
+            __syncthreads();
+        }
+        rf_pair_tile<NT, OutT>(*reinterpret_cast<const RfParams *>(s_par), it.x, it.y, it.z, e.pos, e.amp_eff,
+                               nullptr, (OutT *)e.rf, tile, s_red);
+    }
+}
+
 template <typename OutT>
 fq_status launch_rf_pair(const RfParams &p, int F, const float *pos, const float *amp, const float *base, OutT *rf,
                          cudaStream_t st)
@@ -583,29 +617,8 @@ fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *a
     }
 }
 
-}  // namespace
-
-extern "C" fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, const float *pos,
-                                    const float *amp, int64_t S, int32_t n_frames, const float *rf_base,
-                                    int32_t out_dtype, void *rf, void *stream)
+fq_status make_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, RfParams &p)
 {
-    FQ_REQUIRE(probe && tx && rf, FQ_ERR_INVALID_ARG, "fq_simulate_rf: null argument");
-    FQ_REQUIRE(S >= 0 && n_frames >= 1, FQ_ERR_INVALID_ARG, "fq_simulate_rf: S=%lld n_frames=%d",
-               (long long)S, n_frames);
-    FQ_REQUIRE(S == 0 || (pos && amp), FQ_ERR_INVALID_ARG, "fq_simulate_rf: null pos/amp");
-    FQ_REQUIRE(tx->n_angles >= 1 && tx->n_angles <= FQ_MAX_ANGLES && tx->tilt_x && tx->tilt_y, FQ_ERR_SHAPE,
-               "fq_simulate_rf: n_angles must be in [1, %d]", FQ_MAX_ANGLES);
-    FQ_REQUIRE(probe->nx >= 1 && probe->ny >= 1 && (int64_t)probe->nx * probe->ny <= 65536, FQ_ERR_SHAPE,
-               "fq_simulate_rf: bad element count");
-    FQ_REQUIRE(probe->n_samples >= 1 && probe->n_samples <= 8192, FQ_ERR_SHAPE,
-               "fq_simulate_rf: n_samples must be in [1, 8192]");
-    FQ_REQUIRE(probe->f0 > 0 && probe->fs > 0 && probe->c > 0 && probe->n_cycles >= 1, FQ_ERR_INVALID_ARG,
-               "fq_simulate_rf: f0, fs, c, n_cycles must be positive");
-    FQ_REQUIRE(out_dtype == FQ_F32 || out_dtype == FQ_BF16, FQ_ERR_UNSUPPORTED,
-               "fq_simulate_rf: out_dtype must be FQ_F32 or FQ_BF16");
-    FQ_REQUIRE(fqi::aligned(rf, 4), FQ_ERR_ALIGN, "fq_simulate_rf: rf must be 4-byte aligned");
-
-    RfParams p;
     std::memset(&p, 0, sizeof p);
     fqi::make_probe_ff(probe, p.pr);
     p.A = tx->n_angles;
@@ -639,7 +652,77 @@ extern "C" fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, cons
     p.two_cos_c = (float)(2.0 * std::cos(wc));
     p.two_cycle = probe->n_cycles == 2;
     fqi::make_angles_ff(probe, tx, p.ang);
+    return FQ_OK;
+}
+
+}  // namespace
+
+extern "C" fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, const float *pos,
+                                    const float *amp, int64_t S, int32_t n_frames, const float *rf_base,
+                                    int32_t out_dtype, void *rf, void *stream)
+{
+    FQ_REQUIRE(probe && tx && rf, FQ_ERR_INVALID_ARG, "fq_simulate_rf: null argument");
+    FQ_REQUIRE(S >= 0 && n_frames >= 1, FQ_ERR_INVALID_ARG, "fq_simulate_rf: S=%lld n_frames=%d",
+               (long long)S, n_frames);
+    FQ_REQUIRE(S == 0 || (pos && amp), FQ_ERR_INVALID_ARG, "fq_simulate_rf: null pos/amp");
+    FQ_REQUIRE(tx->n_angles >= 1 && tx->n_angles <= FQ_MAX_ANGLES && tx->tilt_x && tx->tilt_y, FQ_ERR_SHAPE,
+               "fq_simulate_rf: n_angles must be in [1, %d]", FQ_MAX_ANGLES);
+    FQ_REQUIRE(probe->nx >= 1 && probe->ny >= 1 && (int64_t)probe->nx * probe->ny <= 65536, FQ_ERR_SHAPE,
+               "fq_simulate_rf: bad element count");
+    FQ_REQUIRE(probe->n_samples >= 1 && probe->n_samples <= 8192, FQ_ERR_SHAPE,
+               "fq_simulate_rf: n_samples must be in [1, 8192]");
+    FQ_REQUIRE(probe->f0 > 0 && probe->fs > 0 && probe->c > 0 && probe->n_cycles >= 1, FQ_ERR_INVALID_ARG,
+               "fq_simulate_rf: f0, fs, c, n_cycles must be positive");
+    FQ_REQUIRE(out_dtype == FQ_F32 || out_dtype == FQ_BF16, FQ_ERR_UNSUPPORTED,
+               "fq_simulate_rf: out_dtype must be FQ_F32 or FQ_BF16");
+    FQ_REQUIRE(fqi::aligned(rf, 4), FQ_ERR_ALIGN, "fq_simulate_rf: rf must be 4-byte aligned");
+
+    RfParams p;
+    fq_status bs = make_rf_params(probe, tx, S, p);
+    if (bs) return bs;
     cudaStream_t st = (cudaStream_t)stream;
     if (out_dtype == FQ_F32) return dispatch_rf(p, n_frames, pos, amp, rf_base, (float *)rf, st);
     return dispatch_rf(p, n_frames, pos, amp, rf_base, (__nv_bfloat16 *)rf, st);
 }
+
+namespace fqi {
+
+size_t rf_params_bytes() { return kRfParamBytes; }
+
+fq_status build_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, void *out)
+{
+    std::memset(out, 0, kRfParamBytes);
+    return make_rf_params(probe, tx, S, *reinterpret_cast<RfParams *>(out));
+}
+
+int rf_ntap_ok(const void *rf_params)
+{
+    const RfParams &p = *reinterpret_cast<const RfParams *>(rf_params);
+    return p.two_cycle && p.ntap_max <= 9;
+}
+
+template <int MINB, typename OutT>
+fq_status launch_rf_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int ns_max, cudaStream_t st)
+{
+    constexpr int NT = 256;
+    const size_t smem = 4 * sizeof(int) * (size_t)ns_max;
+    auto kern = rf_pair_batched_kernel<NT, MINB, OutT>;
+    fq_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                             "batched RF: smem attribute");
+    if (s) return s;
+    const int grid = fqb::persistent_grid(kern, NT, smem, items);
+    kern<<<grid, NT, smem, st>>>(ens, q);
+    return launch_check("batched RF");
+}
+
+fq_status batched_rf(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, int ns_max, int minb,
+                     cudaStream_t st)
+{
+    if (rf_dtype == FQ_F32)
+        return minb == 2 ? launch_rf_batched<2, float>(ens, q, items, ns_max, st)
+                         : launch_rf_batched<3, float>(ens, q, items, ns_max, st);
+    return minb == 2 ? launch_rf_batched<2, __nv_bfloat16>(ens, q, items, ns_max, st)
+                     : launch_rf_batched<3, __nv_bfloat16>(ens, q, items, ns_max, st);
+}
+
+}  // namespace fqi

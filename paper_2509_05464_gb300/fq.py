@@ -68,6 +68,25 @@ class Motion(C.Structure):
                 ("rot_center", C.c_double * 3)]
 
 
+class EnsembleDesc(C.Structure):
+    _fields_ = [("probe", Probe), ("tx", Tx), ("grid", Grid), ("flow", Flow), ("motion", Motion),
+                ("S", C.c_int64), ("n_frames", C.c_int32), ("t0", C.c_double), ("dt", C.c_double),
+                ("k_cut", C.c_int32), ("energy_thresh", C.c_double), ("p0", C.c_void_p), ("seg_id", C.c_void_p),
+                ("flow_coord", C.c_void_p), ("amp", C.c_void_p), ("pd", C.c_void_p), ("eigvals", C.c_void_p),
+                ("k_used", C.c_void_p)]
+
+
+class TileChoice(C.Structure):
+    _fields_ = [("op", C.c_int32), ("choice", C.c_int32), ("n_tried", C.c_int32), ("tried", C.c_int32 * 4),
+                ("tried_ms", C.c_float * 4), ("ms", C.c_float)]
+
+
+FQ_OP_RF, FQ_OP_DAS = 0, 1
+STAGES = ("classify", "advect", "rf", "rf2iq", "das", "gram", "gram_reduce", "eig", "project")
+# ctypes structs of the ABI, in the order of fq_sizeof's argument
+ABI_STRUCTS = (Probe, Tx, Grid, Segment, Flow, Motion, EnsembleDesc, TileChoice)
+
+
 # ------------------------------------------------------------------ loading --
 _lock = threading.Lock()
 _lib = None
@@ -113,11 +132,26 @@ def lib():
             "fq_power_doppler": [_P, _I32, _I64, _I32, _P, _P],
             "fq_clutter_svd_noalloc": [_P, _I32, _I64, _I32, _I32, _D, _P, _P, _P, _P, _P],
             "fq_clutter_status": [_P, _P],
+            "fq_batch_plan": [C.POINTER(EnsembleDesc), _I32, _I32, _I32, _I32, _SZ, C.POINTER(_P), C.POINTER(_SZ)],
+            "fq_batch_info": [_P, C.POINTER(_I32), C.POINTER(_I64)],
+            "fq_batch_set_tile": [_P, C.POINTER(TileChoice)],
+            "fq_batch_launch": [_P, _P, _SZ, _P],
+            "fq_batch_status": [_P, _P, _P],
+            "fq_run_batched": [C.POINTER(EnsembleDesc), _I32, _I32, _P, _SZ, _P],
+            "fq_graph_capture": [_P, _P, _SZ, C.POINTER(_P)],
+            "fq_graph_launch": [_P, _P],
+            "fq_autotune": [_I32, C.POINTER(EnsembleDesc), _I32, _P, _SZ, C.POINTER(TileChoice), _P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_int
+        L.fq_batch_free.argtypes = [_P]
+        L.fq_batch_free.restype = None
+        L.fq_graph_free.argtypes = [_P]
+        L.fq_graph_free.restype = None
+        L.fq_sizeof.argtypes = [_I32]
+        L.fq_sizeof.restype = _SZ
         _lib = L
         return L
 
@@ -413,3 +447,126 @@ def fq_clutter_svd_noalloc(iq, k_cut=2, energy_thresh=0.9, want_iq_f=True, iq_f=
     _check(lib().fq_clutter_svd_noalloc(_ptr(iq), _dt(iq), P, F, int(k_cut), float(energy_thresh), _ptr(iq_f),
                                         _ptr(pd), _ptr(eigvals), _ptr(k_used), _stream(stream)))
     return dict(iq_f=iq_f, pd=pd, eigvals=eigvals, k=k_used)
+
+
+# ------------------------------------------------------------ batched (a11) --
+class Batch:
+    """Many uneven ensembles through the persistent per-stage kernels.
+
+    ``members`` is a list of workloads (``workload.Workload``); their inputs
+    are uploaded once to device tensors held here, and each ensemble's
+    power Doppler image lands in ``self.pd[i]``.  ``max_arena_bytes`` bounds
+    the scratch arena (0: one wave).
+    """
+
+    def __init__(self, members, dtype=torch.float32, max_arena_bytes=0, device="cuda", plan_only=False):
+        self.members = list(members)
+        self.dev = torch.device(device)
+        n = len(self.members)
+        self.descs = (EnsembleDesc * n)()
+        self._keep = []
+        self.inputs, self.pd, self.eigvals, self.k_used = [], [], [], []
+        for i, w in enumerate(self.members):
+            d = self.descs[i]
+            d.probe = make_probe(w.probe)
+            th = _TxHolder(w.tilt_x, w.tilt_y)
+            fh = _FlowHolder(w.segments)
+            self._keep += [th, fh]
+            d.tx = th.st
+            d.grid = make_grid(w.grid)
+            d.flow = fh.st
+            d.motion = make_motion(w.motion)
+            d.S = int(w.S)
+            d.n_frames = int(w.n_frames)
+            d.t0, d.dt = 0.0, 1.0 / w.prf
+            d.k_cut = int(w.k_cut)
+            d.energy_thresh = float(w.energy_thresh)
+            if plan_only:  # placeholders: the plan reads no device memory
+                d.p0 = d.seg_id = d.flow_coord = d.amp = d.pd = 256
+                continue
+            t = [torch.from_numpy(np.ascontiguousarray(a)).to(self.dev) for a in (w.p0, w.seg, w.flow, w.amp)]
+            self.inputs.append(t)
+            P = w.grid.nx * w.grid.ny * w.grid.nz
+            self.pd.append(torch.empty(P, dtype=torch.float32, device=self.dev))
+            self.eigvals.append(torch.empty(w.n_frames, dtype=torch.float64, device=self.dev))
+            self.k_used.append(torch.empty(1, dtype=torch.int32, device=self.dev))
+            d.p0, d.seg_id, d.flow_coord, d.amp = (x.data_ptr() for x in t)
+            d.pd = self.pd[i].data_ptr()
+            d.eigvals = self.eigvals[i].data_ptr()
+            d.k_used = self.k_used[i].data_ptr()
+        code = FQ_F32 if dtype == torch.float32 else FQ_BF16
+        self.dtype = code
+        plan = C.c_void_p()
+        need = _SZ(0)
+        _check(lib().fq_batch_plan(self.descs, n, code, code, code, int(max_arena_bytes), C.byref(plan),
+                                   C.byref(need)))
+        self.plan = plan
+        self.arena_bytes = need.value
+        self.arena = None
+        self.graph = None
+
+    def info(self):
+        nw = _I32(0)
+        items = (_I64 * 9)()
+        _check(lib().fq_batch_info(self.plan, C.byref(nw), items))
+        return nw.value, dict(zip(STAGES, list(items)))
+
+    def _arena(self):
+        if self.arena is None:
+            self.arena = workspace(self.arena_bytes, self.dev)
+        return self.arena
+
+    def set_tile(self, choice: TileChoice):
+        _check(lib().fq_batch_set_tile(self.plan, C.byref(choice)))
+
+    def launch(self, stream=None):
+        a = self._arena()
+        _check(lib().fq_batch_launch(self.plan, _ptr(a), a.numel(), _stream(stream)))
+
+    def status(self, stream=None):
+        _check(lib().fq_batch_status(self.plan, _ptr(self._arena()), _stream(stream)))
+
+    def capture(self):
+        a = self._arena()
+        g = C.c_void_p()
+        _check(lib().fq_graph_capture(self.plan, _ptr(a), a.numel(), C.byref(g)))
+        if self.graph is not None:
+            lib().fq_graph_free(self.graph)
+        self.graph = g
+
+    def graph_launch(self, stream=None):
+        _check(lib().fq_graph_launch(self.graph, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "graph", None) is not None:
+            lib().fq_graph_free(self.graph)
+            self.graph = None
+        if getattr(self, "plan", None) is not None:
+            lib().fq_batch_free(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fq_autotune(op, batch: Batch, index=0, stream=None):
+    """Time the candidate tile shapes of ``op`` on ensemble ``index`` of
+    ``batch`` (a batch of one on a scratch arena of its own)."""
+    d = batch.descs[index]
+    one = (EnsembleDesc * 1)(d)
+    plan = C.c_void_p()
+    need = _SZ(0)
+    _check(lib().fq_batch_plan(one, 1, batch.dtype, batch.dtype, batch.dtype, 0, C.byref(plan), C.byref(need)))
+    lib().fq_batch_free(plan)
+    arena = workspace(need.value, batch.dev)
+    out = TileChoice()
+    _check(lib().fq_autotune(int(op), one, batch.dtype, _ptr(arena), arena.numel(), C.byref(out), _stream(stream)))
+    return out
+
+
+def abi_sizes():
+    """sizeof of every descriptor struct as the library was compiled."""
+    return [lib().fq_sizeof(i) for i in range(len(ABI_STRUCTS))]

@@ -397,6 +397,74 @@ def config3(seed: int = 3, n_frames: int = 100, n_scat: int = 500_000) -> Worklo
                     bin_dz=0.1e-3, bin_z0=4e-3, n_bins=170)
 
 
+C4_GRIDS = ((128, 1, 128), (192, 1, 192), (256, 1, 256), (64, 64, 64), (96, 96, 96))
+
+
+def _c4_member(rng, probe_kind, n_scat, n_frames, gdims, n_samples=None):
+    """One member of the uneven batch: the C1 or C2 probe and medium with
+    n_scat scatterers (10 % blood), tissue motion, n_frames frames and a
+    2D or 3D grid of gdims over the probe's field of view."""
+    if probe_kind == 1:
+        probe = Probe(64, 1, 0.3e-3, 0.3e-3, 0.3e-3, 0.3e-3, 5e6, 20e6, 1540.0, 0.5, 2, n_samples or 1024)
+        tilt = np.zeros(1)
+        xh, z0, z1 = 10e-3, 2e-3, 32e-3
+        ang = math.radians(30.0)
+        d = np.array([math.cos(ang), 0.0, math.sin(ang)])
+        n_in = np.array([-math.sin(ang), 0.0, math.cos(ang)])
+        L = 20e-3 / math.cos(ang)
+        centre = np.array([0.0, 0.0, 17e-3])
+        segs = [line_segment(centre - 0.5 * L * d, d, L, 0.5e-3, 10e-3, planar_frame=(d, n_in, np.cross(d, n_in)))]
+    else:
+        probe = Probe(128, 1, 0.1e-3, 0.1e-3, 0.1e-3, 0.1e-3, 15.6e6, 62.5e6, 1540.0, 0.5, 2, n_samples or 2048)
+        tilt = np.radians(np.linspace(-6.0, 6.0, 5))
+        xh, z0, z1 = 6.4e-3, 1e-3, 21e-3
+        segs = []
+        for (cx, cz), rc, beta, span, dia, vmax in (((-2.0e-3, 7.0e-3), 3.5e-3, -60, 150, 0.1e-3, 5e-3),
+                                                   ((1.5e-3, 12.0e-3), 4.0e-3, 100, 160, 0.3e-3, 15e-3),
+                                                   ((0.0e-3, 15.0e-3), 5.0e-3, -170, 140, 0.5e-3, 30e-3)):
+            b = math.radians(beta)
+            a1 = np.array([math.cos(b), 0.0, math.sin(b)])
+            a2 = np.array([-math.sin(b), 0.0, math.cos(b)])
+            segs.append(arc_segment((cx, 0.0, cz), a1, a2, rc, math.radians(span), 0.5 * dia, vmax))
+    nx, ny, nz = gdims
+    yh = xh if ny > 1 else 0.0
+    grid = Grid(nx, ny, nz, -xh, -yh, z0, 2 * xh / (nx - 1), (2 * yh / (ny - 1)) if ny > 1 else 0.0,
+                (z1 - z0) / (nz - 1), 1.0)
+    nb = max(1, n_scat // 10)
+    nt = n_scat - nb
+    wts = np.array([s.radius * (s.length if s.kind == SEG_LINE else s.arc_radius * s.phi1) for s in segs])
+    counts = np.floor(nb * wts / wts.sum()).astype(int)
+    counts[-1] += nb - counts.sum()
+    ty = rng.uniform(-yh, yh, nt) if ny > 1 else np.zeros(nt)
+    tx = np.stack([rng.uniform(-1.1 * xh, 1.1 * xh, nt), ty, rng.uniform(0.5 * z0, z1 + 0.5e-3, nt)])
+    seg_ids, q, x1, x2 = _blood_flow_coords(rng, segs, counts, planar=True)
+    amp_t = rayleigh_mean_one(rng, nt)
+    amp_b = 0.1 * rayleigh_mean_one(rng, nb)
+    p0, seg, flow, amp = _assemble(tx, amp_t, seg_ids, q, x1, x2, amp_b)
+    s2 = 1.0 / math.sqrt(2.0)
+    motion = Motion(amp=[50e-6, 200e-6], freq=[1.0, 0.25], phase=[0.0, 0.0], dir=[(0.0, 0.0, 1.0), (s2, 0.0, s2)])
+    k_cut = 2 if ny == 1 else -1
+    name = f"C4 member: C{probe_kind} probe, {n_scat} scat, {n_frames} frames, {nx}x{ny}x{nz}"
+    return Workload(name, probe, tilt, np.zeros_like(tilt), grid, segs, motion, n_frames, 1000.0,
+                    p0, seg, flow, amp, k_cut=k_cut, energy_thresh=0.9)
+
+
+def config4(seed: int = 1000, n: int = 64, s_range=(10_000, 300_000), f_range=(50, 400), grids=C4_GRIDS,
+            n_samples=None) -> list:
+    """The uneven batch: n ensembles, member i seeded with seed + i; S
+    log-uniform over s_range, F uniform over f_range, the grid drawn from
+    ``grids`` (2D 128^2 ... 3D 96^3), the C1 or C2 probe with equal odds."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed + i)
+        S = int(round(math.exp(rng.uniform(math.log(s_range[0]), math.log(s_range[1])))))
+        F = int(rng.integers(f_range[0], f_range[1] + 1))
+        g = grids[int(rng.integers(0, len(grids)))]
+        kind = 1 if rng.uniform() < 0.5 else 2
+        out.append(_c4_member(rng, kind, S, F, g, n_samples))
+    return out
+
+
 def shrink(w: Workload, n_frames=None, max_scat=None, grid_div=None, n_elem=None, n_angles=None,
            n_samples=None, seed=0) -> Workload:
     """A smaller workload of the same shape (for tests that need the oracle

@@ -1,0 +1,116 @@
+"""Batched persistent execution on the GPU: a batch of uneven ensembles
+gives, ensemble by ensemble, exactly what the single-ensemble calls give
+(same tile code), agrees with the FP64 oracle on a member it can finish in
+seconds, and is unchanged by waves, CUDA graph replay and the tile shapes
+the autotuner picks."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_05464_gb300 import build as fqbuild
+from paper_2509_05464_gb300 import fq
+from paper_2509_05464_gb300 import workload as W
+from paper_2509_05464_gb300.pipeline import Pipeline
+
+pytestmark = pytest.mark.gpu
+
+PD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    fqbuild.build()
+    fq.lib()
+
+
+def members(seed=60, n=5):
+    return W.config4(seed=seed, n=n, s_range=(500, 3000), f_range=(8, 40),
+                     grids=((32, 1, 40), (24, 1, 24), (12, 12, 12)))
+
+
+def single(w):
+    pl = Pipeline(w)
+    pl.upload()
+    pl.step()
+    fq.fq_clutter_status(pl.ws_svd)
+    torch.cuda.synchronize()
+    return pl.pd.cpu().numpy(), pl.eigvals.cpu().numpy(), int(pl.k_used.cpu()[0])
+
+
+def results(b):
+    torch.cuda.synchronize()
+    return [(p.cpu().numpy(), e.cpu().numpy(), int(k.cpu()[0])) for p, e, k in zip(b.pd, b.eigvals, b.k_used)]
+
+
+@pytest.fixture(scope="module")
+def batch_and_reference():
+    ms = members()
+    b = fq.Batch(ms)
+    b.launch()
+    b.status()
+    got = results(b)
+    ref = [single(w) for w in ms]
+    return ms, b, got, ref
+
+
+def test_batched_equals_single_ensemble_calls(batch_and_reference):
+    ms, b, got, ref = batch_and_reference
+    for i, ((pd, ev, k), (pd1, ev1, k1)) in enumerate(zip(got, ref)):
+        assert k == k1, i
+        assert np.array_equal(ev, ev1), i
+        assert np.array_equal(pd, pd1), i
+        assert np.isfinite(pd).all() and pd.max() > 0
+
+
+def test_batched_matches_oracle_on_a_small_member():
+    w = W.config4(seed=70, n=1, s_range=(400, 400), f_range=(8, 8), grids=((24, 1, 32),))[0]
+    b = fq.Batch([w])
+    b.launch()
+    b.status()
+    pd = b.pd[0].cpu().numpy()
+    r = oracle.pipeline(w, W.segment_table(w), W.motion_table(w.motion))
+    err = np.linalg.norm(pd - r["pd"]) / np.linalg.norm(r["pd"])
+    assert err <= PD_TOL, err
+    b.close()
+
+
+def test_waves_and_graph_replay_give_the_same_result(batch_and_reference):
+    ms, b, got, _ = batch_and_reference
+    sizes = [fq.Batch([w], plan_only=True).arena_bytes for w in ms]
+    bw = fq.Batch(ms, max_arena_bytes=max(sizes))
+    assert bw.info()[0] >= 2
+    bw.launch()
+    bw.status()
+    for (pd, ev, k), (pd2, ev2, k2) in zip(got, results(bw)):
+        assert np.array_equal(pd, pd2) and np.array_equal(ev, ev2) and k == k2
+    # graph: capture, clear the outputs, replay twice
+    bw.capture()
+    for p in bw.pd:
+        p.zero_()
+    bw.graph_launch()
+    bw.graph_launch()
+    bw.status()
+    for (pd, _, _), (pd2, _, _) in zip(got, results(bw)):
+        assert np.array_equal(pd, pd2)
+    bw.close()
+
+
+def test_autotuned_tiles_keep_results(batch_and_reference):
+    ms, b, got, _ = batch_and_reference
+    big = int(np.argmax([w.S * w.n_frames * w.A * w.M for w in ms]))
+    for op, cands in ((fq.FQ_OP_RF, {2, 3}), (fq.FQ_OP_DAS, {64, 128, 256})):
+        c = fq.fq_autotune(op, b, big)
+        assert c.op == op and c.choice in cands
+        assert c.n_tried == len(cands) and set(c.tried[:c.n_tried]) == cands
+        assert all(t > 0 for t in c.tried_ms[:c.n_tried]) and c.ms == min(c.tried_ms[:c.n_tried])
+        again = fq.fq_autotune(op, b, big)  # cached
+        assert again.n_tried == 0 and again.choice == c.choice
+    for op, ch in ((fq.FQ_OP_RF, 2), (fq.FQ_OP_DAS, 64), (fq.FQ_OP_DAS, 256)):
+        t = fq.TileChoice()
+        t.op, t.choice = op, ch
+        b.set_tile(t)
+        b.launch()
+        b.status()
+        for (pd, _, _), (pd2, _, _) in zip(got, results(b)):
+            assert np.allclose(pd, pd2, rtol=1e-6, atol=0.0)
