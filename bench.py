@@ -356,6 +356,142 @@ def run_ours(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------- batched (uneven C4) --
+def run_batched(args, rank, world, local):
+    """The 64-ensemble uneven batch through the persistent per-stage kernels
+    under a captured CUDA graph, tiles from the autotuner."""
+    import torch
+    from paper_2509_05464_gb300 import fq
+    from paper_2509_05464_gb300 import workload as W
+    from paper_2509_05464_gb300.pipeline import Pipeline
+
+    torch.cuda.set_device(local)
+    fq.lib()
+    ms = W.config4(seed=1000 + 64 * rank)  # an independent batch per rank (weak scaling)
+    b = fq.Batch(ms, max_arena_bytes=args.arena_gb << 30)
+    cost = [w.n_frames * w.A * w.M * w.S for w in ms]
+    big = int(np.argmax(cost))
+    tiles = {}
+    for op, name in ((fq.FQ_OP_RF, "rf_min_ctas_per_sm"), (fq.FQ_OP_DAS, "das_threads")):
+        c = fq.fq_autotune(op, b, big)
+        b.set_tile(c)
+        tiles[name] = {"choice": c.choice, "tried": list(c.tried[:c.n_tried]),
+                       "tried_ms": [round(x, 3) for x in c.tried_ms[:c.n_tried]]}
+    torch.cuda.empty_cache()
+    n_waves, items = b.info()
+    b.launch()
+    b.status()
+    evs = b.launch_profiled()
+    torch.cuda.synchronize()
+    b.status()
+    stage_ms = {st: 0.0 for st in fq.STAGES}
+    for wv in range(n_waves):
+        for j, st in enumerate(fq.STAGES):
+            stage_ms[st] += evs[wv * 9 + j].elapsed_time(evs[wv * 9 + j + 1])
+    b.capture()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        b.graph_launch()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.graph_launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    b.status()
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+
+    # end to end: pinned host inputs copied in, PD images copied out, every step
+    h_in = [[t.cpu().pin_memory() for t in ins] for ins in b.inputs]
+    h_pd = [p.cpu().pin_memory() for p in b.pd]
+    h2d = sum(t.numel() * t.element_size() for ins in h_in for t in ins)
+    d2h = sum(t.numel() * t.element_size() for t in h_pd)
+    e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e2[0].record(stream)
+    for _ in range(args.steps):
+        for hs, ds in zip(h_in, b.inputs):
+            for h, d in zip(hs, ds):
+                d.copy_(h, non_blocking=True)
+        b.graph_launch()
+        for h, d in zip(h_pd, b.pd):
+            h.copy_(d, non_blocking=True)
+        stream.synchronize()
+    e2[1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e2[0].elapsed_time(e2[1]) / args.steps)
+
+    # the same ensembles one by one through the single-ensemble calls
+    seq_ms = 0.0
+    if args.sequential:
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+        for w in ms:
+            pl = Pipeline(w)
+            pl.upload()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pl.step()
+            z.record(stream)
+            torch.cuda.synchronize()
+            seq_ms += a.elapsed_time(z)
+            del pl
+            torch.cuda.empty_cache()
+    cs = float(sum(w.n_frames * w.A * w.M * w.Ns for w in ms))
+    total_cs = sum_over_ranks(cs)
+    if rank != 0:
+        return
+    pk, src = peaks()
+    sm_for_peak = float(pk.get("sm_max_mhz", 2070.0))
+    peak = fp32_alu_peak_tflops(sm_for_peak)
+    pairs = float(sum(w.n_frames * w.A * w.M * w.S for w in ms))
+    taps = sum(w.n_frames * w.A * w.M * w.S * w.probe.n_cycles * w.probe.fs / w.probe.f0 for w in ms) / pairs
+    flop = pairs * (GEOM_FLOP_PER_PAIR + FLOP_PER_TAP * taps)
+    achieved = flop / (stage_ms["rf"] * 1e-3) / 1e12
+    launches = sum(1 for st in fq.STAGES if items[st] > 0) * n_waves
+    line = {
+        "metric": METRIC, "value": total_cs / (ms_step * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "C4 uneven batch: 64 ensembles, S 10k-300k log-uniform, F 50-400, "
+                               "grids 128^2..96^3, C1/C2 probes",
+                   "ensembles": len(ms), "waves": n_waves, "arena_gb": round(b_arena_gb(ms, args), 1),
+                   "graph": True, "tiles": tiles, "items": items,
+                   "parallelism": f"independent batch per GPU x{world}",
+                   "l2": "no flush: every stage's working set is several GB, far above L2"},
+        "stage_ms": stage_ms,
+        "sequential_ms": seq_ms if args.sequential else None,
+        "batched_speedup_vs_sequential": (seq_ms / ms_step) if args.sequential else None,
+        "roofline": {"bound": "alu", "kernel": "rf_pair_batched_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
+                                    f"({src} max clock)",
+                     "work": f"{GEOM_FLOP_PER_PAIR:.0f} + {FLOP_PER_TAP:.0f} x {taps:.3f} taps FLOP per pair, "
+                             f"{pairs:.3e} pairs"},
+        "cpu_baseline": None,
+        "e2e": {"value": total_cs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def b_arena_gb(ms, args):
+    from paper_2509_05464_gb300 import fq
+    b = fq.Batch(ms, plan_only=True, max_arena_bytes=args.arena_gb << 30)
+    n = b.arena_bytes / 1e9
+    b.close()
+    return n
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,6 +504,11 @@ def main():
     ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
+    ap.add_argument("--workload", choices=["c2", "c4"], default="c2",
+                    help="c2: one 200-frame 2D ensemble (default); c4: the 64-ensemble uneven batch")
+    ap.add_argument("--arena-gb", type=int, default=64, help="c4: arena budget in GiB (waves beyond it)")
+    ap.add_argument("--no-sequential", dest="sequential", action="store_false",
+                    help="c4: skip the one-by-one comparison run")
     ap.add_argument("--gram", choices=["f32", "tf32", "bf16"], default="f32",
                     help="Casorati Gram arithmetic: FP32 CUDA cores or TF32 / BF16 tensor cores")
     args = ap.parse_args()
@@ -375,6 +516,8 @@ def main():
     rank, world, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "c4":
+        run_batched(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     import torch.distributed as dist

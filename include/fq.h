@@ -456,6 +456,13 @@ fq_status fq_batch_set_tile(fq_batch *plan, const fq_tile_choice *choice);
  * word per ensemble; fq_batch_status reads them. */
 fq_status fq_batch_launch(fq_batch *plan, void *arena, size_t arena_bytes, void *stream);
 
+/* fq_batch_launch that also records events[0] before the first stage and
+ * events[1 + w * 9 + s] after stage s of wave w (events: host array of
+ * n_events >= 1 + 9 n_waves cudaEvent_t, created by the caller), for
+ * per-stage device times. */
+fq_status fq_batch_launch_profiled(fq_batch *plan, void *arena, size_t arena_bytes, void *stream, void **events,
+                                   int32_t n_events);
+
 /* Reads (and clears) every ensemble's device status word; synchronises the
  * stream.  Returns the first non-OK status with the ensemble index in the
  * message. */

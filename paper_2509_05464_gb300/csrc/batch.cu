@@ -287,14 +287,24 @@ fq_status launch_stage(fq_batch *b, char *arena, int w, int s, cudaStream_t st)
 
 // Everything after the upload: counter and status reset, then the stages of
 // every wave in order (stream-ordered, so each stage sees the previous one).
-fq_status launch_all(fq_batch *b, char *arena, cudaStream_t st)
+// With `ev`, ev[0] is recorded after the reset and ev[1 + w NS + s] after
+// each stage.
+fq_status launch_all(fq_batch *b, char *arena, cudaStream_t st, cudaEvent_t *ev = nullptr)
 {
     fq_status s = fqi::cuda_check(cudaMemsetAsync(arena, 0, b->off_ens, st), "batch: counter reset");
     if (s) return s;
+    if (ev) {
+        s = fqi::cuda_check(cudaEventRecord(ev[0], st), "batch: event");
+        if (s) return s;
+    }
     for (int w = 0; w < (int)b->waves.size(); ++w)
         for (int stage = 0; stage < NS; ++stage) {
             s = launch_stage(b, arena, w, stage, st);
             if (s) return s;
+            if (ev) {
+                s = fqi::cuda_check(cudaEventRecord(ev[1 + w * NS + stage], st), "batch: event");
+                if (s) return s;
+            }
         }
     return FQ_OK;
 }
@@ -453,6 +463,19 @@ fq_status fq_batch_launch(fq_batch *plan, void *arena, size_t arena_bytes, void 
     s = upload(plan, (char *)arena, st);
     if (s) return s;
     return launch_all(plan, (char *)arena, st);
+}
+
+fq_status fq_batch_launch_profiled(fq_batch *plan, void *arena, size_t arena_bytes, void *stream, void **events,
+                                   int32_t n_events)
+{
+    fq_status s = check_arena(plan, arena, arena_bytes, "fq_batch_launch_profiled");
+    if (s) return s;
+    FQ_REQUIRE(events && n_events >= 1 + NS * (int)plan->waves.size(), FQ_ERR_INVALID_ARG,
+               "fq_batch_launch_profiled: needs %d events", 1 + NS * (int)plan->waves.size());
+    cudaStream_t st = (cudaStream_t)stream;
+    s = upload(plan, (char *)arena, st);
+    if (s) return s;
+    return launch_all(plan, (char *)arena, st, reinterpret_cast<cudaEvent_t *>(events));
 }
 
 fq_status fq_batch_status(fq_batch *plan, void *arena, void *stream)

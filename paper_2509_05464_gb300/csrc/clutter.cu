@@ -861,7 +861,9 @@ fq_status launch_eig(const float2 *G, int F, float2 *big, float2 *hv, float *tau
                      float *ii_scr = nullptr)
 {
     size_t smem = big ? 0 : sizeof(float2) * (size_t)F * (F + 1) / 2;
-    if (smem > 48 * 1024) {
+    if (smem > 0) {
+        // the kernel's static arrays count against the same 48 KB default,
+        // so the opt-in is needed for much smaller packed matrices too
         fq_status s = fqi::cuda_check(cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                            (int)smem), "eig: smem attribute");
         if (s) return s;

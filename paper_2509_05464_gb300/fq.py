@@ -137,6 +137,7 @@ def lib():
             "fq_batch_set_tile": [_P, C.POINTER(TileChoice)],
             "fq_batch_launch": [_P, _P, _SZ, _P],
             "fq_batch_status": [_P, _P, _P],
+            "fq_batch_launch_profiled": [_P, _P, _SZ, _P, C.POINTER(_P), _I32],
             "fq_run_batched": [C.POINTER(EnsembleDesc), _I32, _I32, _P, _SZ, _P],
             "fq_graph_capture": [_P, _P, _SZ, C.POINTER(_P)],
             "fq_graph_launch": [_P, _P],
@@ -522,6 +523,18 @@ class Batch:
     def launch(self, stream=None):
         a = self._arena()
         _check(lib().fq_batch_launch(self.plan, _ptr(a), a.numel(), _stream(stream)))
+
+    def launch_profiled(self, stream=None):
+        """Launch with a torch CUDA event after every stage; returns the
+        events (start, then wave-major stage order)."""
+        a = self._arena()
+        nw = self.info()[0]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(1 + 9 * nw)]
+        for e in evs:  # torch creates the CUDA event on its first record
+            e.record()
+        arr = (_P * len(evs))(*[e.cuda_event for e in evs])
+        _check(lib().fq_batch_launch_profiled(self.plan, _ptr(a), a.numel(), _stream(stream), arr, len(evs)))
+        return evs
 
     def status(self, stream=None):
         _check(lib().fq_batch_status(self.plan, _ptr(self._arena()), _stream(stream)))
