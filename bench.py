@@ -36,6 +36,10 @@ UNIT = "channel-samples/s"
 # 10 per pulse tap, 2 * n_cycles * fs / (2 f0) taps on average.
 GEOM_FLOP_PER_PAIR = 17.0
 FLOP_PER_TAP = 10.0
+# DRAM bytes (read + write) of one full-size C2 RF launch, from one ncu
+# capture of rf_synth_pair_kernel (profiles/rf_synth_pair_c2_full_dram.md);
+# None once the kernel changes until it is captured again.
+RF_TRAFFIC_BYTES = 260.75e6 + 993.31e6
 
 
 def peaks():
@@ -340,7 +344,8 @@ def run_ours(args, rank, world, local):
         "das_voxel_angle_per_s": total_va / (ms * 1e-3),
         "stage_ms": stage_ms,
         "roofline": {"bound": "alu", "kernel": "rf_synth_pair_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": RF_TRAFFIC_BYTES if w.n_frames == 200 and w.S == 100_000 else None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
                                     f"({src} max clock)",
                      "work": f"{GEOM_FLOP_PER_PAIR:.0f} + {FLOP_PER_TAP:.0f} x {taps:.3f} taps FLOP per pair, "
