@@ -489,6 +489,64 @@ void fq_graph_free(fq_graph *graph);
 fq_status fq_autotune(int32_t op, const fq_ensemble_desc *ens, int32_t rf_dtype, void *arena, size_t arena_bytes,
                       fq_tile_choice *out, void *stream);
 
+/* ------------------------------------------------------------------ */
+/* a10: learned clutter filter (3D convolutional network)              */
+/* ------------------------------------------------------------------ */
+/* Filters learned from simulated ensembles are the paper's future work
+ * (Sec. 1, Sec. 4).  Network: four 3D convolutions over the IQ ensemble,
+ * 2 -> 32 -> 32 -> 32 -> 2 channels, kernels of 5 frames x 3 x 3 pixels,
+ * zero "same" padding, bias, ReLU after the first three; input = (Re, Im)
+ * of the IQ times a normalisation `scale`, output = estimated blood IQ,
+ * power Doppler = mean over frames of |output|^2 / scale^2.  Convention:
+ *   y[v, o] = b[o] + sum_t sum_i x[v + d_t, i] W[t][i][o],
+ *   d_t = (dt, dz, dx), dt in -2..2, dz, dx in -1..1, t = (dt+2) 9 + (dz+1) 3 + (dx+1).
+ * Volumes are channels-last [n_vol][F][Z][X][32] (Z a multiple of 4, X a
+ * multiple of 32), BF16 activations (channels beyond the real ones are 0),
+ * FP32 network output.  Convolutions run on the tcgen05 tensor cores (BF16
+ * in, FP32 accumulate); weight gradients on the CUDA cores in FP32.
+ *
+ * Parameters: one device block of fq_cnn_param_bytes() (256-byte aligned),
+ * owned by the caller.  FP32 master weights W[layer] [45][32][32] (tap, in,
+ * out; entries beyond the layer's channels must be 0) and biases b[layer]
+ * [32], then the Adam moments m and v over the same span, then the BF16
+ * tap tiles the kernels read.  fq_cnn_param_offset(what, layer) gives byte
+ * offsets: what = 0 W[layer], 1 b[layer], 2 m, 3 v, 4 size of the trainable
+ * span (W and b of all layers, the layout of `grads`).  After writing the
+ * master weights call fq_cnn_pack; fq_cnn_adam repacks by itself.
+ * `status`: device int, set to FQ_ERR_TIMEOUT if a bounded wait inside a
+ * convolution ran out. */
+size_t fq_cnn_param_bytes(void);
+size_t fq_cnn_param_offset(int32_t what, int32_t layer);
+/* Activation workspace for n_vol volumes; fq_cnn_act_offset(which, ...)
+ * gives the byte offset of hidden layer `which` (0..2) or, for 3, of the
+ * FP32 output [n_vol][F][Z][X][32] (channels 0, 1 used). */
+size_t fq_cnn_act_bytes(int32_t n_vol, int32_t F, int32_t Z, int32_t X);
+size_t fq_cnn_act_offset(int32_t which, int32_t n_vol, int32_t F, int32_t Z, int32_t X);
+fq_status fq_cnn_pack(void *params, void *stream);
+/* Casorati [P][F][2] FP32 (pixel p = x + X z) -> input volume (BF16,
+ * nullable) and / or training target [F][Z][X][2] FP32 (nullable), both
+ * multiplied by scale. */
+fq_status fq_cnn_from_casorati(const float *iq, int32_t F, int32_t Z, int32_t X, float scale, void *vol,
+                               float *target, void *stream);
+/* One convolution layer: mode 0 = bias + ReLU -> BF16, 1 = bias -> FP32,
+ * 2 = (no bias) x (mask > 0) -> BF16; backward != 0 uses the flipped,
+ * channel-swapped kernel of the data gradient. */
+fq_status fq_cnn_conv(int32_t mode, const void *in, const void *params, int32_t layer, int32_t backward,
+                      void *out, const void *mask, int32_t n_vol, int32_t F, int32_t Z, int32_t X,
+                      int32_t *status, void *stream);
+fq_status fq_cnn_forward(const void *params, const void *vol, int32_t n_vol, int32_t F, int32_t Z, int32_t X,
+                         void *acts, size_t act_bytes, int32_t *status, void *stream);
+/* After fq_cnn_forward on the same acts: MSE against target [n_vol][F][Z][X][2]
+ * into *loss (device float), gradients of W and b into grads (device FP32,
+ * the trainable-span layout). */
+fq_status fq_cnn_backward(const void *params, const void *vol, const float *target, int32_t n_vol, int32_t F,
+                          int32_t Z, int32_t X, void *acts, size_t act_bytes, float *grads, float *loss,
+                          int32_t *status, void *stream);
+/* Adam (beta 0.9, 0.999, eps 1e-8), step >= 1, then repack. */
+fq_status fq_cnn_adam(void *params, const float *grads, float lr, int32_t step, void *stream);
+fq_status fq_cnn_power_doppler(const float *out, int32_t F, int32_t Z, int32_t X, float scale, float *pd,
+                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

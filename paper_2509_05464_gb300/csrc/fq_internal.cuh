@@ -241,6 +241,10 @@ struct ProbeFF {
 bool make_probe_ff(const fq_probe *p, ProbeFF &o);
 void make_angles_ff(const fq_probe *p, const fq_tx *tx, AngleFF *out);
 
+// the driver's cuTensorMapEncodeTiled through the runtime's entry-point query
+// (nullptr if unavailable); declared with the driver types by its users
+void *tensor_map_encoder_ptr();
+
 // tensor-core Casorati Gram (gram_tc.cu); esz = operand bytes (2 BF16, 4 TF32)
 size_t gram_tc_workspace_bytes(int64_t P, int F, int esz);
 fq_status gram_tc(const void *S, int dtype, int64_t P, int F, int esz, float2 *G, char *ws, int *status,

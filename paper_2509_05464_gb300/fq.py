@@ -142,6 +142,13 @@ def lib():
             "fq_graph_capture": [_P, _P, _SZ, C.POINTER(_P)],
             "fq_graph_launch": [_P, _P],
             "fq_autotune": [_I32, C.POINTER(EnsembleDesc), _I32, _P, _SZ, C.POINTER(TileChoice), _P],
+            "fq_cnn_pack": [_P, _P],
+            "fq_cnn_from_casorati": [_P, _I32, _I32, _I32, C.c_float, _P, _P, _P],
+            "fq_cnn_conv": [_I32, _P, _P, _I32, _I32, _P, _P, _I32, _I32, _I32, _I32, _P, _P],
+            "fq_cnn_forward": [_P, _P, _I32, _I32, _I32, _I32, _P, _SZ, _P, _P],
+            "fq_cnn_backward": [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _SZ, _P, _P, _P, _P],
+            "fq_cnn_adam": [_P, _P, C.c_float, _I32, _P],
+            "fq_cnn_power_doppler": [_P, _I32, _I32, _I32, C.c_float, _P, _P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -153,6 +160,14 @@ def lib():
         L.fq_graph_free.restype = None
         L.fq_sizeof.argtypes = [_I32]
         L.fq_sizeof.restype = _SZ
+        L.fq_cnn_param_bytes.argtypes = []
+        L.fq_cnn_param_bytes.restype = _SZ
+        L.fq_cnn_param_offset.argtypes = [_I32, _I32]
+        L.fq_cnn_param_offset.restype = _SZ
+        L.fq_cnn_act_bytes.argtypes = [_I32, _I32, _I32, _I32]
+        L.fq_cnn_act_bytes.restype = _SZ
+        L.fq_cnn_act_offset.argtypes = [_I32, _I32, _I32, _I32, _I32]
+        L.fq_cnn_act_offset.restype = _SZ
         _lib = L
         return L
 
@@ -583,3 +598,121 @@ def fq_autotune(op, batch: Batch, index=0, stream=None):
 def abi_sizes():
     """sizeof of every descriptor struct as the library was compiled."""
     return [lib().fq_sizeof(i) for i in range(len(ABI_STRUCTS))]
+
+
+# ------------------------------------------------------- learned filter (a10) --
+CNN_CHANNELS = (2, 32, 32, 32, 2)
+CNN_MODE_RELU, CNN_MODE_LINEAR, CNN_MODE_MASK = 0, 1, 2
+
+
+class CNN:
+    """Parameters of the 3D convolutional clutter filter in one device block
+    (layout of include/fq.h), initialised He-normal from ``seed``."""
+
+    def __init__(self, seed=0, device="cuda"):
+        self.dev = torch.device(device)
+        L = lib()
+        self.params = workspace(L.fq_cnn_param_bytes(), self.dev)
+        self.params.zero_()
+        self.pf = self.params[: (L.fq_cnn_param_bytes() // 4) * 4].view(torch.float32)
+        self.n_train = L.fq_cnn_param_offset(4, 0) // 4
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.dev)
+        rng = np.random.default_rng(seed)
+        layers = []
+        for cin, cout in zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:]):
+            w = rng.standard_normal((45, cin, cout)) * np.sqrt(2.0 / (45 * cin))
+            layers.append((w, np.zeros(cout)))
+        self.set_weights(layers)
+
+    def w_view(self, layer):
+        o = lib().fq_cnn_param_offset(0, layer) // 4
+        return self.pf[o:o + 45 * 32 * 32].view(45, 32, 32)
+
+    def b_view(self, layer):
+        o = lib().fq_cnn_param_offset(1, layer) // 4
+        return self.pf[o:o + 32]
+
+    def set_weights(self, layers, stream=None):
+        """layers: [(w [45, cin, cout], b [cout])] (numpy, any float dtype)."""
+        for l, (w, b) in enumerate(layers):
+            W = torch.zeros((45, 32, 32), dtype=torch.float32)
+            W[:, : w.shape[1], : w.shape[2]] = torch.from_numpy(np.asarray(w, np.float32))
+            B = torch.zeros(32, dtype=torch.float32)
+            B[: b.shape[0]] = torch.from_numpy(np.asarray(b, np.float32))
+            self.w_view(l).copy_(W)
+            self.b_view(l).copy_(B)
+        mo = lib().fq_cnn_param_offset(2, 0) // 4
+        self.pf[mo:mo + 2 * self.n_train].zero_()
+        _check(lib().fq_cnn_pack(_ptr(self.params), _stream(stream)))
+
+    def get_weights(self):
+        out = []
+        for l, (cin, cout) in enumerate(zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:])):
+            out.append((self.w_view(l)[:, :cin, :cout].double().cpu().numpy(),
+                        self.b_view(l)[:cout].double().cpu().numpy()))
+        return out
+
+    def grads_buffer(self):
+        return torch.zeros(self.n_train, dtype=torch.float32, device=self.dev)
+
+
+def cnn_act_workspace(n_vol, F, Z, X, device="cuda"):
+    return workspace(lib().fq_cnn_act_bytes(n_vol, F, Z, X), device)
+
+
+def cnn_output(acts, n_vol, F, Z, X):
+    """The FP32 network output [n_vol, F, Z, X, 32] inside an activation workspace."""
+    o = lib().fq_cnn_act_offset(3, n_vol, F, Z, X)
+    n = n_vol * F * Z * X * 32
+    return acts[o:o + 4 * n].view(torch.float32).view(n_vol, F, Z, X, 32)
+
+
+def cnn_hidden(acts, which, n_vol, F, Z, X):
+    o = lib().fq_cnn_act_offset(which, n_vol, F, Z, X)
+    n = n_vol * F * Z * X * 32
+    return acts[o:o + 2 * n].view(torch.bfloat16).view(n_vol, F, Z, X, 32)
+
+
+def fq_cnn_from_casorati(iq, F, Z, X, scale, vol=None, target=None, stream=None):
+    _check(lib().fq_cnn_from_casorati(_ptr(iq), int(F), int(Z), int(X), float(scale), _ptr(vol), _ptr(target),
+                                      _stream(stream)))
+    return vol, target
+
+
+def fq_cnn_conv(mode, x, net: CNN, layer, backward, out, mask=None, stream=None):
+    n, F, Z, X = x.shape[:4]
+    _check(lib().fq_cnn_conv(int(mode), _ptr(x), _ptr(net.params), int(layer), int(backward), _ptr(out), _ptr(mask),
+                             n, F, Z, X, _ptr(net.status), _stream(stream)))
+    return out
+
+
+def fq_cnn_forward(net: CNN, vol, acts=None, stream=None):
+    n, F, Z, X = vol.shape[:4]
+    if acts is None:
+        acts = cnn_act_workspace(n, F, Z, X, vol.device)
+    _check(lib().fq_cnn_forward(_ptr(net.params), _ptr(vol), n, F, Z, X, _ptr(acts), acts.numel(),
+                                _ptr(net.status), _stream(stream)))
+    return acts
+
+
+def fq_cnn_backward(net: CNN, vol, target, acts, grads=None, loss=None, stream=None):
+    n, F, Z, X = vol.shape[:4]
+    if grads is None:
+        grads = net.grads_buffer()
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=vol.device)
+    _check(lib().fq_cnn_backward(_ptr(net.params), _ptr(vol), _ptr(target), n, F, Z, X, _ptr(acts), acts.numel(),
+                                 _ptr(grads), _ptr(loss), _ptr(net.status), _stream(stream)))
+    return grads, loss
+
+
+def fq_cnn_adam(net: CNN, grads, lr, step, stream=None):
+    _check(lib().fq_cnn_adam(_ptr(net.params), _ptr(grads), float(lr), int(step), _stream(stream)))
+
+
+def fq_cnn_power_doppler(out, scale, pd=None, stream=None):
+    F, Z, X = out.shape[:3]
+    if pd is None:
+        pd = torch.empty(Z * X, dtype=torch.float32, device=out.device)
+    _check(lib().fq_cnn_power_doppler(_ptr(out), F, Z, X, float(scale), _ptr(pd), _stream(stream)))
+    return pd
