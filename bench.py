@@ -489,6 +489,106 @@ def run_batched(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------ learned clutter filter (C5) --
+def run_cnn(args, rank, world, local):
+    """Training throughput and held-out PD quality of the learned filter on
+    GPU-simulated C1-like ensembles, and inference on a 200-frame 256x256
+    ensemble of the benchmark workload."""
+    import torch
+    from paper_2509_05464_gb300 import fq
+    from paper_2509_05464_gb300 import learned
+    from paper_2509_05464_gb300 import workload as W
+    from paper_2509_05464_gb300.pipeline import Pipeline
+
+    torch.cuda.set_device(local)
+    fq.lib()
+    n_ens = args.cnn_ensembles
+    n_test = max(2, n_ens // 8)
+    seeds = list(range(10000 + rank * 100000, 10000 + rank * 100000 + n_ens))
+    t0 = time.perf_counter()
+    vol, tgt, scales, pd_gt, pd_svd = learned.ensembles(seeds, target_gain=args.cnn_gain)
+    gen_s = time.perf_counter() - t0
+    n_tr = n_ens - n_test
+    F, Z, X = vol.shape[1:4]
+    net = fq.CNN(0)
+    batch = 4
+    learned.train(net, vol[:n_tr], tgt[:n_tr], steps=max(1, args.warmup), batch=batch, lr=args.cnn_lr, seed=1)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    hist = learned.train(net, vol[:n_tr], tgt[:n_tr], steps=args.cnn_train_steps, batch=batch, lr=args.cnn_lr, seed=2,
+                         log_every=max(1, args.cnn_train_steps // 10))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1) / args.cnn_train_steps
+    held = slice(n_tr, n_ens)
+    pd_cnn = learned.predict_pd(net, vol[held], scales[n_tr:], args.cnn_gain)
+    inv = torch.tensor([1.0 / (s * s) for s in scales[n_tr:]], device=vol.device)[:, None]
+    raw = (vol[held, ..., :2].float() ** 2).sum(-1).mean(1).reshape(n_test, -1) * inv  # after mean removal
+    quality = {"pd_rel_l2_cnn": learned.rel_l2(pd_cnn, pd_gt[held]),
+               "pd_rel_l2_svd_k2": learned.rel_l2(pd_svd[held], pd_gt[held]),
+               "pd_rel_l2_unfiltered": learned.rel_l2(raw, pd_gt[held]),
+               "held_out_ensembles": n_test}
+
+    # inference on the benchmark ensemble (200 frames, 256 x 256 pixels)
+    w = W.config2(n_frames=args.cnn_infer_frames)
+    pl = Pipeline(w)
+    pl.upload()
+    pl.step()
+    Fi, Zi, Xi = w.n_frames, w.grid.nz, w.grid.nx
+    vin = torch.empty((1, Fi, Zi, Xi, 32), dtype=torch.bfloat16, device="cuda")
+    _, _, sc = fq.fq_cnn_from_casorati(pl.iq, Fi, Zi, Xi, True, vol=vin[0])
+    scale = float(sc.item()) * args.cnn_gain
+    del pl
+    torch.cuda.empty_cache()
+    acts = fq.cnn_act_workspace(1, Fi, Zi, Xi)
+    for _ in range(max(1, args.warmup)):
+        fq.fq_cnn_forward(net, vin, acts)
+    clk = ClockSampler(local)
+    clk.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        fq.fq_cnn_forward(net, vin, acts)
+        pd = fq.fq_cnn_power_doppler(fq.cnn_output(acts, 1, Fi, Zi, Xi)[0], scale)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    assert int(net.status.item()) == 0, "a bounded wait in a convolution ran out"
+    inf_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    V = Fi * Zi * Xi
+    mac_true = sum(45 * a * b for a, b in zip(fq.CNN_CHANNELS[:-1], fq.CNN_CHANNELS[1:]))
+    mac_exec = 4 * 45 * 32 * 32
+    pk, src = peaks()
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    ach = 2.0 * mac_true * V / (inf_ms * 1e-3) / 1e12
+    total_v = sum_over_ranks(float(V))
+    if rank != 0:
+        return
+    line = {
+        "metric": "CNN clutter-filter inference voxel-frames/s (4 x 3D conv, 5x3x3, 32 ch, BF16/FP32)",
+        "value": total_v / (inf_ms * 1e-3), "unit": "voxel-frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": inf_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"C5 learned filter: inference on {Fi} x {Zi} x {Xi} (C2 ensemble); training on "
+                               f"{n_tr} C1-like 64 x 32 x 32 ensembles, batch {batch}",
+                   "train_ms_per_step": train_ms, "train_voxels_per_s": batch * F * Z * X / (train_ms * 1e-3),
+                   "train_loss": hist, "data_generation_s": gen_s,
+                   "l2": "inference working set (activations 0.84 GB per layer) far above L2"},
+        "quality": quality,
+        "roofline": {"bound": "tensor", "kernel": "conv_tc_kernel", "achieved": ach, "peak": peak,
+                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                     "peak_source": f"bf16_tflops of {src} peaks (cuBLAS burst)",
+                     "work": f"2 x {mac_true} MAC per voxel (the 2-32-32-32-2 network); the kernels execute "
+                             f"{mac_exec} (2-channel ends padded to 32)"},
+        "cpu_baseline": None,
+        "e2e": None,
+        "gpu_launches": 5 * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def b_arena_gb(ms, args):
     from paper_2509_05464_gb300 import fq
     b = fq.Batch(ms, plan_only=True, max_arena_bytes=args.arena_gb << 30)
@@ -509,8 +609,14 @@ def main():
     ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
-    ap.add_argument("--workload", choices=["c2", "c4"], default="c2",
-                    help="c2: one 200-frame 2D ensemble (default); c4: the 64-ensemble uneven batch")
+    ap.add_argument("--workload", choices=["c2", "c4", "c5"], default="c2",
+                    help="c2: one 200-frame 2D ensemble (default); c4: the 64-ensemble uneven batch; "
+                         "c5: the learned clutter filter")
+    ap.add_argument("--cnn-ensembles", type=int, default=64, help="c5: simulated training + held-out ensembles")
+    ap.add_argument("--cnn-train-steps", type=int, default=1500, help="c5: timed training steps")
+    ap.add_argument("--cnn-infer-frames", type=int, default=200, help="c5: frames of the inference ensemble")
+    ap.add_argument("--cnn-gain", type=float, default=8.0, help="c5: target gain of the training pairs")
+    ap.add_argument("--cnn-lr", type=float, default=3e-4, help="c5: Adam learning rate")
     ap.add_argument("--arena-gb", type=int, default=64, help="c4: arena budget in GiB (waves beyond it)")
     ap.add_argument("--no-sequential", dest="sequential", action="store_false",
                     help="c4: skip the one-by-one comparison run")
@@ -523,6 +629,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "c4":
         run_batched(args, rank, world, local)
+    elif args.workload == "c5":
+        run_cnn(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     import torch.distributed as dist

@@ -524,10 +524,16 @@ size_t fq_cnn_act_bytes(int32_t n_vol, int32_t F, int32_t Z, int32_t X);
 size_t fq_cnn_act_offset(int32_t which, int32_t n_vol, int32_t F, int32_t Z, int32_t X);
 fq_status fq_cnn_pack(void *params, void *stream);
 /* Casorati [P][F][2] FP32 (pixel p = x + X z) -> input volume (BF16,
- * nullable) and / or training target [F][Z][X][2] FP32 (nullable), both
- * multiplied by scale. */
-fq_status fq_cnn_from_casorati(const float *iq, int32_t F, int32_t Z, int32_t X, float scale, void *vol,
-                               float *target, void *stream);
+ * nullable) and / or training target [F][Z][X][2] FP32 (nullable):
+ * (s - m_p) * scale * gain, m_p = the pixel's temporal mean when
+ * remove_mean != 0 (the static part of the echo), else 0.  scale = *scale_in
+ * (device float) if given, else 1 / RMS of the deviations of this ensemble,
+ * written to *scale_out (device float).  Workspace: fq_cnn_prep_bytes(Z, X)
+ * bytes, 256-byte aligned. */
+size_t fq_cnn_prep_bytes(int32_t Z, int32_t X);
+fq_status fq_cnn_from_casorati(const float *iq, int32_t F, int32_t Z, int32_t X, int32_t remove_mean,
+                               const float *scale_in, float *scale_out, float gain, void *vol, float *target,
+                               void *workspace, size_t workspace_bytes, void *stream);
 /* One convolution layer: mode 0 = bias + ReLU -> BF16, 1 = bias -> FP32,
  * 2 = (no bias) x (mask > 0) -> BF16; backward != 0 uses the flipped,
  * channel-swapped kernel of the data gradient. */

@@ -276,34 +276,76 @@ __global__ void pack_weights_kernel(const float *__restrict__ w, __nv_bfloat16 *
     wb[((size_t)(NTAP - 1 - t) * C + ci) * C + co] = v;
 }
 
-// Casorati [P][F][2] (pixel p = x + X z) -> channels-last BF16 volume
-// [F][Z][X][32] with channels 0, 1 = scale * (Re, Im), the rest 0.
-__global__ void casorati_to_volume_kernel(const float *__restrict__ iq, int F, int Z, int X, float scale,
-                                          __nv_bfloat16 *__restrict__ vol)
+// Packing of a Casorati ensemble [P][F][2] (pixel p = x + X z) for the
+// network.  Pass 1 (one thread per pixel): the pixel's temporal mean (when
+// removing it) and its sum of squared deviations, accumulated per CTA.
+__global__ void casorati_stats_kernel(const float *__restrict__ iq, int F, int64_t P, int remove_mean,
+                                      float2 *__restrict__ mean, double *__restrict__ part)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)F * Z * X;
-    if (i >= total) return;
-    const int x = (int)(i % X), z = (int)((i / X) % Z), f = (int)(i / ((int64_t)X * Z));
-    const float2 s = reinterpret_cast<const float2 *>(iq)[((int64_t)z * X + x) * F + f];
-    uint4 out[4] = {};
-    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(out);
-    h[0] = __floats2bfloat162_rn(scale * s.x, scale * s.y);
-    uint4 *o = reinterpret_cast<uint4 *>(vol + i * C);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o[k] = out[k];
+    __shared__ double red[8];
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double ss = 0.0;
+    if (p < P) {
+        const float2 *s = reinterpret_cast<const float2 *>(iq) + p * F;
+        float mr = 0.0f, mi = 0.0f;
+        if (remove_mean) {
+            for (int f = 0; f < F; ++f) {
+                mr += s[f].x;
+                mi += s[f].y;
+            }
+            mr /= (float)F;
+            mi /= (float)F;
+        }
+        mean[p] = make_float2(mr, mi);
+        for (int f = 0; f < F; ++f) {
+            const float a = s[f].x - mr, b = s[f].y - mi;
+            ss += (double)a * a + (double)b * b;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
 }
 
-// Same for the FP32 training target [F][Z][X][2].
-__global__ void casorati_to_target_kernel(const float *__restrict__ iq, int F, int Z, int X, float scale,
-                                          float *__restrict__ tgt)
+// scale = 1 / RMS of the deviations over the whole ensemble (real and
+// imaginary parts counted separately), into *scale.
+__global__ void casorati_scale_kernel(const double *__restrict__ part, int n, int64_t count, float *__restrict__ scale)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)F * Z * X;
-    if (i >= total) return;
-    const int x = (int)(i % X), z = (int)((i / X) % Z), f = (int)(i / ((int64_t)X * Z));
-    const float2 s = reinterpret_cast<const float2 *>(iq)[((int64_t)z * X + x) * F + f];
-    reinterpret_cast<float2 *>(tgt)[i] = make_float2(scale * s.x, scale * s.y);
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) s += part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *scale = s > 0.0 ? (float)(1.0 / sqrt(s / (double)count)) : 1.0f;
+}
+
+// Pass 2 (one thread per pixel, frames in turn): (s - mean) * scale * gain
+// into the BF16 volume [F][Z][X][32] (channels 0, 1; the rest 0) and / or
+// the FP32 target [F][Z][X][2].
+__global__ void casorati_pack_kernel(const float *__restrict__ iq, int F, int64_t P, const float2 *__restrict__ mean,
+                                     const float *__restrict__ scale, float gain, __nv_bfloat16 *__restrict__ vol,
+                                     float *__restrict__ tgt)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const float g = *scale * gain;
+    const float2 m = mean[p];
+    const float2 *s = reinterpret_cast<const float2 *>(iq) + p * F;
+    for (int f = 0; f < F; ++f) {
+        const float a = (s[f].x - m.x) * g, b = (s[f].y - m.y) * g;
+        const int64_t i = (int64_t)f * P + p;
+        if (vol) {
+            uint4 out[4] = {};
+            reinterpret_cast<__nv_bfloat162 *>(out)[0] = __floats2bfloat162_rn(a, b);
+            uint4 *o = reinterpret_cast<uint4 *>(vol + i * C);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[k] = out[k];
+        }
+        if (tgt) reinterpret_cast<float2 *>(tgt)[i] = make_float2(a, b);
+    }
 }
 
 // MSE loss of channels 0, 1 of y [V][32] against t [V][2]: gradient
@@ -577,6 +619,13 @@ extern "C" {
 
 size_t fq_cnn_param_bytes(void) { return param_layout().total_bytes; }
 
+size_t fq_cnn_prep_bytes(int32_t Z, int32_t X)
+{
+    const int64_t P = (int64_t)Z * X;
+    const int64_t blocks = (P + 255) / 256;
+    return (((size_t)P * 8 + 255) & ~(size_t)255) + (size_t)blocks * 8 + 256;
+}
+
 size_t fq_cnn_act_bytes(int32_t n_vol, int32_t F, int32_t Z, int32_t X)
 {
     if (n_vol < 1 || F < 1 || Z < 1 || X < 1) return 0;
@@ -598,18 +647,30 @@ fq_status fq_cnn_pack(void *params, void *stream)
     return fqi::launch_check("fq_cnn_pack");
 }
 
-fq_status fq_cnn_from_casorati(const float *iq, int32_t F, int32_t Z, int32_t X, float scale, void *vol,
-                               float *target, void *stream)
+fq_status fq_cnn_from_casorati(const float *iq, int32_t F, int32_t Z, int32_t X, int32_t remove_mean,
+                               const float *scale_in, float *scale_out, float gain, void *vol, float *target,
+                               void *workspace, size_t workspace_bytes, void *stream)
 {
-    FQ_REQUIRE(iq && (vol || target) && F >= 1 && Z >= 1 && X >= 1, FQ_ERR_INVALID_ARG,
+    FQ_REQUIRE(iq && (vol || target) && F >= 1 && Z >= 1 && X >= 1 && workspace, FQ_ERR_INVALID_ARG,
                "fq_cnn_from_casorati: bad arguments");
-    FQ_REQUIRE(fqi::aligned(iq, 8) && fqi::aligned(vol, 16) && fqi::aligned(target, 8), FQ_ERR_ALIGN,
-               "fq_cnn_from_casorati: alignment");
+    FQ_REQUIRE(scale_in || scale_out, FQ_ERR_INVALID_ARG, "fq_cnn_from_casorati: needs scale_in or scale_out");
+    FQ_REQUIRE(fqi::aligned(iq, 8) && fqi::aligned(vol, 16) && fqi::aligned(target, 8) &&
+                   fqi::aligned(workspace, 256),
+               FQ_ERR_ALIGN, "fq_cnn_from_casorati: alignment");
+    const int64_t P = (int64_t)Z * X;
+    const int blocks = (int)((P + 255) / 256);
+    const size_t need = fq_cnn_prep_bytes(Z, X);
+    FQ_REQUIRE(workspace_bytes >= need, FQ_ERR_WORKSPACE, "fq_cnn_from_casorati: workspace needs %zu bytes", need);
+    float2 *mean = (float2 *)workspace;
+    double *part = (double *)((char *)workspace + (((size_t)P * 8 + 255) & ~(size_t)255));
     cudaStream_t st = (cudaStream_t)stream;
-    const int64_t n = (int64_t)F * Z * X;
-    const unsigned blocks = (unsigned)((n + 255) / 256);
-    if (vol) casorati_to_volume_kernel<<<blocks, 256, 0, st>>>(iq, F, Z, X, scale, (__nv_bfloat16 *)vol);
-    if (target) casorati_to_target_kernel<<<blocks, 256, 0, st>>>(iq, F, Z, X, scale, target);
+    casorati_stats_kernel<<<blocks, 256, 0, st>>>(iq, F, P, remove_mean, mean, part);
+    const float *scale = scale_in;
+    if (!scale_in) {
+        casorati_scale_kernel<<<1, 32, 0, st>>>(part, blocks, 2 * P * F, scale_out);
+        scale = scale_out;
+    }
+    casorati_pack_kernel<<<blocks, 256, 0, st>>>(iq, F, P, mean, scale, gain, (__nv_bfloat16 *)vol, target);
     return fqi::launch_check("fq_cnn_from_casorati");
 }
 

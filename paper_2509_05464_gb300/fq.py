@@ -143,7 +143,7 @@ def lib():
             "fq_graph_launch": [_P, _P],
             "fq_autotune": [_I32, C.POINTER(EnsembleDesc), _I32, _P, _SZ, C.POINTER(TileChoice), _P],
             "fq_cnn_pack": [_P, _P],
-            "fq_cnn_from_casorati": [_P, _I32, _I32, _I32, C.c_float, _P, _P, _P],
+            "fq_cnn_from_casorati": [_P, _I32, _I32, _I32, _I32, _P, _P, C.c_float, _P, _P, _P, _SZ, _P],
             "fq_cnn_conv": [_I32, _P, _P, _I32, _I32, _P, _P, _I32, _I32, _I32, _I32, _P, _P],
             "fq_cnn_forward": [_P, _P, _I32, _I32, _I32, _I32, _P, _SZ, _P, _P],
             "fq_cnn_backward": [_P, _P, _P, _I32, _I32, _I32, _I32, _P, _SZ, _P, _P, _P, _P],
@@ -168,6 +168,8 @@ def lib():
         L.fq_cnn_act_bytes.restype = _SZ
         L.fq_cnn_act_offset.argtypes = [_I32, _I32, _I32, _I32, _I32]
         L.fq_cnn_act_offset.restype = _SZ
+        L.fq_cnn_prep_bytes.argtypes = [_I32, _I32]
+        L.fq_cnn_prep_bytes.restype = _SZ
         _lib = L
         return L
 
@@ -607,9 +609,11 @@ CNN_MODE_RELU, CNN_MODE_LINEAR, CNN_MODE_MASK = 0, 1, 2
 
 class CNN:
     """Parameters of the 3D convolutional clutter filter in one device block
-    (layout of include/fq.h), initialised He-normal from ``seed``."""
+    (layout of include/fq.h), initialised He-normal from ``seed``; the last
+    layer starts at zero (``zero_last``) so that the initial output is 0 and
+    early training does not silence the hidden ReLUs to shrink it."""
 
-    def __init__(self, seed=0, device="cuda"):
+    def __init__(self, seed=0, device="cuda", zero_last=True):
         self.dev = torch.device(device)
         L = lib()
         self.params = workspace(L.fq_cnn_param_bytes(), self.dev)
@@ -622,6 +626,8 @@ class CNN:
         for cin, cout in zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:]):
             w = rng.standard_normal((45, cin, cout)) * np.sqrt(2.0 / (45 * cin))
             layers.append((w, np.zeros(cout)))
+        if zero_last:
+            layers[-1] = (np.zeros_like(layers[-1][0]), layers[-1][1])
         self.set_weights(layers)
 
     def w_view(self, layer):
@@ -673,10 +679,18 @@ def cnn_hidden(acts, which, n_vol, F, Z, X):
     return acts[o:o + 2 * n].view(torch.bfloat16).view(n_vol, F, Z, X, 32)
 
 
-def fq_cnn_from_casorati(iq, F, Z, X, scale, vol=None, target=None, stream=None):
-    _check(lib().fq_cnn_from_casorati(_ptr(iq), int(F), int(Z), int(X), float(scale), _ptr(vol), _ptr(target),
+def fq_cnn_from_casorati(iq, F, Z, X, remove_mean=True, scale_in=None, scale_out=None, gain=1.0, vol=None,
+                         target=None, ws=None, stream=None):
+    """Pack a Casorati ensemble for the network; returns (vol, target, scale
+    tensor).  The scale is computed on the device unless ``scale_in``."""
+    if scale_in is None and scale_out is None:
+        scale_out = torch.empty(1, dtype=torch.float32, device=iq.device)
+    if ws is None:
+        ws = workspace(lib().fq_cnn_prep_bytes(int(Z), int(X)), iq.device)
+    _check(lib().fq_cnn_from_casorati(_ptr(iq), int(F), int(Z), int(X), int(bool(remove_mean)), _ptr(scale_in),
+                                      _ptr(scale_out), float(gain), _ptr(vol), _ptr(target), _ptr(ws), ws.numel(),
                                       _stream(stream)))
-    return vol, target
+    return vol, target, (scale_in if scale_in is not None else scale_out)
 
 
 def fq_cnn_conv(mode, x, net: CNN, layer, backward, out, mask=None, stream=None):

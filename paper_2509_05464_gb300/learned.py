@@ -41,9 +41,13 @@ def casorati(w):
     return pl.iq.clone(), pl.pd.clone()
 
 
-def ensembles(seeds, n_frames=64, Z=32, X=32, n_scat=2000, device="cuda"):
+def ensembles(seeds, n_frames=64, Z=32, X=32, n_scat=2000, target_gain=1.0, remove_mean=True, device="cuda"):
     """Input volumes [n, F, Z, X, 32] BF16, targets [n, F, Z, X, 2] FP32,
-    scales [n], blood-only PD [n, Z X] and SVD-filtered PD [n, Z X]."""
+    scales [n], blood-only PD [n, Z X] and SVD-filtered PD [n, Z X].  Input:
+    the whole-scene IQ less each pixel's temporal mean (the static echo),
+    divided by its RMS; target: the blood-only IQ treated the same way with
+    the input's scale, times target_gain (the blood is 20-30 dB below the
+    tissue; a gain > 1 keeps its share of the loss from vanishing)."""
     n = len(seeds)
     vol = torch.empty((n, n_frames, Z, X, 32), dtype=torch.bfloat16, device=device)
     tgt = torch.empty((n, n_frames, Z, X, 2), dtype=torch.float32, device=device)
@@ -52,9 +56,9 @@ def ensembles(seeds, n_frames=64, Z=32, X=32, n_scat=2000, device="cuda"):
         w = member(s, n_frames, Z, X, n_scat)
         iq, pdsvd = casorati(w)
         iqb, _ = casorati(blood_only(w))
-        scale = float(1.0 / torch.sqrt(torch.mean(iq.double() ** 2)).item())
-        fq.fq_cnn_from_casorati(iq, n_frames, Z, X, scale, vol=vol[i])
-        fq.fq_cnn_from_casorati(iqb, n_frames, Z, X, scale, target=tgt[i])
+        _, _, sc = fq.fq_cnn_from_casorati(iq, n_frames, Z, X, remove_mean, vol=vol[i])
+        fq.fq_cnn_from_casorati(iqb, n_frames, Z, X, remove_mean, scale_in=sc, gain=target_gain, target=tgt[i])
+        scale = float(sc.item())
         b = iqb.double()
         pd_gt.append((b[..., 0] ** 2 + b[..., 1] ** 2).mean(dim=1).float())
         pd_svd.append(pdsvd)
@@ -86,15 +90,15 @@ def train(net, vol, tgt, steps, batch=4, lr=1e-3, seed=0, log_every=0):
     return hist
 
 
-def predict_pd(net, vol, scales):
-    """Power Doppler [n, Z X] of the network output (scale undone)."""
+def predict_pd(net, vol, scales, target_gain=1.0):
+    """Power Doppler [n, Z X] of the network output (scale and gain undone)."""
     n, F, Z, X = vol.shape[:4]
     acts = fq.cnn_act_workspace(1, F, Z, X, vol.device)
     out = []
     for i in range(n):
         fq.fq_cnn_forward(net, vol[i:i + 1], acts)
         y = fq.cnn_output(acts, 1, F, Z, X)[0]
-        out.append(fq.fq_cnn_power_doppler(y, scales[i]).clone())
+        out.append(fq.fq_cnn_power_doppler(y, scales[i] * target_gain).clone())
     return torch.stack(out)
 
 
