@@ -387,7 +387,7 @@ fq_status fq_batch_plan(const fq_ensemble_desc *ens, int32_t n, int32_t rf_dtype
         h.par_rf = po;
         s = fqi::build_rf_params(&d.probe, &d.tx, d.S, pb + po);
         if (!s && !fqi::rf_ntap_ok(pb + po))
-            s = fqi::set_error(FQ_ERR_UNSUPPORTED, "batch: ensemble %d: the pulse spans more than 9 samples", i);
+            s = fqi::set_error(FQ_ERR_UNSUPPORTED, "batch: ensemble %d: the batched RF kernel needs 8 <= n_cycles fs / f0 < 9", i);
         po += rf_b;
         if (!s) {
             h.par_iq = po;

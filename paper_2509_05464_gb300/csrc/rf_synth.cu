@@ -58,10 +58,10 @@ constexpr float kPi = 3.14159265358979f;
 // [-pi, pi] where the hardware sine is accurate to ~4e-7 absolute.
 __device__ __forceinline__ float sinc_f(float u)
 {
-    float v = u;
-    if (v > kPi) v -= 2.0f * kPi;
-    if (v < -kPi) v += 2.0f * kPi;
-    return fabsf(u) < 1e-3f ? fmaf(-u * u, 1.0f / 6.0f, 1.0f) : __fdividef(__sinf(v), u);
+    const float v = fmaf(-2.0f * kPi, rintf(u * (0.5f / kPi)), u);  // u less whole turns, in [-pi, pi]
+    const float small = fmaf(-u * u, 1.0f / 6.0f, 1.0f);
+    const float big = __fdividef(__sinf(v), u);
+    return fabsf(u) < 1e-3f ? small : big;
 }
 
 // (cos, sin) of w * (jlo - frac) as exp(i w jlo) exp(-i w frac): the
@@ -292,23 +292,46 @@ __global__ void __launch_bounds__(NT, 2) rf_synth_kernel(const RfParams p, const
 // ---------------------------------------------------------------------------
 using fqi::f2;
 
-__device__ __forceinline__ void add_fixed2(int *hi0, int *lo0, int *hi1, int *lo1, int k0, int k1, f2 V, bool on0,
-                                           bool on1)
+// (hi, lo) = (rint(V / 2^16), V - 2^16 hi) of both lanes, as int32 pairs
+__device__ __forceinline__ void split_fixed2(f2 V, int &h0, int &h1, int &l0, int &l1)
 {
     const f2 ht = fqi::f2_fma(V, fqi::f2_dup(1.0f / 65536.0f), fqi::f2_dup(kMagic));
     const f2 hb = fqi::f2_sub(ht, fqi::f2_dup(kMagic));
-    const f2 lt = fqi::f2_add(fqi::f2_fma(fqi::f2_neg(hb), fqi::f2_dup(65536.0f), V), fqi::f2_dup(kMagic));
-    float h0, h1, l0, l1;
-    fqi::f2_split(ht, h0, h1);
-    fqi::f2_split(lt, l0, l1);
+    const f2 lt = fqi::f2_add(fqi::f2_fma(hb, fqi::f2_dup(-65536.0f), V), fqi::f2_dup(kMagic));
+    float a, b, c, d;
+    fqi::f2_split(ht, a, b);
+    fqi::f2_split(lt, c, d);
+    h0 = __float_as_int(a) - kMagicBits;
+    h1 = __float_as_int(b) - kMagicBits;
+    l0 = __float_as_int(c) - kMagicBits;
+    l1 = __float_as_int(d) - kMagicBits;
+}
+
+__device__ __forceinline__ void add_fixed2(int *hi0, int *lo0, int *hi1, int *lo1, int k0, int k1, f2 V, bool on0,
+                                           bool on1)
+{
+    int h0, h1, l0, l1;
+    split_fixed2(V, h0, h1, l0, l1);
     if (on0) {
-        atomicAdd(hi0 + k0, __float_as_int(h0) - kMagicBits);
-        atomicAdd(lo0 + k0, __float_as_int(l0) - kMagicBits);
+        atomicAdd(hi0 + k0, h0);
+        atomicAdd(lo0 + k0, l0);
     }
     if (on1) {
-        atomicAdd(hi1 + k1, __float_as_int(h1) - kMagicBits);
-        atomicAdd(lo1 + k1, __float_as_int(l1) - kMagicBits);
+        atomicAdd(hi1 + k1, h1);
+        atomicAdd(lo1 + k1, l1);
     }
+}
+
+// Unpredicated form for taps known to lie in both records (a lane without
+// an echo carries V = 0 and a valid index).
+__device__ __forceinline__ void add_fixed2_all(int *hi0, int *lo0, int *hi1, int *lo1, int k0, int k1, f2 V)
+{
+    int h0, h1, l0, l1;
+    split_fixed2(V, h0, h1, l0, l1);
+    atomicAdd(hi0 + k0, h0);
+    atomicAdd(lo0 + k0, l0);
+    atomicAdd(hi1 + k1, h1);
+    atomicAdd(lo1 + k1, l1);
 }
 
 // the two-cycle tap value for the pair: ((A C + A) C - A/2) C - A/2
@@ -441,8 +464,13 @@ __device__ __forceinline__ void rf_pair_tile(const RfParams &p, int bx, int a, i
         const f2 FR = fqi::f2_add(fqi::f2_sub(uh, fqi::f2_make(fl0, fl1)), ul);
         float fr0, fr1;
         fqi::f2_split(FR, fr0, fr1);
-        if (fr0 < 0.0f) { fr0 += 1.0f; fl0 -= 1.0f; } else if (fr0 >= 1.0f) { fr0 -= 1.0f; fl0 += 1.0f; }
-        if (fr1 < 0.0f) { fr1 += 1.0f; fl1 -= 1.0f; } else if (fr1 >= 1.0f) { fr1 -= 1.0f; fl1 += 1.0f; }
+        {  // bring frac into [0, 1) (it is within one of it): move whole samples into fl
+            const float c0 = floorf(fr0), c1 = floorf(fr1);
+            fr0 -= c0;
+            fl0 += c0;
+            fr1 -= c1;
+            fl1 += c1;
+        }
         // amplitude in fixed-point units
         float dxh0, dxh1, rs0, rs1, sp0, sp1;
         fqi::f2_split(dxh, dxh0, dxh1);
@@ -477,10 +505,11 @@ __device__ __forceinline__ void rf_pair_tile(const RfParams &p, int bx, int a, i
         const f2 hA = fqi::f2_mul(HALF, A2);
         const bool in0 = live0 && k0 >= 0 && k0 + nt0 <= ns;
         const bool in1 = live1 && k1 >= 0 && k1 + nt1 <= ns;
-        if ((in0 || !live0) && (in1 || !live1)) {
+        if (ns >= 8 && (in0 || !live0) && (in1 || !live1)) {
+            const int q0 = live0 ? k0 : 0, q1 = live1 ? k1 : 0;  // dead lanes: A = 0 at samples 0-7
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                add_fixed2(hi0, lo0, hi1, lo1, k0 + j, k1 + j, tap2x2(A2, hA, C0), live0, live1);
+                add_fixed2_all(hi0, lo0, hi1, lo1, q0 + j, q1 + j, tap2x2(A2, hA, C0));
                 const f2 C2 = fqi::f2_fma(TWOCOS, C1, fqi::f2_neg(C0));
                 C0 = C1;
                 C1 = C2;
@@ -606,8 +635,9 @@ fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *a
         const char *env = std::getenv("FQ_RF_SCALAR");
         scalar_only = env && env[0] == '1';
     }
-    // the common pulse (two cycles, <= 9 taps) runs on the packed-pair kernel
-    if (!scalar_only && p.two_cycle && p.ntap_max <= 9 && 4 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
+    // the common pulse (two cycles, 8 <= n_cycles fs / f0 < 9, so every echo
+    // has 8 or 9 taps) runs on the packed-pair kernel
+    if (!scalar_only && p.two_cycle && p.ntap_max == 9 && 4 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
         return launch_rf_pair(p, F, pos, amp, base, rf, st);
     switch (rf_elems(p.pr.ns)) {
     case 16: return launch_rf<16>(p, F, pos, amp, base, rf, st);
@@ -698,7 +728,7 @@ fq_status build_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, voi
 int rf_ntap_ok(const void *rf_params)
 {
     const RfParams &p = *reinterpret_cast<const RfParams *>(rf_params);
-    return p.two_cycle && p.ntap_max <= 9;
+    return p.two_cycle && p.ntap_max == 9;
 }
 
 template <int MINB, typename OutT>
