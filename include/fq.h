@@ -500,9 +500,9 @@ fq_status fq_autotune(int32_t op, const fq_ensemble_desc *ens, int32_t rf_dtype,
  * power Doppler = mean over frames of |output|^2 / scale^2.  Convention:
  *   y[v, o] = b[o] + sum_t sum_i x[v + d_t, i] W[t][i][o],
  *   d_t = (dt, dz, dx), dt in -2..2, dz, dx in -1..1, t = (dt+2) 9 + (dz+1) 3 + (dx+1).
- * Volumes are channels-last [n_vol][F][Z][X][32] (Z a multiple of 4, X a
- * multiple of 32), BF16 activations (channels beyond the real ones are 0),
- * FP32 network output.  Convolutions run on the tcgen05 tensor cores (BF16
+ * Volumes are channels-last [n_vol][F][Z][X][32] (X a multiple of 128, or
+ * of 32 with Z a multiple of 4), BF16 activations (channels beyond the real
+ * ones are 0), FP32 network output.  Convolutions run on the tcgen05 tensor cores (BF16
  * in, FP32 accumulate); weight gradients on the CUDA cores in FP32.
  *
  * Parameters: one device block of fq_cnn_param_bytes() (256-byte aligned),

@@ -94,6 +94,53 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
+// Epilogue of one accumulator row (32 channels of voxel `vox`).
+template <int EPI>
+__device__ __forceinline__ void epilogue_store(const float (&v)[32], const float *s_bias, int64_t vox, void *out,
+                                               const __nv_bfloat16 *mask)
+{
+    if (EPI == EPI_LINEAR_F32) {
+        float4 *o = reinterpret_cast<float4 *>((float *)out + vox * C);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            o[i] = make_float4(v[4 * i] + s_bias[4 * i], v[4 * i + 1] + s_bias[4 * i + 1],
+                               v[4 * i + 2] + s_bias[4 * i + 2], v[4 * i + 3] + s_bias[4 * i + 3]);
+    } else {
+        float m[32];
+        if (EPI == EPI_MASK_BF16) {
+            const uint4 *mp = reinterpret_cast<const uint4 *>(mask + vox * C);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint4 u = mp[i];
+                const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float2 fl = __bfloat1622float2(h[k]);
+                    m[8 * i + 2 * k] = fl.x;
+                    m[8 * i + 2 * k + 1] = fl.y;
+                }
+            }
+        }
+        uint4 packed[4];
+        __nv_bfloat162 *pb = reinterpret_cast<__nv_bfloat162 *>(packed);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float a0 = v[2 * k], a1 = v[2 * k + 1];
+            if (EPI == EPI_RELU_BF16) {
+                a0 = fmaxf(a0 + s_bias[2 * k], 0.0f);
+                a1 = fmaxf(a1 + s_bias[2 * k + 1], 0.0f);
+            } else {
+                a0 = m[2 * k] > 0.0f ? a0 : 0.0f;
+                a1 = m[2 * k + 1] > 0.0f ? a1 : 0.0f;
+            }
+            pb[k] = __floats2bfloat162_rn(a0, a1);
+        }
+        uint4 *o = reinterpret_cast<uint4 *>((__nv_bfloat16 *)out + vox * C);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = packed[i];
+    }
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(CONV_THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap w_map,
@@ -210,45 +257,220 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             int n, f, z0, x0;
             tile_coords(d, tile, n, f, z0, x0);
             const int64_t vox = (((int64_t)n * d.F + f) * d.Z + (z0 + q)) * d.X + x0 + lane;
-            if (EPI == EPI_LINEAR_F32) {
-                float4 *o = reinterpret_cast<float4 *>((float *)out + vox * C);
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    o[i] = make_float4(v[4 * i] + s_bias[4 * i], v[4 * i + 1] + s_bias[4 * i + 1],
-                                       v[4 * i + 2] + s_bias[4 * i + 2], v[4 * i + 3] + s_bias[4 * i + 3]);
-            } else {
-                float m[32];
-                if (EPI == EPI_MASK_BF16) {
-                    const uint4 *mp = reinterpret_cast<const uint4 *>(mask + vox * C);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        uint4 u = mp[i];
-                        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            float2 fl = __bfloat1622float2(h[k]);
-                            m[8 * i + 2 * k] = fl.x;
-                            m[8 * i + 2 * k + 1] = fl.y;
+            epilogue_store<EPI>(v, s_bias, vox, out, mask);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+    if (threadIdx.x == 0 && s_fail) atomicExch(status, (int)FQ_ERR_TIMEOUT);
+}
+
+// ------------------------------------------------- frame-ring convolution --
+// For volumes whose width X is a multiple of 128: a tile is 128 pixels of
+// one depth row of one frame.  A CTA takes work units (n, depth row z,
+// 128-pixel block, run of up to RING_FCH frames) and walks the frames of a
+// unit in order.  Input frames live in a ring of 5 shared-memory slots; one
+// slot holds rows z - 1 .. z + 1 x pixels x0 - 1 .. x0 + 128 of one frame
+// in 4 chunks of 8 channels, each chunk a [3][130] array of 16-byte rows
+// (one TMA box per chunk; zero fill outside the volume).  In this
+// no-swizzle K-major layout rows sit 16 bytes apart, so the operand of tap
+// (dt, dz, dx) is the slot of frame f + dt at row offset (1 + dz) 130 +
+// 1 + dx: each tap is a descriptor, and each output frame loads one new
+// input frame (25 KB) instead of 45 shifted tiles.  The MMA thread issues
+// the dt = -2 taps first and then frees that frame's slot, so the next
+// frame's load overlaps the remaining 36 taps.
+constexpr int RING_X = 128;
+constexpr int RING_W = RING_X + 2;                  // with the lateral halo
+constexpr int RING_BOX = 3 * RING_W * 16;          // 6240 bytes: one TMA box (3 rows x 130 pixels x 8 channels)
+constexpr int RING_CHUNK = 6272;                    // the box's stride in a slot, padded to a multiple of 128
+constexpr int RING_SLOT = 4 * RING_CHUNK;           // 25088 bytes
+constexpr int RING_SLOTS = 5;
+constexpr int RING_FCH = 32;                        // frames per work unit
+constexpr int RING_SMEM = W_BYTES + RING_SLOTS * RING_SLOT + 1024;
+
+// K-major shared-memory matrix descriptor without swizzle: 8-row core
+// matrices of 16-byte rows; `lbo` = bytes between core matrices along K,
+// `sbo` = bytes between 8-row groups.
+__device__ __forceinline__ uint64_t nosw_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version; layout type 0 = no swizzle
+    return d;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+struct RingUnit {
+    int n, z, x0, fa, fb;
+};
+
+__device__ __forceinline__ RingUnit ring_unit(const ConvDims &d, int u)
+{
+    const int nfc = (d.F + RING_FCH - 1) / RING_FCH, nxb = d.X / RING_X;
+    RingUnit r;
+    const int fc = u % nfc;
+    u /= nfc;
+    r.x0 = (u % nxb) * RING_X;
+    u /= nxb;
+    r.z = u % d.Z;
+    r.n = u / d.Z;
+    r.fa = fc * RING_FCH;
+    r.fb = min(d.F, r.fa + RING_FCH);
+    return r;
+}
+
+__device__ __forceinline__ int ring_slot(int g) { return (g + 10) % RING_SLOTS; }  // g >= -2
+
+template <int EPI>
+__global__ void __launch_bounds__(CONV_THREADS, 1)
+    conv_ring_kernel(const __grid_constant__ CUtensorMap in_map, const __nv_bfloat16 *__restrict__ wchunk,
+                     const ConvDims d, int units, const float *__restrict__ bias, void *__restrict__ out,
+                     const __nv_bfloat16 *__restrict__ mask, int *__restrict__ status)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *w_s = base;
+    unsigned char *ring = base + W_BYTES;
+    __shared__ __align__(8) uint64_t slot_full[RING_SLOTS], slot_free[RING_SLOTS], acc_full[2], acc_empty[2], w_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    __shared__ float s_bias[C];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RING_SLOTS; ++s) {
+            mbar_init(&slot_full[s], 1);
+            mbar_init(&slot_free[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
+        mbar_init(&w_bar, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < C) s_bias[threadIdx.x] = bias ? bias[threadIdx.x] : 0.0f;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer: weights once, then the frames of each unit in order
+            mbar_expect_tx(&w_bar, W_BYTES);
+            bulk_load(w_s, wchunk, W_BYTES, &w_bar);
+            int nload[RING_SLOTS] = {0, 0, 0, 0, 0};
+            bool fail = false;
+            for (int u = blockIdx.x; u < units && !fail; u += gridDim.x) {
+                const RingUnit r = ring_unit(d, u);
+                for (int g = r.fa - 2; g <= r.fb + 1; ++g) {
+                    const int s = ring_slot(g);
+                    if (nload[s] > 0 && !mbar_wait(&slot_free[s], (uint32_t)(nload[s] - 1) & 1u)) {
+                        fail = true;
+                        break;
+                    }
+                    mbar_expect_tx(&slot_full[s], 4 * RING_BOX);
+                    unsigned char *dst = ring + s * RING_SLOT;
+                    for (int k = 0; k < 4; ++k)
+                        tma_load_5d(dst + k * RING_CHUNK, &in_map, &slot_full[s], 8 * k, r.x0 - 1, r.z - 1, g, r.n);
+                    ++nload[s];
+                }
+            }
+            if (fail) {
+                s_fail = 1;
+                for (int s = 0; s < RING_SLOTS; ++s)  // let issued copies land
+                    if (nload[s] > 0) mbar_wait(&slot_full[s], (uint32_t)(nload[s] - 1) & 1u);
+                mbar_wait(&w_bar, 0);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            bool fail = !mbar_wait(&w_bar, 0);
+            tc_fence_after();
+            int nwait[RING_SLOTS] = {0, 0, 0, 0, 0};
+            int j = 0;
+            const uint32_t ring_a = smem_u32(ring), w_a = smem_u32(w_s);
+            for (int u = blockIdx.x; u < units && !fail; u += gridDim.x) {
+                const RingUnit r = ring_unit(d, u);
+                for (int f = r.fa; f < r.fb && !fail; ++f, ++j) {
+                    const int buf = j & 1;
+                    if (!mbar_wait(&acc_empty[buf], (((uint32_t)j >> 1) & 1u) ^ 1u)) { fail = true; break; }
+                    tc_fence_after();
+                    const uint32_t acc = tmem + (uint32_t)(buf * C);
+                    for (int dt = -2; dt <= 2; ++dt) {
+                        const int g = f + dt, s = ring_slot(g);
+                        if (f == r.fa || dt == 2) {  // first use of frame g in this unit
+                            if (!mbar_wait(&slot_full[s], (uint32_t)nwait[s] & 1u)) { fail = true; break; }
+                            ++nwait[s];
+                            tc_fence_after();
                         }
-                    }
-                }
-                uint4 packed[4];
-                __nv_bfloat162 *pb = reinterpret_cast<__nv_bfloat162 *>(packed);
+                        const uint32_t slot_a = ring_a + (uint32_t)(s * RING_SLOT);
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    float a0 = v[2 * k], a1 = v[2 * k + 1];
-                    if (EPI == EPI_RELU_BF16) {
-                        a0 = fmaxf(a0 + s_bias[2 * k], 0.0f);
-                        a1 = fmaxf(a1 + s_bias[2 * k + 1], 0.0f);
-                    } else {
-                        a0 = m[2 * k] > 0.0f ? a0 : 0.0f;
-                        a1 = m[2 * k + 1] > 0.0f ? a1 : 0.0f;
-                    }
-                    pb[k] = __floats2bfloat162_rn(a0, a1);
-                }
-                uint4 *o = reinterpret_cast<uint4 *>((__nv_bfloat16 *)out + vox * C);
+                        for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) o[i] = packed[i];
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const int t = (dt + 2) * 9 + (dz + 1) * 3 + (dx + 1);
+                                const uint32_t a = slot_a + (uint32_t)(((1 + dz) * RING_W + 1 + dx) * 16);
+                                const uint32_t b = w_a + (uint32_t)(t * W_TAP_BYTES);
+                                mma_bf16_n32(acc, nosw_desc(a, RING_CHUNK, 128), nosw_desc(b, C * 16, 128),
+                                             t > 0 ? 1u : 0u);
+                                mma_bf16_n32(acc, nosw_desc(a + 2 * RING_CHUNK, RING_CHUNK, 128),
+                                             nosw_desc(b + 2 * C * 16, C * 16, 128), 1u);
+                            }
+                        if (dt == -2) mma_commit(&slot_free[ring_slot(f - 2)]);  // its last use
+                    }
+                    if (fail) break;
+                    mma_commit(&acc_full[buf]);
+                }
+                if (fail) break;
+                for (int g = r.fb - 2; g <= r.fb + 1; ++g) mma_commit(&slot_free[ring_slot(g)]);
+            }
+            if (fail) s_fail = 1;
+        }
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = pixels x0 + 32 (w % 4) + lane
+        const int q = warp & 3;
+        int j = 0;
+        bool stop = false;
+        for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+            const RingUnit r = ring_unit(d, u);
+            for (int f = r.fa; f < r.fb; ++f, ++j) {
+                const int buf = j & 1;
+                if (!warp_wait(&acc_full[buf], ((uint32_t)j >> 1) & 1u)) {
+                    if (lane == 0) s_fail = 1;
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * C), v);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                const int64_t vox = (((int64_t)r.n * d.F + f) * d.Z + r.z) * d.X + r.x0 + q * 32 + lane;
+                epilogue_store<EPI>(v, s_bias, vox, out, mask);
             }
         }
     }
@@ -265,15 +487,21 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
 // Master FP32 weights [45][32 in][32 out] -> BF16 tap tiles for the forward
 // pass (rows = out channel, 32 in channels each) and for the data gradient
 // (kernel flipped in all three axes: tap 44 - t; rows = in channel).
+// The chunked images hold the same tiles as [tap][K chunk of 8][row][8]
+// (16-byte core-matrix rows) for the frame-ring kernel.
 __global__ void pack_weights_kernel(const float *__restrict__ w, __nv_bfloat16 *__restrict__ wf,
-                                    __nv_bfloat16 *__restrict__ wb)
+                                    __nv_bfloat16 *__restrict__ wb, __nv_bfloat16 *__restrict__ wfc,
+                                    __nv_bfloat16 *__restrict__ wbc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NTAP * C * C) return;
     const int t = i / (C * C), ci = (i / C) % C, co = i % C;
     const __nv_bfloat16 v = __float2bfloat16_rn(w[i]);
+    const int tb = NTAP - 1 - t;
     wf[((size_t)t * C + co) * C + ci] = v;
-    wb[((size_t)(NTAP - 1 - t) * C + ci) * C + co] = v;
+    wb[((size_t)tb * C + ci) * C + co] = v;
+    wfc[(((size_t)t * 4 + ci / 8) * C + co) * 8 + ci % 8] = v;
+    wbc[(((size_t)tb * 4 + co / 8) * C + ci) * 8 + co % 8] = v;
 }
 
 // Packing of a Casorati ensemble [P][F][2] (pixel p = x + X z) for the
@@ -490,7 +718,9 @@ __global__ void cnn_pd_kernel(const float *__restrict__ y, int F, int Z, int X, 
 // ------------------------------------------------------------------- host --
 struct ParamLayout {   // offsets in floats inside the parameter block
     size_t w[4], b[4], m, v, n_train;  // master weights/biases, then Adam m and v over the same span
-    size_t wf_bytes_off, wb_bytes_off, total_bytes;
+    size_t wf_bytes_off, wb_bytes_off;   // 64-byte-row tap tiles (per-tap kernel)
+    size_t wfc_bytes_off, wbc_bytes_off; // 16-byte-chunk tap tiles (frame-ring kernel)
+    size_t total_bytes;
 };
 
 ParamLayout param_layout()
@@ -505,6 +735,8 @@ ParamLayout param_layout()
     size_t bytes = (o * 4 + 255) & ~(size_t)255;
     L.wf_bytes_off = bytes; bytes += (size_t)4 * NTAP * C * C * 2;
     L.wb_bytes_off = bytes; bytes += (size_t)4 * NTAP * C * C * 2;
+    L.wfc_bytes_off = bytes; bytes += (size_t)4 * NTAP * C * C * 2;
+    L.wbc_bytes_off = bytes; bytes += (size_t)4 * NTAP * C * C * 2;
     L.total_bytes = bytes;
     return L;
 }
@@ -529,7 +761,7 @@ ActLayout act_layout(int N, int F, int Z, int X)
     return L;
 }
 
-fq_status encode_act_map(CUtensorMap *map, const void *p, int N, int F, int Z, int X)
+fq_status encode_act_map(CUtensorMap *map, const void *p, int N, int F, int Z, int X, bool ring)
 {
     auto enc = (PFN_cuTensorMapEncodeTiled_v12000)fqi::tensor_map_encoder_ptr();
     FQ_REQUIRE(enc, FQ_ERR_CUDA, "cnn: cuTensorMapEncodeTiled unavailable");
@@ -537,10 +769,14 @@ fq_status encode_act_map(CUtensorMap *map, const void *p, int N, int F, int Z, i
     cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)X, (cuuint64_t)Z, (cuuint64_t)F, (cuuint64_t)N};
     cuuint64_t strides[4] = {(cuuint64_t)C * 2, (cuuint64_t)X * C * 2, (cuuint64_t)Z * X * C * 2,
                              (cuuint64_t)F * Z * X * C * 2};
-    cuuint32_t box[5] = {(cuuint32_t)C, (cuuint32_t)TILE_X, (cuuint32_t)TILE_Z, 1, 1};
+    // per-tap kernel: 32 channels x 32 pixels x 4 rows, 64-byte swizzle;
+    // frame-ring kernel: 8 channels x 130 pixels x 3 rows, no swizzle
+    cuuint32_t box_tap[5] = {(cuuint32_t)C, (cuuint32_t)TILE_X, (cuuint32_t)TILE_Z, 1, 1};
+    cuuint32_t box_ring[5] = {8, (cuuint32_t)RING_W, 3, 1, 1};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(p), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(p), dims, strides,
+                     ring ? box_ring : box_tap, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     ring ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     FQ_REQUIRE(r == CUDA_SUCCESS, FQ_ERR_CUDA, "cnn: activation tensor map (%d)", (int)r);
     return FQ_OK;
@@ -574,13 +810,35 @@ int num_sms()
     return sms;
 }
 
-fq_status conv(int epi, const void *in, const void *wpack, const float *bias, void *out,
+// One convolution of layer `layer` (forward or data-gradient kernel): the
+// frame-ring kernel when the width is a multiple of 128, else the per-tap one.
+fq_status conv(int epi, const void *in, const void *params, int layer, bool backward, const float *bias, void *out,
                const __nv_bfloat16 *mask, const ConvDims &d, int *status, cudaStream_t st)
 {
-    CUtensorMap in_map, w_map;
-    fq_status s = encode_act_map(&in_map, in, d.N, d.F, d.Z, d.X);
+    const ParamLayout L = param_layout();
+    const char *pb = (const char *)params;
+    const size_t lo = (size_t)layer * NTAP * C * C * 2;
+    const bool ring = d.X % RING_X == 0;
+    CUtensorMap in_map;
+    fq_status s = encode_act_map(&in_map, in, d.N, d.F, d.Z, d.X, ring);
     if (s) return s;
-    s = encode_w_map(&w_map, wpack);
+    if (ring) {
+        const __nv_bfloat16 *wc = (const __nv_bfloat16 *)(pb + (backward ? L.wbc_bytes_off : L.wfc_bytes_off) + lo);
+        const int units = d.N * d.Z * (d.X / RING_X) * ((d.F + RING_FCH - 1) / RING_FCH);
+        const int grid = units < num_sms() ? units : num_sms();
+        auto launch = [&](auto kern) -> fq_status {
+            fq_status r = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                               RING_SMEM), "cnn: smem attribute");
+            if (r) return r;
+            kern<<<grid, CONV_THREADS, RING_SMEM, st>>>(in_map, wc, d, units, bias, out, mask, status);
+            return fqi::launch_check("cnn: conv (frame ring)");
+        };
+        if (epi == EPI_RELU_BF16) return launch(conv_ring_kernel<EPI_RELU_BF16>);
+        if (epi == EPI_LINEAR_F32) return launch(conv_ring_kernel<EPI_LINEAR_F32>);
+        return launch(conv_ring_kernel<EPI_MASK_BF16>);
+    }
+    CUtensorMap w_map;
+    s = encode_w_map(&w_map, pb + (backward ? L.wb_bytes_off : L.wf_bytes_off) + lo);
     if (s) return s;
     const int grid = d.tiles < num_sms() ? d.tiles : num_sms();
     auto launch = [&](auto kern) -> fq_status {
@@ -597,9 +855,9 @@ fq_status conv(int epi, const void *in, const void *wpack, const float *bias, vo
 
 fq_status check_dims(int N, int F, int Z, int X, const char *who)
 {
-    FQ_REQUIRE(N >= 1 && F >= 1 && Z >= TILE_Z && X >= TILE_X, FQ_ERR_SHAPE, "%s: bad volume size", who);
-    FQ_REQUIRE(Z % TILE_Z == 0 && X % TILE_X == 0, FQ_ERR_SHAPE,
-               "%s: Z must be a multiple of 4 and X a multiple of 32 (got %d, %d)", who, Z, X);
+    FQ_REQUIRE(N >= 1 && F >= 1 && Z >= 1 && X >= TILE_X, FQ_ERR_SHAPE, "%s: bad volume size", who);
+    FQ_REQUIRE(X % RING_X == 0 || (Z % TILE_Z == 0 && X % TILE_X == 0), FQ_ERR_SHAPE,
+               "%s: X must be a multiple of 128, or of 32 with Z a multiple of 4 (got Z %d, X %d)", who, Z, X);
     FQ_REQUIRE((int64_t)N * F * (Z / TILE_Z) * (X / TILE_X) < ((int64_t)1 << 31), FQ_ERR_SHAPE, "%s: too many tiles",
                who);
     return FQ_OK;
@@ -642,7 +900,9 @@ fq_status fq_cnn_pack(void *params, void *stream)
     for (int l = 0; l < 4; ++l) {
         __nv_bfloat16 *wf = (__nv_bfloat16 *)(pb + L.wf_bytes_off) + (size_t)l * NTAP * C * C;
         __nv_bfloat16 *wb = (__nv_bfloat16 *)(pb + L.wb_bytes_off) + (size_t)l * NTAP * C * C;
-        pack_weights_kernel<<<(NTAP * C * C + 255) / 256, 256, 0, st>>>(pf + L.w[l], wf, wb);
+        __nv_bfloat16 *wfc = (__nv_bfloat16 *)(pb + L.wfc_bytes_off) + (size_t)l * NTAP * C * C;
+        __nv_bfloat16 *wbc = (__nv_bfloat16 *)(pb + L.wbc_bytes_off) + (size_t)l * NTAP * C * C;
+        pack_weights_kernel<<<(NTAP * C * C + 255) / 256, 256, 0, st>>>(pf + L.w[l], wf, wb, wfc, wbc);
     }
     return fqi::launch_check("fq_cnn_pack");
 }
@@ -686,11 +946,9 @@ fq_status fq_cnn_conv(int32_t mode, const void *in, const void *params, int32_t 
     FQ_REQUIRE(fqi::aligned(in, 16) && fqi::aligned(out, 16) && fqi::aligned(mask, 16) && fqi::aligned(params, 256),
                FQ_ERR_ALIGN, "fq_cnn_conv: alignment");
     const ParamLayout L = param_layout();
-    const char *pb = (const char *)params;
-    const void *w = pb + (backward ? L.wb_bytes_off : L.wf_bytes_off) + (size_t)layer * NTAP * C * C * 2;
     const float *bias = backward ? nullptr : (const float *)params + L.b[layer];
-    return conv(mode, in, w, bias, out, (const __nv_bfloat16 *)mask, make_dims(n_vol, F, Z, X), (int *)status,
-                (cudaStream_t)stream);
+    return conv(mode, in, params, layer, backward != 0, bias, out, (const __nv_bfloat16 *)mask,
+                make_dims(n_vol, F, Z, X), (int *)status, (cudaStream_t)stream);
 }
 
 fq_status fq_cnn_forward(const void *params, const void *vol, int32_t n_vol, int32_t F, int32_t Z, int32_t X,
@@ -704,16 +962,15 @@ fq_status fq_cnn_forward(const void *params, const void *vol, int32_t n_vol, int
     FQ_REQUIRE(fqi::aligned(acts, 256) && fqi::aligned(vol, 16) && fqi::aligned(params, 256), FQ_ERR_ALIGN,
                "fq_cnn_forward: alignment");
     const ParamLayout L = param_layout();
-    const char *pb = (const char *)params;
     char *ab = (char *)acts;
     const ConvDims d = make_dims(n_vol, F, Z, X);
     cudaStream_t st = (cudaStream_t)stream;
     const void *in = vol;
     for (int l = 0; l < 4; ++l) {
-        const void *w = pb + L.wf_bytes_off + (size_t)l * NTAP * C * C * 2;
         const float *bias = (const float *)params + L.b[l];
         void *out = l < 3 ? (void *)(ab + A.act[l]) : (void *)(ab + A.out);
-        s = conv(l < 3 ? EPI_RELU_BF16 : EPI_LINEAR_F32, in, w, bias, out, nullptr, d, (int *)status, st);
+        s = conv(l < 3 ? EPI_RELU_BF16 : EPI_LINEAR_F32, in, params, l, false, bias, out, nullptr, d, (int *)status,
+                 st);
         if (s) return s;
         in = out;
     }
@@ -731,7 +988,6 @@ fq_status fq_cnn_backward(const void *params, const void *vol, const float *targ
                "fq_cnn_backward: null argument");
     FQ_REQUIRE(act_bytes >= A.total, FQ_ERR_WORKSPACE, "fq_cnn_backward: activations need %zu bytes", A.total);
     const ParamLayout L = param_layout();
-    const char *pb = (const char *)params;
     char *ab = (char *)acts;
     const ConvDims d = make_dims(n_vol, F, Z, X);
     const int64_t V = (int64_t)n_vol * F * Z * X;
@@ -757,8 +1013,7 @@ fq_status fq_cnn_backward(const void *params, const void *vol, const float *targ
         if (s) return s;
         if (l == 0) break;
         // data gradient through layer l, masked by the ReLU of layer l - 1
-        const void *wb = pb + L.wb_bytes_off + (size_t)l * NTAP * C * C * 2;
-        s = conv(EPI_MASK_BF16, dy[cur], wb, nullptr, dy[cur ^ 1], act_in[l], d, (int *)status, st);
+        s = conv(EPI_MASK_BF16, dy[cur], params, l, true, nullptr, dy[cur ^ 1], act_in[l], d, (int *)status, st);
         if (s) return s;
         cur ^= 1;
     }

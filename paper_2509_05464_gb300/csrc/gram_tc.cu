@@ -43,7 +43,6 @@ constexpr int TC_THREADS = 128;
 constexpr int TMEM_COLS = 256;
 constexpr int PIX_PAD = 64;       // Xt row length is a multiple of this
 constexpr int MAX_TILES = 64;     // upper tiles for 2F <= 1024
-constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
 struct TileList {
     int n;

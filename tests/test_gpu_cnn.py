@@ -47,7 +47,8 @@ def random_net(seed, full=True):
     return net, seen
 
 
-@pytest.mark.parametrize("shape", [(1, 12, 8, 64), (2, 5, 4, 32)])
+# widths 32, 64: the per-tap kernel; 128, 256: the frame-ring kernel
+@pytest.mark.parametrize("shape", [(1, 12, 8, 64), (2, 5, 4, 32), (1, 40, 6, 128), (2, 7, 3, 256)])
 def test_conv_forward_modes(shape):
     n, F, Z, X = shape
     rng = np.random.default_rng(sum(shape))
@@ -71,8 +72,9 @@ def test_conv_forward_modes(shape):
     assert np.all(np.abs(got16 - relu) <= 2.0 ** -8 * np.abs(relu) + 1e-5 * np.abs(ref).max())
 
 
-def test_conv_data_gradient_with_mask():
-    n, F, Z, X = 1, 9, 8, 32
+@pytest.mark.parametrize("X", [32, 128])
+def test_conv_data_gradient_with_mask(X):
+    n, F, Z = 1, 9, 8
     rng = np.random.default_rng(11)
     net, seen = random_net(8)
     dy = bf16(rng.standard_normal((n, F, Z, X, 32))).cuda()
