@@ -377,16 +377,19 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---- producer: weights once, then the frames of each unit in order
+            // ---- producer: weights once, then the frames of each unit in order.
+            // Per slot: bit s of `loaded` = the slot has been filled before,
+            // bit s of `par` = parity of its fill count.
             mbar_expect_tx(&w_bar, W_BYTES);
             bulk_load(w_s, wchunk, W_BYTES, &w_bar);
-            int nload[RING_SLOTS] = {0, 0, 0, 0, 0};
+            uint32_t loaded = 0, par = 0;
             bool fail = false;
             for (int u = blockIdx.x; u < units && !fail; u += gridDim.x) {
                 const RingUnit r = ring_unit(d, u);
                 for (int g = r.fa - 2; g <= r.fb + 1; ++g) {
                     const int s = ring_slot(g);
-                    if (nload[s] > 0 && !mbar_wait(&slot_free[s], (uint32_t)(nload[s] - 1) & 1u)) {
+                    // the previous fill of this slot has count parity par ^ 1 ... its release phase
+                    if (((loaded >> s) & 1u) && !mbar_wait(&slot_free[s], ((par >> s) & 1u) ^ 1u)) {
                         fail = true;
                         break;
                     }
@@ -394,24 +397,28 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     unsigned char *dst = ring + s * RING_SLOT;
                     for (int k = 0; k < 4; ++k)
                         tma_load_5d(dst + k * RING_CHUNK, &in_map, &slot_full[s], 8 * k, r.x0 - 1, r.z - 1, g, r.n);
-                    ++nload[s];
+                    loaded |= 1u << s;
+                    par ^= 1u << s;
                 }
             }
             if (fail) {
                 s_fail = 1;
                 for (int s = 0; s < RING_SLOTS; ++s)  // let issued copies land
-                    if (nload[s] > 0) mbar_wait(&slot_full[s], (uint32_t)(nload[s] - 1) & 1u);
+                    if ((loaded >> s) & 1u) mbar_wait(&slot_full[s], ((par >> s) & 1u) ^ 1u);
                 mbar_wait(&w_bar, 0);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---- MMA issuer
+            // ---- MMA issuer.  Descriptors: one base per operand array; a tap's
+            // operand is the base plus its byte offset / 16 in the start-address
+            // field (addresses stay below 256 KB, so the field never carries).
             bool fail = !mbar_wait(&w_bar, 0);
             tc_fence_after();
-            int nwait[RING_SLOTS] = {0, 0, 0, 0, 0};
+            uint32_t wpar = 0;  // bit s: parity of the waits on slot s so far
             int j = 0;
-            const uint32_t ring_a = smem_u32(ring), w_a = smem_u32(w_s);
+            const uint64_t ring_d = nosw_desc(smem_u32(ring), RING_CHUNK, 128);
+            const uint64_t w_d = nosw_desc(smem_u32(w_s), C * 16, 128);
             for (int u = blockIdx.x; u < units && !fail; u += gridDim.x) {
                 const RingUnit r = ring_unit(d, u);
                 for (int f = r.fa; f < r.fb && !fail; ++f, ++j) {
@@ -419,25 +426,25 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     if (!mbar_wait(&acc_empty[buf], (((uint32_t)j >> 1) & 1u) ^ 1u)) { fail = true; break; }
                     tc_fence_after();
                     const uint32_t acc = tmem + (uint32_t)(buf * C);
+#pragma unroll
                     for (int dt = -2; dt <= 2; ++dt) {
-                        const int g = f + dt, s = ring_slot(g);
-                        if (f == r.fa || dt == 2) {  // first use of frame g in this unit
-                            if (!mbar_wait(&slot_full[s], (uint32_t)nwait[s] & 1u)) { fail = true; break; }
-                            ++nwait[s];
+                        const int s = ring_slot(f + dt);
+                        if (f == r.fa || dt == 2) {  // first use of frame f + dt in this unit
+                            if (!mbar_wait(&slot_full[s], (wpar >> s) & 1u)) { fail = true; break; }
+                            wpar ^= 1u << s;
                             tc_fence_after();
                         }
-                        const uint32_t slot_a = ring_a + (uint32_t)(s * RING_SLOT);
+                        const uint64_t a0 = ring_d + (uint64_t)((s * RING_SLOT) >> 4);
 #pragma unroll
                         for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
                             for (int dx = -1; dx <= 1; ++dx) {
                                 const int t = (dt + 2) * 9 + (dz + 1) * 3 + (dx + 1);
-                                const uint32_t a = slot_a + (uint32_t)(((1 + dz) * RING_W + 1 + dx) * 16);
-                                const uint32_t b = w_a + (uint32_t)(t * W_TAP_BYTES);
-                                mma_bf16_n32(acc, nosw_desc(a, RING_CHUNK, 128), nosw_desc(b, C * 16, 128),
-                                             t > 0 ? 1u : 0u);
-                                mma_bf16_n32(acc, nosw_desc(a + 2 * RING_CHUNK, RING_CHUNK, 128),
-                                             nosw_desc(b + 2 * C * 16, C * 16, 128), 1u);
+                                const uint64_t ad = a0 + (uint64_t)((((1 + dz) * RING_W + 1 + dx) * 16) >> 4);
+                                const uint64_t bd = w_d + (uint64_t)((t * W_TAP_BYTES) >> 4);
+                                mma_bf16_n32(acc, ad, bd, t > 0 ? 1u : 0u);
+                                mma_bf16_n32(acc, ad + (uint64_t)((2 * RING_CHUNK) >> 4),
+                                             bd + (uint64_t)((2 * C * 16) >> 4), 1u);
                             }
                         if (dt == -2) mma_commit(&slot_free[ring_slot(f - 2)]);  // its last use
                     }
