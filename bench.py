@@ -39,7 +39,7 @@ FLOP_PER_TAP = 10.0
 # DRAM bytes (read + write) of one full-size C2 RF launch, from one ncu
 # capture of rf_synth_pair_kernel (profiles/rf_synth_pair_c2_full_dram.md);
 # None once the kernel changes until it is captured again.
-RF_TRAFFIC_BYTES = None
+RF_TRAFFIC_BYTES = 255.61e6 + 992.73e6
 
 
 def peaks():
