@@ -367,6 +367,14 @@ fq_status fq_power_doppler(const void *iq_f, int32_t dtype, int64_t P, int32_t F
  * `stream`. */
 fq_status fq_clutter_status(void *workspace, void *stream);
 
+/* Test hook (the paper has no counterpart).  FQ_DEBUG_SKIP_TC_LOADS = 1
+ * makes the tensor-core Gram kernels issue no operand loads, so that every
+ * bounded wait inside them runs out (~2 s per launch) and the call reports
+ * FQ_ERR_TIMEOUT through its status word; 0 (the default) restores normal
+ * operation.  For testing the timeout path only. */
+enum { FQ_DEBUG_SKIP_TC_LOADS = 1 };
+fq_status fq_debug_set(int32_t what, int32_t value);
+
 /* sizeof of the ABI's structs as this library was compiled, for bindings
  * that check their own layouts: 0 fq_probe, 1 fq_tx, 2 fq_grid,
  * 3 fq_segment, 4 fq_flow, 5 fq_motion, 6 fq_ensemble_desc,

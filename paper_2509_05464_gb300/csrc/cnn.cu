@@ -86,14 +86,6 @@ __device__ __forceinline__ void mma_bf16_n32(uint32_t d_tmem, uint64_t adesc, ui
         : "memory");
 }
 
-// Lane 0 waits, the warp learns the answer (all lanes then stay converged).
-__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
-{
-    int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity) ? 1 : 0;
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
 // Epilogue of one accumulator row (32 channels of voxel `vox`).
 template <int EPI>
 __device__ __forceinline__ void epilogue_store(const float (&v)[32], const float *s_bias, int64_t vox, void *out,

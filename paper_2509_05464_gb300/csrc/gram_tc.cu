@@ -113,7 +113,7 @@ template <int ESZ>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TileList tiles,
                    int ksteps_total, int ksteps_per_chunk, int Mp, int Np, float *__restrict__ part,
-                   int *__restrict__ status)
+                   int *__restrict__ status, int skip_loads)
 {
     constexpr int BK = ROW_BYTES / ESZ;   // pixels per stage
     extern __shared__ unsigned char smem_raw[];
@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = tmem_base;
 
     if (warp == 0 && lane == 0) {
-        // ---- TMA producer
-        for (int it = 0; it < nk; ++it) {
+        // ---- TMA producer (skip_loads: the test hook that lets every wait run out)
+        for (int it = 0; it < nk && !skip_loads; ++it) {
             const int s = it % STAGES;
             const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
             if (!mbar_wait(&empty_bar[s], ph ^ 1u)) { s_fail = 1; break; }
@@ -186,9 +186,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     // ---- epilogue: TMEM -> FP32 partial tile (warp w owns rows 32w .. 32w + 31)
     bool ok = nk > 0;
-    if (ok) ok = mbar_wait(&done_bar, 0);
+    if (ok) ok = warp_wait(&done_bar, 0);
     tc_fence_after();
-    if (!ok && nk > 0) s_fail = 1;
+    if (!ok && nk > 0 && lane == 0) s_fail = 1;
     float *dst = part + (size_t)chunk * Mp * Np;
     const int row = m0 + warp * 32 + lane;
     for (int c = 0; c < BN; c += 32) {
@@ -231,6 +231,8 @@ __global__ void gram_tc_reduce_kernel(const float *__restrict__ part, int n_chun
 }
 
 // ------------------------------------------------------------------- host --
+int g_skip_loads = 0;  // fq_debug_set(FQ_DEBUG_SKIP_TC_LOADS, ...)
+
 struct TcPlan {
     int64_t Pp;
     int esz, bk, C, Mp, Np, ksteps, chunks, per_chunk;
@@ -282,7 +284,7 @@ fq_status launch_tc(const TcPlan &t, const CUtensorMap &map, float *part, int *s
     if (s) return s;
     dim3 grid((unsigned)t.chunks, (unsigned)t.tiles.n);
     gram_tc_kernel<ESZ><<<grid, TC_THREADS, smem, st>>>(map, t.tiles, t.ksteps, t.per_chunk, t.Mp, t.Np, part,
-                                                        status);
+                                                        status, g_skip_loads);
     return fqi::launch_check("tensor-core Gram: mma");
 }
 
@@ -359,3 +361,10 @@ fq_status gram_tc(const void *S, int dtype, int64_t P, int F, int esz, float2 *G
 }
 
 }  // namespace fqi
+
+extern "C" fq_status fq_debug_set(int32_t what, int32_t value)
+{
+    FQ_REQUIRE(what == FQ_DEBUG_SKIP_TC_LOADS, FQ_ERR_INVALID_ARG, "fq_debug_set: unknown setting %d", what);
+    g_skip_loads = value != 0;
+    return FQ_OK;
+}

@@ -40,15 +40,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 // Bounded wait on a phase of an mbarrier: false once ~2 s have passed.
-static __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+static __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         for (int i = 0; i < 256; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
+}
+
+// Warp-uniform wait for the warps that read tensor memory: lane 0 waits,
+// the warp shares its answer (the tcgen05.ld that follows is warp-wide).
+// Its limit is twice the producer's and MMA thread's, so that they always
+// give up, and commit what they issued, first.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
+{
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, 2 * kWaitNs) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
