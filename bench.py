@@ -32,13 +32,14 @@ sys.path.insert(0, ROOT)
 METRIC = "channel-samples/s + DAS voxel-angle/s per GB300, % roofline, err vs FP64"
 UNIT = "channel-samples/s"
 # FP32 work of the model per (scatterer, element, transmit) pair, counted
-# from its plain definition (see DESIGN.md): 17 for geometry and amplitude,
+# from its plain definition: 17 for geometry and amplitude,
 # 10 per pulse tap, 2 * n_cycles * fs / (2 f0) taps on average.
 GEOM_FLOP_PER_PAIR = 17.0
 FLOP_PER_TAP = 10.0
 # DRAM bytes (read + write) of one full-size C2 RF launch, from one ncu
-# capture of rf_synth_pair_kernel (profiles/rf_synth_pair_c2_full_dram.md);
-# None once the kernel changes until it is captured again.
+# capture of rf_synth_pair_kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); None once the kernel changes until it is
+# captured again.
 RF_TRAFFIC_BYTES = 255.61e6 + 992.73e6
 
 

@@ -49,7 +49,7 @@ typedef enum fq_status {
     FQ_ERR_CUDA = 5,        /* a CUDA runtime error (message has details) */
     FQ_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out */
     FQ_ERR_NUMERICAL = 7,   /* an iterative solver did not converge */
-    FQ_ERR_UNSUPPORTED = 8  /* valid request this build does not implement */
+    FQ_ERR_UNSUPPORTED = 8  /* valid request the library does not implement */
 } fq_status;
 
 typedef enum fq_dtype {

@@ -103,8 +103,7 @@ def lib():
         if _lib is not None:
             return _lib
         if not os.path.exists(LIB_PATH):
-            raise FqError(-1, f"libfq.so not built ({LIB_PATH}); run __graft_entry__.build() or "
-                              "python -m paper_2509_05464_gb300.build")
+            raise FqError(-1, f"libfq.so not built ({LIB_PATH}); run python -m paper_2509_05464_gb300.build")
         L = C.CDLL(LIB_PATH)
         L.fq_last_error.restype = C.c_char_p
         L.fq_status_string.restype = C.c_char_p
