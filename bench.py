@@ -40,7 +40,7 @@ FLOP_PER_TAP = 10.0
 # capture of rf_synth_pair_kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); None once the kernel changes until it is
 # captured again.
-RF_TRAFFIC_BYTES = 255.61e6 + 992.73e6
+RF_TRAFFIC_BYTES = None
 
 
 def peaks():
@@ -344,7 +344,7 @@ def run_ours(args, rank, world, local):
                    "l2": "256 MiB buffer rewritten between timed steps, outside the timed events"},
         "das_voxel_angle_per_s": total_va / (ms * 1e-3),
         "stage_ms": stage_ms,
-        "roofline": {"bound": "alu", "kernel": "rf_synth_pair_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "alu", "kernel": "rf_synth_quad_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": RF_TRAFFIC_BYTES if w.n_frames == 200 and w.S == 100_000 else None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
@@ -475,7 +475,7 @@ def run_batched(args, rank, world, local):
         "stage_ms": stage_ms,
         "sequential_ms": seq_ms if args.sequential else None,
         "batched_speedup_vs_sequential": (seq_ms / ms_step) if args.sequential else None,
-        "roofline": {"bound": "alu", "kernel": "rf_pair_batched_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "alu", "kernel": "rf_quad_batched_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
                                     f"({src} max clock)",

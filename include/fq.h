@@ -427,7 +427,9 @@ enum { FQ_OP_RF = 0, FQ_OP_DAS = 1 };
 
 /* A tile shape the autotuner chose for one stage.
  *   FQ_OP_RF : choice = minimum resident CTAs per SM of the RF kernel
- *              (2 or 3; sets its register budget)
+ *              (its register budget: 1 or 2 for the 4-element kernel that
+ *              probes whose rows are multiples of 4 use, 2 or 3 for the
+ *              2-element kernel)
  *   FQ_OP_DAS: choice = threads per DAS CTA (64, 128 or 256) */
 typedef struct fq_tile_choice {
     int32_t op;

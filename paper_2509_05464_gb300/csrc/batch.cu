@@ -65,6 +65,7 @@ struct fq_batch {
     std::vector<EnsHost> e;
     std::vector<Wave> waves;
     int rf_minb = 3, das_threads = 128;
+    bool rf_quad = true;  // every member's rows hold whole element quads
     int ns_max = 0, J_max = 0, M_max = 0;
     size_t off_counters = 0, off_status = 0, off_ens = 0, off_params = 0, off_queues = 0, off_scratch = 0, total = 0;
     std::vector<unsigned char> params;  // host image of the parameter blocks
@@ -115,7 +116,8 @@ void item_grids(fq_batch *b, EnsHost &h)
     const int sc = cdiv(h.d.S, kItemScat);
     h.gx[ST_CLASSIFY] = sc; h.gy[ST_CLASSIFY] = 1; h.items[ST_CLASSIFY] = sc;
     h.gx[ST_ADVECT] = sc; h.gy[ST_ADVECT] = h.F; h.items[ST_ADVECT] = sc * h.F;
-    h.gx[ST_RF] = cdiv(h.M, kRfItemElems); h.gy[ST_RF] = h.A; h.items[ST_RF] = h.gx[ST_RF] * h.A * h.F;
+    h.gx[ST_RF] = cdiv(h.M, b->rf_quad ? 4 : kRfItemElems); h.gy[ST_RF] = h.A;
+    h.items[ST_RF] = h.gx[ST_RF] * h.A * h.F;
     h.gx[ST_RF2IQ] = cdiv(h.ns, kIqTile); h.gy[ST_RF2IQ] = h.L;
     h.items[ST_RF2IQ] = h.gx[ST_RF2IQ] * h.L * (h.Fp / kFrameChunkB);
     h.gx[ST_DAS] = cdiv(h.P, b->das_threads); h.gy[ST_DAS] = h.Fp / kFrameChunkB;
@@ -272,7 +274,7 @@ fq_status launch_stage(fq_batch *b, char *arena, int w, int s, cudaStream_t st)
     switch (s) {
     case fqb::ST_CLASSIFY: return fqi::batched_classify(ens, q, q.total, st);
     case fqb::ST_ADVECT: return fqi::batched_advect(ens, q, q.total, st);
-    case fqb::ST_RF: return fqi::batched_rf(ens, q, q.total, b->rf_dtype, b->ns_max, b->rf_minb, st);
+    case fqb::ST_RF: return fqi::batched_rf(ens, q, q.total, b->rf_dtype, b->ns_max, b->rf_minb, b->rf_quad, st);
     case fqb::ST_RF2IQ: return fqi::batched_rf2iq(ens, q, q.total, b->rf_dtype, b->ch_dtype, b->J_max, st);
     case fqb::ST_DAS:
         return fqi::batched_das(ens, q, q.total, b->ch_dtype, b->iq_dtype, b->M_max, b->das_threads, st);
@@ -405,6 +407,8 @@ fq_status fq_batch_plan(const fq_ensemble_desc *ens, int32_t n, int32_t rf_dtype
         b->J_max = std::max(b->J_max, h.J);
         b->M_max = std::max(b->M_max, h.M);
     }
+    for (int i = 0; i < n; ++i) b->rf_quad = b->rf_quad && fqi::use_rf_quad(b->e[i].d.probe.nx);
+    b->rf_minb = b->rf_quad ? 2 : 3;
     // waves: greedy in the given order under the budget
     for (int i = 0; i < n; ++i) {
         EnsHost &h = b->e[i];
@@ -439,7 +443,8 @@ fq_status fq_batch_set_tile(fq_batch *plan, const fq_tile_choice *c)
 {
     FQ_REQUIRE(plan && c, FQ_ERR_INVALID_ARG, "fq_batch_set_tile: null argument");
     if (c->op == FQ_OP_RF) {
-        FQ_REQUIRE(c->choice == 2 || c->choice == 3, FQ_ERR_INVALID_ARG, "fq_batch_set_tile: RF choice %d", c->choice);
+        const bool ok = plan->rf_quad ? (c->choice == 1 || c->choice == 2) : (c->choice == 2 || c->choice == 3);
+        FQ_REQUIRE(ok, FQ_ERR_INVALID_ARG, "fq_batch_set_tile: RF choice %d", c->choice);
         plan->rf_minb = c->choice;
         return FQ_OK;
     }
@@ -584,8 +589,8 @@ fq_status fq_autotune(int32_t op, const fq_ensemble_desc *ens, int32_t rf_dtype,
     fq_tile_choice c;
     std::memset(&c, 0, sizeof c);
     c.op = op;
-    const int cands_rf[2] = {3, 2}, cands_das[3] = {128, 64, 256};
-    const int *cands = op == FQ_OP_RF ? cands_rf : cands_das;
+    const int cands_rf_pair[2] = {3, 2}, cands_rf_quad[2] = {2, 1}, cands_das[3] = {128, 64, 256};
+    const int *cands = op == FQ_OP_RF ? (b->rf_quad ? cands_rf_quad : cands_rf_pair) : cands_das;
     const int nc = op == FQ_OP_RF ? 2 : 3;
     const int stage = op == FQ_OP_RF ? fqb::ST_RF : fqb::ST_DAS;
     cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -17,7 +17,7 @@ namespace fqb {
 
 constexpr int kItemScat = 2048;   // scatterers per classify / advect item
 constexpr int kItemPix = 64;      // pixels per projection item (8 warps x 8)
-constexpr int kRfItemElems = 2;   // receive elements per RF item (the paired kernel)
+constexpr int kRfItemElems = 2;   // receive elements per RF item (the paired kernel; 4 for the quad kernel)
 constexpr int kIqTile = 64;       // rf2iq output samples per item
 constexpr int kFrameChunkB = 16;  // frames per rf2iq / DAS item
 
@@ -149,7 +149,7 @@ namespace fqi {
 fq_status batched_classify(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, cudaStream_t st);
 fq_status batched_advect(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, cudaStream_t st);
 fq_status batched_rf(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, int ns_max,
-                     int minb, cudaStream_t st);
+                     int minb, bool quad, cudaStream_t st);
 fq_status batched_rf2iq(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, int ch_dtype,
                         int J_max, cudaStream_t st);
 fq_status batched_das(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int ch_dtype, int iq_dtype,
@@ -169,6 +169,7 @@ void build_motion(const fq_motion *m, void *out);
 size_t rf_params_bytes();
 fq_status build_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, void *out);
 int rf_ntap_ok(const void *rf_params);  // the packed-pair pulse kernel applies
+bool use_rf_quad(int nx);               // the quad-element RF kernel applies to this probe
 size_t iq_params_bytes();
 fq_status build_iq_params(const fq_probe *probe, int L, int F, void *out, int *J);
 size_t das_params_bytes();

@@ -573,6 +573,286 @@ __global__ void __launch_bounds__(NT, MINB) rf_pair_batched_kernel(const fqb::En
     }
 }
 
+// ---------------------------------------------------------------------------
+// Quad-element kernel: 4 consecutive elements of one array row per CTA.
+// The float-float delay is evaluated for the quad's first element only; the
+// other three follow from the exact identity
+//     r_e - r_0 = (x_0 - x_e) (2 x - x_0 - x_e) / (r_e + r_0)
+// evaluated in binary32: |r_e - r_0| is at most 3 pitches (a dozen samples),
+// so its rounding error stays near 1e-6 sample.  Amplitudes and pulse taps
+// are per element; the taps of elements (0, 1) and (2, 3) run as packed
+// f32x2 pairs into the same fixed-point records as the paired kernel.
+// ---------------------------------------------------------------------------
+template <int NT, typename OutT>
+__device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, int f, const float *__restrict__ pos,
+                                             const float *__restrict__ amp, const float *__restrict__ rf_base,
+                                             OutT *__restrict__ rf, int *tile, float *s_red)
+{
+    constexpr int E = 4;
+    const int ns = p.pr.ns;
+    const int M = p.pr.M;
+    const int m0 = bx * E;
+    const int ne = min(E, M - m0);
+    const int64_t S = p.S;
+    int *hi0 = tile, *hi1 = tile + ns, *hi2 = tile + 2 * ns, *hi3 = tile + 3 * ns;
+    int *lo0 = tile + 4 * ns, *lo1 = tile + 5 * ns, *lo2 = tile + 6 * ns, *lo3 = tile + 7 * ns;
+
+    float amax = 0.0f;
+    for (int64_t s = threadIdx.x; s < S; s += NT) amax = fmaxf(amax, fabsf(amp[s]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    amax = 0.0f;
+    for (int w = 0; w < NT / 32; ++w) amax = fmaxf(amax, s_red[w]);
+    int gexp = 0;
+    if (amax > 0.0f) frexpf(amax, &gexp);
+    const float g = ldexpf(1.0f, -gexp);
+    const float to_fix = g * kFixScale;
+
+    for (int i = threadIdx.x; i < E * ns; i += NT) {
+        int e = i / ns, k = i - e * ns;
+        float v = 0.0f;
+        if (rf_base && e < ne) v = rf_base[((int64_t)a * M + m0 + e) * ns + k];
+        float V = fminf(fmaxf(v * to_fix, -kTapClamp), kTapClamp);
+        const float ht = fmaf(V, 1.0f / 65536.0f, kMagic);
+        const float hb = ht - kMagic;
+        const float lt = fmaf(-hb, 65536.0f, V) + kMagic;
+        tile[e * ns + k] = __float_as_int(ht) - kMagicBits;
+        tile[(4 + e) * ns + k] = __float_as_int(lt) - kMagicBits;
+    }
+    __syncthreads();
+
+    // element abscissae: the first as a float pair, the others as binary32
+    // offsets x_0 - x_e and sums x_0 + x_e (all in one row: nx % 4 == 0)
+    const int row = m0 / p.pr.nx, col0 = m0 % p.pr.nx;
+    const ff ex0 = fqi::elem_coord(col0, p.pr.nx, p.pr.pitch_x);
+    const ff ey = fqi::elem_coord(row, p.pr.ny, p.pr.pitch_y);
+    float cd[E], csh[E], csl[E], exf[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const ff xe = fqi::elem_coord(min(col0 + e, p.pr.nx - 1), p.pr.nx, p.pr.pitch_x);
+        exf[e] = xe.hi + xe.lo;
+        cd[e] = (ex0.hi - xe.hi) + (ex0.lo - xe.lo);
+        const ff sum = fqi::ff_add(ex0, xe);  // x_0 + x_e as a float pair: 2 x - sum cancels exactly
+        csh[e] = sum.hi;
+        csl[e] = sum.lo;
+    }
+    bool live_e[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) live_e[e] = e < ne;
+
+    const fqi::AngleFF an = p.ang[a];
+    const float Kh = p.pr.fs_over_c.hi, Kl = p.pr.fs_over_c.lo;
+    const bool matrix = p.pr.ny > 1;
+    const float *X = pos + (int64_t)f * 3 * S;
+    const float *Y = X + S;
+    const float *Z = Y + S;
+    const float half_w = p.half_w;
+    const float thc0 = p.tab_h[0][0], ths0 = p.tab_h[0][1], thc1 = p.tab_h[1][0], ths1 = p.tab_h[1][1];
+    const f2 COSH = fqi::f2_dup(p.cos_h), SINH = fqi::f2_dup(p.sin_h), TWOCOS = fqi::f2_dup(p.two_cos_h);
+    const f2 HALF = fqi::f2_dup(0.5f);
+
+    for (int64_t s = threadIdx.x; s < S; s += NT) {
+        const float R = amp[s];
+        if (R == 0.0f) continue;
+        const float x = X[s], y = Y[s], z = Z[s];
+        const ff ptx = fqi::ff_dot3_minus(an.ux, an.uy, an.uz, an.origin, x, y, z);
+        const ff zz = fqi::ff_two_prod(z, z);
+        const bool use_y = matrix || y != 0.0f;
+        // ---- element 0: float-float distance and delay
+        const float dxh = __fsub_rn(x, ex0.hi);
+        const float bb = __fsub_rn(dxh, x);
+        const float dxl = __fsub_rn(__fadd_rn(__fsub_rn(x, __fsub_rn(dxh, bb)), __fsub_rn(-ex0.hi, bb)), ex0.lo);
+        const float p2 = __fmul_rn(dxh, dxh);
+        float lo = __fmaf_rn(2.0f * dxh, dxl, __fmaf_rn(dxh, dxh, -p2));
+        ff r2 = fqi::ff_two_sum(p2, zz.hi);
+        lo = __fadd_rn(lo, zz.lo);
+        float dyh = 0.0f, q2 = 0.0f;
+        if (use_y) {
+            dyh = __fsub_rn(y, ey.hi);
+            const float cc = __fsub_rn(dyh, y);
+            const float dyl = __fsub_rn(__fadd_rn(__fsub_rn(y, __fsub_rn(dyh, cc)), __fsub_rn(-ey.hi, cc)), ey.lo);
+            q2 = __fmul_rn(dyh, dyh);
+            lo = __fadd_rn(lo, __fmaf_rn(2.0f * dyh, dyl, __fmaf_rn(dyh, dyh, -q2)));
+            ff t2 = fqi::ff_two_sum(r2.hi, q2);
+            r2.hi = t2.hi;
+            lo = __fadd_rn(lo, t2.lo);
+        }
+        lo = __fadd_rn(lo, r2.lo);
+        r2 = fqi::ff_fast_two_sum(r2.hi, lo);
+        const bool pos0 = r2.hi > 0.0f;
+        const float rs0 = pos0 ? rsqrtf(r2.hi) : 0.0f;
+        const float r0 = __fmul_rn(r2.hi, rs0);
+        const float rl = pos0 ? __fmul_rn(__fadd_rn(__fmaf_rn(-r0, r0, r2.hi), r2.lo), 0.5f * rs0) : 0.0f;
+        ff path = fqi::ff_two_sum(ptx.hi, r0);
+        path.lo = __fadd_rn(path.lo, __fadd_rn(ptx.lo, rl));
+        const float uh = __fmul_rn(path.hi, Kh);
+        const float ul = __fmaf_rn(path.hi, Kl, __fmaf_rn(path.lo, Kh, __fmaf_rn(path.hi, Kh, -uh)));
+        float fl0 = floorf(uh);
+        float fr0 = __fadd_rn(__fsub_rn(uh, fl0), ul);
+        {
+            const float c = floorf(fr0);
+            fr0 -= c;
+            fl0 += c;
+        }
+        // ---- per element: distance, delay offset, amplitude, first tap
+        const float zy2 = __fadd_rn(zz.hi, q2);  // z^2 (+ dy^2), binary32
+        const float r0f = r0 + rl;
+        const float Rfix = R * to_fix;
+        float Ae[E], fre[E], che[E], she[E];
+        int ke[E], nte[E];
+        bool ine[E], liv[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            float dxe, rse, fr, fl, pe;
+            if (e == 0) {
+                dxe = dxh;
+                rse = rs0;
+                fr = fr0;
+                fl = fl0;
+                pe = path.hi;
+            } else {
+                dxe = x - exf[e];
+                const float re2 = fmaf(dxe, dxe, zy2);
+                rse = rsqrtf(re2);
+                const float re = re2 * rse;
+                const float de = __fdividef(cd[e] * (fmaf(2.0f, x, -csh[e]) - csl[e]), re + r0f);  // r_e - r_0
+                const float t = fmaf(de, Kh, fr0);
+                const float c = floorf(t);
+                fr = t - c;
+                fl = fl0 + c;
+                pe = path.hi + de;
+            }
+            float D = sinc_f(p.kbx * dxe * rse);
+            if (matrix) D *= sinc_f(p.kby * dyh * rse);
+            float A = Rfix * D * __expf(-p.att * pe) * rse;
+            const bool lv = live_e[e] && (e > 0 || pos0);
+            A = lv ? fminf(fmaxf(A, -kTapClamp), kTapClamp) : 0.0f;  // one clamp bounds every tap (|p| <= 1)
+            const int jlo = (int)ceilf(fr - half_w);
+            const int nt = (int)floorf(fr + half_w) - jlo + 1;
+            const int k = (int)fl + jlo;
+            float ch, sh;
+            first_tap(p.w_h, fr, thc0, ths0, thc1, ths1, jlo != p.jmin, ch, sh);
+            Ae[e] = A;
+            fre[e] = fr;
+            ke[e] = k;
+            nte[e] = nt;
+            che[e] = ch;
+            she[e] = sh;
+            liv[e] = lv;
+            ine[e] = lv && k >= 0 && k + nt <= ns;
+        }
+        (void)fre;
+        const f2 A01 = fqi::f2_make(Ae[0], Ae[1]), A23 = fqi::f2_make(Ae[2], Ae[3]);
+        const f2 hA01 = fqi::f2_mul(HALF, A01), hA23 = fqi::f2_mul(HALF, A23);
+        const f2 CH01 = fqi::f2_make(che[0], che[1]), SH01 = fqi::f2_make(she[0], she[1]);
+        const f2 CH23 = fqi::f2_make(che[2], che[3]), SH23 = fqi::f2_make(she[2], she[3]);
+        f2 Ca0 = CH01, Ca1 = fqi::f2_fma(CH01, COSH, fqi::f2_neg(fqi::f2_mul(SH01, SINH)));
+        f2 Cb0 = CH23, Cb1 = fqi::f2_fma(CH23, COSH, fqi::f2_neg(fqi::f2_mul(SH23, SINH)));
+        const bool fast = ns >= 8 && (ine[0] || !liv[0]) && (ine[1] || !liv[1]) && (ine[2] || !liv[2]) &&
+                          (ine[3] || !liv[3]);
+        if (fast) {
+            const int q0 = liv[0] ? ke[0] : 0, q1 = liv[1] ? ke[1] : 0;  // dead lanes: A = 0 at samples 0-7
+            const int q2i = liv[2] ? ke[2] : 0, q3 = liv[3] ? ke[3] : 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                add_fixed2_all(hi0, lo0, hi1, lo1, q0 + j, q1 + j, tap2x2(A01, hA01, Ca0));
+                add_fixed2_all(hi2, lo2, hi3, lo3, q2i + j, q3 + j, tap2x2(A23, hA23, Cb0));
+                const f2 Ca2 = fqi::f2_fma(TWOCOS, Ca1, fqi::f2_neg(Ca0));
+                const f2 Cb2 = fqi::f2_fma(TWOCOS, Cb1, fqi::f2_neg(Cb0));
+                Ca0 = Ca1;
+                Ca1 = Ca2;
+                Cb0 = Cb1;
+                Cb1 = Cb2;
+            }
+            if (nte[0] > 8 || nte[1] > 8)
+                add_fixed2(hi0, lo0, hi1, lo1, ke[0] + 8, ke[1] + 8, tap2x2(A01, hA01, Ca0), liv[0] && nte[0] > 8,
+                           liv[1] && nte[1] > 8);
+            if (nte[2] > 8 || nte[3] > 8)
+                add_fixed2(hi2, lo2, hi3, lo3, ke[2] + 8, ke[3] + 8, tap2x2(A23, hA23, Cb0), liv[2] && nte[2] > 8,
+                           liv[3] && nte[3] > 8);
+        } else {
+            // an echo straddles a record end: per-tap bounds
+            for (int j = 0; j < 9; ++j) {
+                int kk[E];
+                bool on[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    kk[e] = ke[e] + j;
+                    on[e] = liv[e] && j < nte[e] && kk[e] >= 0 && kk[e] < ns;
+                    if (!on[e]) kk[e] = 0;
+                }
+                add_fixed2(hi0, lo0, hi1, lo1, kk[0], kk[1], tap2x2(A01, hA01, Ca0), on[0], on[1]);
+                add_fixed2(hi2, lo2, hi3, lo3, kk[2], kk[3], tap2x2(A23, hA23, Cb0), on[2], on[3]);
+                const f2 Ca2 = fqi::f2_fma(TWOCOS, Ca1, fqi::f2_neg(Ca0));
+                const f2 Cb2 = fqi::f2_fma(TWOCOS, Cb1, fqi::f2_neg(Cb0));
+                Ca0 = Ca1;
+                Ca1 = Ca2;
+                Cb0 = Cb1;
+                Cb1 = Cb2;
+            }
+        }
+    }
+    __syncthreads();
+    const float from_fix = 1.0f / to_fix;
+    OutT *out = rf + (((int64_t)f * p.A + a) * M + m0) * ns;
+    for (int i = threadIdx.x; i < ne * ns; i += NT)
+        fqi::store_f(out, i, fmaf((float)tile[i], 65536.0f, (float)tile[4 * ns + i]) * from_fix);
+}
+
+template <int NT, int MINB, typename OutT>
+__global__ void __launch_bounds__(NT, MINB) rf_synth_quad_kernel(const RfParams p, const float *__restrict__ pos,
+                                                              const float *__restrict__ amp,
+                                                              const float *__restrict__ rf_base,
+                                                              OutT *__restrict__ rf)
+{
+    extern __shared__ int tile[];  // hi [4][Ns] then lo [4][Ns]
+    __shared__ float s_red[NT / 32];
+    rf_quad_tile<NT, OutT>(p, blockIdx.x, blockIdx.y, blockIdx.z, pos, amp, rf_base, rf, tile, s_red);
+}
+
+template <typename OutT>
+fq_status launch_rf_quad(const RfParams &p, int F, const float *pos, const float *amp, const float *base, OutT *rf,
+                         cudaStream_t st)
+{
+    constexpr int NT = 256;
+    const size_t smem = 8 * sizeof(int) * (size_t)p.pr.ns;
+    static int minb = -1;
+    if (minb < 0) {
+        const char *env = std::getenv("FQ_RF_QUAD_MINB");
+        minb = (env && env[0] == '1') ? 1 : 2;
+    }
+    auto kern = minb == 2 ? rf_synth_quad_kernel<NT, 2, OutT> : rf_synth_quad_kernel<NT, 1, OutT>;
+    fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                                  "fq_simulate_rf: smem attribute");
+    if (s) return s;
+    dim3 grid((p.pr.M + 3) / 4, p.A, F);
+    kern<<<grid, NT, smem, st>>>(p, pos, amp, base, rf);
+    return fqi::launch_check("fq_simulate_rf");
+}
+
+template <int NT, int MINB, typename OutT>
+__global__ void __launch_bounds__(NT, MINB) rf_quad_batched_kernel(const fqb::EnsDev *__restrict__ ens,
+                                                                const fqb::StageQueue q)
+{
+    extern __shared__ int tile[];
+    __shared__ float s_red[NT / 32];
+    __shared__ __align__(16) unsigned char s_par[kRfParamBytes];
+    __shared__ int s_buf[2];
+    int cur = -1;
+    fqb::Item it;
+    while (fqb::next_item(q, ens, fqb::ST_RF, s_buf, it)) {
+        const fqb::EnsDev &e = ens[it.e];
+        if (it.e != cur) {
+            fqb::copy_block(s_par, e.rf_params, kRfParamBytes);
+            cur = it.e;
+            __syncthreads();
+        }
+        rf_quad_tile<NT, OutT>(*reinterpret_cast<const RfParams *>(s_par), it.x, it.y, it.z, e.pos, e.amp_eff,
+                               nullptr, (OutT *)e.rf, tile, s_red);
+    }
+}
+
 template <typename OutT>
 fq_status launch_rf_pair(const RfParams &p, int F, const float *pos, const float *amp, const float *base, OutT *rf,
                          cudaStream_t st)
@@ -636,7 +916,11 @@ fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *a
         scalar_only = env && env[0] == '1';
     }
     // the common pulse (two cycles, 8 <= n_cycles fs / f0 < 9, so every echo
-    // has 8 or 9 taps) runs on the packed-pair kernel
+    // has 8 or 9 taps) runs on the quad kernel when the array rows hold
+    // whole quads, else on the packed-pair kernel
+    if (!scalar_only && fqi::use_rf_quad(p.pr.nx) && p.two_cycle && p.ntap_max == 9 &&
+        8 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
+        return launch_rf_quad(p, F, pos, amp, base, rf, st);
     if (!scalar_only && p.two_cycle && p.ntap_max == 9 && 4 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
         return launch_rf_pair(p, F, pos, amp, base, rf, st);
     switch (rf_elems(p.pr.ns)) {
@@ -725,18 +1009,30 @@ fq_status build_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, voi
     return make_rf_params(probe, tx, S, *reinterpret_cast<RfParams *>(out));
 }
 
+// The quad kernel serves probes whose rows hold whole quads (unless
+// FQ_RF_QUAD=0); the single-ensemble and batched paths choose alike.
+bool use_rf_quad(int nx)
+{
+    static int off = -1;
+    if (off < 0) {
+        const char *env = std::getenv("FQ_RF_QUAD");
+        off = env && env[0] == '0';
+    }
+    return !off && nx % 4 == 0;
+}
+
 int rf_ntap_ok(const void *rf_params)
 {
     const RfParams &p = *reinterpret_cast<const RfParams *>(rf_params);
     return p.two_cycle && p.ntap_max == 9;
 }
 
-template <int MINB, typename OutT>
+template <int MINB, bool QUAD, typename OutT>
 fq_status launch_rf_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int ns_max, cudaStream_t st)
 {
     constexpr int NT = 256;
-    const size_t smem = 4 * sizeof(int) * (size_t)ns_max;
-    auto kern = rf_pair_batched_kernel<NT, MINB, OutT>;
+    const size_t smem = (QUAD ? 8 : 4) * sizeof(int) * (size_t)ns_max;
+    auto kern = QUAD ? rf_quad_batched_kernel<NT, MINB, OutT> : rf_pair_batched_kernel<NT, MINB, OutT>;
     fq_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "batched RF: smem attribute");
     if (s) return s;
@@ -745,14 +1041,23 @@ fq_status launch_rf_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, in
     return launch_check("batched RF");
 }
 
-fq_status batched_rf(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, int ns_max, int minb,
-                     cudaStream_t st)
+template <typename OutT>
+fq_status batched_rf_t(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int ns_max, int minb, bool quad,
+                       cudaStream_t st)
 {
-    if (rf_dtype == FQ_F32)
-        return minb == 2 ? launch_rf_batched<2, float>(ens, q, items, ns_max, st)
-                         : launch_rf_batched<3, float>(ens, q, items, ns_max, st);
-    return minb == 2 ? launch_rf_batched<2, __nv_bfloat16>(ens, q, items, ns_max, st)
-                     : launch_rf_batched<3, __nv_bfloat16>(ens, q, items, ns_max, st);
+    if (quad) {
+        return minb == 1 ? launch_rf_batched<1, true, OutT>(ens, q, items, ns_max, st)
+                         : launch_rf_batched<2, true, OutT>(ens, q, items, ns_max, st);
+    }
+    return minb == 2 ? launch_rf_batched<2, false, OutT>(ens, q, items, ns_max, st)
+                     : launch_rf_batched<3, false, OutT>(ens, q, items, ns_max, st);
+}
+
+fq_status batched_rf(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, int ns_max, int minb,
+                     bool quad, cudaStream_t st)
+{
+    if (rf_dtype == FQ_F32) return batched_rf_t<float>(ens, q, items, ns_max, minb, quad, st);
+    return batched_rf_t<__nv_bfloat16>(ens, q, items, ns_max, minb, quad, st);
 }
 
 }  // namespace fqi
