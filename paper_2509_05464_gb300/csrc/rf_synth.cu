@@ -652,10 +652,23 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, i
     const f2 COSH = fqi::f2_dup(p.cos_h), SINH = fqi::f2_dup(p.sin_h), TWOCOS = fqi::f2_dup(p.two_cos_h);
     const f2 HALF = fqi::f2_dup(0.5f);
 
+    // the next scatterer's inputs are loaded one iteration ahead
+    float nR = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
+    if ((int64_t)threadIdx.x < S) {
+        nR = amp[threadIdx.x];
+        nx = X[threadIdx.x];
+        ny = Y[threadIdx.x];
+        nz = Z[threadIdx.x];
+    }
     for (int64_t s = threadIdx.x; s < S; s += NT) {
-        const float R = amp[s];
+        const float R = nR, x = nx, y = ny, z = nz;
+        if (s + NT < S) {
+            nR = amp[s + NT];
+            nx = X[s + NT];
+            ny = Y[s + NT];
+            nz = Z[s + NT];
+        }
         if (R == 0.0f) continue;
-        const float x = X[s], y = Y[s], z = Z[s];
         const ff ptx = fqi::ff_dot3_minus(an.ux, an.uy, an.uz, an.origin, x, y, z);
         const ff zz = fqi::ff_two_prod(z, z);
         const bool use_y = matrix || y != 0.0f;
