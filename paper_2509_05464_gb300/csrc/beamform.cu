@@ -216,6 +216,146 @@ struct ChunkLoad<__nv_bfloat16> {
 
 // One tile: pixels bx * blockDim.x .. + blockDim.x - 1, frames 16 by ..
 // 16 by + 15.  `etab` is the dynamic shared memory (6 M floats).
+// 4 complex values (4 consecutive frames) of one channel sample
+template <typename ChT>
+struct QuadLoad;
+template <>
+struct QuadLoad<float> {
+    static __device__ __forceinline__ void load(const float *base, float2 (&v)[4])
+    {
+        const float4 *q = reinterpret_cast<const float4 *>(base);
+        const float4 a = __ldg(q), b = __ldg(q + 1);
+        v[0] = make_float2(a.x, a.y);
+        v[1] = make_float2(a.z, a.w);
+        v[2] = make_float2(b.x, b.y);
+        v[3] = make_float2(b.z, b.w);
+    }
+};
+template <>
+struct QuadLoad<__nv_bfloat16> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16 *base, float2 (&v)[4])
+    {
+        const uint4 t = __ldg(reinterpret_cast<const uint4 *>(base));
+        const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&t);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = __bfloat1622float2(b[j]);
+    }
+};
+
+// One tile with four threads per pixel: pixels bx * blockDim.x / 4 ..,
+// frames 16 by .. 16 by + 15.  Thread (pixel, quarter q) accumulates frames
+// 4q .. 4q + 3.  Elements go in groups of four: the four threads of a pixel
+// evaluate the float-float delays of four different elements, share them by
+// shuffles within the group, and each reads its 32-byte quarter of the two
+// interpolation samples; a warp load touches 8 rows instead of 32.
+// `etab` is the dynamic shared memory (6 M floats).
+template <typename ChT, typename OutT>
+__device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, const ChT *__restrict__ ch,
+                                          OutT *__restrict__ iq, float *etab)
+{
+    const int M = p.pr.M;
+    float *exf = etab, *exh = etab + M, *exl = etab + 2 * M;
+    float *eyf = etab + 3 * M, *eyh = etab + 4 * M, *eyl = etab + 5 * M;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        int ix = m % p.pr.nx, iy = m / p.pr.nx;
+        double ex = __dmul_rn(__dsub_rn((double)ix, __dmul_rn(0.5, (double)(p.pr.nx - 1))), p.pitch_x);
+        double ey = __dmul_rn(__dsub_rn((double)iy, __dmul_rn(0.5, (double)(p.pr.ny - 1))), p.pitch_y);
+        fqi::df2 sx = fqi::split_double(ex), sy = fqi::split_double(ey);
+        exf[m] = (float)ex; exh[m] = sx.hi; exl[m] = sx.lo;
+        eyf[m] = (float)ey; eyh[m] = sy.hi; eyl[m] = sy.lo;
+    }
+    __syncthreads();
+
+    const int q = threadIdx.x & 3;  // frame quarter, and element slot within a group of four
+    const int64_t pix = (int64_t)bx * (blockDim.x >> 2) + (threadIdx.x >> 2);
+    const int fbase = by * kFrameChunk;
+    const bool live = pix < p.P;
+    const int64_t pp = live ? pix : 0;
+    const int ix = (int)(pp % p.gx);
+    const int iz = (int)((pp / p.gx) % p.gz);
+    const int iy = (int)(pp / ((int64_t)p.gx * p.gz));
+    const double xd = __dadd_rn(p.x0, __dmul_rn((double)ix, p.dx));
+    const double yd = __dadd_rn(p.y0, __dmul_rn((double)iy, p.dy));
+    const double zd = __dadd_rn(p.z0, __dmul_rn((double)iz, p.dz));
+    const float xf = (float)xd, yf = (float)yd, zf = (float)zd;
+    const fqi::df2 xs = fqi::split_double(xd), ys = fqi::split_double(yd), zs = fqi::split_double(zd);
+    const ff X = {xs.hi, xs.lo}, Y = {ys.hi, ys.lo}, Z = {zs.hi, zs.lo};
+    const ff zz = fqi::ff_sqr(Z);
+    const float half = __fmul_rn(zf, p.half_per_z);
+    const bool matrix = p.pr.ny > 1;
+    const ff fs_c = fqi::ff_load(p.pr.fs_over_c);
+    const ff f0_fs = fqi::ff_load(p.pr.f0_over_fs);
+    const int ns = p.pr.ns;
+    const int64_t row_stride = (int64_t)p.Fp * 2;  // scalars per channel sample (all frames)
+
+    float2 acc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = make_float2(0.0f, 0.0f);
+
+    for (int a = 0; a < p.A; ++a) {
+        const fqi::AngleFF an = p.ang[a];
+        ff ptx = fqi::ff_add(fqi::ff_mul(fqi::ff_load(an.ux), X), fqi::ff_mul(fqi::ff_load(an.uy), Y));
+        ptx = fqi::ff_add(ptx, fqi::ff_mul(fqi::ff_load(an.uz), Z));
+        ptx = fqi::ff_add(ptx, fqi::ff_neg(fqi::ff_load(an.origin)));
+        const ChT *cha = ch + (int64_t)a * M * ns * row_stride + (fbase + 4 * q) * 2;
+        for (int m0 = 0; m0 < M; m0 += 4) {
+            // this thread's element of the group
+            const int m = m0 + q;
+            bool on = live && m < M;
+            const int mm = on ? m : 0;
+            on = on && fabsf(__fsub_rn(xf, exf[mm])) <= half;
+            if (matrix) on = on && fabsf(__fsub_rn(yf, eyf[mm])) <= half;
+            if (!__any_sync(0xffffffffu, on)) continue;
+            int i = 0;
+            float phi = 0.0f, sn = 0.0f, cs = 1.0f;
+            if (on) {
+                ff dxx = fqi::ff_add(X, ff{-exh[mm], -exl[mm]});
+                ff r2 = fqi::ff_add(fqi::ff_sqr(dxx), zz);
+                if (matrix || yf != 0.0f) {
+                    ff dyy = fqi::ff_add(Y, ff{-eyh[mm], -eyl[mm]});
+                    r2 = fqi::ff_add(r2, fqi::ff_sqr(dyy));
+                }
+                const ff path = fqi::ff_add(ptx, fqi::ff_sqrt(r2));
+                const ff u = fqi::ff_mul(path, fs_c);
+                fqi::ff_floor_frac(u, i, phi);
+                if (i < 0 || i + 1 >= ns) {
+                    on = false;
+                } else {
+                    const float cyc = fqi::ff_frac(fqi::ff_mul(u, f0_fs));
+                    sincospif(2.0f * cyc, &sn, &cs);
+                }
+            }
+            // the group's four elements in turn (values shared within the 4 lanes of a pixel)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int ij = __shfl_sync(0xffffffffu, i, j, 4);
+                const float phj = __shfl_sync(0xffffffffu, phi, j, 4);
+                const float snj = __shfl_sync(0xffffffffu, sn, j, 4);
+                const float csj = __shfl_sync(0xffffffffu, cs, j, 4);
+                const bool onj = __shfl_sync(0xffffffffu, on ? 1 : 0, j, 4) != 0;
+                if (!onj) continue;
+                const ChT *b0 = cha + ((int64_t)(m0 + j) * ns + ij) * row_stride;
+                float2 v0[4], v1[4];
+                QuadLoad<ChT>::load(b0, v0);
+                QuadLoad<ChT>::load(b0 + row_stride, v1);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float vr = fmaf(phj, v1[k].x - v0[k].x, v0[k].x);
+                    const float vi = fmaf(phj, v1[k].y - v0[k].y, v0[k].y);
+                    acc[k].x = fmaf(vr, csj, fmaf(-vi, snj, acc[k].x));
+                    acc[k].y = fmaf(vr, snj, fmaf(vi, csj, acc[k].y));
+                }
+            }
+        }
+    }
+    if (!live) return;
+    const int f0 = fbase + 4 * q;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (f0 + k < p.F)
+            fqi::store_c(iq, pix * p.F + f0 + k, make_float2(acc[k].x * p.inv_A, acc[k].y * p.inv_A));
+}
+
 template <typename ChT, typename OutT>
 __device__ __forceinline__ void das_tile(const DasParams &p, int bx, int by, const ChT *__restrict__ ch,
                                          OutT *__restrict__ iq, float *etab)
@@ -306,7 +446,7 @@ template <typename ChT, typename OutT, int NT>
 __global__ void __launch_bounds__(NT) das_kernel(const DasParams p, const ChT *__restrict__ ch, OutT *__restrict__ iq)
 {
     extern __shared__ float etab[];  // [6][M]: x as float, x hi, x lo, y float, y hi, y lo
-    das_tile<ChT, OutT>(p, blockIdx.x, blockIdx.y, ch, iq, etab);
+    das_tile4<ChT, OutT>(p, blockIdx.x, blockIdx.y, ch, iq, etab);
 }
 
 constexpr int kDasParamBytes = (sizeof(DasParams) + 15) & ~15;
@@ -326,7 +466,7 @@ __global__ void __launch_bounds__(NT) das_batched_kernel(const fqb::EnsDev *__re
             cur = it.e;
             __syncthreads();
         }
-        das_tile<ChT, OutT>(*reinterpret_cast<const DasParams *>(s_par), it.x, it.y, (const ChT *)e.ch,
+        das_tile4<ChT, OutT>(*reinterpret_cast<const DasParams *>(s_par), it.x, it.y, (const ChT *)e.ch,
                             (OutT *)e.iq, etab);
     }
 }
@@ -354,7 +494,8 @@ fq_status launch_das(const DasParams &p, const void *ch, void *iq, cudaStream_t 
                                                            (int)smem), "fq_das: smem attribute");
         if (s) return s;
     }
-    dim3 grid((unsigned)((p.P + kDasThreads - 1) / kDasThreads), p.Fp / kFrameChunk);
+    const int px_per_cta = kDasThreads / 4;
+    dim3 grid((unsigned)((p.P + px_per_cta - 1) / px_per_cta), p.Fp / kFrameChunk);
     kern<<<grid, kDasThreads, smem, st>>>(p, (const ChT *)ch, (OutT *)iq);
     return fqi::launch_check("fq_das");
 }
