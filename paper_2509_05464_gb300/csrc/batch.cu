@@ -120,7 +120,7 @@ void item_grids(fq_batch *b, EnsHost &h)
     h.items[ST_RF] = h.gx[ST_RF] * h.A * h.F;
     h.gx[ST_RF2IQ] = cdiv(h.ns, kIqTile); h.gy[ST_RF2IQ] = h.L;
     h.items[ST_RF2IQ] = h.gx[ST_RF2IQ] * h.L * (h.Fp / kFrameChunkB);
-    h.gx[ST_DAS] = cdiv(h.P, b->das_threads / 4); h.gy[ST_DAS] = h.Fp / kFrameChunkB;  // 4 threads per pixel
+    h.gx[ST_DAS] = cdiv(h.P, b->das_threads / kDasThreadsPerPixel); h.gy[ST_DAS] = h.Fp / kFrameChunkB;
     h.items[ST_DAS] = h.gx[ST_DAS] * h.gy[ST_DAS];
     const int nt = cdiv(h.F, 32);
     h.gx[ST_GRAM] = nt * (nt + 1) / 2; h.gy[ST_GRAM] = h.n_chunks; h.items[ST_GRAM] = h.gx[ST_GRAM] * h.n_chunks;

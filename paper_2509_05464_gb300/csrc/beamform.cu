@@ -182,6 +182,7 @@ struct DasParams {
 };
 
 constexpr int kDasThreads = 128;
+constexpr int kDasTPP = fqb::kDasThreadsPerPixel;  // threads per pixel
 
 // 16 complex values of one channel sample for the frame chunk
 template <typename ChT>
@@ -216,11 +217,11 @@ struct ChunkLoad<__nv_bfloat16> {
 
 // One tile: pixels bx * blockDim.x .. + blockDim.x - 1, frames 16 by ..
 // 16 by + 15.  `etab` is the dynamic shared memory (6 M floats).
-// 4 complex values (4 consecutive frames) of one channel sample
-template <typename ChT>
-struct QuadLoad;
+// N complex values (N consecutive frames, N = 2 or 4) of one channel sample
+template <int N, typename ChT>
+struct FramesLoad;
 template <>
-struct QuadLoad<float> {
+struct FramesLoad<4, float> {
     static __device__ __forceinline__ void load(const float *base, float2 (&v)[4])
     {
         const float4 *q = reinterpret_cast<const float4 *>(base);
@@ -232,7 +233,16 @@ struct QuadLoad<float> {
     }
 };
 template <>
-struct QuadLoad<__nv_bfloat16> {
+struct FramesLoad<2, float> {
+    static __device__ __forceinline__ void load(const float *base, float2 (&v)[2])
+    {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(base));
+        v[0] = make_float2(a.x, a.y);
+        v[1] = make_float2(a.z, a.w);
+    }
+};
+template <>
+struct FramesLoad<4, __nv_bfloat16> {
     static __device__ __forceinline__ void load(const __nv_bfloat16 *base, float2 (&v)[4])
     {
         const uint4 t = __ldg(reinterpret_cast<const uint4 *>(base));
@@ -241,18 +251,30 @@ struct QuadLoad<__nv_bfloat16> {
         for (int j = 0; j < 4; ++j) v[j] = __bfloat1622float2(b[j]);
     }
 };
+template <>
+struct FramesLoad<2, __nv_bfloat16> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16 *base, float2 (&v)[2])
+    {
+        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(base));
+        const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&t);
+        v[0] = __bfloat1622float2(b[0]);
+        v[1] = __bfloat1622float2(b[1]);
+    }
+};
 
-// One tile with four threads per pixel: pixels bx * blockDim.x / 4 ..,
-// frames 16 by .. 16 by + 15.  Thread (pixel, quarter q) accumulates frames
-// 4q .. 4q + 3.  Elements go in groups of four: the four threads of a pixel
-// evaluate the float-float delays of four different elements, share them by
-// shuffles within the group, and each reads its 32-byte quarter of the two
-// interpolation samples; a warp load touches 8 rows instead of 32.
-// `etab` is the dynamic shared memory (6 M floats).
-template <typename ChT, typename OutT>
+// One tile with TPP threads per pixel (TPP = 4 or 8): pixels
+// bx * blockDim.x / TPP .., frames 16 by .. 16 by + 15.  Thread (pixel, part
+// q) accumulates frames FPT q .. FPT q + FPT - 1, FPT = 16 / TPP.  Elements
+// go in groups of TPP: the threads of a pixel evaluate the float-float delays
+// of TPP different elements, share them by shuffles within the group, and
+// each reads its slice of the two interpolation samples, so that a warp
+// load covers 32 / TPP whole rows instead of 32 partial ones.  `etab` is the
+// dynamic shared memory (6 M floats).
+template <int TPP, typename ChT, typename OutT>
 __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, const ChT *__restrict__ ch,
                                           OutT *__restrict__ iq, float *etab)
 {
+    constexpr int FPT = kFrameChunk / TPP;
     const int M = p.pr.M;
     float *exf = etab, *exh = etab + M, *exl = etab + 2 * M;
     float *eyf = etab + 3 * M, *eyh = etab + 4 * M, *eyl = etab + 5 * M;
@@ -266,8 +288,8 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, co
     }
     __syncthreads();
 
-    const int q = threadIdx.x & 3;  // frame quarter, and element slot within a group of four
-    const int64_t pix = (int64_t)bx * (blockDim.x >> 2) + (threadIdx.x >> 2);
+    const int q = threadIdx.x % TPP;  // frame part, and element slot within a group of TPP
+    const int64_t pix = (int64_t)bx * (blockDim.x / TPP) + (threadIdx.x / TPP);
     const int fbase = by * kFrameChunk;
     const bool live = pix < p.P;
     const int64_t pp = live ? pix : 0;
@@ -288,17 +310,17 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, co
     const int ns = p.pr.ns;
     const int64_t row_stride = (int64_t)p.Fp * 2;  // scalars per channel sample (all frames)
 
-    float2 acc[4];
+    float2 acc[FPT];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = make_float2(0.0f, 0.0f);
+    for (int k = 0; k < FPT; ++k) acc[k] = make_float2(0.0f, 0.0f);
 
     for (int a = 0; a < p.A; ++a) {
         const fqi::AngleFF an = p.ang[a];
         ff ptx = fqi::ff_add(fqi::ff_mul(fqi::ff_load(an.ux), X), fqi::ff_mul(fqi::ff_load(an.uy), Y));
         ptx = fqi::ff_add(ptx, fqi::ff_mul(fqi::ff_load(an.uz), Z));
         ptx = fqi::ff_add(ptx, fqi::ff_neg(fqi::ff_load(an.origin)));
-        const ChT *cha = ch + (int64_t)a * M * ns * row_stride + (fbase + 4 * q) * 2;
-        for (int m0 = 0; m0 < M; m0 += 4) {
+        const ChT *cha = ch + (int64_t)a * M * ns * row_stride + (fbase + FPT * q) * 2;
+        for (int m0 = 0; m0 < M; m0 += TPP) {
             // this thread's element of the group
             const int m = m0 + q;
             bool on = live && m < M;
@@ -327,19 +349,19 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, co
             }
             // the group's four elements in turn (values shared within the 4 lanes of a pixel)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int ij = __shfl_sync(0xffffffffu, i, j, 4);
-                const float phj = __shfl_sync(0xffffffffu, phi, j, 4);
-                const float snj = __shfl_sync(0xffffffffu, sn, j, 4);
-                const float csj = __shfl_sync(0xffffffffu, cs, j, 4);
-                const bool onj = __shfl_sync(0xffffffffu, on ? 1 : 0, j, 4) != 0;
+            for (int j = 0; j < TPP; ++j) {
+                const int ij = __shfl_sync(0xffffffffu, i, j, TPP);
+                const float phj = __shfl_sync(0xffffffffu, phi, j, TPP);
+                const float snj = __shfl_sync(0xffffffffu, sn, j, TPP);
+                const float csj = __shfl_sync(0xffffffffu, cs, j, TPP);
+                const bool onj = __shfl_sync(0xffffffffu, on ? 1 : 0, j, TPP) != 0;
                 if (!onj) continue;
                 const ChT *b0 = cha + ((int64_t)(m0 + j) * ns + ij) * row_stride;
-                float2 v0[4], v1[4];
-                QuadLoad<ChT>::load(b0, v0);
-                QuadLoad<ChT>::load(b0 + row_stride, v1);
+                float2 v0[FPT], v1[FPT];
+                FramesLoad<FPT, ChT>::load(b0, v0);
+                FramesLoad<FPT, ChT>::load(b0 + row_stride, v1);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < FPT; ++k) {
                     const float vr = fmaf(phj, v1[k].x - v0[k].x, v0[k].x);
                     const float vi = fmaf(phj, v1[k].y - v0[k].y, v0[k].y);
                     acc[k].x = fmaf(vr, csj, fmaf(-vi, snj, acc[k].x));
@@ -349,9 +371,9 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, co
         }
     }
     if (!live) return;
-    const int f0 = fbase + 4 * q;
+    const int f0 = fbase + FPT * q;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < FPT; ++k)
         if (f0 + k < p.F)
             fqi::store_c(iq, pix * p.F + f0 + k, make_float2(acc[k].x * p.inv_A, acc[k].y * p.inv_A));
 }
@@ -446,7 +468,7 @@ template <typename ChT, typename OutT, int NT>
 __global__ void __launch_bounds__(NT) das_kernel(const DasParams p, const ChT *__restrict__ ch, OutT *__restrict__ iq)
 {
     extern __shared__ float etab[];  // [6][M]: x as float, x hi, x lo, y float, y hi, y lo
-    das_tile4<ChT, OutT>(p, blockIdx.x, blockIdx.y, ch, iq, etab);
+    das_tile4<kDasTPP, ChT, OutT>(p, blockIdx.x, blockIdx.y, ch, iq, etab);
 }
 
 constexpr int kDasParamBytes = (sizeof(DasParams) + 15) & ~15;
@@ -466,7 +488,7 @@ __global__ void __launch_bounds__(NT) das_batched_kernel(const fqb::EnsDev *__re
             cur = it.e;
             __syncthreads();
         }
-        das_tile4<ChT, OutT>(*reinterpret_cast<const DasParams *>(s_par), it.x, it.y, (const ChT *)e.ch,
+        das_tile4<kDasTPP, ChT, OutT>(*reinterpret_cast<const DasParams *>(s_par), it.x, it.y, (const ChT *)e.ch,
                             (OutT *)e.iq, etab);
     }
 }
@@ -494,7 +516,7 @@ fq_status launch_das(const DasParams &p, const void *ch, void *iq, cudaStream_t 
                                                            (int)smem), "fq_das: smem attribute");
         if (s) return s;
     }
-    const int px_per_cta = kDasThreads / 4;
+    const int px_per_cta = kDasThreads / kDasTPP;
     dim3 grid((unsigned)((p.P + px_per_cta - 1) / px_per_cta), p.Fp / kFrameChunk);
     kern<<<grid, kDasThreads, smem, st>>>(p, (const ChT *)ch, (OutT *)iq);
     return fqi::launch_check("fq_das");
