@@ -37,10 +37,10 @@ UNIT = "channel-samples/s"
 GEOM_FLOP_PER_PAIR = 17.0
 FLOP_PER_TAP = 10.0
 # DRAM bytes (read + write) of one full-size C2 RF launch, from one ncu
-# capture of rf_synth_pair_kernel (dram__bytes_read.sum +
+# capture of rf_synth_quad_kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); None once the kernel changes until it is
 # captured again.
-RF_TRAFFIC_BYTES = None
+RF_TRAFFIC_BYTES = 255.59e6 + 991.65e6
 
 
 def peaks():
