@@ -209,15 +209,18 @@ def precision_variants(w, ref, n_ref, steps, warmup):
         pl.upload()
         for _ in range(warmup):
             pl.step()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        names = ("classify", "advect", "simulate", "beamform", "clutter")
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(steps)]
         torch.cuda.synchronize()
-        ev[0].record(stream)
-        for _ in range(steps):
-            pl.step()
-        ev[1].record(stream)
+        for i in range(steps):
+            ev[i][0].record(stream)
+            for j, nm in enumerate(names):
+                getattr(pl, nm)()
+                ev[i][j + 1].record(stream)
         torch.cuda.synchronize()
         fq.fq_clutter_status(pl.ws_svd)
-        ms = ev[0].elapsed_time(ev[1]) / steps
+        ms = sum(e[0].elapsed_time(e[-1]) for e in ev) / steps
+        stage = {nm: sum(e[j].elapsed_time(e[j + 1]) for e in ev) / steps for j, nm in enumerate(names)}
         rf = pl.rf[:n_ref].float().cpu().numpy()
         iq = pl.iq[:, :n_ref].float().cpu().numpy()
         iq_c = iq[..., 0] + 1j * iq[..., 1]
@@ -229,7 +232,7 @@ def precision_variants(w, ref, n_ref, steps, warmup):
         pd = ps.download().numpy().copy()
         del ps
         out.append({"variant": name, "rf": rf_t, "channel_iq": ch_t, "casorati": iq_t, "gram": gm,
-                    "ms_per_step": ms,
+                    "ms_per_step": ms, "stage_ms": stage,
                     "err_vs_fp64": {"rf_rel_l2": rel_l2(rf, ref["rf"]),
                                     "iq_rel_l2": rel_l2(np.stack([iq_c.real, iq_c.imag]),
                                                         np.stack([S_ref.real, S_ref.imag])),

@@ -18,7 +18,7 @@ namespace fqb {
 constexpr int kItemScat = 2048;   // scatterers per classify / advect item
 constexpr int kItemPix = 64;      // pixels per projection item (8 warps x 8)
 constexpr int kRfItemElems = 2;   // receive elements per RF item (the paired kernel; 4 for the quad kernel)
-constexpr int kIqTile = 64;       // rf2iq output samples per item
+constexpr int kIqTile = 128;      // rf2iq output samples per item
 constexpr int kFrameChunkB = 16;  // frames per rf2iq / DAS item
 constexpr int kDasThreadsPerPixel = 4;  // 8 measured slower on the 2D benchmark (more shuffles)
 

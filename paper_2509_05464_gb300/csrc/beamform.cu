@@ -32,7 +32,7 @@ struct Rf2iqParams {
     float h[2 * kMaxHalfTaps + 1];
 };
 
-constexpr int kRfTile = 64;  // output samples per CTA
+constexpr int kRfTile = 128;  // output samples per CTA
 
 static_assert(kRfTile == fqb::kIqTile && kFrameChunk == fqb::kFrameChunkB, "batched item shapes");
 
@@ -88,12 +88,77 @@ __device__ __forceinline__ void rf2iq_tile(const Rf2iqParams &p, int bx, int l, 
     }
 }
 
+// The same tile for the common half-length J = 8 (fs / f0 near 4): the
+// window size is a compile-time constant and each thread filters 8
+// consecutive samples of one frame from a 24-value register window (24
+// shared-memory reads instead of 8 x 17), with the taps in registers.
+template <typename InT, typename OutT>
+__device__ __forceinline__ void rf2iq_tile_j8(const Rf2iqParams &p, int bx, int l, int bz, const InT *__restrict__ rf,
+                                              OutT *__restrict__ iq, float2 *mix)
+{
+    constexpr int J = 8, W = kRfTile + 2 * J, WS = W | 1, G = 8;
+    static_assert(kRfTile == 16 * G, "256 threads = 16 frames x 16 groups of 8 samples");
+    const int k0 = bx * kRfTile;
+    const int f0 = bz * kFrameChunk;
+    float2 *rot = mix + kFrameChunk * WS;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        int n = k0 - J + i;
+        ff cyc = fqi::ff_mul_f(fqi::ff_load(p.f0_over_fs), (float)n);
+        float fr = fqi::ff_frac(cyc);
+        float sn, cs;
+        sincospif(2.0f * fr, &sn, &cs);
+        rot[i] = make_float2(cs, -sn);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kFrameChunk * W; i += blockDim.x) {
+        const int fl = i / W, w = i - fl * W;
+        const int n = k0 - J + w;
+        const int f = f0 + fl;
+        float v = 0.0f;
+        if (n >= 0 && n < p.ns && f < p.F) v = fqi::load_f(rf, ((int64_t)f * p.L + l) * p.ns + n);
+        const float2 r = rot[w];
+        mix[fl * WS + w] = make_float2(v * r.x, v * r.y);
+    }
+    __syncthreads();
+    const int fl = threadIdx.x % kFrameChunk, g = threadIdx.x / kFrameChunk;
+    float h[2 * J + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * J + 1; ++j) h[j] = p.h[j];
+    // window index of sample n is n - (k0 - J); output k0 + G g + o reads
+    // window indices G g + o + J - j, j = -J .. J
+    const float2 *src = mix + fl * WS + G * g;
+    float2 m[G + 2 * J];
+#pragma unroll
+    for (int t = 0; t < G + 2 * J; ++t) m[t] = src[t];
+    const int f = f0 + fl;
+#pragma unroll
+    for (int o = 0; o < G; ++o) {
+        float re = 0.0f, im = 0.0f;
+#pragma unroll
+        for (int j = -J; j <= J; ++j) {
+            re = fmaf(h[j + J], m[o + J - j].x, re);
+            im = fmaf(h[j + J], m[o + J - j].y, im);
+        }
+        const int k = k0 + G * g + o;
+        if (k < p.ns && f < p.Fp)
+            fqi::store_c(iq, ((int64_t)l * p.ns + k) * p.Fp + f, make_float2(2.0f * re, 2.0f * im));
+    }
+}
+
+template <typename InT, typename OutT>
+__device__ __forceinline__ void rf2iq_any(const Rf2iqParams &p, int bx, int l, int bz, const InT *__restrict__ rf,
+                                          OutT *__restrict__ iq, float2 *mix)
+{
+    if (p.J == 8) rf2iq_tile_j8<InT, OutT>(p, bx, l, bz, rf, iq, mix);
+    else rf2iq_tile<InT, OutT>(p, bx, l, bz, rf, iq, mix);
+}
+
 template <typename InT, typename OutT>
 __global__ void __launch_bounds__(256) rf2iq_kernel(const Rf2iqParams p, const InT *__restrict__ rf,
                                                     OutT *__restrict__ iq)
 {
     extern __shared__ float2 mix[];  // [kFrameChunk][W | 1] then the rotation row [W]
-    rf2iq_tile<InT, OutT>(p, blockIdx.x, blockIdx.y, blockIdx.z, rf, iq, mix);
+    rf2iq_any<InT, OutT>(p, blockIdx.x, blockIdx.y, blockIdx.z, rf, iq, mix);
 }
 
 constexpr int kIqParamBytes = (sizeof(Rf2iqParams) + 15) & ~15;
@@ -114,7 +179,7 @@ __global__ void __launch_bounds__(256) rf2iq_batched_kernel(const fqb::EnsDev *_
             cur = it.e;
             __syncthreads();
         }
-        rf2iq_tile<InT, OutT>(*reinterpret_cast<const Rf2iqParams *>(s_par), it.x, it.y, it.z,
+        rf2iq_any<InT, OutT>(*reinterpret_cast<const Rf2iqParams *>(s_par), it.x, it.y, it.z,
                               (const InT *)e.rf, (OutT *)e.ch, mix);
     }
 }

@@ -33,7 +33,7 @@ def expected_items(w, das_threads=128):
     L = w.A * w.M
     nt = cd(w.n_frames, 32)
     return {"classify": cd(w.S, 2048), "advect": cd(w.S, 2048) * w.n_frames,
-            "rf": cd(w.M, 4) * w.A * w.n_frames, "rf2iq": cd(w.Ns, 64) * L * (Fp // 16),
+            "rf": cd(w.M, 4) * w.A * w.n_frames, "rf2iq": cd(w.Ns, 128) * L * (Fp // 16),
             "das": cd(w.P, das_threads // 4) * (Fp // 16), "gram_reduce": cd(w.n_frames ** 2, 256), "eig": 1,
             "project": cd(w.P, 64), "gram_pairs": nt * (nt + 1) // 2}
 
