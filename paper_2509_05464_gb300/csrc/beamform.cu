@@ -110,14 +110,28 @@ __device__ __forceinline__ void rf2iq_tile_j8(const Rf2iqParams &p, int bx, int 
         rot[i] = make_float2(cs, -sn);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kFrameChunk * W; i += blockDim.x) {
-        const int fl = i / W, w = i - fl * W;
+    // two samples per thread: windows start at even samples (k0 - J, J even)
+    // and rows hold an even number of samples when Ns is even
+    const bool pairs = (p.ns & 1) == 0;
+    for (int i = threadIdx.x; i < kFrameChunk * (W / 2); i += blockDim.x) {
+        const int fl = i / (W / 2), w = 2 * (i - fl * (W / 2));
         const int n = k0 - J + w;
         const int f = f0 + fl;
-        float v = 0.0f;
-        if (n >= 0 && n < p.ns && f < p.F) v = fqi::load_f(rf, ((int64_t)f * p.L + l) * p.ns + n);
-        const float2 r = rot[w];
-        mix[fl * WS + w] = make_float2(v * r.x, v * r.y);
+        float v0 = 0.0f, v1 = 0.0f;
+        if (f < p.F) {
+            const int64_t base = ((int64_t)f * p.L + l) * p.ns;
+            if (pairs && n >= 0 && n + 1 < p.ns) {
+                const float2 vv = fqi::load_f2(rf, base + n);
+                v0 = vv.x;
+                v1 = vv.y;
+            } else {
+                if (n >= 0 && n < p.ns) v0 = fqi::load_f(rf, base + n);
+                if (n + 1 >= 0 && n + 1 < p.ns) v1 = fqi::load_f(rf, base + n + 1);
+            }
+        }
+        const float2 r0 = rot[w], r1 = rot[w + 1];
+        mix[fl * WS + w] = make_float2(v0 * r0.x, v0 * r0.y);
+        mix[fl * WS + w + 1] = make_float2(v1 * r1.x, v1 * r1.y);
     }
     __syncthreads();
     const int fl = threadIdx.x % kFrameChunk, g = threadIdx.x / kFrameChunk;

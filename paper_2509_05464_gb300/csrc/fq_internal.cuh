@@ -202,6 +202,12 @@ __device__ __forceinline__ f2 f2_neg(f2 a) { return f2{a.v ^ 0x8000000080000000u
 
 // -------------------------------------------------------------- storage --
 __device__ __forceinline__ float load_f(const float *p, int64_t i) { return p[i]; }
+// two consecutive values starting at an even index
+__device__ __forceinline__ float2 load_f2(const float *p, int64_t i) { return *reinterpret_cast<const float2 *>(p + i); }
+__device__ __forceinline__ float2 load_f2(const __nv_bfloat16 *p, int64_t i)
+{
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p + i));
+}
 __device__ __forceinline__ float load_f(const __nv_bfloat16 *p, int64_t i) { return __bfloat162float(p[i]); }
 __device__ __forceinline__ void store_f(float *p, int64_t i, float v) { p[i] = v; }
 __device__ __forceinline__ void store_f(__nv_bfloat16 *p, int64_t i, float v) { p[i] = __float2bfloat16_rn(v); }
