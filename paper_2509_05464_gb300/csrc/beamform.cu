@@ -341,6 +341,39 @@ struct FramesLoad<2, __nv_bfloat16> {
     }
 };
 
+// The N frames of one channel at the interpolated sample i + phi:
+// v = v(i) + phi (v(i + 1) - v(i)).  FP32 channel data interpolate in FP32;
+// BF16 channel data interpolate as packed bf16x2 (re, im) pairs and are
+// widened once afterwards, which keeps the ALU work per frame at the FP32
+// count (the widening of both samples would add four instructions per frame).
+template <int N, typename ChT>
+struct InterpFrames;
+template <int N>
+struct InterpFrames<N, float> {
+    static __device__ __forceinline__ void run(const float *b0, int64_t stride, float phi, float2 (&v)[N])
+    {
+        float2 v0[N], v1[N];
+        FramesLoad<N, float>::load(b0, v0);
+        FramesLoad<N, float>::load(b0 + stride, v1);
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            v[k] = make_float2(fmaf(phi, v1[k].x - v0[k].x, v0[k].x), fmaf(phi, v1[k].y - v0[k].y, v0[k].y));
+    }
+};
+template <>
+struct InterpFrames<4, __nv_bfloat16> {
+    static __device__ __forceinline__ void run(const __nv_bfloat16 *b0, int64_t stride, float phi, float2 (&v)[4])
+    {
+        const uint4 t0 = __ldg(reinterpret_cast<const uint4 *>(b0));
+        const uint4 t1 = __ldg(reinterpret_cast<const uint4 *>(b0 + stride));
+        const __nv_bfloat162 *a = reinterpret_cast<const __nv_bfloat162 *>(&t0);
+        const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&t1);
+        const __nv_bfloat162 ph = __float2bfloat162_rn(phi);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = __bfloat1622float2(__hfma2(ph, __hsub2(b[k], a[k]), a[k]));
+    }
+};
+
 // One tile with TPP threads per pixel (TPP = 4 or 8): pixels
 // bx * blockDim.x / TPP .., frames 16 by .. 16 by + 15.  Thread (pixel, part
 // q) accumulates frames FPT q .. FPT q + FPT - 1, FPT = 16 / TPP.  Elements
@@ -436,15 +469,12 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, co
                 const bool onj = __shfl_sync(0xffffffffu, on ? 1 : 0, j, TPP) != 0;
                 if (!onj) continue;
                 const ChT *b0 = cha + ((int64_t)(m0 + j) * ns + ij) * row_stride;
-                float2 v0[FPT], v1[FPT];
-                FramesLoad<FPT, ChT>::load(b0, v0);
-                FramesLoad<FPT, ChT>::load(b0 + row_stride, v1);
+                float2 v[FPT];
+                InterpFrames<FPT, ChT>::run(b0, row_stride, phj, v);
 #pragma unroll
                 for (int k = 0; k < FPT; ++k) {
-                    const float vr = fmaf(phj, v1[k].x - v0[k].x, v0[k].x);
-                    const float vi = fmaf(phj, v1[k].y - v0[k].y, v0[k].y);
-                    acc[k].x = fmaf(vr, csj, fmaf(-vi, snj, acc[k].x));
-                    acc[k].y = fmaf(vr, snj, fmaf(vi, csj, acc[k].y));
+                    acc[k].x = fmaf(v[k].x, csj, fmaf(-v[k].y, snj, acc[k].x));
+                    acc[k].y = fmaf(v[k].x, snj, fmaf(v[k].y, csj, acc[k].y));
                 }
             }
         }

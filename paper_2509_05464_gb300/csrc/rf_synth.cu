@@ -26,6 +26,7 @@
 
 #include "batch.cuh"
 #include "fq_internal.cuh"
+#include "rf_poly.cuh"
 
 namespace {
 
@@ -49,6 +50,10 @@ struct RfParams {
     float tab_h[2][2];  // (cos, sin)(w_h * j) for j = jmin, jmin + 1
     float tab_c[2][2];  // (cos, sin)(w_c * j) for j = jmin, jmin + 1
     int two_cycle;      // n_cycles == 2: carrier = 2 C^2 - 1 of the Hann phase
+    // first-tap thresholds on frac for the fast kernels: jlo = jmin + (frac > theta),
+    // floor(frac + half_w) = floor(half_w) + (frac >= theta2)
+    float theta, theta2, jmin_f;
+    float att_l2;       // -att log2(e): exp(-att path) = 2^(att_l2 path)
     fqi::AngleFF ang[FQ_MAX_ANGLES];
 };
 
@@ -64,25 +69,47 @@ __device__ __forceinline__ float sinc_f(float u)
     return fabsf(u) < 1e-3f ? small : big;
 }
 
-// (sin x, cos x) for |x| <= 0.8 from their Taylor series through x^9 and
-// x^10 (truncation error below 2.2e-9).  The hardware approximations carry
-// an absolute error near 4e-7 that does not average out over fractional
-// delays, and delay-and-sum adds such a bias coherently over the elements:
-// with them the compounded image error was 3.7x the RF error.
-constexpr float kTaylorMax = 0.8f;
+// Fitted polynomials (rf_poly.cuh, written by rf_poly_fit.py; Chebyshev
+// interpolants rounded to binary32).  The hardware sin/cos approximations
+// carry an absolute error near 4e-7 that does not average out over
+// fractional delays, and delay-and-sum adds such a bias coherently over the
+// elements: with them the compounded image error was 3.7x the RF error.
 
-__device__ __forceinline__ void sincos_taylor(float x, float &s, float &c)
+// (sin x, cos x) for |x| <= 0.8 (binary32 evaluation error below 6e-8)
+__device__ __forceinline__ void sincos_poly(float x, float &s, float &c)
 {
-    const float x2 = x * x;
-    float ps = fmaf(x2, 1.0f / 362880.0f, -1.0f / 5040.0f);
-    ps = fmaf(ps, x2, 1.0f / 120.0f);
-    ps = fmaf(ps, x2, -1.0f / 6.0f);
-    s = fmaf(x * x2, ps, x);
-    float pc = fmaf(x2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
-    pc = fmaf(pc, x2, -1.0f / 720.0f);
-    pc = fmaf(pc, x2, 1.0f / 24.0f);
-    pc = fmaf(pc, x2, -0.5f);
-    c = fmaf(pc, x2, 1.0f);
+    using namespace fqpoly;
+    const float t = x * x;
+    float ps = fmaf(kSinPoly3, t, kSinPoly2);
+    ps = fmaf(ps, t, kSinPoly1);
+    ps = fmaf(ps, t, kSinPoly0);
+    s = x * ps;
+    float pc = fmaf(kCosPoly4, t, kCosPoly3);
+    pc = fmaf(pc, t, kCosPoly2);
+    pc = fmaf(pc, t, kCosPoly1);
+    c = fmaf(pc, t, kCosPoly0);
+}
+
+// sin(u) / u for |u| <= 5 (binary32 evaluation error below 2e-7)
+__device__ __forceinline__ float sinc_poly(float u)
+{
+    using namespace fqpoly;
+    const float v = fmaf(u, u, -kSincCentre);
+    float r = fmaf(kSincPoly7, v, kSincPoly6);
+    r = fmaf(r, v, kSincPoly5);
+    r = fmaf(r, v, kSincPoly4);
+    r = fmaf(r, v, kSincPoly3);
+    r = fmaf(r, v, kSincPoly2);
+    r = fmaf(r, v, kSincPoly1);
+    return fmaf(r, v, kSincPoly0);
+}
+
+// 2^x (ex2.approx: relative error near 2^-22)
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // (cos, sin) of w * (jlo - frac) as exp(i w jlo) exp(-i w frac), with
@@ -94,8 +121,8 @@ __device__ __forceinline__ void first_tap(float w, float frac, float tc0, float 
                                           float &c, float &s)
 {
     float sf, cf;
-    if (SMALL || w <= kTaylorMax)
-        sincos_taylor(w * frac, sf, cf);
+    if (SMALL || w <= fqpoly::kTapXMax)
+        sincos_poly(w * frac, sf, cf);
     else
         sincosf(w * frac, &sf, &cf);
     const float tc = sel1 ? tc1 : tc0, ts = sel1 ? ts1 : ts0;
@@ -503,12 +530,12 @@ __device__ __forceinline__ void rf_pair_tile(const RfParams &p, int bx, int a, i
         fqi::f2_split(dxh, dxh0, dxh1);
         fqi::f2_split(RS, rs0, rs1);
         fqi::f2_split(sp, sp0, sp1);
-        float D0 = sinc_f(p.kbx * dxh0 * rs0), D1 = sinc_f(p.kbx * dxh1 * rs1);
+        float D0 = sinc_poly(p.kbx * dxh0 * rs0), D1 = sinc_poly(p.kbx * dxh1 * rs1);
         if (matrix) {
             float dy0, dy1;
             fqi::f2_split(dyh, dy0, dy1);
-            D0 *= sinc_f(p.kby * dy0 * rs0);
-            D1 *= sinc_f(p.kby * dy1 * rs1);
+            D0 *= sinc_poly(p.kby * dy0 * rs0);
+            D1 *= sinc_poly(p.kby * dy1 * rs1);
         }
         const float Rfix = R * to_fix;
         f2 A2 = fqi::f2_mul(fqi::f2_mul(fqi::f2_dup(Rfix), fqi::f2_make(D0, D1)),
@@ -674,7 +701,8 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, i
     const float *X = pos + (int64_t)f * 3 * S;
     const float *Y = X + S;
     const float *Z = Y + S;
-    const float half_w = p.half_w;
+    const float theta = p.theta, theta2 = p.theta2, jmin_f = p.jmin_f, att_l2 = p.att_l2;
+    const int kfast = ns - 9;  // records k .. k + 8 inside [0, ns): 0 <= k <= kfast
     const float thc0 = p.tab_h[0][0], ths0 = p.tab_h[0][1], thc1 = p.tab_h[1][0], ths1 = p.tab_h[1][1];
     const f2 COSH = fqi::f2_dup(p.cos_h), SINH = fqi::f2_dup(p.sin_h), TWOCOS = fqi::f2_dup(p.two_cos_h);
     const f2 HALF = fqi::f2_dup(0.5f);
@@ -739,9 +767,9 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, i
         const float zy2 = __fadd_rn(zz.hi, q2);  // z^2 (+ dy^2), binary32
         const float r0f = r0 + rl;
         const float Rfix = R * to_fix;
-        float Ae[E], fre[E], che[E], she[E];
-        int ke[E], nte[E];
-        bool ine[E], liv[E];
+        float Ae[E], che[E], she[E];
+        int ke[E];
+        bool ine[E], liv[E], nine[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             float dxe, rse, fr, fl, pe;
@@ -763,34 +791,32 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, i
                 fl = fl0 + c;
                 pe = path.hi + de;
             }
-            float D = sinc_f(p.kbx * dxe * rse);
-            if (matrix) D *= sinc_f(p.kby * dyh * rse);
-            float A = Rfix * D * __expf(-p.att * pe) * rse;
+            float D = sinc_poly(p.kbx * dxe * rse);
+            if (matrix) D *= sinc_poly(p.kby * dyh * rse);
+            float A = Rfix * D * ex2_approx(att_l2 * pe) * rse;
             const bool lv = live_e[e] && (e > 0 || pos0);
             A = lv ? fminf(fmaxf(A, -kTapClamp), kTapClamp) : 0.0f;  // one clamp bounds every tap (|p| <= 1)
-            const int jlo = (int)ceilf(fr - half_w);
-            const int nt = (int)floorf(fr + half_w) - jlo + 1;
-            const int k = (int)fl + jlo;
+            // taps j = jlo .. jlo + nt - 1 with |j - frac| < half_w: jlo is jmin
+            // or jmin + 1, nt is 8 or 9
+            const bool first_lo = fr <= theta;
+            const int k = (int)(fl + (first_lo ? jmin_f : jmin_f + 1.0f));
             float ch, sh;
-            first_tap<true>(p.w_h, fr, thc0, ths0, thc1, ths1, jlo != p.jmin, ch, sh);
+            first_tap<true>(p.w_h, fr, thc0, ths0, thc1, ths1, !first_lo, ch, sh);
             Ae[e] = A;
-            fre[e] = fr;
             ke[e] = k;
-            nte[e] = nt;
+            nine[e] = first_lo || fr >= theta2;
             che[e] = ch;
             she[e] = sh;
             liv[e] = lv;
-            ine[e] = lv && k >= 0 && k + nt <= ns;
+            ine[e] = lv && (unsigned)k <= (unsigned)kfast;
         }
-        (void)fre;
         const f2 A01 = fqi::f2_make(Ae[0], Ae[1]), A23 = fqi::f2_make(Ae[2], Ae[3]);
         const f2 hA01 = fqi::f2_mul(HALF, A01), hA23 = fqi::f2_mul(HALF, A23);
         const f2 CH01 = fqi::f2_make(che[0], che[1]), SH01 = fqi::f2_make(she[0], she[1]);
         const f2 CH23 = fqi::f2_make(che[2], che[3]), SH23 = fqi::f2_make(she[2], she[3]);
         f2 Ca0 = CH01, Ca1 = fqi::f2_fma(CH01, COSH, fqi::f2_neg(fqi::f2_mul(SH01, SINH)));
         f2 Cb0 = CH23, Cb1 = fqi::f2_fma(CH23, COSH, fqi::f2_neg(fqi::f2_mul(SH23, SINH)));
-        const bool fast = ns >= 8 && (ine[0] || !liv[0]) && (ine[1] || !liv[1]) && (ine[2] || !liv[2]) &&
-                          (ine[3] || !liv[3]);
+        const bool fast = (ine[0] || !liv[0]) && (ine[1] || !liv[1]) && (ine[2] || !liv[2]) && (ine[3] || !liv[3]);
         if (fast) {
             const int q0 = liv[0] ? ke[0] : 0, q1 = liv[1] ? ke[1] : 0;  // dead lanes: A = 0 at samples 0-7
             const int q2i = liv[2] ? ke[2] : 0, q3 = liv[3] ? ke[3] : 0;
@@ -805,12 +831,12 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, i
                 Cb0 = Cb1;
                 Cb1 = Cb2;
             }
-            if (nte[0] > 8 || nte[1] > 8)
-                add_fixed2(hi0, lo0, hi1, lo1, ke[0] + 8, ke[1] + 8, tap2x2(A01, hA01, Ca0), liv[0] && nte[0] > 8,
-                           liv[1] && nte[1] > 8);
-            if (nte[2] > 8 || nte[3] > 8)
-                add_fixed2(hi2, lo2, hi3, lo3, ke[2] + 8, ke[3] + 8, tap2x2(A23, hA23, Cb0), liv[2] && nte[2] > 8,
-                           liv[3] && nte[3] > 8);
+            if (nine[0] || nine[1])
+                add_fixed2(hi0, lo0, hi1, lo1, ke[0] + 8, ke[1] + 8, tap2x2(A01, hA01, Ca0), liv[0] && nine[0],
+                           liv[1] && nine[1]);
+            if (nine[2] || nine[3])
+                add_fixed2(hi2, lo2, hi3, lo3, ke[2] + 8, ke[3] + 8, tap2x2(A23, hA23, Cb0), liv[2] && nine[2],
+                           liv[3] && nine[3]);
         } else {
             // an echo straddles a record end: per-tap bounds
             for (int j = 0; j < 9; ++j) {
@@ -819,7 +845,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, i
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     kk[e] = ke[e] + j;
-                    on[e] = liv[e] && j < nte[e] && kk[e] >= 0 && kk[e] < ns;
+                    on[e] = liv[e] && j < (nine[e] ? 9 : 8) && kk[e] >= 0 && kk[e] < ns;
                     if (!on[e]) kk[e] = 0;
                 }
                 add_fixed2(hi0, lo0, hi1, lo1, kk[0], kk[1], tap2x2(A01, hA01, Ca0), on[0], on[1]);
@@ -946,6 +972,16 @@ int rf_elems(int ns)
     return 2;
 }
 
+// The paired and quad kernels serve the common pulse (two cycles,
+// 8 <= n_cycles fs / f0 < 9, so every echo has 8 or 9 taps and the Hann
+// phase per sample is below pi / 4) with element widths of at most
+// 5 / pi wavelengths (directivity argument |u| <= 5 for the fitted sinc).
+bool rf_fast_ok(const RfParams &p)
+{
+    return p.two_cycle && p.ntap_max == 9 && p.kbx <= fqpoly::kSincUMax && p.kby <= fqpoly::kSincUMax &&
+           p.pr.ns >= 9;
+}
+
 template <typename OutT>
 fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *amp, const float *base,
                       OutT *rf, cudaStream_t st)
@@ -958,10 +994,9 @@ fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *a
     // the common pulse (two cycles, 8 <= n_cycles fs / f0 < 9, so every echo
     // has 8 or 9 taps) runs on the quad kernel when the array rows hold
     // whole quads, else on the packed-pair kernel
-    if (!scalar_only && fqi::use_rf_quad(p.pr.nx) && p.two_cycle && p.ntap_max == 9 &&
-        8 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
+    if (!scalar_only && fqi::use_rf_quad(p.pr.nx) && rf_fast_ok(p) && 8 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
         return launch_rf_quad(p, F, pos, amp, base, rf, st);
-    if (!scalar_only && p.two_cycle && p.ntap_max == 9 && 4 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
+    if (!scalar_only && rf_fast_ok(p) && 4 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
         return launch_rf_pair(p, F, pos, amp, base, rf, st);
     switch (rf_elems(p.pr.ns)) {
     case 16: return launch_rf<16>(p, F, pos, amp, base, rf, st);
@@ -991,6 +1026,10 @@ fq_status make_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, RfPa
     p.w_c = (float)wc;
     p.w_h = (float)wh;
     p.jmin = (int)std::ceil(0.0 - hw);  // frac in [0, 1): jlo in {jmin, jmin + 1}
+    p.jmin_f = (float)p.jmin;
+    p.theta = (float)(p.jmin + hw);
+    p.theta2 = (float)(std::floor(hw) + 1.0 - hw);
+    p.att_l2 = (float)(-(double)p.att / std::log(2.0));
     for (int q = 0; q < 2; ++q) {
         double j = p.jmin + q;
         p.tab_h[q][0] = (float)std::cos(wh * j);
@@ -1063,8 +1102,7 @@ bool use_rf_quad(int nx)
 
 int rf_ntap_ok(const void *rf_params)
 {
-    const RfParams &p = *reinterpret_cast<const RfParams *>(rf_params);
-    return p.two_cycle && p.ntap_max == 9;
+    return rf_fast_ok(*reinterpret_cast<const RfParams *>(rf_params));
 }
 
 template <int MINB, bool QUAD, typename OutT>

@@ -168,6 +168,26 @@ def test_rf_static_tissue_base_and_bf16():
     assert rel_l2(rf16[1], want) <= BF16_TOL
 
 
+@pytest.mark.parametrize("route", ["quad", "pair", "wide_element", "three_cycle"])
+def test_rf_kernel_routes(route):
+    """Every RF kernel route against the oracle: the quad kernel (rows of
+    whole quads), the paired kernel (rows of 6), and the general kernel for
+    elements wider than the fitted directivity covers (k0 w / 2 > 5) and for
+    a three-cycle pulse."""
+    nx, pitch, width, nc = {"quad": (8, 0.3e-3, 0.3e-3, 2), "pair": (6, 0.3e-3, 0.3e-3, 2),
+                            "wide_element": (8, 0.6e-3, 0.55e-3, 2), "three_cycle": (8, 0.3e-3, 0.3e-3, 3)}[route]
+    fs = 20e6 if nc == 2 else 30e6
+    p = W.Probe(nx, 1, pitch, pitch, width, width, 5e6, fs, 1540.0, 0.5, nc, 700)
+    rng = np.random.default_rng(7)
+    S = 600
+    pos = np.stack([rng.uniform(-4e-3, 4e-3, S), np.zeros(S), rng.uniform(2e-3, 24e-3, S)]).astype(np.float32)
+    amp = rng.standard_normal(S).astype(np.float32)
+    tx = [-0.05, 0.0, 0.08]
+    rf = host(fq.fq_simulate_rf(p, tx, [0.0] * 3, dev(pos[None]), dev(amp), 1))
+    want = oracle.simulate_rf(p, tx, [0.0] * 3, pos, amp)
+    assert rel_l2(rf[0], want) <= RF_TOL, route
+
+
 def test_rf_edge_cases():
     """no scatterers -> zeros; scatterers whose echo straddles the record
     ends keep only the in-record samples."""
