@@ -68,6 +68,7 @@ def lib():
             L.or_advect.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _p]
             L.or_classify.argtypes = [_i64, _p, _p, _i, _p, _p, _p, _p]
             L.or_bin.argtypes = [_i64, _p, _d, _d, _i, _p, _p]
+            L.or_advect_field.argtypes = [_i64, _p, _p, _i, _p, _p, _i, _i, _i, _p, _p, _d, _i, _i, _i, _p]
             _lib = L
     return _lib
 
@@ -195,6 +196,28 @@ def advect(p0, seg, flow, seg_table, motion_table, t):
     S = seg.shape[0]
     out = np.zeros((3, S), np.float32)
     lib().or_advect(S, _ptr(p0), _ptr(seg), _ptr(flow), _ptr(st), _ptr(mt), float(t), _ptr(out))
+    return out
+
+
+def advect_field(p0, seg, seg_table, n_seg, v, origin, spacing, dt, n_sub, n_frames, first_frame=0):
+    """Positions float32 [n_frames][3][S] at t = f dt, f = first_frame ..
+    first_frame + n_frames - 1, of scatterers p0 [3][S] moving with the
+    gridded steady field v [nz][ny][nx][4] (RK4, step dt / n_sub); seg [S]
+    (or None) confines blood scatterers to their segment's lumen."""
+    p0 = np.ascontiguousarray(p0, np.float32)
+    S = p0.shape[1]
+    segp = None
+    if seg is not None:
+        seg = np.ascontiguousarray(seg, np.int32)
+        segp = _ptr(seg)
+    st = np.ascontiguousarray(seg_table, np.float64) if seg_table is not None else np.zeros((1, 24))
+    v = np.ascontiguousarray(v, np.float32)
+    nz, ny, nx = v.shape[:3]
+    org = np.ascontiguousarray(origin, np.float64)
+    spc = np.ascontiguousarray(spacing, np.float64)
+    out = np.zeros((n_frames, 3, S), np.float32)
+    lib().or_advect_field(S, _ptr(p0), segp, int(n_seg), _ptr(st), _ptr(v), nx, ny, nz, _ptr(org), _ptr(spc),
+                          float(dt), int(n_sub), int(first_frame), int(n_frames), _ptr(out))
     return out
 
 

@@ -616,3 +616,124 @@ void or_bin(int64_t S, const float *z, double z0, double dz, int B, int32_t *bin
     free(fill);
     free(key);
 }
+
+/* ------------------------------------------------------------------------
+ * Trajectories of a steady gridded velocity field (Sec. 2.2.2:
+ * P(t) = P0 + integral_0^t v(P(s)) ds; App. C: scatterers follow the local
+ * flow), by the classical fourth-order Runge-Kutta method with the fixed
+ * step h = dt / n_sub, with blood scatterers confined to their vessel lumen
+ * (Sec. 2.2.2: the vessel geometry constrains the integration).
+ *
+ *  v(P): trilinear interpolation of the samples v[iz][iy][ix][0..2] (four
+ *        floats per sample, the fourth unused) at the grid coordinates
+ *        g = (P - origin) / spacing, each clamped to [0, n - 1] (the field
+ *        continues constant beyond the grid); the cell is
+ *        i = min(floor(g), n - 2) (i = 0 when n = 1), weight f = g - i.
+ *  step: k1 = v(P), k2 = v(P + h/2 k1), k3 = v(P + h/2 k2), k4 = v(P + h k3),
+ *        P <- P + h/6 (k1 + 2 k2 + 2 k3 + k4).
+ *  confinement of a scatterer with 0 <= seg < n_seg, after every step
+ *  (segment table as for or_advect):
+ *    line: w = P - p0, a = w.a1, x = (w.a2, w.a3); if |x| > R, x <- x R/|x|;
+ *          a wrapped into [0, L); P = p0 + a a1 + x1 a2 + x2 a3.
+ *    arc:  w = P - C, u_k = w.a_k, phi = atan2(u2, u1),
+ *          e = (sqrt(u1^2 + u2^2) - Rc, u3); if |e| > R, e <- e R/|e|;
+ *          phi wrapped into [0, phi1);
+ *          P = C + (Rc + e1)(cos phi a1 + sin phi a2) + e2 a3.
+ *  (the wrap re-injects a scatterer that leaves one end at the other, as
+ *  the closed-form advection does.)
+ * Output: out[f - f0] = (float) P(f dt) for f = f0 .. f0 + F - 1, P(0) = p0.
+ * Pinned by: uniform and linear fields (exact solutions: translation,
+ * matrix exponential, rigid rotation), the fourth-order convergence of the
+ * step, lumen confinement and axial wrap, constant continuation outside
+ * the grid.
+ * ---------------------------------------------------------------------- */
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+static void field_cell(double g, int n, int *i0, int *i1, double *f)
+{
+    if (n <= 1) { *i0 = 0; *i1 = 0; *f = 0.0; return; }
+    g = clampd(g, 0.0, (double)(n - 1));
+    int i = (int)floor(g);
+    if (i > n - 2) i = n - 2;
+    *i0 = i; *i1 = i + 1; *f = g - (double)i;
+}
+
+static void field_eval(const float *v, int nx, int ny, int nz, const double *org, const double *sp,
+                       const double P[3], double out[3])
+{
+    int x0, x1, y0, y1, z0, z1;
+    double fx, fy, fz;
+    field_cell((P[0] - org[0]) / sp[0], nx, &x0, &x1, &fx);
+    field_cell((P[1] - org[1]) / sp[1], ny, &y0, &y1, &fy);
+    field_cell((P[2] - org[2]) / sp[2], nz, &z0, &z1, &fz);
+    for (int c = 0; c < 3; ++c) {
+        double vz[2];
+        for (int kz = 0; kz < 2; ++kz) {
+            int iz = kz ? z1 : z0;
+            double vy[2];
+            for (int ky = 0; ky < 2; ++ky) {
+                int iy = ky ? y1 : y0;
+                const float *row = v + (((int64_t)iz * ny + iy) * nx) * 4;
+                double a = row[4 * x0 + c], b = row[4 * x1 + c];
+                vy[ky] = a + fx * (b - a);
+            }
+            vz[kz] = vy[0] + fy * (vy[1] - vy[0]);
+        }
+        out[c] = vz[0] + fz * (vz[1] - vz[0]);
+    }
+}
+
+static void confine(const double *sg, double P[3])
+{
+    double w[3] = {P[0] - sg[1], P[1] - sg[2], P[2] - sg[3]};
+    double u1 = w[0] * sg[4] + w[1] * sg[5] + w[2] * sg[6];
+    double u2 = w[0] * sg[7] + w[1] * sg[8] + w[2] * sg[9];
+    double u3 = w[0] * sg[10] + w[1] * sg[11] + w[2] * sg[12];
+    double R = sg[14];
+    if ((int)sg[0] == 0) {
+        double r = sqrt(u2 * u2 + u3 * u3);
+        if (r > R) { u2 *= R / r; u3 *= R / r; }
+        double a = wrap_into(u1, sg[13]);
+        for (int d = 0; d < 3; ++d) P[d] = sg[1 + d] + a * sg[4 + d] + u2 * sg[7 + d] + u3 * sg[10 + d];
+    } else {
+        double Rc = sg[16];
+        double phi = atan2(u2, u1);
+        double e1 = sqrt(u1 * u1 + u2 * u2) - Rc, e2 = u3;
+        double r = sqrt(e1 * e1 + e2 * e2);
+        if (r > R) { e1 *= R / r; e2 *= R / r; }
+        phi = wrap_into(phi, sg[17]);
+        double cp = cos(phi), s = sin(phi);
+        for (int d = 0; d < 3; ++d)
+            P[d] = sg[1 + d] + (Rc + e1) * (cp * sg[4 + d] + s * sg[7 + d]) + e2 * sg[10 + d];
+    }
+}
+
+void or_advect_field(int64_t S, const float *p0, const int32_t *seg, int n_seg, const double *segt,
+                     const float *v, int nx, int ny, int nz, const double *origin, const double *spacing,
+                     double dt, int n_sub, int f0, int F, float *out)
+{
+    const double h = dt / (double)n_sub;
+    #pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < S; ++s) {
+        double P[3] = {p0[s], p0[S + s], p0[2 * S + s]};
+        const double *sg = (seg && seg[s] >= 0 && seg[s] < n_seg) ? segt + 24 * (int64_t)seg[s] : NULL;
+        for (int f = 0; f < f0 + F; ++f) {
+            if (f > 0) {
+                for (int j = 0; j < n_sub; ++j) {
+                    double k1[3], k2[3], k3[3], k4[3], Q[3];
+                    field_eval(v, nx, ny, nz, origin, spacing, P, k1);
+                    for (int d = 0; d < 3; ++d) Q[d] = P[d] + 0.5 * h * k1[d];
+                    field_eval(v, nx, ny, nz, origin, spacing, Q, k2);
+                    for (int d = 0; d < 3; ++d) Q[d] = P[d] + 0.5 * h * k2[d];
+                    field_eval(v, nx, ny, nz, origin, spacing, Q, k3);
+                    for (int d = 0; d < 3; ++d) Q[d] = P[d] + h * k3[d];
+                    field_eval(v, nx, ny, nz, origin, spacing, Q, k4);
+                    for (int d = 0; d < 3; ++d) P[d] += h / 6.0 * (k1[d] + 2.0 * k2[d] + 2.0 * k3[d] + k4[d]);
+                    if (sg) confine(sg, P);
+                }
+            }
+            if (f >= f0)
+                for (int d = 0; d < 3; ++d) out[((int64_t)(f - f0) * 3 + d) * S + s] = (float)P[d];
+        }
+    }
+}
