@@ -580,7 +580,7 @@ def run_cnn(args, rank, world, local):
                    "train_loss": hist, "data_generation_s": gen_s,
                    "l2": "inference working set (activations 0.84 GB per layer) far above L2"},
         "quality": quality,
-        "roofline": {"bound": "tensor", "kernel": "conv_tc_kernel", "achieved": ach, "peak": peak,
+        "roofline": {"bound": "tensor", "kernel": "conv_ring_kernel", "achieved": ach, "peak": peak,
                      "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                      "peak_source": f"bf16_tflops of {src} peaks (cuBLAS burst)",
                      "work": f"2 x {mac_true} MAC per voxel (the 2-32-32-32-2 network); the kernels execute "
@@ -588,6 +588,115 @@ def run_cnn(args, rank, world, local):
         "cpu_baseline": None,
         "e2e": None,
         "gpu_launches": 5 * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------- gridded-field advection (Sec. 2.2.2) --
+# FP32 operations of one RK4 step as defined: four trilinear evaluations
+# (grid coordinates 3 x 2, seven lerps per component 7 x 3 x 2 = 42), the
+# three stage points (3 x 3 x 2 = 18) and the weighted sum (3 x 7 = 21)
+FIELD_FLOP_PER_STEP = 4 * (6 + 42) + 18 + 21
+
+
+def run_field(args, rank, world, local):
+    """Trajectories of the C2 medium in a gridded steady velocity field
+    (RK4, lumen confinement of the blood) for a 200-frame ensemble."""
+    import torch
+    from paper_2509_05464_gb300 import fq
+    from paper_2509_05464_gb300 import workload as W
+
+    torch.cuda.set_device(local)
+    fq.lib()
+    fw = W.field_c2(seed=2 + rank, n_frames=args.frames)
+    h_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (fw.p0, fw.seg, fw.v)]
+    p0, seg, v = (t.to("cuda") for t in h_in)
+    pos = torch.empty((fw.n_frames, 3, fw.S), dtype=torch.float32, device="cuda")
+    h_pos = torch.empty(pos.shape, dtype=torch.float32).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fq.fq_advect_field(p0, seg, fw.segments, fw.origin, fw.spacing, v, fw.dt, fw.n_sub, fw.n_frames,
+                           pos_out=pos)
+
+    for _ in range(args.warmup):
+        step()
+    clk = ClockSampler(local)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / args.steps)
+    # end to end: inputs from pinned host memory, every position back
+    e2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in e2:
+        flush.zero_()
+        a.record(stream)
+        for d, hsrc in zip((p0, seg, v), h_in):
+            d.copy_(hsrc, non_blocking=True)
+        step()
+        h_pos.copy_(pos, non_blocking=True)
+        b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2) / args.steps)
+    got = pos.cpu().numpy()
+    units = float(fw.n_frames * fw.S)
+    total = sum_over_ranks(units)
+    if rank != 0:
+        return
+    # parity on a sample of scatterers (every 97th) against the oracle
+    import oracle
+    idx = np.arange(0, fw.S, 97)
+    want = oracle.advect_field(np.ascontiguousarray(fw.p0[:, idx]), np.ascontiguousarray(fw.seg[idx]),
+                               W.segment_table(fw), len(fw.segments), fw.v, fw.origin, fw.spacing, fw.dt,
+                               fw.n_sub, fw.n_frames)
+    d = np.abs(got[:, :, idx].astype(np.float64) - want.astype(np.float64))
+    ulps = d / float(np.spacing(np.float32(np.abs(want).max())))  # in ulps of the largest coordinate
+    cpu = None
+    if args.cpu_baseline:
+        t0 = time.perf_counter()
+        oracle.advect_field(fw.p0, fw.seg, W.segment_table(fw), len(fw.segments), fw.v, fw.origin, fw.spacing,
+                            fw.dt, fw.n_sub, fw.n_frames)
+        dt_cpu = time.perf_counter() - t0
+        cpu = {"value": units / dt_cpu, "unit": "positions/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"the whole workload ({fw.S} scatterers x {fw.n_frames} frames, FP64), {dt_cpu:.1f} s"}
+    steps = (fw.n_frames - 1) * fw.n_sub * fw.S  # RK4 steps (frame 0 is p0)
+    pk, src = peaks()
+    sm_for_peak = float(pk.get("sm_max_mhz", 2070.0))
+    peak = fp32_alu_peak_tflops(sm_for_peak)
+    ach = steps * FIELD_FLOP_PER_STEP / (ms * 1e-3) / 1e12
+    line = {
+        "metric": "scatterer positions/s (steady gridded velocity field, RK4, lumen confinement)",
+        "value": total / (ms * 1e-3), "unit": "positions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": fw.name, "scatterers": fw.S, "frames": fw.n_frames, "rk4_steps_per_frame": fw.n_sub,
+                   "field_samples": int(np.prod(fw.v.shape[:3])),
+                   "parallelism": f"independent ensemble per GPU x{world}",
+                   "l2": "256 MiB buffer rewritten between timed steps, outside the timed events"},
+        "parity": {"sampled_scatterers": int(idx.size), "max_abs_m": float(d.max()),
+                   "max_ulps_of_largest_coordinate": float(ulps.max()),
+                   "frac_over_2_ulps": float((ulps > 2).any(axis=(0, 1)).mean())},
+        "roofline": {"bound": "alu", "kernel": "advect_field_kernel", "achieved": ach, "peak": peak,
+                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
+                                    f"({src} max clock)",
+                     "work": f"{FIELD_FLOP_PER_STEP} FLOP per RK4 step, {steps:.3e} steps"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": total / (e2e_ms * 1e-3), "unit": "positions/s",
+                "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in h_in)),
+                "d2h_bytes_per_step": int(h_pos.numel() * 4), "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -613,9 +722,9 @@ def main():
     ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
-    ap.add_argument("--workload", choices=["c2", "c4", "c5"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c4", "c5", "field"], default="c2",
                     help="c2: one 200-frame 2D ensemble (default); c4: the 64-ensemble uneven batch; "
-                         "c5: the learned clutter filter")
+                         "c5: the learned clutter filter; field: advection in a gridded velocity field")
     ap.add_argument("--cnn-ensembles", type=int, default=64, help="c5: simulated training + held-out ensembles")
     ap.add_argument("--cnn-train-steps", type=int, default=1500, help="c5: timed training steps")
     ap.add_argument("--cnn-infer-frames", type=int, default=200, help="c5: frames of the inference ensemble")
@@ -635,6 +744,8 @@ def main():
         run_batched(args, rank, world, local)
     elif args.workload == "c5":
         run_cnn(args, rank, world, local)
+    elif args.workload == "field":
+        run_field(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     import torch.distributed as dist

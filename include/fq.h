@@ -173,6 +173,46 @@ fq_status fq_advect_scatterers(const float *p0, const int32_t *seg_id, const flo
                                double t0, double dt, int32_t n_frames, float *pos_out,
                                void *stream);
 
+/* Trajectories of a steady gridded velocity field (Sec. 2.2.2: the
+ * position is P(t) = P0 + integral_0^t v(P(s)) ds for a user-defined steady
+ * field v(x, y, z), and the vessel geometry confines the intravascular
+ * scatterers; App. C: scatterers follow the local flow).  The paper
+ * integrates with an adaptive ODE23 (PROTEUS); this call uses the classical
+ * fourth-order Runge-Kutta method with the fixed step h = dt / n_sub:
+ *   k1 = v(P), k2 = v(P + h/2 k1), k3 = v(P + h/2 k2), k4 = v(P + h k3),
+ *   P <- P + h/6 (k1 + 2 k2 + 2 k3 + k4).
+ * v(P) is the trilinear interpolation of the samples at the grid
+ * coordinates g = (P - origin) / spacing, each clamped to [0, n - 1] (the
+ * field continues constant beyond the grid; an axis with n = 1 is
+ * constant along it).  After every step a scatterer with
+ * 0 <= seg_id < n_seg is confined to that segment's lumen and re-injected
+ * at the other end when it leaves one (fq_segment frame (a1, a2, a3)):
+ *   line: a = (P - p0).a1, x = ((P - p0).a2, (P - p0).a3); |x| > radius ->
+ *         x radius / |x|; a wrapped into [0, length).
+ *   arc:  u_k = (P - p0).a_k, phi = atan2(u2, u1), e = (|(u1, u2)| - arc_radius, u3);
+ *         |e| > radius -> e radius / |e|; phi wrapped into [0, phi1).
+ * Other scatterers (seg_id NULL, < 0 or >= n_seg) move freely.
+ *   p0       device float [3][S]   positions at t = 0
+ *   seg_id   device int32 [S] or NULL
+ *   grid     host fq_vfield (sample counts, origin, spacing)
+ *   v        device float [nz][ny][nx][4] (vx, vy, vz, unused) in m/s, 16-byte aligned
+ *   pos_out  device float [n_frames][3][S]: P(f dt) for f = first_frame ..
+ *            first_frame + n_frames - 1 (P(0) = p0)
+ * Arithmetic is binary32 (the displacement from p0 is accumulated, not the
+ * position).  Errors: FQ_ERR_INVALID_ARG (null pointer, S < 0,
+ * n_frames < 1, first_frame < 0, n_sub < 1, dt <= 0, a segment with no
+ * extent), FQ_ERR_SHAPE (a grid axis with n < 1 or spacing <= 0, more than
+ * 2^31 samples, n_seg above the maximum), FQ_ERR_ALIGN (v). */
+typedef struct fq_vfield {
+    int32_t nx, ny, nz;         /* samples per axis (>= 1) */
+    double x0, y0, z0;          /* position of sample (0, 0, 0) (m) */
+    double dx, dy, dz;          /* spacing (m) */
+} fq_vfield;
+
+fq_status fq_advect_field(const float *p0, const int32_t *seg_id, int64_t S, const fq_flow *flow,
+                          const fq_vfield *grid, const float *v, double dt, int32_t n_sub,
+                          int32_t first_frame, int32_t n_frames, float *pos_out, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* a2: vessel membership and depth binning                              */
 /* ------------------------------------------------------------------ */
@@ -378,7 +418,7 @@ fq_status fq_debug_set(int32_t what, int32_t value);
 /* sizeof of the ABI's structs as this library was compiled, for bindings
  * that check their own layouts: 0 fq_probe, 1 fq_tx, 2 fq_grid,
  * 3 fq_segment, 4 fq_flow, 5 fq_motion, 6 fq_ensemble_desc,
- * 7 fq_tile_choice; 0 for any other index.  The paper has no counterpart. */
+ * 7 fq_tile_choice, 8 fq_vfield; 0 for any other index.  The paper has no counterpart. */
 size_t fq_sizeof(int32_t which);
 
 /* ------------------------------------------------------------------ */

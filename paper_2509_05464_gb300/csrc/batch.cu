@@ -346,6 +346,7 @@ size_t fq_sizeof(int32_t which)
     case 5: return sizeof(fq_motion);
     case 6: return sizeof(fq_ensemble_desc);
     case 7: return sizeof(fq_tile_choice);
+    case 8: return sizeof(fq_vfield);
     default: return 0;
     }
 }

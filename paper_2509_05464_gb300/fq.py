@@ -84,7 +84,12 @@ class TileChoice(C.Structure):
 FQ_OP_RF, FQ_OP_DAS = 0, 1
 STAGES = ("classify", "advect", "rf", "rf2iq", "das", "gram", "gram_reduce", "eig", "project")
 # ctypes structs of the ABI, in the order of fq_sizeof's argument
-ABI_STRUCTS = (Probe, Tx, Grid, Segment, Flow, Motion, EnsembleDesc, TileChoice)
+class VField(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("x0", C.c_double), ("y0", C.c_double),
+                ("z0", C.c_double), ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double)]
+
+
+ABI_STRUCTS = (Probe, Tx, Grid, Segment, Flow, Motion, EnsembleDesc, TileChoice, VField)
 
 
 # ------------------------------------------------------------------ loading --
@@ -113,6 +118,7 @@ def lib():
         L.fq_frame_pad.argtypes = [_I32]
         sig = {
             "fq_advect_scatterers": [_P, _P, _P, _I64, C.POINTER(Flow), C.POINTER(Motion), _D, _D, _I32, _P, _P],
+            "fq_advect_field": [_P, _P, _I64, C.POINTER(Flow), C.POINTER(VField), _P, _D, _I32, _I32, _I32, _P, _P],
             "fq_classify_scatterers": [_P, _P, _I64, C.POINTER(Flow), _P, _P, _P, _P],
             "fq_bin_workspace_size": [_I64, _I32, C.POINTER(_SZ)],
             "fq_bin_scatterers": [_P, _I64, _D, _D, _I32, _P, _P, _P, _SZ, _P],
@@ -275,6 +281,25 @@ def fq_advect_scatterers(p0, seg_id, flow_coord, segments, motion, t0, dt, n_fra
     mo = make_motion(motion)
     _check(lib().fq_advect_scatterers(_ptr(p0), _ptr(seg_id), _ptr(flow_coord), S, C.byref(fh.st), C.byref(mo),
                                       float(t0), float(dt), int(n_frames), _ptr(pos_out), _stream(stream)))
+    return pos_out
+
+
+def fq_advect_field(p0, seg_id, segments, origin, spacing, v, dt, n_sub, n_frames, first_frame=0, pos_out=None,
+                    stream=None):
+    """Positions [n_frames][3][S] (float32) at t = f dt, f = first_frame ..,
+    of scatterers p0 [3][S] in the steady field v [nz][ny][nx][4] (RK4 with
+    n_sub steps per frame); seg_id [S] int32 or None confines blood
+    scatterers to the lumen of their segment."""
+    S = p0.shape[1]
+    if pos_out is None:
+        pos_out = torch.empty((n_frames, 3, S), dtype=torch.float32, device=p0.device)
+    nz, ny, nx = v.shape[:3]
+    g = VField(int(nx), int(ny), int(nz), float(origin[0]), float(origin[1]), float(origin[2]),
+               float(spacing[0]), float(spacing[1]), float(spacing[2]))
+    fh = _FlowHolder(segments or [])
+    _check(lib().fq_advect_field(_ptr(p0), _ptr(seg_id) if seg_id is not None else None, S, C.byref(fh.st),
+                                 C.byref(g), _ptr(v), float(dt), int(n_sub), int(first_frame), int(n_frames),
+                                 _ptr(pos_out), _stream(stream)))
     return pos_out
 
 

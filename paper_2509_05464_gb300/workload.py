@@ -333,6 +333,88 @@ def config2(seed: int = 2, n_frames: int = 200, n_scat: int = 100_000) -> Worklo
                     bin_dz=0.1e-3, bin_z0=0.0, n_bins=230)
 
 
+@dataclass
+class FieldWorkload:
+    """Scatterers moving with a steady gridded velocity field: p0 [3][S]
+    (blood placed in its lumen), seg [S] (-1 tissue), the segments that
+    confine the blood, the field v [nz][ny][nx][4] (vx, vy, vz, 0) on the
+    grid origin + spacing * index, frame interval dt and Runge-Kutta steps
+    per frame."""
+    name: str
+    p0: np.ndarray
+    seg: np.ndarray
+    segments: list
+    v: np.ndarray
+    origin: tuple
+    spacing: tuple
+    dt: float
+    n_sub: int
+    n_frames: int
+
+    @property
+    def S(self) -> int:
+        return self.p0.shape[1]
+
+
+def field_c2(seed: int = 2, n_frames: int = 200, n_scat: int = 100_000, spacing: float = 25e-6,
+             n_sub: int = 4, omega: float = 0.05) -> FieldWorkload:
+    """The C2 medium (90k tissue + 10k blood in its three arcs) moving with a
+    gridded steady field over the x-z plane: inside each lumen the Poiseuille
+    speed vmax (1 - rho^2 / R^2) along the arc, elsewhere a slow rigid
+    rotation (omega rad/s about y through (0, 0, 11 mm)).  Grid x in
+    [-7.6, 7.6] mm, z in [0.4, 21.6] mm at `spacing` (609 x 849 samples at
+    25 um), one sample in y; 200 frames at 1 kHz, 4 RK4 steps per frame.
+    Scatterers are listed in spatially coherent order (tissue by 0.2 mm
+    rows, blood along its vessel)."""
+    w = config2(seed=seed, n_frames=n_frames, n_scat=n_scat)
+    nx = int(round(15.2e-3 / spacing)) + 1
+    nz = int(round(21.2e-3 / spacing)) + 1
+    origin = (-7.6e-3, 0.0, 0.4e-3)
+    x = origin[0] + spacing * np.arange(nx)
+    z = origin[2] + spacing * np.arange(nz)
+    Z, X = np.meshgrid(z, x, indexing="ij")
+    c = (0.0, 0.0, 11e-3)
+    v = np.zeros((nz, 1, nx, 4), np.float64)
+    # rigid rotation about +y: v = omega y_hat x (P - c) = omega (dz, 0, -dx)
+    v[:, 0, :, 0] = omega * (Z - c[2])
+    v[:, 0, :, 2] = -omega * (X - c[0])
+    for sg in w.segments:
+        a1, a2 = np.array(sg.a1), np.array(sg.a2)
+        wx, wz = X - sg.p0[0], Z - sg.p0[2]
+        u1 = wx * a1[0] + wz * a1[2]
+        u2 = wx * a2[0] + wz * a2[2]
+        r = np.hypot(u1, u2)
+        phi = np.arctan2(u2, u1)
+        rho2 = (r - sg.arc_radius) ** 2
+        inside = (rho2 < sg.radius ** 2) & (phi >= 0.0) & (phi <= sg.phi1)
+        speed = sg.vmax * (1.0 - rho2 / sg.radius ** 2)
+        tx = -np.sin(phi) * a1[0] + np.cos(phi) * a2[0]
+        tz = -np.sin(phi) * a1[2] + np.cos(phi) * a2[2]
+        v[:, 0, :, 0] = np.where(inside, speed * tx, v[:, 0, :, 0])
+        v[:, 0, :, 2] = np.where(inside, speed * tz, v[:, 0, :, 2])
+    # blood starts at its flow coordinates' position
+    p0 = w.p0.astype(np.float64).copy()
+    for s in np.nonzero(w.seg >= 0)[0]:
+        sg = w.segments[w.seg[s]]
+        q, x1, x2 = (float(t) for t in w.flow[:, s])
+        rr = sg.arc_radius + x1
+        p0[:, s] = (np.array(sg.p0) + rr * (math.cos(q) * np.array(sg.a1) + math.sin(q) * np.array(sg.a2))
+                    + x2 * np.array(sg.a3))
+    # list the scatterers in spatially coherent order, as a voxelised
+    # phantom would: tissue in raster order of 0.2 mm rows, blood along each
+    # vessel (neighbouring scatterers share field samples)
+    nt = int((w.seg < 0).sum())
+    ot = np.lexsort((p0[0, :nt], np.floor(p0[2, :nt] / 0.2e-3)))
+    ob = nt + np.lexsort((w.flow[0, nt:], w.seg[nt:]))
+    order = np.concatenate([ot, ob])
+    p0 = np.ascontiguousarray(p0[:, order])
+    seg = np.ascontiguousarray(w.seg[order])
+    return FieldWorkload(f"C2 medium in a gridded steady field ({nx} x 1 x {nz} samples at "
+                         f"{spacing * 1e6:.0f} um), {w.S} scat, {n_frames} frames, RK4 x {n_sub} per frame",
+                         np.ascontiguousarray(p0, np.float32), seg, w.segments, np.ascontiguousarray(v, np.float32), origin,
+                         (spacing, 1.0, spacing), 1.0 / w.prf, n_sub, n_frames)
+
+
 def vessel_tree(rng, root_p0, root_dir, depth=6, r_root=300e-6, r_min=20e-6, v_root=40e-3,
                 len_scale=10.0, box=None):
     """Seeded random binary tree of straight segments.  Daughter radii obey
