@@ -702,6 +702,109 @@ def run_field(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------ display and quality (Sec. 5.2-5.3) --
+def run_post(args, rank, world, local):
+    """B-mode and uPDI display of the C2 ensemble, MIPs of a 128^3 volume
+    and the quality metrics of the uPDI image against the blood-only
+    ground truth."""
+    import copy
+    import torch
+    from paper_2509_05464_gb300 import fq
+    from paper_2509_05464_gb300 import workload as W
+    from paper_2509_05464_gb300.pipeline import Pipeline
+
+    torch.cuda.set_device(local)
+    fq.lib()
+    w = W.config2(seed=2 + rank, n_frames=args.frames)
+    pl = Pipeline(w)
+    pl.upload()
+    pl.step()
+    pd = pl.pd.clone()
+    iq = pl.iq
+    wb = copy.deepcopy(w)
+    wb.amp = wb.amp.copy()
+    wb.amp[wb.seg < 0] = 0.0
+    pb = Pipeline(wb, keep_iq_f=False)
+    pb.upload()
+    pb.step()
+    b = pb.iq.double()
+    pd_gt = ((b[..., 0] ** 2 + b[..., 1] ** 2).mean(dim=1)).float()
+    del pb
+    torch.cuda.empty_cache()
+    H, Wd = w.grid.nz, w.grid.nx
+    rng = np.random.default_rng(7)
+    vol = torch.from_numpy(rng.lognormal(0.0, 1.5, (128, 128, 128)).astype(np.float32)).cuda()
+    ws = fq.post_workspace(H, Wd)
+    bm = torch.empty(w.P, dtype=torch.float32, device="cuda")
+    disp = torch.empty_like(bm)
+    disp_gt = torch.empty_like(bm)
+    mips = [torch.empty(s, dtype=torch.float32, device="cuda") for s in ((128, 128),) * 3]
+    q = torch.empty(3, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fq.fq_bmode(iq, 0, 75.0, out=bm, ws=ws)
+        fq.fq_log_compress(pd, 60.0, power=True, out=disp, ws=ws)
+        fq.fq_log_compress(pd_gt, 60.0, power=True, out=disp_gt, ws=ws)
+        for a in range(3):
+            fq.fq_mip(vol, a, out=mips[a])
+        fq.fq_image_quality(disp.view(H, Wd), disp_gt.view(H, Wd), out=q, ws=ws)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clk = ClockSampler(local)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for a, bb in ev:
+        flush.zero_()
+        a.record(stream)
+        step()
+        bb.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in ev) / args.steps)
+    # bytes each step reads and writes (algorithmic): B-mode reads one frame
+    # of S (8 B per pixel, strided) twice (max, compress) and writes 4 B;
+    # each display reads 4 B twice and writes 4 B; the MIPs read the volume
+    # three times and write three planes; the metrics read both images twice
+    P, V = w.P, 128 ** 3
+    nbytes = P * (8 * 2 + 4) + 2 * P * (4 * 2 + 4) + 3 * (V * 4) + 3 * 128 * 128 * 4 + 2 * P * 4 * 2
+    pixels = sum_over_ranks(float(3 * P + V))
+    if rank != 0:
+        return
+    qh = q.cpu().numpy()
+    # parity: the metrics against the oracle on the same display images
+    from oracle import post as opost
+    dh, gh = disp.cpu().numpy().reshape(H, Wd), disp_gt.cpu().numpy().reshape(H, Wd)
+    want = (opost.mse(dh, gh), opost.psnr(dh, gh), opost.ssim(dh, gh))
+    pk, src = peaks()
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    ach = nbytes / (ms * 1e-3) / 1e9
+    line = {
+        "metric": "display + quality pixels/s (B-mode, uPDI 60 dB, 3 MIPs of 128^3, MSE/PSNR/SSIM)",
+        "value": pixels / (ms * 1e-3), "unit": "pixels/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"C2 ensemble ({H} x {Wd} px, {w.n_frames} frames): B-mode of frame 0 (75 dB), "
+                               f"uPDI display (60 dB) of the SVD PD and the blood-only PD, their MSE/PSNR/SSIM; "
+                               f"MIPs along x, y, z of a 128^3 lognormal volume",
+                   "l2": "256 MiB buffer rewritten between timed steps, outside the timed events"},
+        "quality_vs_blood_only": {"mse": float(qh[0]), "psnr_db": float(qh[1]), "ssim": float(qh[2]),
+                                  "oracle": {"mse": want[0], "psnr_db": want[1], "ssim": want[2]}},
+        "roofline": {"bound": "hbm", "kernel": "all display / quality kernels of the step", "achieved": ach,
+                     "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                     "peak_source": f"hbm_gbs of {src} peaks",
+                     "work": f"{nbytes / 1e6:.1f} MB algorithmic per step (11 launches: launch-bound at these sizes)"},
+        "cpu_baseline": None,
+        "e2e": None,
+        "gpu_launches": 11 * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def b_arena_gb(ms, args):
     from paper_2509_05464_gb300 import fq
     b = fq.Batch(ms, plan_only=True, max_arena_bytes=args.arena_gb << 30)
@@ -722,9 +825,10 @@ def main():
     ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
-    ap.add_argument("--workload", choices=["c2", "c4", "c5", "field"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c4", "c5", "field", "post"], default="c2",
                     help="c2: one 200-frame 2D ensemble (default); c4: the 64-ensemble uneven batch; "
-                         "c5: the learned clutter filter; field: advection in a gridded velocity field")
+                         "c5: the learned clutter filter; field: advection in a gridded velocity field; "
+                         "post: display compression, MIPs and image quality")
     ap.add_argument("--cnn-ensembles", type=int, default=64, help="c5: simulated training + held-out ensembles")
     ap.add_argument("--cnn-train-steps", type=int, default=1500, help="c5: timed training steps")
     ap.add_argument("--cnn-infer-frames", type=int, default=200, help="c5: frames of the inference ensemble")
@@ -746,6 +850,8 @@ def main():
         run_cnn(args, rank, world, local)
     elif args.workload == "field":
         run_field(args, rank, world, local)
+    elif args.workload == "post":
+        run_post(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     import torch.distributed as dist

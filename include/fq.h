@@ -214,6 +214,56 @@ fq_status fq_advect_field(const float *p0, const int32_t *seg_id, int64_t S, con
                           int32_t first_frame, int32_t n_frames, float *pos_out, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* display and image quality (Sec. 5.2, 5.3, 6.1)                       */
+/* ------------------------------------------------------------------ */
+
+/* Workspace for fq_log_compress / fq_bmode (any H, W) and
+ * fq_image_quality (images of H x W pixels). */
+fq_status fq_post_workspace_size(int32_t H, int32_t W, size_t *bytes);
+
+/* Logarithmic compression and dynamic-range display (Sec. 5.2):
+ *   out[i] = clamp((g log10(in[i] / max_j in[j]) + dr_db) / dr_db, 0, 1),
+ * g = 10 for powers (power Doppler, power != 0), 20 for amplitudes;
+ * in[i] <= 0 gives 0, an all-zero image all 0.  The paper shows B-mode over
+ * 75 dB and uPDI over 60 dB (Sec. 6.1).
+ *   in, out   device float [n]
+ *   workspace device, 256-byte aligned, fq_post_workspace_size bytes
+ * Errors: FQ_ERR_INVALID_ARG (null pointer, n < 0, dr_db <= 0),
+ * FQ_ERR_ALIGN. */
+fq_status fq_log_compress(const float *in, int64_t n, int32_t power, double dr_db, float *out,
+                          void *workspace, void *stream);
+
+/* B-mode of one frame of a Casorati matrix (Sec. 5.2): the envelope
+ * |S[p, frame]| compressed as above with g = 20.
+ *   iq   device [P][F][2] (re, im) in dtype FQ_F32 or FQ_BF16
+ *   out  device float [P]
+ * Errors: FQ_ERR_INVALID_ARG (frame outside [0, F), ...), FQ_ERR_UNSUPPORTED
+ * (dtype), FQ_ERR_ALIGN. */
+fq_status fq_bmode(const void *iq, int32_t dtype, int64_t P, int32_t F, int32_t frame, double dr_db,
+                   float *out, void *workspace, void *stream);
+
+/* Maximum-intensity projection of a volume (Sec. 6.1, Fig. 9d):
+ *   vol device float [nz][ny][nx]; axis 0 (x) -> out [nz][ny],
+ *   axis 1 (y) -> out [nz][nx], axis 2 (z) -> out [ny][nx].
+ * Errors: FQ_ERR_INVALID_ARG (size < 1, axis outside {0, 1, 2}, null). */
+fq_status fq_mip(const float *vol, int32_t nx, int32_t ny, int32_t nz, int32_t axis, float *out,
+                 void *stream);
+
+/* Image quality of x against the reference y (Sec. 5.3: MSE, PSNR, SSIM),
+ * both device float [H][W] with data range L:
+ *   out[0] = MSE = mean (x - y)^2, out[1] = PSNR = 10 log10(L^2 / MSE),
+ *   out[2] = SSIM = mean over the (H - 10)(W - 10) valid positions of
+ *   ((2 mx my + C1)(2 sxy + C2)) / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)),
+ *   weighted statistics of an 11 x 11 Gaussian window (sigma 1.5, weights
+ *   sum 1), C1 = (0.01 L)^2, C2 = (0.03 L)^2 (Wang et al. 2004).
+ *   out device double [3]; sums are per-block FP64 partials added in block
+ *   order (deterministic).
+ * Errors: FQ_ERR_SHAPE (H or W < 11), FQ_ERR_INVALID_ARG (L <= 0, null),
+ * FQ_ERR_WORKSPACE, FQ_ERR_ALIGN. */
+fq_status fq_image_quality(const float *x, const float *y, int32_t H, int32_t W, double L, double *out,
+                           void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* a2: vessel membership and depth binning                              */
 /* ------------------------------------------------------------------ */
 

@@ -119,6 +119,11 @@ def lib():
         sig = {
             "fq_advect_scatterers": [_P, _P, _P, _I64, C.POINTER(Flow), C.POINTER(Motion), _D, _D, _I32, _P, _P],
             "fq_advect_field": [_P, _P, _I64, C.POINTER(Flow), C.POINTER(VField), _P, _D, _I32, _I32, _I32, _P, _P],
+            "fq_post_workspace_size": [_I32, _I32, C.POINTER(_SZ)],
+            "fq_log_compress": [_P, _I64, _I32, _D, _P, _P, _P],
+            "fq_bmode": [_P, _I32, _I64, _I32, _I32, _D, _P, _P, _P],
+            "fq_mip": [_P, _I32, _I32, _I32, _I32, _P, _P],
+            "fq_image_quality": [_P, _P, _I32, _I32, _D, _P, _P, _SZ, _P],
             "fq_classify_scatterers": [_P, _P, _I64, C.POINTER(Flow), _P, _P, _P, _P],
             "fq_bin_workspace_size": [_I64, _I32, C.POINTER(_SZ)],
             "fq_bin_scatterers": [_P, _I64, _D, _D, _I32, _P, _P, _P, _SZ, _P],
@@ -301,6 +306,57 @@ def fq_advect_field(p0, seg_id, segments, origin, spacing, v, dt, n_sub, n_frame
                                  C.byref(g), _ptr(v), float(dt), int(n_sub), int(first_frame), int(n_frames),
                                  _ptr(pos_out), _stream(stream)))
     return pos_out
+
+
+# ------------------------------------------------ display and image quality --
+def post_workspace(H=0, W=0, device="cuda"):
+    n = _SZ(0)
+    _check(lib().fq_post_workspace_size(int(H), int(W), C.byref(n)))
+    return workspace(n.value, device)
+
+
+def fq_log_compress(x, dr_db, power=False, out=None, ws=None, stream=None):
+    """clip((g log10(x / max x) + dr) / dr, 0, 1), g = 10 (power) or 20"""
+    if out is None:
+        out = torch.empty_like(x, dtype=torch.float32)
+    if ws is None:
+        ws = post_workspace(device=x.device)
+    _check(lib().fq_log_compress(_ptr(x), x.numel(), int(bool(power)), float(dr_db), _ptr(out), _ptr(ws),
+                                 _stream(stream)))
+    return out
+
+
+def fq_bmode(iq, frame, dr_db=75.0, out=None, ws=None, stream=None):
+    """B-mode [P] of one frame of the Casorati matrix iq [P][F][2]"""
+    P, F = iq.shape[0], iq.shape[1]
+    if out is None:
+        out = torch.empty(P, dtype=torch.float32, device=iq.device)
+    if ws is None:
+        ws = post_workspace(device=iq.device)
+    _check(lib().fq_bmode(_ptr(iq), _dt(iq), P, F, int(frame), float(dr_db), _ptr(out), _ptr(ws), _stream(stream)))
+    return out
+
+
+def fq_mip(vol, axis, out=None, stream=None):
+    """maximum-intensity projection of vol [nz][ny][nx] along axis 0 (x), 1 (y) or 2 (z)"""
+    nz, ny, nx = vol.shape
+    shape = {0: (nz, ny), 1: (nz, nx), 2: (ny, nx)}[axis]
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=vol.device)
+    _check(lib().fq_mip(_ptr(vol), nx, ny, nz, int(axis), _ptr(out), _stream(stream)))
+    return out
+
+
+def fq_image_quality(x, y, L=1.0, out=None, ws=None, stream=None):
+    """(MSE, PSNR, SSIM) of x against y ([H][W] float32) as a device double [3]"""
+    H, W = x.shape
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=x.device)
+    if ws is None:
+        ws = post_workspace(H, W, x.device)
+    _check(lib().fq_image_quality(_ptr(x), _ptr(y), H, W, float(L), _ptr(out), _ptr(ws), ws.numel(),
+                                  _stream(stream)))
+    return out
 
 
 def fq_classify_scatterers(pos, seg_id, segments, amp_in, vessel_out=None, amp_out=None, want_amp=True,
