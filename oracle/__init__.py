@@ -68,6 +68,8 @@ def lib():
             L.or_advect.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _p]
             L.or_classify.argtypes = [_i64, _p, _p, _i, _p, _p, _p, _p]
             L.or_bin.argtypes = [_i64, _p, _d, _d, _i, _p, _p]
+            L.or_das_matrix.argtypes = [_i, _i, _d, _d, _d, _d, _d, _i, _i, _p, _p,
+                                        _i, _i, _i, _d, _d, _d, _d, _d, _d, _d, _p, _p, _p]
             L.or_advect_field.argtypes = [_i64, _p, _p, _i, _p, _p, _i, _i, _i, _p, _p, _d, _i, _i, _i, _p]
             _lib = L
     return _lib
@@ -139,6 +141,25 @@ def das(probe, tilt_x, tilt_y, iq_ch, grid):
                  grid.nx, grid.ny, grid.nz, grid.x0, grid.y0, grid.z0, grid.dx, grid.dy, grid.dz,
                  grid.fnumber, _ptr(out))
     return out[..., 0] + 1j * out[..., 1]
+
+
+def das_matrix(probe, tilt_x, tilt_y, grid):
+    """The explicit DAS matrices (Alg. 3): row_ptr int64 [A P + 1], col int32
+    [nnz], val complex128 [nnz]; row a * P + p."""
+    tilt_x = np.ascontiguousarray(tilt_x, np.float64)
+    tilt_y = np.ascontiguousarray(tilt_y, np.float64)
+    A = tilt_x.shape[0]
+    P = grid.nx * grid.ny * grid.nz
+    args = (probe.nx, probe.ny, probe.pitch_x, probe.pitch_y, probe.f0, probe.fs, probe.c, probe.n_samples,
+            A, _ptr(tilt_x), _ptr(tilt_y), grid.nx, grid.ny, grid.nz, grid.x0, grid.y0, grid.z0, grid.dx,
+            grid.dy, grid.dz, grid.fnumber)
+    row_ptr = np.zeros(A * P + 1, np.int64)
+    lib().or_das_matrix(*args, _ptr(row_ptr), None, None)
+    nnz = int(row_ptr[-1])
+    col = np.zeros(max(nnz, 1), np.int32)
+    val = np.zeros((max(nnz, 1), 2), np.float64)
+    lib().or_das_matrix(*args, _ptr(row_ptr), _ptr(col), _ptr(val))
+    return row_ptr, col[:nnz], val[:nnz, 0] + 1j * val[:nnz, 1]
 
 
 def beamform(probe, tilt_x, tilt_y, rf, grid):

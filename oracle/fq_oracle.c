@@ -737,3 +737,77 @@ void or_advect_field(int64_t S, const float *p0, const int32_t *seg, int n_seg, 
         }
     }
 }
+
+/* ------------------------------------------------------------------------
+ * The explicit DAS matrices of Sec. 2.4.1 / Alg. 3 (steps 2.2-2.3): one
+ * sparse matrix per transmit, rows = pixels, columns = (element, sample)
+ * of the channel IQ, built once and applied to every frame.  Row (a, p)
+ * holds, for every element m in the receive aperture with a valid sample
+ * pair, the two linear-interpolation weights times the phase rotation of
+ * or_das:  (m Ns + i, (1 - phi) e^{i 2 pi f0 tau}), (m Ns + i + 1, phi e^{...}).
+ * Rows are numbered a * P + p.  With col == NULL only row_ptr is written
+ * (row_ptr[r + 1] - row_ptr[r] = entries of row r, row_ptr[0] = 0); then
+ * col [nnz], val [nnz][2] are filled in the same order.
+ * Pinned by: applying the matrices (scipy.sparse) equals or_das.
+ * ---------------------------------------------------------------------- */
+void or_das_matrix(int nx, int ny, double px, double py, double f0, double fs, double c, int ns,
+                   int n_ang, const double *tilt_x, const double *tilt_y,
+                   int gx, int gy, int gz, double x0, double y0, double z0, double dx, double dy,
+                   double dz, double fnum, int64_t *row_ptr, int32_t *col, double *val)
+{
+    const int M = nx * ny;
+    const int64_t P = (int64_t)gx * gy * gz;
+    const int64_t R = (int64_t)n_ang * P;
+    double *ux = (double *)malloc(sizeof(double) * 4 * n_ang);
+    for (int a = 0; a < n_ang; ++a) {
+        double u[3];
+        pw_dir(tilt_x[a], tilt_y[a], u);
+        ux[4 * a] = u[0]; ux[4 * a + 1] = u[1]; ux[4 * a + 2] = u[2];
+        ux[4 * a + 3] = pw_origin(u, nx, ny, px, py);
+    }
+    int64_t *cnt = col ? NULL : (int64_t *)malloc(sizeof(int64_t) * (R > 0 ? R : 1));
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t row = 0; row < R; ++row) {
+        int a = (int)(row / P);
+        int64_t p = row % P;
+        int ix = (int)(p % gx);
+        int iz = (int)((p / gx) % gz);
+        int iy = (int)(p / ((int64_t)gx * gz));
+        double x = x0 + ix * dx, y = y0 + iy * dy, z = z0 + iz * dz;
+        const double *u = ux + 4 * a;
+        double path_tx = u[0] * x + u[1] * y + u[2] * z - u[3];
+        int64_t k = col ? row_ptr[row] : 0;
+        for (int m = 0; m < M; ++m) {
+            double ex, ey;
+            element_pos(m, nx, ny, px, py, &ex, &ey);
+            float half = (float)z * (float)(0.5 / fnum);
+            if (fabsf((float)x - (float)ex) > half) continue;
+            if (ny > 1 && fabsf((float)y - (float)ey) > half) continue;
+            double r = sqrt((x - ex) * (x - ex) + (y - ey) * (y - ey) + z * z);
+            double tau = (path_tx + r) / c;
+            double uu = tau * fs;
+            double fi = floor(uu);
+            double phi = uu - fi;
+            int64_t i = (int64_t)fi;
+            if (i < 0 || i + 1 >= ns) continue;
+            if (col) {
+                double ph = 2.0 * OR_PI * f0 * tau;
+                double cr = cos(ph), ci = sin(ph);
+                col[k] = (int32_t)(m * ns + i);
+                val[2 * k] = (1.0 - phi) * cr;
+                val[2 * k + 1] = (1.0 - phi) * ci;
+                col[k + 1] = (int32_t)(m * ns + i + 1);
+                val[2 * k + 2] = phi * cr;
+                val[2 * k + 3] = phi * ci;
+            }
+            k += 2;
+        }
+        if (!col) cnt[row] = k;
+    }
+    if (!col) {
+        row_ptr[0] = 0;
+        for (int64_t r = 0; r < R; ++r) row_ptr[r + 1] = row_ptr[r] + cnt[r];
+        free(cnt);
+    }
+    free(ux);
+}

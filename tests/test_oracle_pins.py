@@ -275,8 +275,9 @@ def test_das_psf_peak_at_scatterer():
 def test_das_equals_explicit_das_matrix():
     """The paper precomputes one sparse DAS matrix per transmit and applies
     it to the vectorised IQ of every frame (Sec. 2.4.1, Alg. 3 steps
-    2.2.1-2.4).  Building that matrix explicitly on a tiny grid and applying
-    it with a library sparse product reproduces the direct DAS sum."""
+    2.2.1-2.4).  The oracle's explicit matrices, applied with a library
+    sparse product, reproduce its direct DAS sum; and a hand-built row
+    from the definition matches the stored one."""
     import scipy.sparse as sp
     th = np.radians([-4.0, 3.0])
     p = probe(nx=12, pitch=0.3e-3, f0=5e6, fs=20e6, ns=512)
@@ -286,35 +287,35 @@ def test_das_equals_explicit_das_matrix():
     g = W.Grid(7, 1, 9, -1.5e-3, 0.0, 4e-3, 0.5e-3, 0.0, 0.7e-3, 1.0)
     iq_ch = oracle.rf2iq(p, rf)
     direct = oracle.das(p, th, np.zeros(2), iq_ch, g)
-    ex = elem_x(p)
-    xs = g.x0 + np.arange(g.nx) * g.dx
-    zs = g.z0 + np.arange(g.nz) * g.dz
-    out = np.zeros((g.nz * g.nx, F), complex)
-    for a, t in enumerate(th):
-        rows, cols, vals = [], [], []
-        origin = np.min(ex * math.sin(t))
-        for iz, z in enumerate(zs):
-            for ix, x in enumerate(xs):
-                pidx = iz * g.nx + ix
-                for m in range(p.nx):
-                    half = np.float32(z) * np.float32(0.5 / g.fnumber)
-                    if abs(np.float32(x) - np.float32(ex[m])) > half:
-                        continue
-                    tau = (x * math.sin(t) + z * math.cos(t) - origin + math.hypot(x - ex[m], z)) / p.c
-                    u = tau * p.fs
-                    i = math.floor(u)
-                    ph = u - i
-                    if i < 0 or i + 1 >= p.n_samples:
-                        continue
-                    rot = np.exp(2j * math.pi * p.f0 * tau)
-                    rows += [pidx, pidx]
-                    cols += [m * p.n_samples + i, m * p.n_samples + i + 1]
-                    vals += [(1 - ph) * rot, ph * rot]
-        Mtx = sp.csr_matrix((vals, (rows, cols)), shape=(g.nz * g.nx, p.nx * p.n_samples))
+    row_ptr, col, val = oracle.das_matrix(p, th, np.zeros(2), g)
+    P = g.nz * g.nx
+    out = np.zeros((P, F), complex)
+    for a in range(2):
+        lo, hi = row_ptr[a * P], row_ptr[(a + 1) * P]
+        Mtx = sp.csr_matrix((val[lo:hi], col[lo:hi], row_ptr[a * P:(a + 1) * P + 1] - lo),
+                            shape=(P, p.nx * p.n_samples))
         for f in range(F):
             out[:, f] += Mtx @ iq_ch[f, a].reshape(-1)
     out /= 2
     assert np.abs(out - direct).max() <= 1e-12 * np.abs(direct).max()
+    # one row by hand: transmit 1, pixel (ix 3, iz 6)
+    ex = elem_x(p)
+    t, x, z = th[1], g.x0 + 3 * g.dx, g.z0 + 6 * g.dz
+    origin = np.min(ex * math.sin(t))
+    want = {}
+    for m in range(p.nx):
+        if abs(np.float32(x) - np.float32(ex[m])) > np.float32(z) * np.float32(0.5 / g.fnumber):
+            continue
+        tau = (x * math.sin(t) + z * math.cos(t) - origin + math.hypot(x - ex[m], z)) / p.c
+        i = math.floor(tau * p.fs)
+        ph = tau * p.fs - i
+        rot = np.exp(2j * math.pi * p.f0 * tau)
+        want[m * p.n_samples + i] = (1 - ph) * rot
+        want[m * p.n_samples + i + 1] = ph * rot
+    r = 1 * P + 6 * g.nx + 3
+    got = dict(zip(col[row_ptr[r]:row_ptr[r + 1]], val[row_ptr[r]:row_ptr[r + 1]]))
+    assert got.keys() == want.keys()
+    assert max(abs(got[k] - want[k]) for k in want) <= 1e-12
 
 
 def test_das_mirror_symmetry():
