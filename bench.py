@@ -805,6 +805,89 @@ def run_post(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------ the paper's DAS-matrix route (Alg. 3) --
+def run_das_matrix(args, rank, world, local):
+    """Explicit per-transmit DAS matrices (build once, apply to all frames)
+    against the fused DAS kernel on the C2 ensemble."""
+    import torch
+    from paper_2509_05464_gb300 import fq
+    from paper_2509_05464_gb300 import workload as W
+    from paper_2509_05464_gb300.pipeline import Pipeline
+
+    torch.cuda.set_device(local)
+    fq.lib()
+    w = W.config2(seed=2 + rank, n_frames=args.frames)
+    pl = Pipeline(w)
+    pl.upload()
+    pl.classify()
+    pl.advect()
+    pl.simulate()
+    F, A, M = w.n_frames, w.A, w.M
+    ch = fq.fq_rf2iq(w.probe, A * M, F, pl.rf)
+    del pl
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    t0 = time.perf_counter()
+    dm = fq.DasMatrix(w.probe, w.tilt_x, w.tilt_y, w.grid)
+    torch.cuda.synchronize()
+    build_wall_ms = (time.perf_counter() - t0) * 1e3
+    build_ms = timed(lambda: fq.DasMatrix(w.probe, w.tilt_x, w.tilt_y, w.grid), 2)
+    iq_m = torch.empty((w.P, F, 2), dtype=torch.float32, device="cuda")
+    iq_f = torch.empty_like(iq_m)
+    clk = ClockSampler(local)
+    clk.start()
+    apply_ms = max_over_ranks(timed(lambda: dm.apply(ch, F, iq=iq_m), args.steps))
+    fused_ms = max_over_ranks(timed(lambda: fq.fq_das(w.probe, w.tilt_x, w.tilt_y, ch, F, w.grid, iq=iq_f),
+                                    args.steps))
+    clocks = clk.stop()
+    diff = float(torch.linalg.norm(iq_m - iq_f) / torch.linalg.norm(iq_f))
+    va = float(F * A * w.P)
+    total = sum_over_ranks(va)
+    if rank != 0:
+        return
+    pk, src = peaks()
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    # algorithmic bytes of one apply: the matrices once (12 B per entry +
+    # offsets) and the channel IQ once (the rows the entries touch), the
+    # Casorati written
+    nbytes = dm.nbytes + ch.numel() * 4 + w.P * F * 8
+    ach = nbytes / (apply_ms * 1e-3) / 1e9
+    line = {
+        "metric": "DAS voxel-angle/s, explicit DAS matrices (Alg. 3) vs the fused kernel",
+        "value": total / (apply_ms * 1e-3), "unit": "voxel-angles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": 1, "ms_per_step": apply_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{w.name}: {A} transmits x {M} elements x {w.P} pixels x {F} frames",
+                   "nnz": dm.nnz, "matrix_bytes": dm.nbytes, "build_ms": build_ms,
+                   "first_build_wall_ms": build_wall_ms,
+                   "l2": "inputs (channel IQ 2.2 GB) far above L2"},
+        "fused_das": {"ms": fused_ms, "value": total / (fused_ms * 1e-3),
+                      "matrix_vs_fused_rel_l2": diff,
+                      "break_even_ensembles": build_ms / max(fused_ms - apply_ms, 1e-9) if fused_ms > apply_ms
+                      else None},
+        "roofline": {"bound": "hbm", "kernel": "apply_kernel", "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak, "traffic": None, "peak_source": f"hbm_gbs of {src} peaks",
+                     "work": f"{nbytes / 1e9:.2f} GB algorithmic per apply (matrices + channel IQ + Casorati)"},
+        "cpu_baseline": None,
+        "e2e": None,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def b_arena_gb(ms, args):
     from paper_2509_05464_gb300 import fq
     b = fq.Batch(ms, plan_only=True, max_arena_bytes=args.arena_gb << 30)
@@ -825,10 +908,11 @@ def main():
     ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
-    ap.add_argument("--workload", choices=["c2", "c4", "c5", "field", "post"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c4", "c5", "field", "post", "dasmatrix"], default="c2",
                     help="c2: one 200-frame 2D ensemble (default); c4: the 64-ensemble uneven batch; "
                          "c5: the learned clutter filter; field: advection in a gridded velocity field; "
-                         "post: display compression, MIPs and image quality")
+                         "post: display compression, MIPs and image quality; dasmatrix: the paper's "
+                         "explicit DAS matrices against the fused DAS")
     ap.add_argument("--cnn-ensembles", type=int, default=64, help="c5: simulated training + held-out ensembles")
     ap.add_argument("--cnn-train-steps", type=int, default=1500, help="c5: timed training steps")
     ap.add_argument("--cnn-infer-frames", type=int, default=200, help="c5: frames of the inference ensemble")
@@ -852,6 +936,8 @@ def main():
         run_field(args, rank, world, local)
     elif args.workload == "post":
         run_post(args, rank, world, local)
+    elif args.workload == "dasmatrix":
+        run_das_matrix(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     import torch.distributed as dist

@@ -214,6 +214,38 @@ fq_status fq_advect_field(const float *p0, const int32_t *seg_id, int64_t S, con
                           int32_t first_frame, int32_t n_frames, float *pos_out, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* the paper's explicit DAS-matrix route (Sec. 2.4.1, Alg. 3)           */
+/* ------------------------------------------------------------------ */
+
+/* One sparse matrix per transmit, rows = pixels, columns = (element,
+ * sample) of the channel IQ, computed once and applied to every frame (Alg.
+ * 3 steps 2.2-2.4).  Row a * P + p holds, for every element m in the
+ * receive aperture with a valid sample pair (i, i + 1) at u = tau fs
+ * (i = floor u, phi = u - i), the entries
+ *   (m Ns + i, (1 - phi) e^{i 2 pi f0 tau}) and (m Ns + i + 1, phi e^{i 2 pi f0 tau}),
+ * with the same aperture decision and delays as fq_das, so that
+ *   iq[p][f] = (1/A) sum_a sum_k val[k] iq_ch[a][col[k]][f]   equals fq_das.
+ * Build in two calls: fq_das_matrix_count writes the exclusive row offsets
+ * row_ptr (device int64 [A P + 1]; nnz = row_ptr[A P], read it back to
+ * size col and val), fq_das_matrix_fill writes col (device int32 [nnz]) and
+ * val (device float [nnz][2], 8-byte aligned).  The library keeps fq_das as
+ * its hot path (it recomputes delays instead of storing the matrices:
+ * 627 MB for the 2D compounded workload, ~470 GB for the 3D one).
+ * Errors: FQ_ERR_INVALID_ARG, FQ_ERR_SHAPE (sizes, elements x samples
+ * beyond int32), FQ_ERR_WORKSPACE, FQ_ERR_ALIGN. */
+fq_status fq_das_matrix_workspace_size(const fq_tx *tx, const fq_grid *grid, size_t *bytes);
+fq_status fq_das_matrix_count(const fq_probe *probe, const fq_tx *tx, const fq_grid *grid,
+                              int64_t *row_ptr, void *workspace, size_t workspace_bytes, void *stream);
+fq_status fq_das_matrix_fill(const fq_probe *probe, const fq_tx *tx, const fq_grid *grid,
+                             const int64_t *row_ptr, int32_t *col, float *val, void *stream);
+/* Applies the matrices to the channel IQ of fq_rf2iq ([A M][Ns][F_pad][2],
+ * F_pad = fq_frame_pad(n_frames)): iq device [P][n_frames][2].  At most 416
+ * frames (FQ_ERR_UNSUPPORTED beyond). */
+fq_status fq_das_matrix_apply(const int64_t *row_ptr, const int32_t *col, const float *val, int32_t A,
+                              int64_t P, int32_t M, int32_t ns, const void *iq_ch, int32_t ch_dtype,
+                              int32_t n_frames, int32_t iq_dtype, void *iq, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* display and image quality (Sec. 5.2, 5.3, 6.1)                       */
 /* ------------------------------------------------------------------ */
 

@@ -120,6 +120,10 @@ def lib():
             "fq_advect_scatterers": [_P, _P, _P, _I64, C.POINTER(Flow), C.POINTER(Motion), _D, _D, _I32, _P, _P],
             "fq_advect_field": [_P, _P, _I64, C.POINTER(Flow), C.POINTER(VField), _P, _D, _I32, _I32, _I32, _P, _P],
             "fq_post_workspace_size": [_I32, _I32, C.POINTER(_SZ)],
+            "fq_das_matrix_workspace_size": [C.POINTER(Tx), C.POINTER(Grid), C.POINTER(_SZ)],
+            "fq_das_matrix_count": [C.POINTER(Probe), C.POINTER(Tx), C.POINTER(Grid), _P, _P, _SZ, _P],
+            "fq_das_matrix_fill": [C.POINTER(Probe), C.POINTER(Tx), C.POINTER(Grid), _P, _P, _P, _P],
+            "fq_das_matrix_apply": [_P, _P, _P, _I32, _I64, _I32, _I32, _P, _I32, _I32, _I32, _P, _P],
             "fq_log_compress": [_P, _I64, _I32, _D, _P, _P, _P],
             "fq_bmode": [_P, _I32, _I64, _I32, _I32, _D, _P, _P, _P],
             "fq_mip": [_P, _I32, _I32, _I32, _I32, _P, _P],
@@ -306,6 +310,40 @@ def fq_advect_field(p0, seg_id, segments, origin, spacing, v, dt, n_sub, n_frame
                                  C.byref(g), _ptr(v), float(dt), int(n_sub), int(first_frame), int(n_frames),
                                  _ptr(pos_out), _stream(stream)))
     return pos_out
+
+
+# ------------------------------------------- the paper's DAS-matrix route --
+class DasMatrix:
+    """The explicit per-transmit DAS matrices (Alg. 3) on the device: row_ptr
+    int64 [A P + 1], col int32 [nnz], val float32 [nnz][2]."""
+
+    def __init__(self, probe, tilt_x, tilt_y, grid, device="cuda", stream=None):
+        pr, th, gr = make_probe(probe), _TxHolder(tilt_x, tilt_y), make_grid(grid)
+        self.A, self.P = len(tilt_x), grid.nx * grid.ny * grid.nz
+        self.M, self.ns = probe.nx * probe.ny, probe.n_samples
+        n = _SZ(0)
+        _check(lib().fq_das_matrix_workspace_size(C.byref(th.st), C.byref(gr), C.byref(n)))
+        ws = workspace(n.value, device)
+        self.row_ptr = torch.empty(self.A * self.P + 1, dtype=torch.int64, device=device)
+        _check(lib().fq_das_matrix_count(C.byref(pr), C.byref(th.st), C.byref(gr), _ptr(self.row_ptr), _ptr(ws),
+                                         ws.numel(), _stream(stream)))
+        self.nnz = int(self.row_ptr[-1].item())
+        self.col = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=device)
+        self.val = torch.empty((max(self.nnz, 1), 2), dtype=torch.float32, device=device)
+        _check(lib().fq_das_matrix_fill(C.byref(pr), C.byref(th.st), C.byref(gr), _ptr(self.row_ptr),
+                                        _ptr(self.col), _ptr(self.val), _stream(stream)))
+
+    @property
+    def nbytes(self):
+        return self.row_ptr.numel() * 8 + self.nnz * 12
+
+    def apply(self, iq_ch, n_frames, iq_dtype=torch.float32, iq=None, stream=None):
+        if iq is None:
+            iq = torch.empty((self.P, n_frames, 2), dtype=iq_dtype, device=iq_ch.device)
+        _check(lib().fq_das_matrix_apply(_ptr(self.row_ptr), _ptr(self.col), _ptr(self.val), self.A, self.P,
+                                         self.M, self.ns, _ptr(iq_ch), _dt(iq_ch), int(n_frames), _dt(iq),
+                                         _ptr(iq), _stream(stream)))
+        return iq
 
 
 # ------------------------------------------------ display and image quality --
