@@ -68,6 +68,8 @@ def lib():
             L.or_advect.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _p]
             L.or_classify.argtypes = [_i64, _p, _p, _i, _p, _p, _p, _p]
             L.or_bin.argtypes = [_i64, _p, _d, _d, _i, _p, _p]
+            L.or_simulate_rf_freq.argtypes = [_i, _i, _d, _d, _d, _d, _d, _d, _d, _d, _i, _i, _i, _i, _p, _p,
+                                              _i64, _p, _p, _p]
             L.or_das_matrix.argtypes = [_i, _i, _d, _d, _d, _d, _d, _i, _i, _p, _p,
                                         _i, _i, _i, _d, _d, _d, _d, _d, _d, _d, _p, _p, _p]
             L.or_advect_field.argtypes = [_i64, _p, _p, _i, _p, _p, _i, _i, _i, _p, _p, _d, _i, _i, _i, _p]
@@ -107,6 +109,24 @@ def simulate_rf(probe, tilt_x, tilt_y, pos, amp, rf=None, accumulate=False):
                          probe.width_y, probe.f0, probe.fs, probe.c, probe.alpha_db_cm_mhz,
                          probe.n_cycles, probe.n_samples, A, _ptr(tilt_x), _ptr(tilt_y),
                          amp.shape[0], _ptr(pos), _ptr(amp), int(bool(accumulate)), _ptr(rf))
+    return rf
+
+
+def simulate_rf_freq(probe, tilt_x, tilt_y, pos, amp, n_fft=None):
+    """Frequency-domain RF [A][M][Ns] float64 (attenuation and directivity
+    per frequency); n_fft defaults to 2 Ns."""
+    tilt_x = np.ascontiguousarray(tilt_x, np.float64)
+    tilt_y = np.ascontiguousarray(tilt_y, np.float64)
+    pos = np.ascontiguousarray(pos, np.float32)
+    amp = np.ascontiguousarray(amp, np.float32)
+    A = tilt_x.shape[0]
+    M = probe.nx * probe.ny
+    N = 2 * probe.n_samples if n_fft is None else int(n_fft)
+    rf = np.zeros((A, M, probe.n_samples), np.float64)
+    lib().or_simulate_rf_freq(probe.nx, probe.ny, probe.pitch_x, probe.pitch_y, probe.width_x, probe.width_y,
+                              probe.f0, probe.fs, probe.c, probe.alpha_db_cm_mhz, probe.n_cycles,
+                              probe.n_samples, N, A, _ptr(tilt_x), _ptr(tilt_y), amp.shape[0], _ptr(pos),
+                              _ptr(amp), _ptr(rf))
     return rf
 
 

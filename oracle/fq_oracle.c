@@ -811,3 +811,91 @@ void or_das_matrix(int nx, int ny, double px, double py, double f0, double fs, d
     }
     free(ux);
 }
+
+/* ------------------------------------------------------------------------
+ * RF synthesis in the frequency domain (Eq. 1 evaluated per frequency, as
+ * Alg. 2 step 2.6 does: wavenumber, attenuation and directivity at each
+ * frequency, spectral weights, then the inverse transform), with the same
+ * geometry as or_simulate_rf (ideal plane-wave transmit, receive at the
+ * element centre):
+ *
+ *   RF_{a,m}[n] = df sum_s sum_{j=0}^{N/2-1} w_j Re{ S(f_j) A_j e^{i 2 pi f_j (n/fs - tau)} }
+ *   A_j = R_s D_j exp(-alpha f_j c tau) / |r_s - e_m|,  D_j = sinc(k_j b sin theta),
+ *   f_j = j df, df = fs / N, k_j = 2 pi f_j / c, w_0 = 1, w_j = 2 (j >= 1),
+ *   S(f) = Fourier transform of the pulse p(t) of or_simulate_rf:
+ *     p = rect_T(t) [1/2 cos(2 pi f0 t) + 1/4 cos(2 pi (f0 + 1/T) t) + 1/4 cos(2 pi (f0 - 1/T) t)]
+ *     S(f) = T/2 sum_g c_g [sinc(pi (f - g) T) + sinc(pi (f + g) T)],
+ *     (g, c_g) = (f0, 1/2), (f0 + 1/T, 1/4), (f0 - 1/T, 1/4).
+ * The sum over frequencies represents the echo periodised with period
+ * N / fs (N = n_fft >= Ns; 2 Ns keeps every echo of the record inside one
+ * period) and band-limited to fs / 2.  The spectrum of each line is summed
+ * over scatterers first, then transformed by a direct inverse sum.
+ * rf: double [A][M][Ns].  Pinned by: the discrete spectrum of a single
+ * echo (numpy FFT of the output over one full period) equals
+ * N df S(f_j) A_j e^{-i 2 pi f_j tau} with S from numerical integration of
+ * p(t); superposition.
+ * ---------------------------------------------------------------------- */
+static double pulse_spectrum(double f, double f0, double T)
+{
+    const double g[3] = {f0, f0 + 1.0 / T, f0 - 1.0 / T}, c[3] = {0.5, 0.25, 0.25};
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k)
+        s += c[k] * (sinc_unnorm(OR_PI * (f - g[k]) * T) + sinc_unnorm(OR_PI * (f + g[k]) * T));
+    return 0.5 * T * s;
+}
+
+void or_simulate_rf_freq(int nx, int ny, double px, double py, double wx, double wy,
+                         double f0, double fs, double c, double alpha_db_cm_mhz, int n_cycles, int ns,
+                         int n_fft, int n_ang, const double *tilt_x, const double *tilt_y,
+                         int64_t S, const float *pos, const float *amp, double *rf)
+{
+    const int M = nx * ny;
+    const double T = (double)n_cycles / f0;
+    const double alpha_np = alpha_db_cm_mhz * 100.0 / (20.0 / log(10.0)); /* Np / (m MHz) */
+    const double df = fs / (double)n_fft;
+    const int J = n_fft / 2;
+    const float *X = pos, *Y = pos + S, *Z = pos + 2 * S;
+    double *Sw = (double *)malloc(sizeof(double) * J);
+    for (int j = 0; j < J; ++j) Sw[j] = pulse_spectrum(j * df, f0, T);
+
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int am = 0; am < n_ang * M; ++am) {
+        int a = am / M, m = am % M;
+        double u[3];
+        pw_dir(tilt_x[a], tilt_y[a], u);
+        double origin = pw_origin(u, nx, ny, px, py);
+        double ex, ey;
+        element_pos(m, nx, ny, px, py, &ex, &ey);
+        double *Pre = (double *)calloc(J, sizeof(double)), *Pim = (double *)calloc(J, sizeof(double));
+        for (int64_t s = 0; s < S; ++s) {
+            double x = X[s], y = Y[s], z = Z[s];
+            double dx = x - ex, dy = y - ey;
+            double r = sqrt(dx * dx + dy * dy + z * z);
+            if (r == 0.0) continue;
+            double tau = (u[0] * x + u[1] * y + u[2] * z - origin + r) / c;
+            for (int j = 0; j < J; ++j) {
+                double f = j * df, k = 2.0 * OR_PI * f / c;
+                double D = sinc_unnorm(k * 0.5 * wx * dx / r);
+                if (ny > 1) D *= sinc_unnorm(k * 0.5 * wy * dy / r);
+                double A = (double)amp[s] * D * exp(-alpha_np * f * 1e-6 * c * tau) / r;
+                double ph = -2.0 * OR_PI * f * tau;
+                Pre[j] += A * cos(ph);
+                Pim[j] += A * sin(ph);
+            }
+        }
+        double *line = rf + (int64_t)am * ns;
+        for (int n = 0; n < ns; ++n) {
+            double t = n / fs, acc = 0.0;
+            for (int j = 0; j < J; ++j) {
+                double w = j == 0 ? 1.0 : 2.0;
+                double ph = 2.0 * OR_PI * j * df * t;
+                /* Re{S_j P_j e^{i ph}} with S_j real */
+                acc += w * Sw[j] * (Pre[j] * cos(ph) - Pim[j] * sin(ph));
+            }
+            line[n] = df * acc;
+        }
+        free(Pre);
+        free(Pim);
+    }
+    free(Sw);
+}
