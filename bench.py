@@ -888,6 +888,93 @@ def run_das_matrix(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------ frequency-domain RF (Alg. 2) --
+def run_rf_freq(args, rank, world, local):
+    """Eq. 1 per frequency (the paper's frequency loop) against the
+    time-domain kernel on the C2 ensemble, a few frames."""
+    import torch
+    from paper_2509_05464_gb300 import fq
+    from paper_2509_05464_gb300 import workload as W
+    from paper_2509_05464_gb300.pipeline import Pipeline
+
+    torch.cuda.set_device(local)
+    fq.lib()
+    F = args.frames if args.frames != 200 else 2
+    w = W.config2(seed=2 + rank, n_frames=F)
+    pl = Pipeline(w)
+    pl.upload()
+    pl.classify()
+    pl.advect()
+    pop = pl.pops[0]
+    pos, amp = pop.pos, pop.amp_eff
+    stream = torch.cuda.current_stream()
+    rf_t = torch.empty((F, w.A, w.M, w.Ns), dtype=torch.float32, device="cuda")
+    rf_f = torch.empty_like(rf_t)
+    n_fft = 2 * w.Ns
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    clk = ClockSampler(local)
+    clk.start()
+    freq_ms = max_over_ranks(timed(lambda: fq.fq_simulate_rf_freq(w.probe, w.tilt_x, w.tilt_y, pos, amp, F,
+                                                                  n_fft=n_fft, rf=rf_f), args.steps))
+    time_ms = max_over_ranks(timed(lambda: fq.fq_simulate_rf(w.probe, w.tilt_x, w.tilt_y, pos, amp, F, rf=rf_t),
+                                   args.steps))
+    clocks = clk.stop()
+    cs = float(F * w.A * w.M * w.Ns)
+    total = sum_over_ranks(cs)
+    if rank != 0:
+        return
+    # parity against the oracle on a sample: the first 2000 scatterers of
+    # frame 0, transmit 2, every element (the oracle's cost is S x M x bins)
+    import oracle
+    ns_s = 2000
+    p1 = np.ascontiguousarray(pos[0, :, :ns_s].cpu().numpy())
+    a1 = np.ascontiguousarray(amp[:ns_s].cpu().numpy())
+    sub = fq.fq_simulate_rf_freq(w.probe, w.tilt_x[2:3], w.tilt_y[2:3],
+                                 torch.from_numpy(p1[None]).cuda(), torch.from_numpy(a1).cuda(), 1, n_fft=n_fft)
+    t0 = time.perf_counter()
+    want = oracle.simulate_rf_freq(w.probe, w.tilt_x[2:3], w.tilt_y[2:3], p1, a1, n_fft=n_fft)
+    oracle_s = time.perf_counter() - t0
+    got = sub[0].cpu().numpy()
+    err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+    td_vs_fd = float(torch.linalg.norm(rf_f - rf_t) / torch.linalg.norm(rf_t))
+    pk, src = peaks()
+    peak = fp32_alu_peak_tflops(float(pk.get("sm_max_mhz", 2070.0)))
+    terms = F * w.A * w.M * w.S * (n_fft // 2)
+    ach = terms * 22 / (freq_ms * 1e-3) / 1e12
+    line = {
+        "metric": "channel-samples/s, RF synthesis in the frequency domain (Eq. 1 per frequency) vs time domain",
+        "value": total / (freq_ms * 1e-3), "unit": "channel-samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": 1, "ms_per_step": freq_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{w.name} ({F} frames)", "n_fft": n_fft, "bins": n_fft // 2,
+                   "l2": "no flush: positions 2.4 MB per frame, spectra 42 MB per frame"},
+        "time_domain": {"ms": time_ms, "value": total / (time_ms * 1e-3), "freq_over_time": freq_ms / time_ms,
+                        "rel_l2_freq_vs_time": td_vs_fd},
+        "parity": {"sample": f"first {ns_s} scatterers of frame 0, transmit 2, every element",
+                   "rel_l2_vs_oracle": err, "oracle_s": oracle_s},
+        "roofline": {"bound": "alu", "kernel": "spectrum_kernel", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                     "frac": ach / peak, "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x max clock ({src})",
+                     "work": f"22 FLOP per (scatterer, element, transmit, frame, bin) term, {terms:.3e} terms"},
+        "cpu_baseline": None,
+        "e2e": None,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def b_arena_gb(ms, args):
     from paper_2509_05464_gb300 import fq
     b = fq.Batch(ms, plan_only=True, max_arena_bytes=args.arena_gb << 30)
@@ -908,11 +995,12 @@ def main():
     ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
-    ap.add_argument("--workload", choices=["c2", "c4", "c5", "field", "post", "dasmatrix"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c4", "c5", "field", "post", "dasmatrix", "rffreq"], default="c2",
                     help="c2: one 200-frame 2D ensemble (default); c4: the 64-ensemble uneven batch; "
                          "c5: the learned clutter filter; field: advection in a gridded velocity field; "
                          "post: display compression, MIPs and image quality; dasmatrix: the paper's "
-                         "explicit DAS matrices against the fused DAS")
+                         "explicit DAS matrices against the fused DAS; rffreq: RF synthesis in the frequency "
+                         "domain against the time-domain kernel (2 frames unless --frames)")
     ap.add_argument("--cnn-ensembles", type=int, default=64, help="c5: simulated training + held-out ensembles")
     ap.add_argument("--cnn-train-steps", type=int, default=1500, help="c5: timed training steps")
     ap.add_argument("--cnn-infer-frames", type=int, default=200, help="c5: frames of the inference ensemble")
@@ -938,6 +1026,8 @@ def main():
         run_post(args, rank, world, local)
     elif args.workload == "dasmatrix":
         run_das_matrix(args, rank, world, local)
+    elif args.workload == "rffreq":
+        run_rf_freq(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     import torch.distributed as dist

@@ -214,6 +214,36 @@ fq_status fq_advect_field(const float *p0, const int32_t *seg_id, int64_t S, con
                           int32_t first_frame, int32_t n_frames, float *pos_out, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* RF synthesis in the frequency domain (Eq. 1 per frequency, Alg. 2)   */
+/* ------------------------------------------------------------------ */
+
+/* Eq. 1 evaluated at each frequency of the transform grid (Alg. 2 step
+ * 2.6: wavenumber, attenuation and directivity per frequency, spectral
+ * weights, then the inverse transform), with the geometry of
+ * fq_simulate_rf (ideal plane-wave transmit, receive at the element
+ * centre):
+ *   RF[f][a][m][n] = df sum_s sum_{j < N/2} w_j Re{ S(f_j) A_j e^{i 2 pi f_j (n/fs - tau)} },
+ *   A_j = R_s D_j exp(-alpha f_j c tau) / |r_s - e_m|, D_j = sinc(k_j b sin theta)
+ *   (matrix arrays: the product of the x and y factors), f_j = j df,
+ *   df = fs / N, w_0 = 1, w_j = 2, S = Fourier transform of the pulse of
+ *   fq_probe, N = n_fft (a power of two, n_samples <= N <= 8192; 2
+ *   n_samples keeps every echo of the record inside one period of the
+ *   transform).  Compared with fq_simulate_rf it drops the narrowband
+ *   approximation (attenuation and directivity at f0) and adds the band
+ *   limit fs / 2.
+ *   pos device float [n_frames][3][S], amp device float [S],
+ *   rf device [n_frames][A][M][n_samples] in out_dtype (FQ_F32 or FQ_BF16),
+ *   workspace device, 256-byte aligned, fq_simulate_rf_freq_workspace_size
+ *   bytes (the spectra [n_frames][A][M][N/2] complex and the weights).
+ * Errors: FQ_ERR_INVALID_ARG, FQ_ERR_SHAPE (n_fft, sizes), FQ_ERR_UNSUPPORTED
+ * (out_dtype), FQ_ERR_WORKSPACE, FQ_ERR_ALIGN. */
+fq_status fq_simulate_rf_freq_workspace_size(const fq_probe *probe, const fq_tx *tx, int32_t n_frames,
+                                             int32_t n_fft, size_t *bytes);
+fq_status fq_simulate_rf_freq(const fq_probe *probe, const fq_tx *tx, const float *pos, const float *amp,
+                              int64_t S, int32_t n_frames, int32_t n_fft, int32_t out_dtype, void *rf,
+                              void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* the paper's explicit DAS-matrix route (Sec. 2.4.1, Alg. 3)           */
 /* ------------------------------------------------------------------ */
 

@@ -121,6 +121,9 @@ def lib():
             "fq_advect_field": [_P, _P, _I64, C.POINTER(Flow), C.POINTER(VField), _P, _D, _I32, _I32, _I32, _P, _P],
             "fq_post_workspace_size": [_I32, _I32, C.POINTER(_SZ)],
             "fq_das_matrix_workspace_size": [C.POINTER(Tx), C.POINTER(Grid), C.POINTER(_SZ)],
+            "fq_simulate_rf_freq_workspace_size": [C.POINTER(Probe), C.POINTER(Tx), _I32, _I32, C.POINTER(_SZ)],
+            "fq_simulate_rf_freq": [C.POINTER(Probe), C.POINTER(Tx), _P, _P, _I64, _I32, _I32, _I32, _P, _P, _SZ,
+                                    _P],
             "fq_das_matrix_count": [C.POINTER(Probe), C.POINTER(Tx), C.POINTER(Grid), _P, _P, _SZ, _P],
             "fq_das_matrix_fill": [C.POINTER(Probe), C.POINTER(Tx), C.POINTER(Grid), _P, _P, _P, _P],
             "fq_das_matrix_apply": [_P, _P, _P, _I32, _I64, _I32, _I32, _P, _I32, _I32, _I32, _P, _P],
@@ -310,6 +313,32 @@ def fq_advect_field(p0, seg_id, segments, origin, spacing, v, dt, n_sub, n_frame
                                  C.byref(g), _ptr(v), float(dt), int(n_sub), int(first_frame), int(n_frames),
                                  _ptr(pos_out), _stream(stream)))
     return pos_out
+
+
+# ------------------------------------------ frequency-domain RF synthesis --
+def fq_simulate_rf_freq(probe, tilt_x, tilt_y, pos, amp, n_frames, n_fft=None, out_dtype=torch.float32, rf=None,
+                        ws=None, stream=None):
+    """RF [n_frames][A][M][Ns] by Eq. 1 evaluated per frequency (n_fft
+    defaults to the power of two >= 2 Ns)."""
+    S = amp.shape[0]
+    A = len(tilt_x)
+    M = probe.nx * probe.ny
+    if n_fft is None:
+        n_fft = 1
+        while n_fft < 2 * probe.n_samples:
+            n_fft *= 2
+    if rf is None:
+        rf = torch.empty((n_frames, A, M, probe.n_samples), dtype=out_dtype, device=amp.device)
+    pr = make_probe(probe)
+    th = _TxHolder(tilt_x, tilt_y)
+    if ws is None:
+        n = _SZ(0)
+        _check(lib().fq_simulate_rf_freq_workspace_size(C.byref(pr), C.byref(th.st), int(n_frames), int(n_fft),
+                                                        C.byref(n)))
+        ws = workspace(n.value, amp.device)
+    _check(lib().fq_simulate_rf_freq(C.byref(pr), C.byref(th.st), _ptr(pos), _ptr(amp), S, int(n_frames), int(n_fft),
+                                     _dt(rf), _ptr(rf), _ptr(ws), ws.numel(), _stream(stream)))
+    return rf
 
 
 # ------------------------------------------- the paper's DAS-matrix route --
