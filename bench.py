@@ -975,6 +975,65 @@ def run_rf_freq(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------- tensor-core Gram at scale --
+def run_gram(args, rank, world, local):
+    """The Casorati Gram S^H S on the tensor cores (BF16 and TF32 operands,
+    FP32 accumulation) at the largest batched ensemble shape (96^3 voxels x
+    400 frames), where it is compute-bound, beside the FP32 CUDA-core Gram."""
+    import torch
+    from paper_2509_05464_gb300 import fq
+
+    torch.cuda.set_device(local)
+    fq.lib()
+    P, F = 96 ** 3, args.frames if args.frames != 200 else 400
+    g = torch.Generator(device="cuda").manual_seed(5 + rank)
+    S = torch.randn((P, F, 2), generator=g, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    clk = ClockSampler(local)
+    clk.start()
+    for name, mode in (("bf16", fq.FQ_GRAM_BF16), ("tf32", fq.FQ_GRAM_TF32), ("f32", fq.FQ_GRAM_F32)):
+        ws = fq.workspace(fq.fq_gram_workspace_size(P, F, mode))
+        G = torch.empty((F, F, 2), dtype=torch.float32, device="cuda")
+        for _ in range(max(args.warmup, 1)):
+            fq.fq_casorati_gram(S, mode, G=G, ws=ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            fq.fq_casorati_gram(S, mode, G=G, ws=ws)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = max_over_ranks(a.elapsed_time(b) / args.steps)
+        del ws, G
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    if rank != 0:
+        return
+    pk, src = peaks()
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    flop = 8.0 * P * F * F  # the complex Gram as defined; the kernels compute the upper tiles only
+    ach = {k: flop / (v * 1e-3) / 1e12 for k, v in out.items()}
+    line = {
+        "metric": "Casorati Gram TFLOP/s (8 P F^2) on tcgen05, BF16 operands",
+        "value": ach["bf16"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": out["bf16"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"Gram of a {P} x {F} complex Casorati matrix (96^3 voxels, {F} frames)",
+                   "ms": out, "tflops": ach,
+                   "l2": "input 2.8 GB FP32, far above L2"},
+        "roofline": {"bound": "tensor", "kernel": "gram_tc_kernel (with its transpose and reduce)",
+                     "achieved": ach["bf16"], "peak": peak, "unit": "TFLOP/s", "frac": ach["bf16"] / peak,
+                     "traffic": None, "peak_source": f"bf16_tflops of {src} peaks (cuBLAS burst)",
+                     "work": f"8 P F^2 = {flop:.3e} FLOP; the upper-triangular tiles execute about half plus the diagonal tiles"},
+        "cpu_baseline": None,
+        "e2e": None,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def b_arena_gb(ms, args):
     from paper_2509_05464_gb300 import fq
     b = fq.Batch(ms, plan_only=True, max_arena_bytes=args.arena_gb << 30)
@@ -995,12 +1054,13 @@ def main():
     ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
-    ap.add_argument("--workload", choices=["c2", "c4", "c5", "field", "post", "dasmatrix", "rffreq"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c4", "c5", "field", "post", "dasmatrix", "rffreq", "gram"], default="c2",
                     help="c2: one 200-frame 2D ensemble (default); c4: the 64-ensemble uneven batch; "
                          "c5: the learned clutter filter; field: advection in a gridded velocity field; "
                          "post: display compression, MIPs and image quality; dasmatrix: the paper's "
                          "explicit DAS matrices against the fused DAS; rffreq: RF synthesis in the frequency "
-                         "domain against the time-domain kernel (2 frames unless --frames)")
+                         "domain against the time-domain kernel (2 frames unless --frames); gram: the tensor-core "
+                         "Gram at 96^3 voxels x 400 frames")
     ap.add_argument("--cnn-ensembles", type=int, default=64, help="c5: simulated training + held-out ensembles")
     ap.add_argument("--cnn-train-steps", type=int, default=1500, help="c5: timed training steps")
     ap.add_argument("--cnn-infer-frames", type=int, default=200, help="c5: frames of the inference ensemble")
@@ -1028,6 +1088,8 @@ def main():
         run_das_matrix(args, rank, world, local)
     elif args.workload == "rffreq":
         run_rf_freq(args, rank, world, local)
+    elif args.workload == "gram":
+        run_gram(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     import torch.distributed as dist

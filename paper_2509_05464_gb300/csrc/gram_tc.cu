@@ -124,9 +124,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int chunk = blockIdx.x;
-    const int m0 = tiles.m0[blockIdx.y];
-    const int n0 = tiles.n0[blockIdx.y];
+    // consecutive CTAs share a pixel chunk (one per output tile), so the
+    // operand rows they stream are re-read from L2 rather than DRAM
+    const int chunk = blockIdx.y;
+    const int m0 = tiles.m0[blockIdx.x];
+    const int n0 = tiles.n0[blockIdx.x];
     const int kbeg = chunk * ksteps_per_chunk;
     const int kend = min(ksteps_total, kbeg + ksteps_per_chunk);
     const int nk = max(0, kend - kbeg);
@@ -261,7 +263,9 @@ TcPlan tc_plan(int64_t P, int F, int esz)
                 ++t.tiles.n;
             }
     t.ksteps = (int)(t.Pp / t.bk);
-    int want = (2 * 152 + t.tiles.n - 1) / t.tiles.n;
+    // about four waves of one CTA per SM: the tail of the last wave is a
+    // quarter of the run instead of half (one CTA per SM fits its ring)
+    int want = (4 * 152 + t.tiles.n - 1) / t.tiles.n;
     want = want < 1 ? 1 : (want > t.ksteps ? t.ksteps : want);
     t.per_chunk = (t.ksteps + want - 1) / want;
     t.chunks = (t.ksteps + t.per_chunk - 1) / t.per_chunk;
@@ -282,7 +286,7 @@ fq_status launch_tc(const TcPlan &t, const CUtensorMap &map, float *part, int *s
         cudaFuncSetAttribute(gram_tc_kernel<ESZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
         "tensor-core Gram: smem attribute");
     if (s) return s;
-    dim3 grid((unsigned)t.chunks, (unsigned)t.tiles.n);
+    dim3 grid((unsigned)t.tiles.n, (unsigned)t.chunks);
     gram_tc_kernel<ESZ><<<grid, TC_THREADS, smem, st>>>(map, t.tiles, t.ksteps, t.per_chunk, t.Mp, t.Np, part,
                                                         status, g_skip_loads);
     return fqi::launch_check("tensor-core Gram: mma");
