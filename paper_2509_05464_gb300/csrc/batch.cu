@@ -67,6 +67,7 @@ struct fq_batch {
     int rf_minb = 3, das_threads = 128;
     bool rf_quad = true;  // every member's rows hold whole element quads
     int ns_max = 0, J_max = 0, M_max = 0;
+    size_t rf_smem = 0;  // dynamic shared memory of the RF stage kernel
     size_t off_counters = 0, off_status = 0, off_ens = 0, off_params = 0, off_queues = 0, off_scratch = 0, total = 0;
     std::vector<unsigned char> params;  // host image of the parameter blocks
     const void *uploaded = nullptr;     // arena holding the current tables
@@ -116,8 +117,13 @@ void item_grids(fq_batch *b, EnsHost &h)
     const int sc = cdiv(h.d.S, kItemScat);
     h.gx[ST_CLASSIFY] = sc; h.gy[ST_CLASSIFY] = 1; h.items[ST_CLASSIFY] = sc;
     h.gx[ST_ADVECT] = sc; h.gy[ST_ADVECT] = h.F; h.items[ST_ADVECT] = sc * h.F;
-    h.gx[ST_RF] = cdiv(h.M, b->rf_quad ? 4 : kRfItemElems); h.gy[ST_RF] = h.A;
-    h.items[ST_RF] = h.gx[ST_RF] * h.A * h.F;
+    int rf_groups = h.A, rf_group = 1;
+    if (b->rf_quad) {
+        size_t smem = 0;
+        fqi::rf_quad_layout(b->params.data() + h.par_rf, &rf_groups, &rf_group, &smem);
+    }
+    h.gx[ST_RF] = cdiv(h.M, b->rf_quad ? 4 : kRfItemElems); h.gy[ST_RF] = rf_groups;
+    h.items[ST_RF] = h.gx[ST_RF] * rf_groups * h.F;
     h.gx[ST_RF2IQ] = cdiv(h.ns, kIqTile); h.gy[ST_RF2IQ] = h.L;
     h.items[ST_RF2IQ] = h.gx[ST_RF2IQ] * h.L * (h.Fp / kFrameChunkB);
     h.gx[ST_DAS] = cdiv(h.P, b->das_threads / kDasThreadsPerPixel); h.gy[ST_DAS] = h.Fp / kFrameChunkB;
@@ -131,7 +137,7 @@ void item_grids(fq_batch *b, EnsHost &h)
     // relative cost of one item: what its inner loop runs over
     for (int s = 0; s < NS; ++s) h.cost[s] = 1.0;
     h.cost[ST_CLASSIFY] = 1.0 + h.d.flow.n_seg;
-    h.cost[ST_RF] = (double)h.d.S;
+    h.cost[ST_RF] = (double)h.d.S * rf_group;
     h.cost[ST_RF2IQ] = 2.0 * h.J + 1.0;
     h.cost[ST_DAS] = (double)h.A * h.M;
     h.cost[ST_GRAM] = (double)h.chunk_len;
@@ -274,7 +280,7 @@ fq_status launch_stage(fq_batch *b, char *arena, int w, int s, cudaStream_t st)
     switch (s) {
     case fqb::ST_CLASSIFY: return fqi::batched_classify(ens, q, q.total, st);
     case fqb::ST_ADVECT: return fqi::batched_advect(ens, q, q.total, st);
-    case fqb::ST_RF: return fqi::batched_rf(ens, q, q.total, b->rf_dtype, b->ns_max, b->rf_minb, b->rf_quad, st);
+    case fqb::ST_RF: return fqi::batched_rf(ens, q, q.total, b->rf_dtype, b->rf_smem, b->rf_minb, b->rf_quad, st);
     case fqb::ST_RF2IQ: return fqi::batched_rf2iq(ens, q, q.total, b->rf_dtype, b->ch_dtype, b->J_max, st);
     case fqb::ST_DAS:
         return fqi::batched_das(ens, q, q.total, b->ch_dtype, b->iq_dtype, b->M_max, b->das_threads, st);
@@ -408,7 +414,16 @@ fq_status fq_batch_plan(const fq_ensemble_desc *ens, int32_t n, int32_t rf_dtype
         b->J_max = std::max(b->J_max, h.J);
         b->M_max = std::max(b->M_max, h.M);
     }
-    for (int i = 0; i < n; ++i) b->rf_quad = b->rf_quad && fqi::use_rf_quad(b->e[i].d.probe.nx);
+    for (int i = 0; i < n; ++i)
+        b->rf_quad = b->rf_quad && fqi::use_rf_quad(b->e[i].d.probe.nx) && fqi::rf_quad_ok(b->params.data() + b->e[i].par_rf);
+    for (int i = 0; i < n; ++i) {
+        size_t smem = 4 * sizeof(int) * (size_t)b->e[i].ns;  // paired kernel: hi and lo of 2 elements
+        if (b->rf_quad) {
+            int groups = 0, group = 0;
+            fqi::rf_quad_layout(b->params.data() + b->e[i].par_rf, &groups, &group, &smem);
+        }
+        b->rf_smem = std::max(b->rf_smem, smem);
+    }
     b->rf_minb = b->rf_quad ? 2 : 3;
     // waves: greedy in the given order under the budget
     for (int i = 0; i < n; ++i) {

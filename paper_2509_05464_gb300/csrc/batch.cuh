@@ -149,7 +149,7 @@ namespace fqi {
 // `ens` and the queue arrays are device pointers into the batch arena.
 fq_status batched_classify(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, cudaStream_t st);
 fq_status batched_advect(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, cudaStream_t st);
-fq_status batched_rf(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, int ns_max,
+fq_status batched_rf(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, size_t smem,
                      int minb, bool quad, cudaStream_t st);
 fq_status batched_rf2iq(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, int ch_dtype,
                         int J_max, cudaStream_t st);
@@ -171,6 +171,9 @@ size_t rf_params_bytes();
 fq_status build_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, void *out);
 int rf_ntap_ok(const void *rf_params);  // the packed-pair pulse kernel applies
 bool use_rf_quad(int nx);               // the quad-element RF kernel applies to this probe
+bool rf_quad_ok(const void *rf_params);  // ... and to these sizes (records fit in shared memory)
+// quad RF kernel: angle groups per (frame, quad), angles per group, shared-memory bytes per CTA
+void rf_quad_layout(const void *rf_params, int *n_groups, int *group, size_t *smem);
 size_t iq_params_bytes();
 fq_status build_iq_params(const fq_probe *probe, int L, int F, void *out, int *J);
 size_t das_params_bytes();

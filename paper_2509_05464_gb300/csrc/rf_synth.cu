@@ -33,6 +33,10 @@ namespace {
 using fqi::ff;
 
 constexpr int kMaxTaps = 64;  // pulse taps per (scatterer, element) pair the kernel supports
+// quad kernel: shared-memory records per CTA (angles x 4 elements x Ns int32)
+// up to this size, and two CTAs per SM while they fit twice
+constexpr size_t kQuadRecordBudget = 96 * 1024;
+constexpr size_t kQuadTwoPerSm = 110 * 1024;
 
 struct RfParams {
     fqi::ProbeFF pr;
@@ -54,6 +58,12 @@ struct RfParams {
     // floor(frac + half_w) = floor(half_w) + (frac >= theta2)
     float theta, theta2, jmin_f;
     float att_l2;       // -att log2(e): exp(-att path) = 2^(att_l2 path)
+    // quad kernel: transmit angles per CTA (ag), angle groups (n_ag), the
+    // half-width of the tap-bound window (ceil(half_w) + 1 samples) and the
+    // factor by which an echo's taps may exceed |amp| |D| / r (attenuation
+    // gain before t = 0, binary32 rounding)
+    int ag, n_ag, win;
+    float bound_margin;
     fqi::AngleFF ang[FQ_MAX_ANGLES];
 };
 
@@ -628,53 +638,134 @@ __global__ void __launch_bounds__(NT, MINB) rf_pair_batched_kernel(const fqb::En
 }
 
 // ---------------------------------------------------------------------------
-// Quad-element kernel: 4 consecutive elements of one array row per CTA.
-// The float-float delay is evaluated for the quad's first element only; the
-// other three follow from the exact identity
+// Quad-element kernel: 4 consecutive elements of one array row and a group of
+// transmit angles per CTA.
+//
+// Geometry.  The float-float delay is evaluated for the quad's first element
+// only; the other three follow from the exact identity
 //     r_e - r_0 = (x_0 - x_e) (2 x - x_0 - x_e) / (r_e + r_0)
 // evaluated in binary32: |r_e - r_0| is at most 3 pitches (a dozen samples),
-// so its rounding error stays near 1e-6 sample.  Amplitudes and pulse taps
-// are per element; the taps of elements (0, 1) and (2, 3) run as packed
-// f32x2 pairs into the same fixed-point records as the paired kernel.
+// so its rounding error stays near 1e-6 sample.  The receive side (the four
+// distances, directivities and 1/r) does not depend on the transmit, so it is
+// evaluated once per scatterer and reused by every angle of the group; the
+// transmit path, delays, attenuation and taps are per angle.  The taps of
+// elements (0, 1) and (2, 3) run as packed f32x2 pairs.
+//
+// Accumulation: one int32 per sample, one shared-memory atomic per tap.
+// Integer sums are exact modulo 2^32 in any order, so a record is exact (and
+// bit-reproducible) as long as its final values fit in int32.  Each record
+// gets the finest quantum q for which that is guaranteed:
+//   pass 0  b_max = largest |amp| / (distance to the quad) sets the integer
+//           units of pass 1;
+//   pass 1  every (scatterer, element, angle) adds an upper bound of its taps,
+//           |amp| D_bound / r in those units (D_bound >= |directivity|), at the
+//           sample of its
+//           binary32 delay rounded to the nearest sample, which is within
+//           0.51 sample of the exact delay, so a window of
+//           2 floor(half_w + 0.52) + 1 samples around a sample bounds the sum
+//           of |taps| that land on it;
+//   scale   1/q = the largest value that keeps (window maximum x margin +
+//           largest |static base|) / q + half a quantum per scatterer (tap
+//           rounding) below 2^31.
+// The margin covers the attenuation gain of echoes that start just before
+// t = 0 and binary32 rounding of the amplitudes.
 // ---------------------------------------------------------------------------
-template <int NT, typename OutT>
-__device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, int f, const float *__restrict__ pos,
-                                             const float *__restrict__ amp, const float *__restrict__ rf_base,
-                                             OutT *__restrict__ rf, int *tile, float *s_red)
+constexpr int kQuadNT = 256;
+constexpr float kInvRCap = 131072.0f;               // 1/r <= 2^17 per metre (r >= 7.6 um)
+constexpr float kTapMax = 2147483520.0f;            // largest binary32 below 2^31: |tap| bound in quanta
+constexpr float kUnitMax = 2097152.0f;              // 2^21: largest pass-1 bound in units
+constexpr float kTwo31 = 2147483648.0f;
+
+struct QuadShared {
+    float red[kQuadNT / 32];
+    float invq[4 * FQ_MAX_ANGLES];     // 1 / q per record (angle in group, element)
+    float q[4 * FQ_MAX_ANGLES];
+    unsigned wmax[4 * FQ_MAX_ANGLES];  // window maximum of the pass-1 bounds (units)
+    unsigned bmax[4 * FQ_MAX_ANGLES];  // largest |static base| (float bits, >= 0)
+    float4 angK[FQ_MAX_ANGLES + 1];    // pass 1: fs / c, then per angle (u, -origin) fs / c
+};
+
+// an upper bound of |sin(u) / u| for |u| <= 5 (the fitted directivity's
+// range): 1 - u^2/6 + u^4/120 bounds sin(u)/u from above for every u (the
+// alternating series), is at least 0.16 on [pi, 5] where |sin(u)/u| < 0.22,
+// and is exact to O(u^6) where the directivity is near 1
+__device__ __forceinline__ float sinc_bound(float u)
 {
+    const float t = u * u;
+    return fmaf(fmaf(t, 1.0f / 120.0f, -1.0f / 6.0f), t, 1.0f);
+}
+
+__device__ __forceinline__ float block_max(float v, float *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = red[0];
+    for (int w = 1; w < kQuadNT / 32; ++w) v = fmaxf(v, red[w]);
+    __syncthreads();
+    return v;
+}
+
+// a non-negative float below 2^22 rounded to the nearest integer
+__device__ __forceinline__ int rint_small(float v) { return __float_as_int(v + kMagic) - kMagicBits; }
+
+// one tap of two records: V = (V0, V1) in quanta (|V| < 2^31) rounded to the
+// nearest integers and added
+__device__ __forceinline__ void add_tap2(int *r0, int *r1, int k0, int k1, f2 V)
+{
+    float a, b;
+    fqi::f2_split(V, a, b);
+    atomicAdd(r0 + k0, __float2int_rn(a));
+    atomicAdd(r1 + k1, __float2int_rn(b));
+}
+
+__device__ __forceinline__ void add_tap2_if(int *r0, int *r1, int k0, int k1, f2 V, bool on0, bool on1)
+{
+    float a, b;
+    fqi::f2_split(V, a, b);
+    if (on0) atomicAdd(r0 + k0, __float2int_rn(a));
+    if (on1) atomicAdd(r1 + k1, __float2int_rn(b));
+}
+
+// the two-cycle tap from the Hann-phase cosine C with nhA = -A/2:
+// ((A C + A) C - A/2) C - A/2
+__device__ __forceinline__ f2 tap2n(f2 A, f2 nhA, f2 C)
+{
+    return fqi::f2_fma(fqi::f2_fma(fqi::f2_fma(A, C, A), C, nhA), C, nhA);
+}
+
+// (C_j, C_{j+1}, -C_j, -C_{j+1}) -> (C_{j+1}, C_{j+2}, -C_{j+1}, -C_{j+2})
+__device__ __forceinline__ void cheb_step(f2 &C0, f2 &C1, f2 &N0, f2 &N1, f2 T, f2 NT)
+{
+    const f2 C2 = fqi::f2_fma(T, C1, N0);
+    const f2 N2 = fqi::f2_fma(NT, C1, C0);
+    C0 = C1;
+    C1 = C2;
+    N0 = N1;
+    N1 = N2;
+}
+
+// One tile: elements 4 bx .. 4 bx + 3, angles ag * p.ag .. (of the group),
+// frame f.  `tile` is the dynamic shared memory (p.ag * 4 * Ns ints).
+template <int NT, typename OutT>
+__device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, int f, const float *__restrict__ pos,
+                                             const float *__restrict__ amp, const float *__restrict__ rf_base,
+                                             OutT *__restrict__ rf, int *tile, QuadShared &sh)
+{
+    static_assert(NT == kQuadNT, "block reductions assume kQuadNT threads");
     constexpr int E = 4;
     const int ns = p.pr.ns;
     const int M = p.pr.M;
     const int m0 = bx * E;
     const int ne = min(E, M - m0);
     const int64_t S = p.S;
-    int *hi0 = tile, *hi1 = tile + ns, *hi2 = tile + 2 * ns, *hi3 = tile + 3 * ns;
-    int *lo0 = tile + 4 * ns, *lo1 = tile + 5 * ns, *lo2 = tile + 6 * ns, *lo3 = tile + 7 * ns;
-
-    float amax = 0.0f;
-    for (int64_t s = threadIdx.x; s < S; s += NT) amax = fmaxf(amax, fabsf(amp[s]));
-    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = amax;
-    __syncthreads();
-    amax = 0.0f;
-    for (int w = 0; w < NT / 32; ++w) amax = fmaxf(amax, s_red[w]);
-    int gexp = 0;
-    if (amax > 0.0f) frexpf(amax, &gexp);
-    const float g = ldexpf(1.0f, -gexp);
-    const float to_fix = g * kFixScale;
-
-    for (int i = threadIdx.x; i < E * ns; i += NT) {
-        int e = i / ns, k = i - e * ns;
-        float v = 0.0f;
-        if (rf_base && e < ne) v = rf_base[((int64_t)a * M + m0 + e) * ns + k];
-        float V = fminf(fmaxf(v * to_fix, -kTapClamp), kTapClamp);
-        const float ht = fmaf(V, 1.0f / 65536.0f, kMagic);
-        const float hb = ht - kMagic;
-        const float lt = fmaf(-hb, 65536.0f, V) + kMagic;
-        tile[e * ns + k] = __float_as_int(ht) - kMagicBits;
-        tile[(4 + e) * ns + k] = __float_as_int(lt) - kMagicBits;
-    }
-    __syncthreads();
+    const int a0 = ag * p.ag;
+    const int na = min(p.ag, p.A - a0);
+    const int nrec = na * E;
+    const bool matrix = p.pr.ny > 1;
+    const float *X = pos + (int64_t)f * 3 * S;
+    const float *Y = X + S;
+    const float *Z = Y + S;
 
     // element abscissae: the first as a float pair, the others as binary32
     // offsets x_0 - x_e and sums x_0 + x_e (all in one row: nx % 4 == 0)
@@ -694,28 +785,165 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, i
     bool live_e[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) live_e[e] = e < ne;
+    const float eyf = ey.hi + ey.lo;
+    // the quad's abscissae span [xlo, xhi] (dead lanes repeat the last element)
+    const float xlo = fminf(fminf(exf[0], exf[1]), fminf(exf[2], exf[3]));
+    const float xhi = fmaxf(fmaxf(exf[0], exf[1]), fmaxf(exf[2], exf[3]));
 
-    const fqi::AngleFF an = p.ang[a];
+    // the previous item of a persistent CTA may still read the tile
+    __syncthreads();
+    for (int i = threadIdx.x; i < nrec * (ns + 2 * p.win); i += NT) tile[i] = 0;
+    if ((int)threadIdx.x < nrec) {
+        sh.wmax[threadIdx.x] = 0u;
+        sh.bmax[threadIdx.x] = 0u;
+    }
+    if ((int)threadIdx.x <= na) {  // [0].w = fs / c; [1 + al] = the transmit direction and origin x fs / c
+        const float K = p.pr.fs_over_c.hi;
+        float4 g = make_float4(0.0f, 0.0f, 0.0f, K);
+        if (threadIdx.x > 0) {
+            const fqi::AngleFF &an = p.ang[a0 + threadIdx.x - 1];
+            g = make_float4(an.ux.hi * K, an.uy.hi * K, an.uz.hi * K, -an.origin.hi * K);
+        }
+        sh.angK[threadIdx.x] = g;
+    }
+    __syncthreads();
+
+    // ---- pass 0: the largest possible tap, and the largest |base| per record
+    float bm = 0.0f;
+    for (int64_t s = threadIdx.x; s < S; s += NT) {
+        const float R = amp[s];
+        if (R == 0.0f) continue;
+        const float x = X[s], y = Y[s], z = Z[s];
+        const float dx = x - fminf(fmaxf(x, xlo), xhi);  // distance to the quad's segment <= to any element
+        const float dy = y - eyf;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, z * z));
+        bm = fmaxf(bm, fabsf(R) * fminf(rsqrtf(r2), kInvRCap));
+    }
+    if (rf_base) {
+        for (int rec = 0; rec < nrec; ++rec) {
+            const int al = rec >> 2, e = rec & 3;
+            if (e >= ne) continue;
+            const float *b = rf_base + ((int64_t)(a0 + al) * M + m0 + e) * ns;
+            float v = 0.0f;
+            for (int k = threadIdx.x; k < ns; k += NT) v = fmaxf(v, fabsf(b[k]));
+            for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if ((threadIdx.x & 31) == 0) atomicMax(&sh.bmax[rec], __float_as_uint(v));
+        }
+    }
+    bm = block_max(bm, sh.red);
+
+    // ---- pass 1: tap bounds at the nearest samples of their binary32 delays,
+    // in records of ns + 2 win bins (bin i holds sample i - win)
+    const int win = p.win;
+    const int wstride = ns + 2 * win;
+    const float margin = p.bound_margin;
+    // units: the sum over every scatterer stays below 2^30 and one bound below 2^21
+    const float unit = fminf(1073741824.0f / ((float)S * bm * 1.0078125f), kUnitMax / (bm * 1.0078125f));
+    unsigned *bins = reinterpret_cast<unsigned *>(tile);
+    if (bm > 0.0f) {
+        float nR = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;  // one scatterer ahead
+        if ((int64_t)threadIdx.x < S) {
+            nR = amp[threadIdx.x];
+            nx = X[threadIdx.x];
+            ny = Y[threadIdx.x];
+            nz = Z[threadIdx.x];
+        }
+        for (int64_t s = threadIdx.x; s < S; s += NT) {
+            const float R = nR, x = nx, y = ny, z = nz;
+            if (s + NT < S) {
+                nR = amp[s + NT];
+                nx = X[s + NT];
+                ny = Y[s + NT];
+                nz = Z[s + NT];
+            }
+            if (R == 0.0f) continue;
+            const float dy = y - eyf;
+            const float zy2 = fmaf(dy, dy, z * z);
+            const float aR = fabsf(R) * unit;
+            float reK[E];
+            int ub[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const float dxe = x - exf[e];
+                const float r2 = fmaf(dxe, dxe, zy2);
+                const float rs = rsqrtf(r2);
+                reK[e] = (r2 > 0.0f ? r2 * rs : 0.0f) * sh.angK[0].w;
+                const float rsa = fminf(rs, kInvRCap);
+                float D = sinc_bound(p.kbx * dxe * rsa);
+                if (matrix) D *= sinc_bound(p.kby * dy * rsa);
+                ub[e] = live_e[e] ? rint_small(aR * rsa * D) + 1 : 0;
+            }
+            for (int al = 0; al < na; ++al) {
+                const float4 g = sh.angK[al + 1];  // (ux, uy, uz, -origin) fs / c
+                const float ptxK = fmaf(g.x, x, fmaf(g.y, y, fmaf(g.z, z, g.w)));
+                unsigned *rb = bins + al * E * wstride;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    // nearest sample of the binary32 delay (within 0.51 of the exact one),
+                    // as a bin index; any other value (huge or NaN delays) fails the test
+                    const int kb = __float_as_int((ptxK + reK[e]) + kMagic) - (kMagicBits - win);
+                    if (ub[e] && (unsigned)kb < (unsigned)wstride) atomicAdd(rb + e * wstride + kb, (unsigned)ub[e]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    {
+        const int nch = (ns + 15) >> 4;
+        for (int c = threadIdx.x; c < nrec * nch; c += NT) {
+            const int rec = c / nch;
+            const int t0 = (c - rec * nch) << 4;
+            const unsigned *b = bins + rec * wstride + t0;  // sample t0 - win .. : the window of sample t0
+            unsigned sum = 0u;
+            for (int i = 0; i <= 2 * win; ++i) sum += b[i];
+            unsigned m = sum;
+            const int t1 = min(16, ns - t0);
+            for (int t = 1; t < t1; ++t) {
+                sum += b[t + 2 * win] - b[t - 1];
+                m = max(m, sum);
+            }
+            atomicMax(&sh.wmax[rec], m);
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nrec) {
+        const int rec = threadIdx.x;
+        const float B = bm > 0.0f ? (float)sh.wmax[rec] / unit : 0.0f;  // bound of sum |taps| (amplitude units)
+        const float den = B * margin + __uint_as_float(sh.bmax[rec]) * 1.0009765625f;
+        float iq = (kTwo31 - (0.5f * (float)S + 64.0f)) / den;
+        if (!(iq > 0.0f && iq < 1e30f)) iq = 1.0f;
+        sh.invq[rec] = iq;
+        sh.q[rec] = 1.0f / iq;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nrec * ns; i += NT) {
+        const int rec = i / ns, k = i - rec * ns;
+        const int e = rec & 3;
+        int v = 0;
+        if (rf_base && e < ne)
+            v = __float2int_rn(rf_base[((int64_t)(a0 + (rec >> 2)) * M + m0 + e) * ns + k] * sh.invq[rec]);
+        tile[i] = v;
+    }
+    __syncthreads();
+
+    // ---- pass 2: the taps
     const float Kh = p.pr.fs_over_c.hi, Kl = p.pr.fs_over_c.lo;
-    const bool matrix = p.pr.ny > 1;
-    const float *X = pos + (int64_t)f * 3 * S;
-    const float *Y = X + S;
-    const float *Z = Y + S;
     const float theta = p.theta, theta2 = p.theta2, jmin_f = p.jmin_f, att_l2 = p.att_l2;
     const int kfast = ns - 9;  // records k .. k + 8 inside [0, ns): 0 <= k <= kfast
     const float thc0 = p.tab_h[0][0], ths0 = p.tab_h[0][1], thc1 = p.tab_h[1][0], ths1 = p.tab_h[1][1];
     const f2 COSH = fqi::f2_dup(p.cos_h), SINH = fqi::f2_dup(p.sin_h), TWOCOS = fqi::f2_dup(p.two_cos_h);
-    const f2 HALF = fqi::f2_dup(0.5f);
+    const f2 NCOSH = fqi::f2_dup(-p.cos_h), NSINH = fqi::f2_dup(-p.sin_h), NTWOCOS = fqi::f2_dup(-p.two_cos_h);
+    const f2 NHALF = fqi::f2_dup(-0.5f);
 
     // the next scatterer's inputs are loaded one iteration ahead
     float nR = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
-    if ((int64_t)threadIdx.x < S) {
+    if (bm > 0.0f && (int64_t)threadIdx.x < S) {
         nR = amp[threadIdx.x];
         nx = X[threadIdx.x];
         ny = Y[threadIdx.x];
         nz = Z[threadIdx.x];
     }
-    for (int64_t s = threadIdx.x; s < S; s += NT) {
+    for (int64_t s = threadIdx.x; bm > 0.0f && s < S; s += NT) {
         const float R = nR, x = nx, y = ny, z = nz;
         if (s + NT < S) {
             nR = amp[s + NT];
@@ -724,10 +952,9 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, i
             nz = Z[s + NT];
         }
         if (R == 0.0f) continue;
-        const ff ptx = fqi::ff_dot3_minus(an.ux, an.uy, an.uz, an.origin, x, y, z);
         const ff zz = fqi::ff_two_prod(z, z);
         const bool use_y = matrix || y != 0.0f;
-        // ---- element 0: float-float distance and delay
+        // ---- receive side, element 0: float-float distance
         const float dxh = __fsub_rn(x, ex0.hi);
         const float bb = __fsub_rn(dxh, x);
         const float dxl = __fsub_rn(__fadd_rn(__fsub_rn(x, __fsub_rn(dxh, bb)), __fsub_rn(-ex0.hi, bb)), ex0.lo);
@@ -752,118 +979,139 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int a, i
         const float rs0 = pos0 ? rsqrtf(r2.hi) : 0.0f;
         const float r0 = __fmul_rn(r2.hi, rs0);
         const float rl = pos0 ? __fmul_rn(__fadd_rn(__fmaf_rn(-r0, r0, r2.hi), r2.lo), 0.5f * rs0) : 0.0f;
-        ff path = fqi::ff_two_sum(ptx.hi, r0);
-        path.lo = __fadd_rn(path.lo, __fadd_rn(ptx.lo, rl));
-        const float uh = __fmul_rn(path.hi, Kh);
-        const float ul = __fmaf_rn(path.hi, Kl, __fmaf_rn(path.lo, Kh, __fmaf_rn(path.hi, Kh, -uh)));
-        float fl0 = floorf(uh);
-        float fr0 = __fadd_rn(__fsub_rn(uh, fl0), ul);
-        {
-            const float c = floorf(fr0);
-            fr0 -= c;
-            fl0 += c;
-        }
-        // ---- per element: distance, delay offset, amplitude, first tap
+        // ---- receive side, every element: delay offset, directivity, R D / r
         const float zy2 = __fadd_rn(zz.hi, q2);  // z^2 (+ dy^2), binary32
         const float r0f = r0 + rl;
-        const float Rfix = R * to_fix;
-        float Ae[E], che[E], she[E];
-        int ke[E];
-        bool ine[E], liv[E], nine[E];
+        float RD[E], dee[E];
+        bool liv[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            float dxe, rse, fr, fl, pe;
+            float dxe, rse;
+            bool ok;
             if (e == 0) {
                 dxe = dxh;
                 rse = rs0;
-                fr = fr0;
-                fl = fl0;
-                pe = path.hi;
+                dee[e] = 0.0f;
+                ok = pos0;
             } else {
                 dxe = x - exf[e];
                 const float re2 = fmaf(dxe, dxe, zy2);
                 rse = rsqrtf(re2);
                 const float re = re2 * rse;
-                const float de = __fdividef(cd[e] * (fmaf(2.0f, x, -csh[e]) - csl[e]), re + r0f);  // r_e - r_0
-                const float t = fmaf(de, Kh, fr0);
-                const float c = floorf(t);
-                fr = t - c;
-                fl = fl0 + c;
-                pe = path.hi + de;
+                dee[e] = __fdividef(cd[e] * (fmaf(2.0f, x, -csh[e]) - csl[e]), re + r0f);  // r_e - r_0
+                ok = re2 > 0.0f;
             }
-            float D = sinc_poly(p.kbx * dxe * rse);
-            if (matrix) D *= sinc_poly(p.kby * dyh * rse);
-            float A = Rfix * D * ex2_approx(att_l2 * pe) * rse;
-            const bool lv = live_e[e] && (e > 0 || pos0);
-            A = lv ? fminf(fmaxf(A, -kTapClamp), kTapClamp) : 0.0f;  // one clamp bounds every tap (|p| <= 1)
-            // taps j = jlo .. jlo + nt - 1 with |j - frac| < half_w: jlo is jmin
-            // or jmin + 1, nt is 8 or 9
-            const bool first_lo = fr <= theta;
-            const int k = (int)(fl + (first_lo ? jmin_f : jmin_f + 1.0f));
-            float ch, sh;
-            first_tap<true>(p.w_h, fr, thc0, ths0, thc1, ths1, !first_lo, ch, sh);
-            Ae[e] = A;
-            ke[e] = k;
-            nine[e] = first_lo || fr >= theta2;
-            che[e] = ch;
-            she[e] = sh;
-            liv[e] = lv;
-            ine[e] = lv && (unsigned)k <= (unsigned)kfast;
+            const float rsa = fminf(rse, kInvRCap);
+            float D = sinc_poly(p.kbx * dxe * rsa);
+            if (matrix) D *= sinc_poly(p.kby * dyh * rsa);
+            RD[e] = R * D * rsa;
+            liv[e] = live_e[e] && ok;
         }
-        const f2 A01 = fqi::f2_make(Ae[0], Ae[1]), A23 = fqi::f2_make(Ae[2], Ae[3]);
-        const f2 hA01 = fqi::f2_mul(HALF, A01), hA23 = fqi::f2_mul(HALF, A23);
-        const f2 CH01 = fqi::f2_make(che[0], che[1]), SH01 = fqi::f2_make(she[0], she[1]);
-        const f2 CH23 = fqi::f2_make(che[2], che[3]), SH23 = fqi::f2_make(she[2], she[3]);
-        f2 Ca0 = CH01, Ca1 = fqi::f2_fma(CH01, COSH, fqi::f2_neg(fqi::f2_mul(SH01, SINH)));
-        f2 Cb0 = CH23, Cb1 = fqi::f2_fma(CH23, COSH, fqi::f2_neg(fqi::f2_mul(SH23, SINH)));
-        const bool fast = (ine[0] || !liv[0]) && (ine[1] || !liv[1]) && (ine[2] || !liv[2]) && (ine[3] || !liv[3]);
-        if (fast) {
-            const int q0 = liv[0] ? ke[0] : 0, q1 = liv[1] ? ke[1] : 0;  // dead lanes: A = 0 at samples 0-7
-            const int q2i = liv[2] ? ke[2] : 0, q3 = liv[3] ? ke[3] : 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                add_fixed2_all(hi0, lo0, hi1, lo1, q0 + j, q1 + j, tap2x2(A01, hA01, Ca0));
-                add_fixed2_all(hi2, lo2, hi3, lo3, q2i + j, q3 + j, tap2x2(A23, hA23, Cb0));
-                const f2 Ca2 = fqi::f2_fma(TWOCOS, Ca1, fqi::f2_neg(Ca0));
-                const f2 Cb2 = fqi::f2_fma(TWOCOS, Cb1, fqi::f2_neg(Cb0));
-                Ca0 = Ca1;
-                Ca1 = Ca2;
-                Cb0 = Cb1;
-                Cb1 = Cb2;
+        for (int al = 0; al < na; ++al) {
+            const fqi::AngleFF an = p.ang[a0 + al];
+            const ff ptx = fqi::ff_dot3_minus(an.ux, an.uy, an.uz, an.origin, x, y, z);
+            ff path = fqi::ff_two_sum(ptx.hi, r0);
+            path.lo = __fadd_rn(path.lo, __fadd_rn(ptx.lo, rl));
+            const float uh = __fmul_rn(path.hi, Kh);
+            const float ul = __fmaf_rn(path.hi, Kl, __fmaf_rn(path.lo, Kh, __fmaf_rn(path.hi, Kh, -uh)));
+            float fl0 = floorf(uh);
+            float fr0 = __fadd_rn(__fsub_rn(uh, fl0), ul);
+            {
+                const float c = floorf(fr0);
+                fr0 -= c;
+                fl0 += c;
             }
-            if (nine[0] || nine[1])
-                add_fixed2(hi0, lo0, hi1, lo1, ke[0] + 8, ke[1] + 8, tap2x2(A01, hA01, Ca0), liv[0] && nine[0],
-                           liv[1] && nine[1]);
-            if (nine[2] || nine[3])
-                add_fixed2(hi2, lo2, hi3, lo3, ke[2] + 8, ke[3] + 8, tap2x2(A23, hA23, Cb0), liv[2] && nine[2],
-                           liv[3] && nine[3]);
-        } else {
-            // an echo straddles a record end: per-tap bounds
-            for (int j = 0; j < 9; ++j) {
-                int kk[E];
-                bool on[E];
+            const float4 iq4 = *reinterpret_cast<const float4 *>(&sh.invq[al * E]);
+            const float iqe[E] = {iq4.x, iq4.y, iq4.z, iq4.w};
+            float Ae[E], che[E], she[E];
+            int ke[E];
+            bool ine[E], nine[E];
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    kk[e] = ke[e] + j;
-                    on[e] = liv[e] && j < (nine[e] ? 9 : 8) && kk[e] >= 0 && kk[e] < ns;
-                    if (!on[e]) kk[e] = 0;
+            for (int e = 0; e < E; ++e) {
+                float fr, fl, pe;
+                if (e == 0) {
+                    fr = fr0;
+                    fl = fl0;
+                    pe = path.hi;
+                } else {
+                    const float t = fmaf(dee[e], Kh, fr0);
+                    const float c = floorf(t);
+                    fr = t - c;
+                    fl = fl0 + c;
+                    pe = path.hi + dee[e];
                 }
-                add_fixed2(hi0, lo0, hi1, lo1, kk[0], kk[1], tap2x2(A01, hA01, Ca0), on[0], on[1]);
-                add_fixed2(hi2, lo2, hi3, lo3, kk[2], kk[3], tap2x2(A23, hA23, Cb0), on[2], on[3]);
-                const f2 Ca2 = fqi::f2_fma(TWOCOS, Ca1, fqi::f2_neg(Ca0));
-                const f2 Cb2 = fqi::f2_fma(TWOCOS, Cb1, fqi::f2_neg(Cb0));
-                Ca0 = Ca1;
-                Ca1 = Ca2;
-                Cb0 = Cb1;
-                Cb1 = Cb2;
+                float A = RD[e] * iqe[e] * ex2_approx(att_l2 * pe);
+                A = liv[e] ? fminf(fmaxf(A, -kTapMax), kTapMax) : 0.0f;  // one clamp bounds every tap (|p| <= 1)
+                // taps j = jlo .. jlo + nt - 1 with |j - frac| < half_w: jlo is jmin
+                // or jmin + 1, nt is 8 or 9
+                const bool first_lo = fr <= theta;
+                const int k = (int)(fl + (first_lo ? jmin_f : jmin_f + 1.0f));
+                float ch, sh_;
+                first_tap<true>(p.w_h, fr, thc0, ths0, thc1, ths1, !first_lo, ch, sh_);
+                Ae[e] = A;
+                ke[e] = k;
+                nine[e] = first_lo || fr >= theta2;
+                che[e] = ch;
+                she[e] = sh_;
+                ine[e] = liv[e] && (unsigned)k <= (unsigned)kfast;
+            }
+            int *rec = tile + al * E * ns;
+            int *r0p = rec, *r1p = rec + ns, *r2p = rec + 2 * ns, *r3p = rec + 3 * ns;
+            const f2 A01 = fqi::f2_make(Ae[0], Ae[1]), A23 = fqi::f2_make(Ae[2], Ae[3]);
+            const f2 nhA01 = fqi::f2_mul(NHALF, A01), nhA23 = fqi::f2_mul(NHALF, A23);
+            const f2 CH01 = fqi::f2_make(che[0], che[1]), SH01 = fqi::f2_make(she[0], she[1]);
+            const f2 CH23 = fqi::f2_make(che[2], che[3]), SH23 = fqi::f2_make(she[2], she[3]);
+            // Hann-phase cosines C_j and their negatives N_j = -C_j (exactly:
+            // fma is symmetric in sign), so that C_{j+1} = 2 cos(w) C_j - C_{j-1}
+            // needs no separate negation
+            f2 Ca0 = CH01, Ca1 = fqi::f2_fma(CH01, COSH, fqi::f2_mul(SH01, NSINH));
+            f2 Cb0 = CH23, Cb1 = fqi::f2_fma(CH23, COSH, fqi::f2_mul(SH23, NSINH));
+            f2 Na0 = fqi::f2_neg(CH01), Na1 = fqi::f2_fma(CH01, NCOSH, fqi::f2_mul(SH01, SINH));
+            f2 Nb0 = fqi::f2_neg(CH23), Nb1 = fqi::f2_fma(CH23, NCOSH, fqi::f2_mul(SH23, SINH));
+            const bool fast = (ine[0] || !liv[0]) && (ine[1] || !liv[1]) && (ine[2] || !liv[2]) && (ine[3] || !liv[3]);
+            if (fast) {
+                const int q0 = liv[0] ? ke[0] : 0, q1 = liv[1] ? ke[1] : 0;  // dead lanes: A = 0 at samples 0-7
+                const int q2i = liv[2] ? ke[2] : 0, q3 = liv[3] ? ke[3] : 0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    add_tap2(r0p, r1p, q0 + j, q1 + j, tap2n(A01, nhA01, Ca0));
+                    add_tap2(r2p, r3p, q2i + j, q3 + j, tap2n(A23, nhA23, Cb0));
+                    cheb_step(Ca0, Ca1, Na0, Na1, TWOCOS, NTWOCOS);
+                    cheb_step(Cb0, Cb1, Nb0, Nb1, TWOCOS, NTWOCOS);
+                }
+                if (nine[0] || nine[1])
+                    add_tap2_if(r0p, r1p, ke[0] + 8, ke[1] + 8, tap2n(A01, nhA01, Ca0),
+                                liv[0] && nine[0], liv[1] && nine[1]);
+                if (nine[2] || nine[3])
+                    add_tap2_if(r2p, r3p, ke[2] + 8, ke[3] + 8, tap2n(A23, nhA23, Cb0),
+                                liv[2] && nine[2], liv[3] && nine[3]);
+            } else {
+                // an echo straddles a record end: per-tap bounds
+                for (int j = 0; j < 9; ++j) {
+                    int kk[E];
+                    bool on[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        kk[e] = ke[e] + j;
+                        on[e] = liv[e] && j < (nine[e] ? 9 : 8) && kk[e] >= 0 && kk[e] < ns;
+                        if (!on[e]) kk[e] = 0;
+                    }
+                    add_tap2_if(r0p, r1p, kk[0], kk[1], tap2n(A01, nhA01, Ca0), on[0], on[1]);
+                    add_tap2_if(r2p, r3p, kk[2], kk[3], tap2n(A23, nhA23, Cb0), on[2], on[3]);
+                    cheb_step(Ca0, Ca1, Na0, Na1, TWOCOS, NTWOCOS);
+                    cheb_step(Cb0, Cb1, Nb0, Nb1, TWOCOS, NTWOCOS);
+                }
             }
         }
     }
     __syncthreads();
-    const float from_fix = 1.0f / to_fix;
-    OutT *out = rf + (((int64_t)f * p.A + a) * M + m0) * ns;
-    for (int i = threadIdx.x; i < ne * ns; i += NT)
-        fqi::store_f(out, i, fmaf((float)tile[i], 65536.0f, (float)tile[4 * ns + i]) * from_fix);
+    for (int i = threadIdx.x; i < nrec * ns; i += NT) {
+        const int rec = i / ns, k = i - rec * ns;
+        const int e = rec & 3;
+        if (e >= ne) continue;
+        OutT *out = rf + (((int64_t)f * p.A + a0 + (rec >> 2)) * M + m0 + e) * ns;
+        fqi::store_f(out, k, (float)tile[i] * sh.q[rec]);
+    }
 }
 
 template <int NT, int MINB, typename OutT>
@@ -872,27 +1120,25 @@ __global__ void __launch_bounds__(NT, MINB) rf_synth_quad_kernel(const RfParams 
                                                               const float *__restrict__ rf_base,
                                                               OutT *__restrict__ rf)
 {
-    extern __shared__ int tile[];  // hi [4][Ns] then lo [4][Ns]
-    __shared__ float s_red[NT / 32];
-    rf_quad_tile<NT, OutT>(p, blockIdx.x, blockIdx.y, blockIdx.z, pos, amp, rf_base, rf, tile, s_red);
+    extern __shared__ int tile[];  // [angles in group][4][Ns]
+    __shared__ __align__(16) QuadShared sh;
+    rf_quad_tile<NT, OutT>(p, blockIdx.x, blockIdx.y, blockIdx.z, pos, amp, rf_base, rf, tile, sh);
 }
+
+size_t quad_smem(const RfParams &p) { return (size_t)p.ag * 4 * sizeof(int) * (size_t)(p.pr.ns + 2 * p.win); }
 
 template <typename OutT>
 fq_status launch_rf_quad(const RfParams &p, int F, const float *pos, const float *amp, const float *base, OutT *rf,
                          cudaStream_t st)
 {
-    constexpr int NT = 256;
-    const size_t smem = 8 * sizeof(int) * (size_t)p.pr.ns;
-    static int minb = -1;
-    if (minb < 0) {
-        const char *env = std::getenv("FQ_RF_QUAD_MINB");
-        minb = (env && env[0] == '1') ? 1 : 2;
-    }
-    auto kern = minb == 2 ? rf_synth_quad_kernel<NT, 2, OutT> : rf_synth_quad_kernel<NT, 1, OutT>;
+    constexpr int NT = kQuadNT;
+    const size_t smem = quad_smem(p);
+    // two CTAs per SM when their records fit twice
+    auto kern = smem <= kQuadTwoPerSm ? rf_synth_quad_kernel<NT, 2, OutT> : rf_synth_quad_kernel<NT, 1, OutT>;
     fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                                   "fq_simulate_rf: smem attribute");
     if (s) return s;
-    dim3 grid((p.pr.M + 3) / 4, p.A, F);
+    dim3 grid((p.pr.M + 3) / 4, p.n_ag, F);
     kern<<<grid, NT, smem, st>>>(p, pos, amp, base, rf);
     return fqi::launch_check("fq_simulate_rf");
 }
@@ -902,7 +1148,7 @@ __global__ void __launch_bounds__(NT, MINB) rf_quad_batched_kernel(const fqb::En
                                                                 const fqb::StageQueue q)
 {
     extern __shared__ int tile[];
-    __shared__ float s_red[NT / 32];
+    __shared__ __align__(16) QuadShared sh;
     __shared__ __align__(16) unsigned char s_par[kRfParamBytes];
     __shared__ int s_buf[2];
     int cur = -1;
@@ -915,7 +1161,7 @@ __global__ void __launch_bounds__(NT, MINB) rf_quad_batched_kernel(const fqb::En
             __syncthreads();
         }
         rf_quad_tile<NT, OutT>(*reinterpret_cast<const RfParams *>(s_par), it.x, it.y, it.z, e.pos, e.amp_eff,
-                               nullptr, (OutT *)e.rf, tile, s_red);
+                               nullptr, (OutT *)e.rf, tile, sh);
     }
 }
 
@@ -982,6 +1228,10 @@ bool rf_fast_ok(const RfParams &p)
            p.pr.ns >= 9;
 }
 
+// the quad kernel's records fit in shared memory and its rounding slack
+// (half a quantum per scatterer) stays far below the int32 range
+bool quad_ok(const RfParams &p) { return quad_smem(p) <= 200 * 1024 && p.S < (int64_t(1) << 30); }
+
 template <typename OutT>
 fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *amp, const float *base,
                       OutT *rf, cudaStream_t st)
@@ -994,7 +1244,7 @@ fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *a
     // the common pulse (two cycles, 8 <= n_cycles fs / f0 < 9, so every echo
     // has 8 or 9 taps) runs on the quad kernel when the array rows hold
     // whole quads, else on the packed-pair kernel
-    if (!scalar_only && fqi::use_rf_quad(p.pr.nx) && rf_fast_ok(p) && 8 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
+    if (!scalar_only && fqi::use_rf_quad(p.pr.nx) && rf_fast_ok(p) && quad_ok(p))
         return launch_rf_quad(p, F, pos, amp, base, rf, st);
     if (!scalar_only && rf_fast_ok(p) && 4 * sizeof(int) * (size_t)p.pr.ns <= 200 * 1024)
         return launch_rf_pair(p, F, pos, amp, base, rf, st);
@@ -1045,6 +1295,21 @@ fq_status make_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, RfPa
     p.two_cos_c = (float)(2.0 * std::cos(wc));
     p.two_cycle = probe->n_cycles == 2;
     fqi::make_angles_ff(probe, tx, p.ang);
+    // quad kernel: angle groups as large as the record budget allows, balanced
+    const size_t per_angle = 4 * sizeof(int) * (size_t)probe->n_samples;
+    size_t budget = kQuadRecordBudget;
+    if (const char *env = std::getenv("FQ_RF_AG_KB")) {
+        const long kb = std::atol(env);
+        if (kb >= 16 && kb <= 200) budget = (size_t)kb * 1024;
+    }
+    int ag = (int)std::max<size_t>(1, budget / per_angle);
+    ag = std::min(ag, p.A);
+    p.n_ag = (p.A + ag - 1) / ag;
+    p.ag = (p.A + p.n_ag - 1) / p.n_ag;
+    // taps t of an echo at delay u have |t - u| <= half_w; the pass-1 sample
+    // kp (u in binary32, rounded to nearest) is within 0.51 of u
+    p.win = (int)std::floor(hw + 0.52);
+    p.bound_margin = (float)(std::exp((double)p.att * (hw + 1.0) / (probe->fs / probe->c)) * (1.0 + 1.0 / 128.0));
     return FQ_OK;
 }
 
@@ -1105,11 +1370,20 @@ int rf_ntap_ok(const void *rf_params)
     return rf_fast_ok(*reinterpret_cast<const RfParams *>(rf_params));
 }
 
+void rf_quad_layout(const void *rf_params, int *n_groups, int *group, size_t *smem)
+{
+    const RfParams &p = *reinterpret_cast<const RfParams *>(rf_params);
+    *n_groups = p.n_ag;
+    *group = p.ag;
+    *smem = quad_smem(p);
+}
+
+bool rf_quad_ok(const void *rf_params) { return quad_ok(*reinterpret_cast<const RfParams *>(rf_params)); }
+
 template <int MINB, bool QUAD, typename OutT>
-fq_status launch_rf_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int ns_max, cudaStream_t st)
+fq_status launch_rf_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, size_t smem, cudaStream_t st)
 {
     constexpr int NT = 256;
-    const size_t smem = (QUAD ? 8 : 4) * sizeof(int) * (size_t)ns_max;
     auto kern = QUAD ? rf_quad_batched_kernel<NT, MINB, OutT> : rf_pair_batched_kernel<NT, MINB, OutT>;
     fq_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "batched RF: smem attribute");
@@ -1120,22 +1394,22 @@ fq_status launch_rf_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, in
 }
 
 template <typename OutT>
-fq_status batched_rf_t(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int ns_max, int minb, bool quad,
+fq_status batched_rf_t(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, size_t smem, int minb, bool quad,
                        cudaStream_t st)
 {
     if (quad) {
-        return minb == 1 ? launch_rf_batched<1, true, OutT>(ens, q, items, ns_max, st)
-                         : launch_rf_batched<2, true, OutT>(ens, q, items, ns_max, st);
+        return minb == 1 ? launch_rf_batched<1, true, OutT>(ens, q, items, smem, st)
+                         : launch_rf_batched<2, true, OutT>(ens, q, items, smem, st);
     }
-    return minb == 2 ? launch_rf_batched<2, false, OutT>(ens, q, items, ns_max, st)
-                     : launch_rf_batched<3, false, OutT>(ens, q, items, ns_max, st);
+    return minb == 2 ? launch_rf_batched<2, false, OutT>(ens, q, items, smem, st)
+                     : launch_rf_batched<3, false, OutT>(ens, q, items, smem, st);
 }
 
-fq_status batched_rf(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, int ns_max, int minb,
+fq_status batched_rf(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, size_t smem, int minb,
                      bool quad, cudaStream_t st)
 {
-    if (rf_dtype == FQ_F32) return batched_rf_t<float>(ens, q, items, ns_max, minb, quad, st);
-    return batched_rf_t<__nv_bfloat16>(ens, q, items, ns_max, minb, quad, st);
+    if (rf_dtype == FQ_F32) return batched_rf_t<float>(ens, q, items, smem, minb, quad, st);
+    return batched_rf_t<__nv_bfloat16>(ens, q, items, smem, minb, quad, st);
 }
 
 }  // namespace fqi

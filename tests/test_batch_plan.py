@@ -27,13 +27,20 @@ def test_struct_layouts_match_library():
     assert fq.abi_sizes() == [C.sizeof(t) for t in fq.ABI_STRUCTS]
 
 
+def rf_angle_groups(A, Ns):
+    """the quad RF kernel holds as many transmits per CTA as 96 KB of int32
+    records (4 elements x Ns samples each) allow, in balanced groups"""
+    ag = min(max(1, 96 * 1024 // (16 * Ns)), A)
+    return -(-A // ag)
+
+
 def expected_items(w, das_threads=128):
     cd = lambda a, b: -(-a // b)
     Fp = fq.frame_pad(w.n_frames)
     L = w.A * w.M
     nt = cd(w.n_frames, 32)
     return {"classify": cd(w.S, 2048), "advect": cd(w.S, 2048) * w.n_frames,
-            "rf": cd(w.M, 4) * w.A * w.n_frames, "rf2iq": cd(w.Ns, 128) * L * (Fp // 16),
+            "rf": cd(w.M, 4) * rf_angle_groups(w.A, w.Ns) * w.n_frames, "rf2iq": cd(w.Ns, 128) * L * (Fp // 16),
             "das": cd(w.P, das_threads // 4) * (Fp // 16), "gram_reduce": cd(w.n_frames ** 2, 256), "eig": 1,
             "project": cd(w.P, 64), "gram_pairs": nt * (nt + 1) // 2}
 

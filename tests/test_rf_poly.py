@@ -45,3 +45,15 @@ def test_against_closed_forms():
     s = x * float(m.horner_f32(c["kSinPoly"], np.array([x * x]))[0])
     co = float(m.horner_f32(c["kCosPoly"], np.array([x * x]))[0])
     assert abs(s - np.sqrt(0.5)) <= 1e-7 and abs(co - np.sqrt(0.5)) <= 1e-7
+
+
+def test_sinc_upper_bound():
+    """the RF kernel bounds |sin(u)/u| on |u| <= 5 by 1 - u^2/6 + u^4/120 (the
+    alternating series truncated after a positive term); the bound must hold
+    on the whole range and be tight where the directivity is near 1"""
+    u = np.linspace(0.0, 5.0, 500_001)
+    t = u * u
+    bound = 1.0 - t / 6.0 + t * t / 120.0
+    s = np.abs(np.sinc(u / np.pi))
+    assert (bound - s).min() >= -1e-15
+    assert (bound / s)[u <= 2.0].max() < 1.03
