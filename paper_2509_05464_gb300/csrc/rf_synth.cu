@@ -34,8 +34,11 @@ using fqi::ff;
 
 constexpr int kMaxTaps = 64;  // pulse taps per (scatterer, element) pair the kernel supports
 // quad kernel: shared-memory records per CTA (angles x 4 elements x Ns int32)
-// up to this size, and two CTAs per SM while they fit twice
-constexpr size_t kQuadRecordBudget = 96 * 1024;
+// up to this size; two CTAs of 256 threads per SM while they fit twice, else
+// one of 512 (the more angles a CTA holds, the more of the receive geometry
+// it shares: on the 2D compounded workload 5 angles per CTA measured 6% faster
+// than 3)
+constexpr size_t kQuadRecordBudget = 200 * 1024;
 constexpr size_t kQuadTwoPerSm = 110 * 1024;
 
 struct RfParams {
@@ -672,14 +675,13 @@ __global__ void __launch_bounds__(NT, MINB) rf_pair_batched_kernel(const fqb::En
 // The margin covers the attenuation gain of echoes that start just before
 // t = 0 and binary32 rounding of the amplitudes.
 // ---------------------------------------------------------------------------
-constexpr int kQuadNT = 256;
 constexpr float kInvRCap = 131072.0f;               // 1/r <= 2^17 per metre (r >= 7.6 um)
 constexpr float kTapMax = 2147483520.0f;            // largest binary32 below 2^31: |tap| bound in quanta
 constexpr float kUnitMax = 2097152.0f;              // 2^21: largest pass-1 bound in units
 constexpr float kTwo31 = 2147483648.0f;
 
 struct QuadShared {
-    float red[kQuadNT / 32];
+    float red[16];                     // one per warp (256 or 512 threads)
     float invq[4 * FQ_MAX_ANGLES];     // 1 / q per record (angle in group, element)
     float q[4 * FQ_MAX_ANGLES];
     unsigned wmax[4 * FQ_MAX_ANGLES];  // window maximum of the pass-1 bounds (units)
@@ -697,13 +699,14 @@ __device__ __forceinline__ float sinc_bound(float u)
     return fmaf(fmaf(t, 1.0f / 120.0f, -1.0f / 6.0f), t, 1.0f);
 }
 
+template <int NT>
 __device__ __forceinline__ float block_max(float v, float *red)
 {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     v = red[0];
-    for (int w = 1; w < kQuadNT / 32; ++w) v = fmaxf(v, red[w]);
+    for (int w = 1; w < NT / 32; ++w) v = fmaxf(v, red[w]);
     __syncthreads();
     return v;
 }
@@ -754,7 +757,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
                                              const float *__restrict__ amp, const float *__restrict__ rf_base,
                                              OutT *__restrict__ rf, int *tile, QuadShared &sh)
 {
-    static_assert(NT == kQuadNT, "block reductions assume kQuadNT threads");
+    static_assert(NT == 256 || NT == 512, "the quad kernel runs 256 or 512 threads");
     constexpr int E = 4;
     const int ns = p.pr.ns;
     const int M = p.pr.M;
@@ -832,7 +835,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
             if ((threadIdx.x & 31) == 0) atomicMax(&sh.bmax[rec], __float_as_uint(v));
         }
     }
-    bm = block_max(bm, sh.red);
+    bm = block_max<NT>(bm, sh.red);
 
     // ---- pass 1: tap bounds per element pair (0, 1), (2, 3).  The segment
     // between a pair's elements is at distance r_s <= r_e <= r_s + pitch from
@@ -1147,15 +1150,15 @@ template <typename OutT>
 fq_status launch_rf_quad(const RfParams &p, int F, const float *pos, const float *amp, const float *base, OutT *rf,
                          cudaStream_t st)
 {
-    constexpr int NT = kQuadNT;
     const size_t smem = quad_smem(p);
-    // two CTAs per SM when their records fit twice
-    auto kern = smem <= kQuadTwoPerSm ? rf_synth_quad_kernel<NT, 2, OutT> : rf_synth_quad_kernel<NT, 1, OutT>;
+    // two CTAs of 8 warps per SM when their records fit twice, else one of 16
+    const bool two = smem <= kQuadTwoPerSm;
+    auto kern = two ? rf_synth_quad_kernel<256, 2, OutT> : rf_synth_quad_kernel<512, 1, OutT>;
     fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                                   "fq_simulate_rf: smem attribute");
     if (s) return s;
     dim3 grid((p.pr.M + 3) / 4, p.n_ag, F);
-    kern<<<grid, NT, smem, st>>>(p, pos, amp, base, rf);
+    kern<<<grid, two ? 256 : 512, smem, st>>>(p, pos, amp, base, rf);
     return fqi::launch_check("fq_simulate_rf");
 }
 
@@ -1404,8 +1407,11 @@ bool rf_quad_ok(const void *rf_params) { return quad_ok(*reinterpret_cast<const 
 template <int MINB, bool QUAD, typename OutT>
 fq_status launch_rf_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, size_t smem, cudaStream_t st)
 {
-    constexpr int NT = 256;
-    auto kern = QUAD ? rf_quad_batched_kernel<NT, MINB, OutT> : rf_pair_batched_kernel<NT, MINB, OutT>;
+    // quad records too large for two CTAs per SM: one CTA of 512 threads
+    const bool wide = QUAD && smem > kQuadTwoPerSm;
+    const int NT = wide ? 512 : 256;
+    auto kern = wide ? rf_quad_batched_kernel<512, 1, OutT>
+                     : (QUAD ? rf_quad_batched_kernel<256, MINB, OutT> : rf_pair_batched_kernel<256, MINB, OutT>);
     fq_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "batched RF: smem attribute");
     if (s) return s;

@@ -28,9 +28,9 @@ def test_struct_layouts_match_library():
 
 
 def rf_angle_groups(A, Ns):
-    """the quad RF kernel holds as many transmits per CTA as 96 KB of int32
+    """the quad RF kernel holds as many transmits per CTA as 200 KB of int32
     records (4 elements x Ns samples each) allow, in balanced groups"""
-    ag = min(max(1, 96 * 1024 // (16 * Ns)), A)
+    ag = min(max(1, 200 * 1024 // (16 * Ns)), A)
     return -(-A // ag)
 
 
