@@ -381,7 +381,7 @@ def run_batched(args, rank, world, local):
     cost = [w.n_frames * w.A * w.M * w.S for w in ms]
     big = int(np.argmax(cost))
     tiles = {}
-    for op, name in ((fq.FQ_OP_RF, "rf_min_ctas_per_sm"), (fq.FQ_OP_DAS, "das_threads")):
+    for op, name in ((fq.FQ_OP_RF, "rf_resident_warps_per_sm"), (fq.FQ_OP_DAS, "das_threads")):
         c = fq.fq_autotune(op, b, big)
         b.set_tile(c)
         tiles[name] = {"choice": c.choice, "tried": list(c.tried[:c.n_tried]),

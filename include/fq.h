@@ -578,10 +578,11 @@ typedef struct fq_graph fq_graph;  /* opaque captured batch */
 enum { FQ_OP_RF = 0, FQ_OP_DAS = 1 };
 
 /* A tile shape the autotuner chose for one stage.
- *   FQ_OP_RF : choice = minimum resident CTAs per SM of the RF kernel
- *              (its register budget: 1 or 2 for the 4-element kernel that
- *              probes whose rows are multiples of 4 use, 2 or 3 for the
- *              2-element kernel)
+ *   FQ_OP_RF : choice = the RF kernel's register budget, for the
+ *              4-element kernel that probes whose rows are multiples of 4
+ *              use as resident warps per SM (32: 64 registers per thread,
+ *              16: 128), for the 2-element kernel as resident CTAs of 256
+ *              threads per SM (2 or 3)
  *   FQ_OP_DAS: choice = threads per DAS CTA (64, 128 or 256) */
 typedef struct fq_tile_choice {
     int32_t op;

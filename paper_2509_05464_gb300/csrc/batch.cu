@@ -64,7 +64,7 @@ struct fq_batch {
     size_t budget = 0;
     std::vector<EnsHost> e;
     std::vector<Wave> waves;
-    int rf_minb = 3, das_threads = 128;
+    int rf_tune = 3, das_threads = 128;  // RF register budget (see fq_tile_choice), DAS CTA size
     bool rf_quad = true;  // every member's rows hold whole element quads
     int ns_max = 0, J_max = 0, M_max = 0;
     size_t rf_smem = 0;  // dynamic shared memory of the RF stage kernel
@@ -280,7 +280,7 @@ fq_status launch_stage(fq_batch *b, char *arena, int w, int s, cudaStream_t st)
     switch (s) {
     case fqb::ST_CLASSIFY: return fqi::batched_classify(ens, q, q.total, st);
     case fqb::ST_ADVECT: return fqi::batched_advect(ens, q, q.total, st);
-    case fqb::ST_RF: return fqi::batched_rf(ens, q, q.total, b->rf_dtype, b->rf_smem, b->rf_minb, b->rf_quad, st);
+    case fqb::ST_RF: return fqi::batched_rf(ens, q, q.total, b->rf_dtype, b->rf_smem, b->rf_tune, b->rf_quad, st);
     case fqb::ST_RF2IQ: return fqi::batched_rf2iq(ens, q, q.total, b->rf_dtype, b->ch_dtype, b->J_max, st);
     case fqb::ST_DAS:
         return fqi::batched_das(ens, q, q.total, b->ch_dtype, b->iq_dtype, b->M_max, b->das_threads, st);
@@ -424,7 +424,7 @@ fq_status fq_batch_plan(const fq_ensemble_desc *ens, int32_t n, int32_t rf_dtype
         }
         b->rf_smem = std::max(b->rf_smem, smem);
     }
-    b->rf_minb = b->rf_quad ? 2 : 3;
+    b->rf_tune = b->rf_quad ? 32 : 3;  // quad: resident warps per SM; pair: resident CTAs
     // waves: greedy in the given order under the budget
     for (int i = 0; i < n; ++i) {
         EnsHost &h = b->e[i];
@@ -459,9 +459,9 @@ fq_status fq_batch_set_tile(fq_batch *plan, const fq_tile_choice *c)
 {
     FQ_REQUIRE(plan && c, FQ_ERR_INVALID_ARG, "fq_batch_set_tile: null argument");
     if (c->op == FQ_OP_RF) {
-        const bool ok = plan->rf_quad ? (c->choice == 1 || c->choice == 2) : (c->choice == 2 || c->choice == 3);
+        const bool ok = plan->rf_quad ? (c->choice == 16 || c->choice == 32) : (c->choice == 2 || c->choice == 3);
         FQ_REQUIRE(ok, FQ_ERR_INVALID_ARG, "fq_batch_set_tile: RF choice %d", c->choice);
-        plan->rf_minb = c->choice;
+        plan->rf_tune = c->choice;
         return FQ_OK;
     }
     if (c->op == FQ_OP_DAS) {
@@ -605,7 +605,7 @@ fq_status fq_autotune(int32_t op, const fq_ensemble_desc *ens, int32_t rf_dtype,
     fq_tile_choice c;
     std::memset(&c, 0, sizeof c);
     c.op = op;
-    const int cands_rf_pair[2] = {3, 2}, cands_rf_quad[2] = {2, 1}, cands_das[3] = {128, 64, 256};
+    const int cands_rf_pair[2] = {3, 2}, cands_rf_quad[2] = {32, 16}, cands_das[3] = {128, 64, 256};
     const int *cands = op == FQ_OP_RF ? (b->rf_quad ? cands_rf_quad : cands_rf_pair) : cands_das;
     const int nc = op == FQ_OP_RF ? 2 : 3;
     const int stage = op == FQ_OP_RF ? fqb::ST_RF : fqb::ST_DAS;

@@ -34,12 +34,13 @@ using fqi::ff;
 
 constexpr int kMaxTaps = 64;  // pulse taps per (scatterer, element) pair the kernel supports
 // quad kernel: shared-memory records per CTA (angles x 4 elements x Ns int32)
-// up to this size; two CTAs of 256 threads per SM while they fit twice, else
-// one of 512 (the more angles a CTA holds, the more of the receive geometry
-// it shares: on the 2D compounded workload 5 angles per CTA measured 6% faster
-// than 3)
+// up to this size (the more angles a CTA holds, the more of the receive
+// geometry it shares: on the 2D compounded workload 5 angles per CTA measured
+// 6% faster than 3).  The CTAs that fit per SM by shared memory split 32
+// resident warps (64 registers per thread): on that workload 32 warps ran
+// 9.4% faster than 16 (128 registers), 24 warps 7.8%.
 constexpr size_t kQuadRecordBudget = 200 * 1024;
-constexpr size_t kQuadTwoPerSm = 110 * 1024;
+inline int quad_ctas_per_sm(size_t smem) { return smem <= 52 * 1024 ? 4 : (smem <= 110 * 1024 ? 2 : 1); }
 
 struct RfParams {
     fqi::ProbeFF pr;
@@ -681,7 +682,7 @@ constexpr float kUnitMax = 2097152.0f;              // 2^21: largest pass-1 boun
 constexpr float kTwo31 = 2147483648.0f;
 
 struct QuadShared {
-    float red[16];                     // one per warp (256 or 512 threads)
+    float red[32];                     // one per warp
     float invq[4 * FQ_MAX_ANGLES];     // 1 / q per record (angle in group, element)
     float q[4 * FQ_MAX_ANGLES];
     unsigned wmax[4 * FQ_MAX_ANGLES];  // window maximum of the pass-1 bounds (units)
@@ -757,7 +758,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
                                              const float *__restrict__ amp, const float *__restrict__ rf_base,
                                              OutT *__restrict__ rf, int *tile, QuadShared &sh)
 {
-    static_assert(NT == 256 || NT == 512, "the quad kernel runs 256 or 512 threads");
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps, at most 1024 threads");
     constexpr int E = 4;
     const int ns = p.pr.ns;
     const int M = p.pr.M;
@@ -1151,14 +1152,14 @@ fq_status launch_rf_quad(const RfParams &p, int F, const float *pos, const float
                          cudaStream_t st)
 {
     const size_t smem = quad_smem(p);
-    // two CTAs of 8 warps per SM when their records fit twice, else one of 16
-    const bool two = smem <= kQuadTwoPerSm;
-    auto kern = two ? rf_synth_quad_kernel<256, 2, OutT> : rf_synth_quad_kernel<512, 1, OutT>;
+    const int ctas = quad_ctas_per_sm(smem);  // x (1024 / ctas) threads = 32 warps per SM
+    auto kern = ctas == 4 ? rf_synth_quad_kernel<256, 4, OutT>
+                          : (ctas == 2 ? rf_synth_quad_kernel<512, 2, OutT> : rf_synth_quad_kernel<1024, 1, OutT>);
     fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                                   "fq_simulate_rf: smem attribute");
     if (s) return s;
     dim3 grid((p.pr.M + 3) / 4, p.n_ag, F);
-    kern<<<grid, two ? 256 : 512, smem, st>>>(p, pos, amp, base, rf);
+    kern<<<grid, 1024 / ctas, smem, st>>>(p, pos, amp, base, rf);
     return fqi::launch_check("fq_simulate_rf");
 }
 
@@ -1404,14 +1405,14 @@ void rf_quad_layout(const void *rf_params, int *n_groups, int *group, size_t *sm
 
 bool rf_quad_ok(const void *rf_params) { return quad_ok(*reinterpret_cast<const RfParams *>(rf_params)); }
 
-template <int MINB, bool QUAD, typename OutT>
+template <int NT, int MINB, bool QUAD, typename OutT>
 fq_status launch_rf_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, size_t smem, cudaStream_t st)
 {
-    // quad records too large for two CTAs per SM: one CTA of 512 threads
-    const bool wide = QUAD && smem > kQuadTwoPerSm;
-    const int NT = wide ? 512 : 256;
-    auto kern = wide ? rf_quad_batched_kernel<512, 1, OutT>
-                     : (QUAD ? rf_quad_batched_kernel<256, MINB, OutT> : rf_pair_batched_kernel<256, MINB, OutT>);
+    void (*kern)(const fqb::EnsDev *, const fqb::StageQueue);
+    if constexpr (QUAD)
+        kern = rf_quad_batched_kernel<NT, MINB, OutT>;
+    else
+        kern = rf_pair_batched_kernel<NT, MINB, OutT>;
     fq_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "batched RF: smem attribute");
     if (s) return s;
@@ -1420,16 +1421,25 @@ fq_status launch_rf_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, in
     return launch_check("batched RF");
 }
 
+// quad: `tune` = resident warps per SM (32 or 16), split over the CTAs that
+// fit by shared memory; pair: `tune` = resident CTAs of 256 threads (2 or 3)
 template <typename OutT>
-fq_status batched_rf_t(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, size_t smem, int minb, bool quad,
+fq_status batched_rf_t(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, size_t smem, int tune, bool quad,
                        cudaStream_t st)
 {
     if (quad) {
-        return minb == 1 ? launch_rf_batched<1, true, OutT>(ens, q, items, smem, st)
-                         : launch_rf_batched<2, true, OutT>(ens, q, items, smem, st);
+        const int ctas = quad_ctas_per_sm(smem);
+        if (tune == 16) {
+            if (ctas == 4) return launch_rf_batched<128, 4, true, OutT>(ens, q, items, smem, st);
+            if (ctas == 2) return launch_rf_batched<256, 2, true, OutT>(ens, q, items, smem, st);
+            return launch_rf_batched<512, 1, true, OutT>(ens, q, items, smem, st);
+        }
+        if (ctas == 4) return launch_rf_batched<256, 4, true, OutT>(ens, q, items, smem, st);
+        if (ctas == 2) return launch_rf_batched<512, 2, true, OutT>(ens, q, items, smem, st);
+        return launch_rf_batched<1024, 1, true, OutT>(ens, q, items, smem, st);
     }
-    return minb == 2 ? launch_rf_batched<2, false, OutT>(ens, q, items, smem, st)
-                     : launch_rf_batched<3, false, OutT>(ens, q, items, smem, st);
+    return tune == 2 ? launch_rf_batched<256, 2, false, OutT>(ens, q, items, smem, st)
+                     : launch_rf_batched<256, 3, false, OutT>(ens, q, items, smem, st);
 }
 
 fq_status batched_rf(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, size_t smem, int minb,

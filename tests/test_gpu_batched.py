@@ -99,14 +99,14 @@ def test_waves_and_graph_replay_give_the_same_result(batch_and_reference):
 def test_autotuned_tiles_keep_results(batch_and_reference):
     ms, b, got, _ = batch_and_reference
     big = int(np.argmax([w.S * w.n_frames * w.A * w.M for w in ms]))
-    for op, cands in ((fq.FQ_OP_RF, {1, 2}), (fq.FQ_OP_DAS, {64, 128, 256})):
+    for op, cands in ((fq.FQ_OP_RF, {16, 32}), (fq.FQ_OP_DAS, {64, 128, 256})):
         c = fq.fq_autotune(op, b, big)
         assert c.op == op and c.choice in cands
         assert c.n_tried == len(cands) and set(c.tried[:c.n_tried]) == cands
         assert all(t > 0 for t in c.tried_ms[:c.n_tried]) and c.ms == min(c.tried_ms[:c.n_tried])
         again = fq.fq_autotune(op, b, big)  # cached
         assert again.n_tried == 0 and again.choice == c.choice
-    for op, ch in ((fq.FQ_OP_RF, 1), (fq.FQ_OP_DAS, 64), (fq.FQ_OP_DAS, 256)):
+    for op, ch in ((fq.FQ_OP_RF, 16), (fq.FQ_OP_DAS, 64), (fq.FQ_OP_DAS, 256)):
         t = fq.TileChoice()
         t.op, t.choice = op, ch
         b.set_tile(t)
