@@ -263,84 +263,6 @@ struct DasParams {
 constexpr int kDasThreads = 128;
 constexpr int kDasTPP = fqb::kDasThreadsPerPixel;  // threads per pixel
 
-// 16 complex values of one channel sample for the frame chunk
-template <typename ChT>
-struct ChunkLoad;
-template <>
-struct ChunkLoad<float> {
-    static __device__ __forceinline__ void load(const float *base, float2 (&v)[kFrameChunk])
-    {
-        const float4 *q = reinterpret_cast<const float4 *>(base);
-#pragma unroll
-        for (int i = 0; i < kFrameChunk / 2; ++i) {
-            float4 t = __ldg(q + i);
-            v[2 * i] = make_float2(t.x, t.y);
-            v[2 * i + 1] = make_float2(t.z, t.w);
-        }
-    }
-};
-template <>
-struct ChunkLoad<__nv_bfloat16> {
-    static __device__ __forceinline__ void load(const __nv_bfloat16 *base, float2 (&v)[kFrameChunk])
-    {
-        const uint4 *q = reinterpret_cast<const uint4 *>(base);
-#pragma unroll
-        for (int i = 0; i < kFrameChunk / 4; ++i) {
-            uint4 t = __ldg(q + i);
-            const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&t);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[4 * i + j] = __bfloat1622float2(b[j]);
-        }
-    }
-};
-
-// One tile: pixels bx * blockDim.x .. + blockDim.x - 1, frames 16 by ..
-// 16 by + 15.  `etab` is the dynamic shared memory (6 M floats).
-// N complex values (N consecutive frames, N = 2 or 4) of one channel sample
-template <int N, typename ChT>
-struct FramesLoad;
-template <>
-struct FramesLoad<4, float> {
-    static __device__ __forceinline__ void load(const float *base, float2 (&v)[4])
-    {
-        const float4 *q = reinterpret_cast<const float4 *>(base);
-        const float4 a = __ldg(q), b = __ldg(q + 1);
-        v[0] = make_float2(a.x, a.y);
-        v[1] = make_float2(a.z, a.w);
-        v[2] = make_float2(b.x, b.y);
-        v[3] = make_float2(b.z, b.w);
-    }
-};
-template <>
-struct FramesLoad<2, float> {
-    static __device__ __forceinline__ void load(const float *base, float2 (&v)[2])
-    {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(base));
-        v[0] = make_float2(a.x, a.y);
-        v[1] = make_float2(a.z, a.w);
-    }
-};
-template <>
-struct FramesLoad<4, __nv_bfloat16> {
-    static __device__ __forceinline__ void load(const __nv_bfloat16 *base, float2 (&v)[4])
-    {
-        const uint4 t = __ldg(reinterpret_cast<const uint4 *>(base));
-        const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&t);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = __bfloat1622float2(b[j]);
-    }
-};
-template <>
-struct FramesLoad<2, __nv_bfloat16> {
-    static __device__ __forceinline__ void load(const __nv_bfloat16 *base, float2 (&v)[2])
-    {
-        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(base));
-        const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&t);
-        v[0] = __bfloat1622float2(b[0]);
-        v[1] = __bfloat1622float2(b[1]);
-    }
-};
-
 // The N frames of one channel at the interpolated sample i + phi:
 // v = v(i) + phi (v(i + 1) - v(i)).  FP32 channel data interpolate in FP32;
 // BF16 channel data interpolate as packed bf16x2 (re, im) pairs and are
@@ -348,18 +270,6 @@ struct FramesLoad<2, __nv_bfloat16> {
 // count (the widening of both samples would add four instructions per frame).
 template <int N, typename ChT>
 struct InterpFrames;
-template <int N>
-struct InterpFrames<N, float> {
-    static __device__ __forceinline__ void run(const float *b0, int64_t stride, float phi, float2 (&v)[N])
-    {
-        float2 v0[N], v1[N];
-        FramesLoad<N, float>::load(b0, v0);
-        FramesLoad<N, float>::load(b0 + stride, v1);
-#pragma unroll
-        for (int k = 0; k < N; ++k)
-            v[k] = make_float2(fmaf(phi, v1[k].x - v0[k].x, v0[k].x), fmaf(phi, v1[k].y - v0[k].y, v0[k].y));
-    }
-};
 template <>
 struct InterpFrames<4, __nv_bfloat16> {
     static __device__ __forceinline__ void run(const __nv_bfloat16 *b0, int64_t stride, float phi, float2 (&v)[4])
@@ -371,6 +281,36 @@ struct InterpFrames<4, __nv_bfloat16> {
         const __nv_bfloat162 ph = __float2bfloat162_rn(phi);
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = __bfloat1622float2(__hfma2(ph, __hsub2(b[k], a[k]), a[k]));
+    }
+};
+
+// The same as packed (re, im) pairs: FP32 channel data are loaded as 64-bit
+// (re, im) words and interpolated with f32x2 instructions (2 per frame
+// instead of 4).
+template <int N, typename ChT>
+struct InterpFramesF2;
+template <int N>
+struct InterpFramesF2<N, float> {
+    static __device__ __forceinline__ void run(const float *b0, int64_t stride, fqi::f2 PHI, fqi::f2 (&v)[N])
+    {
+        const ulonglong2 *q0 = reinterpret_cast<const ulonglong2 *>(b0);
+        const ulonglong2 *q1 = reinterpret_cast<const ulonglong2 *>(b0 + stride);
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const ulonglong2 a = __ldg(q0 + i), b = __ldg(q1 + i);
+            v[2 * i] = fqi::f2_fma(PHI, fqi::f2_sub(fqi::f2{b.x}, fqi::f2{a.x}), fqi::f2{a.x});
+            v[2 * i + 1] = fqi::f2_fma(PHI, fqi::f2_sub(fqi::f2{b.y}, fqi::f2{a.y}), fqi::f2{a.y});
+        }
+    }
+};
+template <int N>
+struct InterpFramesF2<N, __nv_bfloat16> {
+    static __device__ __forceinline__ void run(const __nv_bfloat16 *b0, int64_t stride, fqi::f2 PHI, fqi::f2 (&v)[N])
+    {
+        float2 w[N];
+        InterpFrames<N, __nv_bfloat16>::run(b0, stride, fqi::f2_lo(PHI), w);
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = fqi::f2_make(w[k].x, w[k].y);
     }
 };
 
@@ -422,9 +362,11 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, co
     const int ns = p.pr.ns;
     const int64_t row_stride = (int64_t)p.Fp * 2;  // scalars per channel sample (all frames)
 
-    float2 acc[FPT];
+    // sum of v cos and sum of v sin per frame, as (re, im) pairs: the rotated
+    // sum is (C.re - S.im, C.im + S.re)
+    fqi::f2 accC[FPT], accS[FPT];
 #pragma unroll
-    for (int k = 0; k < FPT; ++k) acc[k] = make_float2(0.0f, 0.0f);
+    for (int k = 0; k < FPT; ++k) accC[k] = accS[k] = fqi::f2_dup(0.0f);
 
     for (int a = 0; a < p.A; ++a) {
         const fqi::AngleFF an = p.ang[a];
@@ -469,12 +411,13 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, co
                 const bool onj = __shfl_sync(0xffffffffu, on ? 1 : 0, j, TPP) != 0;
                 if (!onj) continue;
                 const ChT *b0 = cha + ((int64_t)(m0 + j) * ns + ij) * row_stride;
-                float2 v[FPT];
-                InterpFrames<FPT, ChT>::run(b0, row_stride, phj, v);
+                fqi::f2 v[FPT];
+                InterpFramesF2<FPT, ChT>::run(b0, row_stride, fqi::f2_dup(phj), v);
+                const fqi::f2 CS = fqi::f2_dup(csj), SN = fqi::f2_dup(snj);
 #pragma unroll
                 for (int k = 0; k < FPT; ++k) {
-                    acc[k].x = fmaf(v[k].x, csj, fmaf(-v[k].y, snj, acc[k].x));
-                    acc[k].y = fmaf(v[k].x, snj, fmaf(v[k].y, csj, acc[k].y));
+                    accC[k] = fqi::f2_fma(v[k], CS, accC[k]);
+                    accS[k] = fqi::f2_fma(v[k], SN, accS[k]);
                 }
             }
         }
@@ -482,96 +425,14 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, co
     if (!live) return;
     const int f0 = fbase + FPT * q;
 #pragma unroll
-    for (int k = 0; k < FPT; ++k)
-        if (f0 + k < p.F)
-            fqi::store_c(iq, pix * p.F + f0 + k, make_float2(acc[k].x * p.inv_A, acc[k].y * p.inv_A));
+    for (int k = 0; k < FPT; ++k) {
+        float cr, ci, sr, si;
+        fqi::f2_split(accC[k], cr, ci);
+        fqi::f2_split(accS[k], sr, si);
+        if (f0 + k < p.F) fqi::store_c(iq, pix * p.F + f0 + k, make_float2((cr - si) * p.inv_A, (ci + sr) * p.inv_A));
+    }
 }
 
-template <typename ChT, typename OutT>
-__device__ __forceinline__ void das_tile(const DasParams &p, int bx, int by, const ChT *__restrict__ ch,
-                                         OutT *__restrict__ iq, float *etab)
-{
-    const int M = p.pr.M;
-    float *exf = etab, *exh = etab + M, *exl = etab + 2 * M;
-    float *eyf = etab + 3 * M, *eyh = etab + 4 * M, *eyl = etab + 5 * M;
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        int ix = m % p.pr.nx, iy = m / p.pr.nx;
-        double ex = __dmul_rn(__dsub_rn((double)ix, __dmul_rn(0.5, (double)(p.pr.nx - 1))), p.pitch_x);
-        double ey = __dmul_rn(__dsub_rn((double)iy, __dmul_rn(0.5, (double)(p.pr.ny - 1))), p.pitch_y);
-        fqi::df2 sx = fqi::split_double(ex), sy = fqi::split_double(ey);
-        exf[m] = (float)ex; exh[m] = sx.hi; exl[m] = sx.lo;
-        eyf[m] = (float)ey; eyh[m] = sy.hi; eyl[m] = sy.lo;
-    }
-    __syncthreads();
-
-    const int64_t pix = (int64_t)bx * blockDim.x + threadIdx.x;
-    const int fbase = by * kFrameChunk;
-    const bool live = pix < p.P;
-    const int64_t pp = live ? pix : 0;
-    const int ix = (int)(pp % p.gx);
-    const int iz = (int)((pp / p.gx) % p.gz);
-    const int iy = (int)(pp / ((int64_t)p.gx * p.gz));
-    const double xd = __dadd_rn(p.x0, __dmul_rn((double)ix, p.dx));
-    const double yd = __dadd_rn(p.y0, __dmul_rn((double)iy, p.dy));
-    const double zd = __dadd_rn(p.z0, __dmul_rn((double)iz, p.dz));
-    const float xf = (float)xd, yf = (float)yd, zf = (float)zd;
-    const fqi::df2 xs = fqi::split_double(xd), ys = fqi::split_double(yd), zs = fqi::split_double(zd);
-    const ff X = {xs.hi, xs.lo}, Y = {ys.hi, ys.lo}, Z = {zs.hi, zs.lo};
-    const ff zz = fqi::ff_sqr(Z);
-    const float half = __fmul_rn(zf, p.half_per_z);
-    const bool matrix = p.pr.ny > 1;
-    const ff fs_c = fqi::ff_load(p.pr.fs_over_c);
-    const ff f0_fs = fqi::ff_load(p.pr.f0_over_fs);
-    const int ns = p.pr.ns;
-
-    float2 acc[kFrameChunk];
-#pragma unroll
-    for (int f = 0; f < kFrameChunk; ++f) acc[f] = make_float2(0.0f, 0.0f);
-
-    for (int a = 0; a < p.A; ++a) {
-        const fqi::AngleFF an = p.ang[a];
-        ff ptx = fqi::ff_add(fqi::ff_mul(fqi::ff_load(an.ux), X), fqi::ff_mul(fqi::ff_load(an.uy), Y));
-        ptx = fqi::ff_add(ptx, fqi::ff_mul(fqi::ff_load(an.uz), Z));
-        ptx = fqi::ff_add(ptx, fqi::ff_neg(fqi::ff_load(an.origin)));
-        const ChT *cha = ch + (int64_t)a * M * ns * p.Fp * 2;
-        for (int m = 0; m < M; ++m) {
-            bool on = live && fabsf(__fsub_rn(xf, exf[m])) <= half;
-            if (matrix) on = on && fabsf(__fsub_rn(yf, eyf[m])) <= half;
-            if (!__any_sync(0xffffffffu, on)) continue;
-            if (!on) continue;
-            ff dxx = fqi::ff_add(X, ff{-exh[m], -exl[m]});
-            ff r2 = fqi::ff_add(fqi::ff_sqr(dxx), zz);
-            if (matrix || yf != 0.0f) {
-                ff dyy = fqi::ff_add(Y, ff{-eyh[m], -eyl[m]});
-                r2 = fqi::ff_add(r2, fqi::ff_sqr(dyy));
-            }
-            const ff path = fqi::ff_add(ptx, fqi::ff_sqrt(r2));
-            const ff u = fqi::ff_mul(path, fs_c);
-            int i;
-            float phi;
-            fqi::ff_floor_frac(u, i, phi);
-            if (i < 0 || i + 1 >= ns) continue;
-            const float cyc = fqi::ff_frac(fqi::ff_mul(u, f0_fs));
-            float sn, cs;
-            sincospif(2.0f * cyc, &sn, &cs);
-            const ChT *b0 = cha + (((int64_t)m * ns + i) * p.Fp + fbase) * 2;
-            float2 v0[kFrameChunk], v1[kFrameChunk];
-            ChunkLoad<ChT>::load(b0, v0);
-            ChunkLoad<ChT>::load(b0 + (int64_t)p.Fp * 2, v1);
-#pragma unroll
-            for (int f = 0; f < kFrameChunk; ++f) {
-                float vr = fmaf(phi, v1[f].x - v0[f].x, v0[f].x);
-                float vi = fmaf(phi, v1[f].y - v0[f].y, v0[f].y);
-                acc[f].x = fmaf(vr, cs, fmaf(-vi, sn, acc[f].x));
-                acc[f].y = fmaf(vr, sn, fmaf(vi, cs, acc[f].y));
-            }
-        }
-    }
-    if (!live) return;
-    const int nf = min(kFrameChunk, p.F - fbase);
-    for (int f = 0; f < nf; ++f)
-        fqi::store_c(iq, pix * p.F + fbase + f, make_float2(acc[f].x * p.inv_A, acc[f].y * p.inv_A));
-}
 
 template <typename ChT, typename OutT, int NT>
 __global__ void __launch_bounds__(NT) das_kernel(const DasParams p, const ChT *__restrict__ ch, OutT *__restrict__ iq)
