@@ -662,14 +662,14 @@ __global__ void __launch_bounds__(NT, MINB) rf_pair_batched_kernel(const fqb::En
 // gets the finest quantum q for which that is guaranteed:
 //   pass 0  b_max = largest |amp| / (distance to the quad) sets the integer
 //           units of pass 1;
-//   pass 1  every (scatterer, angle) adds an upper bound of the quad's taps,
-//           |amp| D_b / r_s in those units (r_s = distance to the segment
-//           between the outer elements, D_b >= |directivity|), at the sample
-//           nearest to its binary32 mid-quad delay; the four elements' delays
-//           are within 1.5 pitches of it, and the binary32 delay is within
-//           0.51 sample of the exact one, so a window of
-//           2 floor(half_w + 3 pitch fs / 2c + 0.52) + 1 samples around a
-//           sample bounds the sum of |taps| that land on it in any record;
+//   pass 1  every (scatterer, element pair, angle) adds an upper bound of the
+//           pair's taps, |amp| D_b / r_s in those units (r_s = distance to the
+//           segment between the two elements, D_b >= |directivity|), at the
+//           sample nearest to its binary32 mid-pair delay; both elements'
+//           delays are within half a pitch of it, and the binary32 delay is
+//           within 0.51 sample of the exact one, so a window of
+//           2 floor(half_w + pitch fs / 2c + 0.52) + 1 samples around a sample
+//           bounds the sum of |taps| that land on it in either record;
 //   scale   1/q = the largest value that keeps (window maximum x margin +
 //           largest |static base|) / q + half a quantum per scatterer (tap
 //           rounding) below 2^31.
@@ -798,7 +798,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
 
     // the previous item of a persistent CTA may still read the tile
     __syncthreads();
-    for (int i = threadIdx.x; i < na * (ns + 2 * p.win); i += NT) tile[i] = 0;
+    for (int i = threadIdx.x; i < na * 2 * (ns + 2 * p.win); i += NT) tile[i] = 0;
     if ((int)threadIdx.x < nrec) {
         sh.wmax[threadIdx.x] = 0u;
         sh.bmax[threadIdx.x] = 0u;
@@ -838,13 +838,13 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
     }
     bm = block_max<NT>(bm, sh.red);
 
-    // ---- pass 1: tap bounds per quad.  The segment between the quad's outer
-    // elements is at distance r_s <= r_e <= r_s + 3 pitch from the scatterer,
-    // so the four elements' delays lie within 3 pitch fs / (2 c) of
-    // (ptx + r_s) fs / c + 3 pitch fs / (2 c); the bound |amp| D / r_s is
-    // added at the nearest sample of that binary32 delay, in one record of
-    // ns + 2 win bins per angle (bin i holds sample i - win; win covers
-    // half_w + 1.5 pitches + 0.51 sample of rounding)
+    // ---- pass 1: tap bounds per element pair (0, 1), (2, 3).  The segment
+    // between a pair's elements is at distance r_s <= r_e <= r_s + pitch from
+    // the scatterer, so both elements' delays lie within pitch fs / (2 c) of
+    // (ptx + r_s) fs / c + pitch fs / (2 c); the bound |amp| D / r_s is added
+    // at the nearest sample of that binary32 delay, in records of ns + 2 win
+    // bins (bin i holds sample i - win; win covers half_w + half a pitch +
+    // 0.51 sample of rounding)
     const int win = p.win;
     const int wstride = ns + 2 * win;
     const float margin = p.bound_margin;
@@ -853,7 +853,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
     unsigned *bins = reinterpret_cast<unsigned *>(tile);
     if (bm > 0.0f) {
         const float K = sh.angK[0].w;
-        const float hpK = 0.5f * (exf[3] - exf[0]) * K;  // half the quad's span in samples
+        const float hpK0 = 0.5f * (exf[1] - exf[0]) * K, hpK1 = 0.5f * (exf[3] - exf[2]) * K;
         float nR = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;  // one scatterer ahead
         if ((int64_t)threadIdx.x < S) {
             nR = amp[threadIdx.x];
@@ -873,35 +873,40 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
             const float dy = y - eyf;
             const float zy2 = fmaf(dy, dy, z * z);
             const float aR = fabsf(R) * unit;
-            float reK;
-            int ub;
-            {
-                const float dxs = x - fminf(fmaxf(x, exf[0]), exf[3]);
+            float reK[2];
+            int ub[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float dxs = x - fminf(fmaxf(x, exf[2 * h]), exf[2 * h + 1]);
                 const float r2 = fmaf(dxs, dxs, zy2);
                 const float rs = rsqrtf(r2);
-                reK = fmaf(r2 > 0.0f ? r2 * rs : 0.0f, K, hpK);
-                // |D| of any element: the bound at the quad's smallest
+                reK[h] = fmaf(r2 > 0.0f ? r2 * rs : 0.0f, K, h ? hpK1 : hpK0);
+                // |D| of either element: the bound at the pair's smallest
                 // |argument| or at its largest possible one (k0 w / 2); 1 for
                 // scatterers closer than the 1/r cap; the matrix probe's
                 // y-directivity bounded by 1
                 const float D = rs > kInvRCap ? 1.0f : fmaxf(sinc_bound(p.kbx * dxs * rs), p.dbx_far);
-                ub = rint_small(aR * fminf(rs, kInvRCap) * D) + 1;
+                ub[h] = (live_e[2 * h] || live_e[2 * h + 1]) ? rint_small(aR * fminf(rs, kInvRCap) * D) + 1 : 0;
             }
             for (int al = 0; al < na; ++al) {
                 const float4 g = sh.angK[al + 1];  // (ux, uy, uz, -origin) fs / c
                 const float ptxK = fmaf(g.x, x, fmaf(g.y, y, fmaf(g.z, z, g.w)));
-                // nearest sample of the binary32 delay (within 0.51 of the exact
-                // one) as a bin index; any other value (huge or NaN delays) fails
-                // the test
-                const int kb = __float_as_int((ptxK + reK) + kMagic) - (kMagicBits - win);
-                if ((unsigned)kb < (unsigned)wstride) atomicAdd(bins + al * wstride + kb, (unsigned)ub);
+                unsigned *rb = bins + al * 2 * wstride;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    // nearest sample of the binary32 delay (within 0.51 of the exact
+                    // one) as a bin index; any other value (huge or NaN delays)
+                    // fails the test
+                    const int kb = __float_as_int((ptxK + reK[h]) + kMagic) - (kMagicBits - win);
+                    if (ub[h] && (unsigned)kb < (unsigned)wstride) atomicAdd(rb + h * wstride + kb, (unsigned)ub[h]);
+                }
             }
         }
     }
     __syncthreads();
     {
         const int nch = (ns + 15) >> 4;
-        for (int c = threadIdx.x; c < na * nch; c += NT) {
+        for (int c = threadIdx.x; c < na * 2 * nch; c += NT) {
             const int rec = c / nch;
             const int t0 = (c - rec * nch) << 4;
             const unsigned *b = bins + rec * wstride + t0;  // sample t0 - win .. : the window of sample t0
@@ -919,7 +924,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
     __syncthreads();
     if ((int)threadIdx.x < nrec) {
         const int rec = threadIdx.x;
-        const float B = bm > 0.0f ? (float)sh.wmax[rec >> 2] / unit : 0.0f;  // bound of sum |taps| (amplitude units)
+        const float B = bm > 0.0f ? (float)sh.wmax[rec >> 1] / unit : 0.0f;  // bound of sum |taps| (amplitude units)
         const float den = B * margin + __uint_as_float(sh.bmax[rec]) * 1.0009765625f;
         float iq = (kTwo31 - (0.5f * (float)S + 64.0f)) / den;
         if (!(iq > 0.0f && iq < 1e30f)) iq = 1.0f;
@@ -1138,8 +1143,8 @@ __global__ void __launch_bounds__(NT, MINB) rf_synth_quad_kernel(const RfParams 
 
 size_t quad_smem(const RfParams &p)
 {
-    // the records (4 x Ns per angle) and, before them, the pass-1 bins (Ns + 2 win)
-    return (size_t)p.ag * sizeof(int) * std::max<size_t>(4 * (size_t)p.pr.ns, (size_t)(p.pr.ns + 2 * p.win));
+    // the records (4 x Ns per angle) and, before them, the pass-1 bins (2 x (Ns + 2 win))
+    return (size_t)p.ag * sizeof(int) * std::max<size_t>(4 * (size_t)p.pr.ns, 2 * (size_t)(p.pr.ns + 2 * p.win));
 }
 
 template <typename OutT>
@@ -1324,8 +1329,7 @@ fq_status make_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, RfPa
     // taps t of an echo at delay u have |t - u| <= half_w; the pass-1 sample
     // kp (u in binary32, rounded to nearest) is within 0.51 of u
     const double pitch_k = probe->pitch_x * probe->fs / probe->c;  // adjacent elements' delay difference bound
-    // (the quad spans 3 pitches)
-    p.win = (int)std::floor(hw + 1.5 * pitch_k + 0.52);
+    p.win = (int)std::floor(hw + 0.5 * pitch_k + 0.52);
     {
         const double t = (double)p.kbx * p.kbx;
         p.dbx_far = (float)((1.0 - t / 6.0 + t * t / 120.0) * (1.0 + 1e-6));

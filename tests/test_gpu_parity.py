@@ -188,6 +188,49 @@ def test_rf_kernel_routes(route):
     assert rel_l2(rf[0], want) <= RF_TOL, route
 
 
+def test_rf_quantum_extremes():
+    """The 4-element kernel picks each record's integer quantum from an upper
+    bound of the sum of |taps| per sample, so the int32 records cannot wrap:
+    a coherent pile of 3000 scatterers at one point (the bound is the whole
+    sum), one bright near-field scatterer among weak ones (its record's
+    quantum follows the bright echo; the weak echoes elsewhere keep 1e-4 of
+    their own norm), a large static base, and a single scatterer."""
+    p = W.Probe(8, 1, 0.3e-3, 0.3e-3, 0.3e-3, 0.3e-3, 5e6, 20e6, 1540.0, 0.5, 2, 700)
+    tx, ty = [-0.05, 0.0, 0.08], [0.0] * 3
+    rng = np.random.default_rng(23)
+
+    def run(pos, amp, base=None):
+        got = fq.fq_simulate_rf(p, tx, ty, dev(pos[None]), dev(amp), 1,
+                                rf_base=None if base is None else dev(base))
+        want = oracle.simulate_rf(p, tx, ty, pos, amp, rf=None if base is None else base.astype(np.float64),
+                                  accumulate=base is not None)
+        return host(got)[0], want
+
+    pile = np.tile(np.array([[1e-3], [0.0], [6e-3]], np.float32), (1, 3000))
+    got, want = run(pile, np.ones(3000, np.float32))
+    assert np.abs(want).max() > 1000.0 * np.abs(oracle.simulate_rf(p, tx, ty, pile[:, :1], np.ones(1, np.float32))).max() / 1.001
+    assert rel_l2(got, want) <= RF_TOL
+
+    S = 2000
+    pos = np.stack([rng.uniform(-4e-3, 4e-3, S), np.zeros(S), rng.uniform(8e-3, 16e-3, S)]).astype(np.float32)
+    pos[:, 0] = (0.0, 0.0, 0.4e-3)  # bright echo near t = 0.5 us
+    amp = rng.standard_normal(S).astype(np.float32)
+    amp[0] = 1000.0
+    got, want = run(pos, amp)
+    assert rel_l2(got, want) <= RF_TOL
+    late = np.zeros(want.shape, bool)
+    late[..., 150:] = True  # past the bright echo
+    assert rel_l2(got[late], want[late]) <= 1e-4
+
+    base = (1e4 * rng.standard_normal((3, 8, 700))).astype(np.float32)
+    got, want = run(pos[:, 1:].copy(), amp[1:].copy(), base)
+    assert rel_l2(got, want) <= RF_TOL
+    assert rel_l2(got - base, want - base) <= 1e-3
+
+    got, want = run(pos[:, 5:6].copy(), np.array([0.7], np.float32))
+    assert rel_l2(got, want) <= RF_TOL
+
+
 def test_rf_edge_cases():
     """no scatterers -> zeros; scatterers whose echo straddles the record
     ends keep only the in-record samples."""
