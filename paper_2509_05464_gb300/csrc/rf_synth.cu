@@ -1,17 +1,20 @@
 // rf_synth.cu -- a3 pulse-echo RF synthesis (Eq. 1 restated as a
 // narrowband time-domain sum; App. D; Sec. 2.3).
 //
-// Design (GB300): one CTA owns the complete RF record of E consecutive
-// receive elements for one (frame, transmit) pair and keeps it in shared
-// memory.  Its threads stream every scatterer of the frame once (coalesced
-// structure-of-arrays loads, one scatterer per thread), and for each of the
-// E elements evaluate the delay, amplitude and the pulse taps that land in
-// the record.  Taps are accumulated in fixed point with native shared-memory
-// int32 atomics (hi/lo split, see add_fixed): on this GPU shared-memory FP32
-// atomic adds run as compare-and-swap loops and sustain ~3.7x fewer adds per
-// second than int32 ones.  Nothing is atomically added in global memory: the
-// record is converted back and written out once, coalesced, after the last
-// scatterer.  Integer sums make the RF bit-reproducible.
+// Design (GB300): one CTA owns the complete RF records of E consecutive
+// receive elements for one frame (and one transmit, or a group of transmits
+// in the 4-element kernel) and keeps them in shared memory.  Its threads
+// stream every scatterer of the frame (coalesced structure-of-arrays loads,
+// one scatterer per thread), and for each element evaluate the delay,
+// amplitude and the pulse taps that land in the record.  Taps are
+// accumulated in fixed point with native shared-memory int32 atomics: on this
+// GPU shared-memory FP32 atomic adds run as compare-and-swap loops and
+// sustain ~3.7x fewer adds per second than int32 ones.  The 4-element kernel
+// adds one int32 per tap with a per-record quantum that provably keeps the
+// record in range (see rf_quad_tile); the 2-element and general kernels add
+// a hi/lo pair (see add_fixed).  Nothing is atomically added in global
+// memory: the records are converted back and written out once, coalesced,
+// after the last scatterer.  Integer sums make the RF bit-reproducible.
 //
 // Precision: the delay u = tau fs (hundreds to thousands of samples) must
 // be known to ~1e-6 sample for the carrier phase, so the geometry
