@@ -14,6 +14,7 @@
 // accumulation is FP32.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "batch.cuh"
 #include "fq_internal.cuh"
@@ -88,6 +89,26 @@ __device__ __forceinline__ void rf2iq_tile(const Rf2iqParams &p, int bx, int l, 
     }
 }
 
+// The 8 outputs k .. k + 7 of frame f from the 24 demodulated samples
+// k - 8 .. k + 15 of that frame (taps from the parameters).
+template <typename OutT>
+__device__ __forceinline__ void fir_j8_store(const Rf2iqParams &p, const float2 (&m)[24], int l, int k, int f,
+                                             OutT *__restrict__ iq)
+{
+    constexpr int J = 8, G = 8;
+#pragma unroll
+    for (int o = 0; o < G; ++o) {
+        float re = 0.0f, im = 0.0f;
+#pragma unroll
+        for (int j = -J; j <= J; ++j) {
+            re = fmaf(p.h[j + J], m[o + J - j].x, re);
+            im = fmaf(p.h[j + J], m[o + J - j].y, im);
+        }
+        if (k + o < p.ns && f < p.Fp)
+            fqi::store_c(iq, ((int64_t)l * p.ns + k + o) * p.Fp + f, make_float2(2.0f * re, 2.0f * im));
+    }
+}
+
 // The same tile for the common half-length J = 8 (fs / f0 near 4): the
 // window size is a compile-time constant and each thread filters 8
 // consecutive samples of one frame from a 24-value register window (24
@@ -135,28 +156,13 @@ __device__ __forceinline__ void rf2iq_tile_j8(const Rf2iqParams &p, int bx, int 
     }
     __syncthreads();
     const int fl = threadIdx.x % kFrameChunk, g = threadIdx.x / kFrameChunk;
-    float h[2 * J + 1];
-#pragma unroll
-    for (int j = 0; j < 2 * J + 1; ++j) h[j] = p.h[j];
     // window index of sample n is n - (k0 - J); output k0 + G g + o reads
     // window indices G g + o + J - j, j = -J .. J
     const float2 *src = mix + fl * WS + G * g;
     float2 m[G + 2 * J];
 #pragma unroll
     for (int t = 0; t < G + 2 * J; ++t) m[t] = src[t];
-    const int f = f0 + fl;
-#pragma unroll
-    for (int o = 0; o < G; ++o) {
-        float re = 0.0f, im = 0.0f;
-#pragma unroll
-        for (int j = -J; j <= J; ++j) {
-            re = fmaf(h[j + J], m[o + J - j].x, re);
-            im = fmaf(h[j + J], m[o + J - j].y, im);
-        }
-        const int k = k0 + G * g + o;
-        if (k < p.ns && f < p.Fp)
-            fqi::store_c(iq, ((int64_t)l * p.ns + k) * p.Fp + f, make_float2(2.0f * re, 2.0f * im));
-    }
+    fir_j8_store(p, m, l, k0 + G * g, f0 + fl, iq);
 }
 
 template <typename InT, typename OutT>
@@ -173,6 +179,83 @@ __global__ void __launch_bounds__(256) rf2iq_kernel(const Rf2iqParams p, const I
 {
     extern __shared__ float2 mix[];  // [kFrameChunk][W | 1] then the rotation row [W]
     rf2iq_any<InT, OutT>(p, blockIdx.x, blockIdx.y, blockIdx.z, rf, iq, mix);
+}
+
+// FP32 RF with J = 8 and Ns a multiple of 4: one CTA per (128-sample tile,
+// channel line) walks every frame chunk, with the next chunk's raw samples
+// in flight (cp.async into the other half of a double buffer) while the
+// current one is filtered, so that the loads of a CTA overlap its filter and
+// stores instead of alternating with them.  Same products and sums as
+// rf2iq_tile_j8, so the results are identical.
+constexpr int kStreamRow = 37;  // float4 per frame row in shared memory: odd, so 128-bit reads of 8 rows do not conflict
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename OutT>
+__global__ void __launch_bounds__(256, 3) rf2iq_stream_kernel(const Rf2iqParams p, const float *__restrict__ rf,
+                                                           OutT *__restrict__ iq)
+{
+    constexpr int J = 8, W = kRfTile + 2 * J, G = 8, NV = W / 4;
+    static_assert(NV < kStreamRow && kRfTile == 16 * G, "tile shape");
+    extern __shared__ float4 raw[];  // [2][kFrameChunk][kStreamRow] raw samples, then the rotation row [W]
+    float2 *rot = reinterpret_cast<float2 *>(raw + 2 * kFrameChunk * kStreamRow);
+    const int l = blockIdx.y, k0 = blockIdx.x * kRfTile;
+    const int nch = p.Fp / kFrameChunk;
+    const float *line = rf + (int64_t)l * p.ns;
+    const int64_t fstride = (int64_t)p.L * p.ns;
+    auto issue = [&](int c) {
+        float4 *dst = raw + (c & 1) * kFrameChunk * kStreamRow;
+        for (int i = threadIdx.x; i < kFrameChunk * NV; i += blockDim.x) {
+            const int fl = i / NV, v = i - fl * NV;
+            const int n = k0 - J + 4 * v, f = c * kFrameChunk + fl;
+            const bool ok = f < p.F && n >= 0 && n < p.ns;  // Ns % 4 == 0: a vector is wholly in or out
+            cp_async16(dst + fl * kStreamRow + v, ok ? line + f * fstride + n : rf, ok ? 16 : 0);
+        }
+        cp_async_commit();
+    };
+    issue(0);
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        const int n = k0 - J + i;
+        ff cyc = fqi::ff_mul_f(fqi::ff_load(p.f0_over_fs), (float)n);
+        float fr = fqi::ff_frac(cyc);
+        float sn, cs;
+        sincospif(2.0f * fr, &sn, &cs);
+        rot[i] = make_float2(cs, -sn);
+    }
+    const int fl = threadIdx.x % kFrameChunk, g = threadIdx.x / kFrameChunk;
+    for (int c = 0; c < nch; ++c) {
+        if (c + 1 < nch) {
+            issue(c + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float4 *row = raw + ((c & 1) * kFrameChunk + fl) * kStreamRow + 2 * g;
+        float2 m[G + 2 * J];
+#pragma unroll
+        for (int q = 0; q < (G + 2 * J) / 4; ++q) {
+            const float4 v = row[q];
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float2 r = rot[G * g + 4 * q + t];
+                m[4 * q + t] = make_float2(vv[t] * r.x, vv[t] * r.y);
+            }
+        }
+        fir_j8_store(p, m, l, k0 + G * g, c * kFrameChunk + fl, iq);
+        __syncthreads();  // the buffer is refilled by the next issue
+    }
 }
 
 constexpr int kIqParamBytes = (sizeof(Rf2iqParams) + 15) & ~15;
@@ -226,6 +309,14 @@ bool make_rf2iq_params(const fq_probe *probe, int L, int F, Rf2iqParams &p)
 template <typename InT, typename OutT>
 fq_status launch_rf2iq(const Rf2iqParams &p, const void *rf, void *iq, cudaStream_t st)
 {
+    if constexpr (std::is_same<InT, float>::value) {
+        if (p.J == 8 && p.ns % 4 == 0 && fqi::aligned(rf, 16)) {
+            const size_t smem = sizeof(float4) * 2 * kFrameChunk * kStreamRow + sizeof(float2) * (kRfTile + 16);
+            dim3 grid((p.ns + kRfTile - 1) / kRfTile, p.L);
+            rf2iq_stream_kernel<OutT><<<grid, 256, smem, st>>>(p, (const float *)rf, (OutT *)iq);
+            return fqi::launch_check("fq_rf2iq");
+        }
+    }
     int W = kRfTile + 2 * p.J;
     size_t smem = sizeof(float2) * ((size_t)kFrameChunk * (W | 1) + W);
     dim3 grid((p.ns + kRfTile - 1) / kRfTile, p.L, p.Fp / kFrameChunk);
@@ -402,14 +493,14 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, co
                 }
             }
             // the group's four elements in turn (values shared within the 4 lanes of a pixel)
+            const int ion = on ? i : -1;  // the sample index, or -1 for an element outside the aperture
 #pragma unroll
             for (int j = 0; j < TPP; ++j) {
-                const int ij = __shfl_sync(0xffffffffu, i, j, TPP);
+                const int ij = __shfl_sync(0xffffffffu, ion, j, TPP);
                 const float phj = __shfl_sync(0xffffffffu, phi, j, TPP);
                 const float snj = __shfl_sync(0xffffffffu, sn, j, TPP);
                 const float csj = __shfl_sync(0xffffffffu, cs, j, TPP);
-                const bool onj = __shfl_sync(0xffffffffu, on ? 1 : 0, j, TPP) != 0;
-                if (!onj) continue;
+                if (ij < 0) continue;
                 const ChT *b0 = cha + ((int64_t)(m0 + j) * ns + ij) * row_stride;
                 fqi::f2 v[FPT];
                 InterpFramesF2<FPT, ChT>::run(b0, row_stride, fqi::f2_dup(phj), v);
