@@ -61,6 +61,7 @@ __device__ __forceinline__ double wrap_into(double a, double span)
 struct FrameConst {
     double t, ct, st, kx, ky, kz, wn;
     double dsum[3];
+    bool rigid;  // no elastic gain and no drift: out = P + dsum (1 + 0 and + 0 are exact)
 };
 
 __device__ void frame_constants(const MotionParams &mp, double t, FrameConst &fc)
@@ -79,6 +80,8 @@ __device__ void frame_constants(const MotionParams &mp, double t, FrameConst &fc
         fc.ct = cos(wn * t);
         fc.st = sin(wn * t);
     }
+    fc.rigid = mp.g[0] == 0.0 && mp.g[1] == 0.0 && mp.g[2] == 0.0 && mp.vel[0] == 0.0 && mp.vel[1] == 0.0 &&
+               mp.vel[2] == 0.0;
     fc.dsum[0] = fc.dsum[1] = fc.dsum[2] = 0.0;
     for (int j = 0; j < mp.n_terms; ++j) {
         double sj = mp.amp[j] * sin(2.0 * 3.14159265358979323846 * mp.freq[j] * t + mp.phase[j]);
@@ -110,7 +113,9 @@ __device__ __forceinline__ void advect_point(const float *__restrict__ p0, const
                 P[d] = sg[1 + d] + a * sg[4 + d] + x1 * sg[7 + d] + x2 * sg[10 + d];
         } else {
             double phi = wrap_into(q + v * t / sg[16], sg[17]);
-            double cp = cos(phi), sp = sin(phi), rr = sg[16] + x1;
+            double cp, sp;
+            sincos(phi, &sp, &cp);
+            const double rr = sg[16] + x1;
             for (int d = 0; d < 3; ++d)
                 P[d] = sg[1 + d] + rr * (cp * sg[4 + d] + sp * sg[7 + d]) + x2 * sg[10 + d];
         }
@@ -125,6 +130,12 @@ __device__ __forceinline__ void advect_point(const float *__restrict__ p0, const
         P[0] = cr[0] + w0 * fc.ct + c0 * fc.st + fc.kx * kw * omc;
         P[1] = cr[1] + w1 * fc.ct + c1 * fc.st + fc.ky * kw * omc;
         P[2] = cr[2] + w2 * fc.ct + c2 * fc.st + fc.kz * kw * omc;
+    }
+    if (fc.rigid) {
+        // the general form below with gain 1 + 0 = 1 and drift 0 t = 0, whose
+        // operations are exact: the same doubles
+        for (int d = 0; d < 3; ++d) o[d * S + s] = (float)(P[d] + fc.dsum[d]);
+        return;
     }
     double gain = 1.0 + (mp.g[0] * (Q0 - mp.ce[0]) + mp.g[1] * (Q1 - mp.ce[1]) + mp.g[2] * (Q2 - mp.ce[2]));
     for (int d = 0; d < 3; ++d) o[d * S + s] = (float)(P[d] + mp.vel[d] * t + gain * fc.dsum[d]);
