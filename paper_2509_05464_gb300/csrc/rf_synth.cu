@@ -108,6 +108,23 @@ __device__ __forceinline__ void sincos_poly(float x, float &s, float &c)
     c = fmaf(pc, t, kCosPoly0);
 }
 
+// the same for two arguments in packed f32x2 (the same operations per lane)
+__device__ __forceinline__ void sincos_poly2(fqi::f2 x, fqi::f2 &s, fqi::f2 &c)
+{
+    using namespace fqpoly;
+    using fqi::f2_dup;
+    using fqi::f2_fma;
+    const fqi::f2 t = fqi::f2_mul(x, x);
+    fqi::f2 ps = f2_fma(f2_dup(kSinPoly3), t, f2_dup(kSinPoly2));
+    ps = f2_fma(ps, t, f2_dup(kSinPoly1));
+    ps = f2_fma(ps, t, f2_dup(kSinPoly0));
+    s = fqi::f2_mul(x, ps);
+    fqi::f2 pc = f2_fma(f2_dup(kCosPoly4), t, f2_dup(kCosPoly3));
+    pc = f2_fma(pc, t, f2_dup(kCosPoly2));
+    pc = f2_fma(pc, t, f2_dup(kCosPoly1));
+    c = f2_fma(pc, t, f2_dup(kCosPoly0));
+}
+
 // sin(u) / u for |u| <= 5 (binary32 evaluation error below 2e-7)
 __device__ __forceinline__ float sinc_poly(float u)
 {
@@ -1026,6 +1043,8 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
             RD[e] = R * D * rsa;
             liv[e] = live_e[e] && ok;
         }
+        const f2 RD2[2] = {fqi::f2_make(RD[0], RD[1]), fqi::f2_make(RD[2], RD[3])};
+        const f2 DE2[2] = {fqi::f2_make(0.0f, dee[1]), fqi::f2_make(dee[2], dee[3])};
         for (int al = 0; al < na; ++al) {
             const fqi::AngleFF an = p.ang[a0 + al];
             const ff ptx = fqi::ff_dot3_minus(an.ux, an.uy, an.uz, an.origin, x, y, z);
@@ -1040,46 +1059,61 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
                 fr0 -= c;
                 fl0 += c;
             }
-            const float4 iq4 = *reinterpret_cast<const float4 *>(&sh.invq[al * E]);
-            const float iqe[E] = {iq4.x, iq4.y, iq4.z, iq4.w};
-            float Ae[E], che[E], she[E];
+            // per element pair (0, 1), (2, 3), two lanes of packed f32x2 (element
+            // 0's offset from itself is 0); FRND, MUFU, conversions and
+            // selects stay scalar
+            const ulonglong2 iqv = *reinterpret_cast<const ulonglong2 *>(&sh.invq[al * E]);
+            const f2 IQ2[2] = {f2{iqv.x}, f2{iqv.y}};
+            const f2 FR0 = fqi::f2_dup(fr0), FL0 = fqi::f2_dup(fl0), PH = fqi::f2_dup(path.hi);
+            f2 A2[2], CH2[2], SH2[2];
             int ke[E];
             bool ine[E], nine[E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                float fr, fl, pe;
-                if (e == 0) {
-                    fr = fr0;
-                    fl = fl0;
-                    pe = path.hi;
-                } else {
-                    const float t = fmaf(dee[e], Kh, fr0);
-                    const float c = floorf(t);
-                    fr = t - c;
-                    fl = fl0 + c;
-                    pe = path.hi + dee[e];
-                }
-                float A = RD[e] * iqe[e] * ex2_approx(att_l2 * pe);
-                A = liv[e] ? fminf(fmaxf(A, -kTapMax), kTapMax) : 0.0f;  // one clamp bounds every tap (|p| <= 1)
+            for (int h = 0; h < 2; ++h) {
+                const f2 T = fqi::f2_fma(DE2[h], fqi::f2_dup(Kh), FR0);
+                float t0, t1;
+                fqi::f2_split(T, t0, t1);
+                const f2 C = fqi::f2_make(floorf(t0), floorf(t1));
+                const f2 FR = fqi::f2_sub(T, C);
+                const f2 FL = fqi::f2_add(FL0, C);
+                float q0, q1;
+                fqi::f2_split(fqi::f2_mul(fqi::f2_dup(att_l2), fqi::f2_add(PH, DE2[h])), q0, q1);
+                float a0, a1;
+                fqi::f2_split(fqi::f2_mul(fqi::f2_mul(RD2[h], IQ2[h]), fqi::f2_make(ex2_approx(q0), ex2_approx(q1))), a0,
+                              a1);
+                // one clamp bounds every tap (|p| <= 1)
+                a0 = liv[2 * h] ? fminf(fmaxf(a0, -kTapMax), kTapMax) : 0.0f;
+                a1 = liv[2 * h + 1] ? fminf(fmaxf(a1, -kTapMax), kTapMax) : 0.0f;
+                A2[h] = fqi::f2_make(a0, a1);
                 // taps j = jlo .. jlo + nt - 1 with |j - frac| < half_w: jlo is jmin
                 // or jmin + 1, nt is 8 or 9
-                const bool first_lo = fr <= theta;
-                const int k = (int)(fl + (first_lo ? jmin_f : jmin_f + 1.0f));
-                float ch, sh_;
-                first_tap<true>(p.w_h, fr, thc0, ths0, thc1, ths1, !first_lo, ch, sh_);
-                Ae[e] = A;
-                ke[e] = k;
-                nine[e] = first_lo || fr >= theta2;
-                che[e] = ch;
-                she[e] = sh_;
-                ine[e] = liv[e] && (unsigned)k <= (unsigned)kfast;
+                float fr_0, fr_1;
+                fqi::f2_split(FR, fr_0, fr_1);
+                const bool lo0 = fr_0 <= theta, lo1 = fr_1 <= theta;
+                float k0f, k1f;
+                fqi::f2_split(fqi::f2_add(FL, fqi::f2_make(lo0 ? jmin_f : jmin_f + 1.0f, lo1 ? jmin_f : jmin_f + 1.0f)),
+                              k0f, k1f);
+                ke[2 * h] = (int)k0f;
+                ke[2 * h + 1] = (int)k1f;
+                // first tap (cos, sin)(w (jlo - frac)) = e^{i w jlo} e^{-i w frac}
+                f2 SF, CF;
+                sincos_poly2(fqi::f2_mul(fqi::f2_dup(p.w_h), FR), SF, CF);
+                const f2 TC = fqi::f2_make(lo0 ? thc0 : thc1, lo1 ? thc0 : thc1);
+                const f2 TS = fqi::f2_make(lo0 ? ths0 : ths1, lo1 ? ths0 : ths1);
+                const f2 NTC = fqi::f2_make(lo0 ? -thc0 : -thc1, lo1 ? -thc0 : -thc1);
+                CH2[h] = fqi::f2_fma(CF, TC, fqi::f2_mul(SF, TS));
+                SH2[h] = fqi::f2_fma(TS, CF, fqi::f2_mul(NTC, SF));
+                nine[2 * h] = lo0 || fr_0 >= theta2;
+                nine[2 * h + 1] = lo1 || fr_1 >= theta2;
+                ine[2 * h] = liv[2 * h] && (unsigned)ke[2 * h] <= (unsigned)kfast;
+                ine[2 * h + 1] = liv[2 * h + 1] && (unsigned)ke[2 * h + 1] <= (unsigned)kfast;
             }
             int *rec = tile + al * E * ns;
             int *r0p = rec, *r1p = rec + ns, *r2p = rec + 2 * ns, *r3p = rec + 3 * ns;
-            const f2 A01 = fqi::f2_make(Ae[0], Ae[1]), A23 = fqi::f2_make(Ae[2], Ae[3]);
+            const f2 A01 = A2[0], A23 = A2[1];
             const f2 nhA01 = fqi::f2_mul(NHALF, A01), nhA23 = fqi::f2_mul(NHALF, A23);
-            const f2 CH01 = fqi::f2_make(che[0], che[1]), SH01 = fqi::f2_make(she[0], she[1]);
-            const f2 CH23 = fqi::f2_make(che[2], che[3]), SH23 = fqi::f2_make(she[2], she[3]);
+            const f2 CH01 = CH2[0], SH01 = SH2[0];
+            const f2 CH23 = CH2[1], SH23 = SH2[1];
             // Hann-phase cosines C_j and their negatives N_j = -C_j (exactly:
             // fma is symmetric in sign), so that C_{j+1} = 2 cos(w) C_j - C_{j-1}
             // needs no separate negation
