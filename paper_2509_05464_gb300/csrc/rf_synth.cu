@@ -125,6 +125,22 @@ __device__ __forceinline__ void sincos_poly2(fqi::f2 x, fqi::f2 &s, fqi::f2 &c)
     c = f2_fma(pc, t, f2_dup(kCosPoly0));
 }
 
+// sin(u) / u for two arguments in packed f32x2 (the same operations per lane)
+__device__ __forceinline__ fqi::f2 sinc_poly2(fqi::f2 u)
+{
+    using namespace fqpoly;
+    using fqi::f2_dup;
+    using fqi::f2_fma;
+    const fqi::f2 v = f2_fma(u, u, f2_dup(-kSincCentre));
+    fqi::f2 r = f2_fma(f2_dup(kSincPoly7), v, f2_dup(kSincPoly6));
+    r = f2_fma(r, v, f2_dup(kSincPoly5));
+    r = f2_fma(r, v, f2_dup(kSincPoly4));
+    r = f2_fma(r, v, f2_dup(kSincPoly3));
+    r = f2_fma(r, v, f2_dup(kSincPoly2));
+    r = f2_fma(r, v, f2_dup(kSincPoly1));
+    return f2_fma(r, v, f2_dup(kSincPoly0));
+}
+
 // sin(u) / u for |u| <= 5 (binary32 evaluation error below 2e-7)
 __device__ __forceinline__ float sinc_poly(float u)
 {
@@ -708,6 +724,7 @@ struct QuadShared {
     unsigned wmax[4 * FQ_MAX_ANGLES];  // window maximum of the pass-1 bounds (units)
     unsigned bmax[4 * FQ_MAX_ANGLES];  // largest |static base| (float bits, >= 0)
     float4 angK[FQ_MAX_ANGLES + 1];    // pass 1: fs / c, then per angle (u, -origin) fs / c
+    float4 angFF[2 * FQ_MAX_ANGLES];   // pass 2: per angle (ux, uy) and (uz, origin) as float pairs
 };
 
 // an upper bound of |sin(u) / u| for |u| <= 5 (the fitted directivity's
@@ -829,6 +846,8 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
         if (threadIdx.x > 0) {
             const fqi::AngleFF &an = p.ang[a0 + threadIdx.x - 1];
             g = make_float4(an.ux.hi * K, an.uy.hi * K, an.uz.hi * K, -an.origin.hi * K);
+            sh.angFF[2 * threadIdx.x - 2] = make_float4(an.ux.hi, an.ux.lo, an.uy.hi, an.uy.lo);
+            sh.angFF[2 * threadIdx.x - 1] = make_float4(an.uz.hi, an.uz.lo, an.origin.hi, an.origin.lo);
         }
         sh.angK[threadIdx.x] = g;
     }
@@ -1018,7 +1037,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
         // ---- receive side, every element: delay offset, directivity, R D / r
         const float zy2 = __fadd_rn(zz.hi, q2);  // z^2 (+ dy^2), binary32
         const float r0f = r0 + rl;
-        float RD[E], dee[E];
+        float dxa[E], rsa[E], dee[E];
         bool liv[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -1037,17 +1056,23 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
                 dee[e] = __fdividef(cd[e] * (fmaf(2.0f, x, -csh[e]) - csl[e]), re + r0f);  // r_e - r_0
                 ok = re2 > 0.0f;
             }
-            const float rsa = fminf(rse, kInvRCap);
-            float D = sinc_poly(p.kbx * dxe * rsa);
-            if (matrix) D *= sinc_poly(p.kby * dyh * rsa);
-            RD[e] = R * D * rsa;
+            dxa[e] = dxe;
+            rsa[e] = fminf(rse, kInvRCap);
             liv[e] = live_e[e] && ok;
         }
-        const f2 RD2[2] = {fqi::f2_make(RD[0], RD[1]), fqi::f2_make(RD[2], RD[3])};
+        // R D / r per element pair, D = sinc(k0 w/2 dx / r) (x sinc(k0 h/2 dy / r))
+        f2 RD2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const f2 RS = fqi::f2_make(rsa[2 * h], rsa[2 * h + 1]);
+            f2 D = sinc_poly2(fqi::f2_mul(fqi::f2_mul(fqi::f2_dup(p.kbx), fqi::f2_make(dxa[2 * h], dxa[2 * h + 1])), RS));
+            if (matrix) D = fqi::f2_mul(D, sinc_poly2(fqi::f2_mul(fqi::f2_dup(p.kby * dyh), RS)));
+            RD2[h] = fqi::f2_mul(fqi::f2_mul(fqi::f2_dup(R), D), RS);
+        }
         const f2 DE2[2] = {fqi::f2_make(0.0f, dee[1]), fqi::f2_make(dee[2], dee[3])};
         for (int al = 0; al < na; ++al) {
-            const fqi::AngleFF an = p.ang[a0 + al];
-            const ff ptx = fqi::ff_dot3_minus(an.ux, an.uy, an.uz, an.origin, x, y, z);
+            const float4 g0 = sh.angFF[2 * al], g1 = sh.angFF[2 * al + 1];
+            const ff ptx = fqi::ff_dot3_minus({g0.x, g0.y}, {g0.z, g0.w}, {g1.x, g1.y}, {g1.z, g1.w}, x, y, z);
             ff path = fqi::ff_two_sum(ptx.hi, r0);
             path.lo = __fadd_rn(path.lo, __fadd_rn(ptx.lo, rl));
             const float uh = __fmul_rn(path.hi, Kh);
