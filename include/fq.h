@@ -373,10 +373,16 @@ fq_status fq_bin_scatterers(const float *z, int64_t S, double z0, double dz, int
  *   rf      device [n_frames][A][M][Ns] of out_dtype (FQ_F32 or FQ_BF16),
  *           4-byte aligned
  * Delays use float-float (~48-bit) arithmetic.  Taps are accumulated in
- * fixed point (resolution 2^-20 of the largest |amp| per unit RF, range
- * 2^27 of it), so results are bit-reproducible; a single tap is clamped to
- * 2^17 |amp|max, i.e. scatterers closer than ~8 um to an element centre
- * (far inside the element's near field, outside the model) saturate.
+ * fixed point, so results are bit-reproducible.  For probes whose rows hold
+ * whole groups of 4 elements (two-cycle pulse of 8-9 taps, elements up to
+ * 5/pi wavelengths wide, S < 2^30) every (transmit, element) record is one
+ * int32 per sample with its own quantum, about 2^-31 of an upper bound of
+ * the sum of |taps| at any of its samples (plus the largest |rf_base|), so
+ * the record cannot overflow and its precision is relative to its largest
+ * possible sum; otherwise records are 47-bit (resolution 2^-20 of the
+ * largest |amp|, range 2^27 of it).  1/r is capped at 2^17 per metre:
+ * scatterers closer than ~8 um to an element centre (far inside the
+ * element's near field, outside the model) saturate.
  * Errors: FQ_ERR_INVALID_ARG, FQ_ERR_SHAPE (Ns > 8192, n_angles outside
  * [1, FQ_MAX_ANGLES], M > 65536), FQ_ERR_UNSUPPORTED (out_dtype FQ_F16). */
 fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, const float *pos,
