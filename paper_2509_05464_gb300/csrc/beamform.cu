@@ -14,7 +14,6 @@
 // accumulation is FP32.
 #include <cmath>
 #include <cstring>
-#include <type_traits>
 
 #include "batch.cuh"
 #include "fq_internal.cuh"
@@ -181,14 +180,12 @@ __global__ void __launch_bounds__(256) rf2iq_kernel(const Rf2iqParams p, const I
     rf2iq_any<InT, OutT>(p, blockIdx.x, blockIdx.y, blockIdx.z, rf, iq, mix);
 }
 
-// FP32 RF with J = 8 and Ns a multiple of 4: one CTA per (128-sample tile,
-// channel line) walks every frame chunk, with the next chunk's raw samples
-// in flight (cp.async into the other half of a double buffer) while the
-// current one is filtered, so that the loads of a CTA overlap its filter and
-// stores instead of alternating with them.  Same products and sums as
-// rf2iq_tile_j8, so the results are identical.
-constexpr int kStreamRow = 37;  // float4 per frame row in shared memory: odd, so 128-bit reads of 8 rows do not conflict
-
+// RF with J = 8 and Ns a multiple of the samples per 16 bytes: one CTA per
+// (128-sample tile, channel line) walks every frame chunk, with the next
+// chunk's raw samples in flight (cp.async into the other half of a double
+// buffer) while the current one is filtered, so that the loads of a CTA
+// overlap its filter and stores instead of alternating with them.  Same
+// products and sums as rf2iq_tile_j8, so the results are identical.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -201,25 +198,38 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <typename OutT>
-__global__ void __launch_bounds__(256, 3) rf2iq_stream_kernel(const Rf2iqParams p, const float *__restrict__ rf,
-                                                           OutT *__restrict__ iq)
+template <typename InT>
+struct StreamShape {
+    static constexpr int J = 8, W = kRfTile + 2 * J;
+    static constexpr int VE = 16 / (int)sizeof(InT);  // samples per 16-byte vector
+    static constexpr int NV = W / VE;                 // vectors per frame row
+    static constexpr int ROW = NV + 1;                // odd row stride: 128-bit reads of 8 rows do not conflict
+    static constexpr size_t smem = sizeof(float4) * 2 * kFrameChunk * ROW + sizeof(float2) * W;
+};
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename InT, typename OutT>
+__global__ void __launch_bounds__(256, 3) rf2iq_stream_kernel(const Rf2iqParams p, const InT *__restrict__ rf,
+                                                              OutT *__restrict__ iq)
 {
-    constexpr int J = 8, W = kRfTile + 2 * J, G = 8, NV = W / 4;
-    static_assert(NV < kStreamRow && kRfTile == 16 * G, "tile shape");
-    extern __shared__ float4 raw[];  // [2][kFrameChunk][kStreamRow] raw samples, then the rotation row [W]
-    float2 *rot = reinterpret_cast<float2 *>(raw + 2 * kFrameChunk * kStreamRow);
+    using SS = StreamShape<InT>;
+    constexpr int J = SS::J, W = SS::W, G = 8, VE = SS::VE, NV = SS::NV, ROW = SS::ROW;
+    static_assert(W % VE == 0 && (G * sizeof(InT)) % 16 == 0 && kRfTile == 16 * G, "tile shape");
+    extern __shared__ float4 raw[];  // [2][kFrameChunk][ROW] raw sample vectors, then the rotation row [W]
+    float2 *rot = reinterpret_cast<float2 *>(raw + 2 * kFrameChunk * ROW);
     const int l = blockIdx.y, k0 = blockIdx.x * kRfTile;
     const int nch = p.Fp / kFrameChunk;
-    const float *line = rf + (int64_t)l * p.ns;
+    const InT *line = rf + (int64_t)l * p.ns;
     const int64_t fstride = (int64_t)p.L * p.ns;
     auto issue = [&](int c) {
-        float4 *dst = raw + (c & 1) * kFrameChunk * kStreamRow;
+        float4 *dst = raw + (c & 1) * kFrameChunk * ROW;
         for (int i = threadIdx.x; i < kFrameChunk * NV; i += blockDim.x) {
             const int fl = i / NV, v = i - fl * NV;
-            const int n = k0 - J + 4 * v, f = c * kFrameChunk + fl;
-            const bool ok = f < p.F && n >= 0 && n < p.ns;  // Ns % 4 == 0: a vector is wholly in or out
-            cp_async16(dst + fl * kStreamRow + v, ok ? line + f * fstride + n : rf, ok ? 16 : 0);
+            const int n = k0 - J + VE * v, f = c * kFrameChunk + fl;
+            const bool ok = f < p.F && n >= 0 && n < p.ns;  // Ns % VE == 0: a vector is wholly in or out
+            cp_async16(dst + fl * ROW + v, ok ? line + f * fstride + n : rf, ok ? 16 : 0);
         }
         cp_async_commit();
     };
@@ -241,16 +251,17 @@ __global__ void __launch_bounds__(256, 3) rf2iq_stream_kernel(const Rf2iqParams 
             cp_async_wait<0>();
         }
         __syncthreads();
-        const float4 *row = raw + ((c & 1) * kFrameChunk + fl) * kStreamRow + 2 * g;
+        const float4 *row = raw + ((c & 1) * kFrameChunk + fl) * ROW + G * g / VE;
         float2 m[G + 2 * J];
 #pragma unroll
-        for (int q = 0; q < (G + 2 * J) / 4; ++q) {
-            const float4 v = row[q];
-            const float vv[4] = {v.x, v.y, v.z, v.w};
+        for (int q = 0; q < (G + 2 * J) / VE; ++q) {
+            const float4 v4 = row[q];
+            const InT *vv = reinterpret_cast<const InT *>(&v4);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float2 r = rot[G * g + 4 * q + t];
-                m[4 * q + t] = make_float2(vv[t] * r.x, vv[t] * r.y);
+            for (int t = 0; t < VE; ++t) {
+                const float v = to_f(vv[t]);
+                const float2 r = rot[G * g + VE * q + t];
+                m[VE * q + t] = make_float2(v * r.x, v * r.y);
             }
         }
         fir_j8_store(p, m, l, k0 + G * g, c * kFrameChunk + fl, iq);
@@ -309,13 +320,10 @@ bool make_rf2iq_params(const fq_probe *probe, int L, int F, Rf2iqParams &p)
 template <typename InT, typename OutT>
 fq_status launch_rf2iq(const Rf2iqParams &p, const void *rf, void *iq, cudaStream_t st)
 {
-    if constexpr (std::is_same<InT, float>::value) {
-        if (p.J == 8 && p.ns % 4 == 0 && fqi::aligned(rf, 16)) {
-            const size_t smem = sizeof(float4) * 2 * kFrameChunk * kStreamRow + sizeof(float2) * (kRfTile + 16);
-            dim3 grid((p.ns + kRfTile - 1) / kRfTile, p.L);
-            rf2iq_stream_kernel<OutT><<<grid, 256, smem, st>>>(p, (const float *)rf, (OutT *)iq);
-            return fqi::launch_check("fq_rf2iq");
-        }
+    if (p.J == 8 && p.ns % StreamShape<InT>::VE == 0 && fqi::aligned(rf, 16)) {
+        dim3 grid((p.ns + kRfTile - 1) / kRfTile, p.L);
+        rf2iq_stream_kernel<InT, OutT><<<grid, 256, StreamShape<InT>::smem, st>>>(p, (const InT *)rf, (OutT *)iq);
+        return fqi::launch_check("fq_rf2iq");
     }
     int W = kRfTile + 2 * p.J;
     size_t smem = sizeof(float2) * ((size_t)kFrameChunk * (W | 1) + W);
