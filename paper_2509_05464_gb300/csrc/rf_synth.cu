@@ -1378,6 +1378,7 @@ fq_status make_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, RfPa
     p.two_cycle = probe->n_cycles == 2;
     fqi::make_angles_ff(probe, tx, p.ang);
     // quad kernel: angle groups as large as the record budget allows, balanced
+    // (FQ_RF_AG_KB, 16-200, overrides the budget in KB for tuning)
     const size_t per_angle = 4 * sizeof(int) * (size_t)probe->n_samples;
     size_t budget = kQuadRecordBudget;
     if (const char *env = std::getenv("FQ_RF_AG_KB")) {
