@@ -40,7 +40,7 @@ FLOP_PER_TAP = 10.0
 # capture of rf_synth_quad_kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); None once the kernel changes until it is
 # captured again.
-RF_TRAFFIC_BYTES = 249.54e6 + 995.05e6
+RF_TRAFFIC_BYTES = None
 
 
 def peaks():

@@ -1069,6 +1069,11 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
             if (matrix) D = fqi::f2_mul(D, sinc_poly2(fqi::f2_mul(fqi::f2_dup(p.kby * dyh), RS)));
             RD2[h] = fqi::f2_mul(fqi::f2_mul(fqi::f2_dup(R), D), RS);
         }
+        // the attenuation exp(-att (path_0 + r_e - r_0)) as the per-transmit
+        // factor of element 0 times a per-element factor that does not depend
+        // on the transmit (1 for element 0)
+        RD2[0] = fqi::f2_mul(RD2[0], fqi::f2_make(1.0f, ex2_approx(att_l2 * dee[1])));
+        RD2[1] = fqi::f2_mul(RD2[1], fqi::f2_make(ex2_approx(att_l2 * dee[2]), ex2_approx(att_l2 * dee[3])));
         const f2 DE2[2] = {fqi::f2_make(0.0f, dee[1]), fqi::f2_make(dee[2], dee[3])};
         for (int al = 0; al < na; ++al) {
             const float4 g0 = sh.angFF[2 * al], g1 = sh.angFF[2 * al + 1];
@@ -1089,7 +1094,8 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
             // selects stay scalar
             const ulonglong2 iqv = *reinterpret_cast<const ulonglong2 *>(&sh.invq[al * E]);
             const f2 IQ2[2] = {f2{iqv.x}, f2{iqv.y}};
-            const f2 FR0 = fqi::f2_dup(fr0), FL0 = fqi::f2_dup(fl0), PH = fqi::f2_dup(path.hi);
+            const f2 FR0 = fqi::f2_dup(fr0), FL0 = fqi::f2_dup(fl0);
+            const f2 ATT0 = fqi::f2_dup(ex2_approx(att_l2 * path.hi));
             f2 A2[2], CH2[2], SH2[2];
             int ke[E];
             bool ine[E], nine[E];
@@ -1101,11 +1107,8 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
                 const f2 C = fqi::f2_make(floorf(t0), floorf(t1));
                 const f2 FR = fqi::f2_sub(T, C);
                 const f2 FL = fqi::f2_add(FL0, C);
-                float q0, q1;
-                fqi::f2_split(fqi::f2_mul(fqi::f2_dup(att_l2), fqi::f2_add(PH, DE2[h])), q0, q1);
                 float a0, a1;
-                fqi::f2_split(fqi::f2_mul(fqi::f2_mul(RD2[h], IQ2[h]), fqi::f2_make(ex2_approx(q0), ex2_approx(q1))), a0,
-                              a1);
+                fqi::f2_split(fqi::f2_mul(fqi::f2_mul(RD2[h], IQ2[h]), ATT0), a0, a1);
                 // one clamp bounds every tap (|p| <= 1)
                 a0 = liv[2 * h] ? fminf(fmaxf(a0, -kTapMax), kTapMax) : 0.0f;
                 a1 = liv[2 * h + 1] ? fminf(fmaxf(a1, -kTapMax), kTapMax) : 0.0f;
