@@ -188,6 +188,21 @@ def test_rf_kernel_routes(route):
     assert rel_l2(rf[0], want) <= RF_TOL, route
 
 
+@pytest.mark.parametrize("A,ns", [(1, 1024), (2, 2048), (5, 2048)])
+def test_rf_quad_cta_shapes(A, ns):
+    """The 4-element kernel at each of its CTA shapes: records of 16 KB (four
+    256-thread CTAs per SM), 64 KB (two of 512) and 160 KB (one of 1024)."""
+    p = W.Probe(8, 1, 0.1e-3, 0.1e-3, 0.1e-3, 0.1e-3, 15.6e6, 62.5e6, 1540.0, 0.5, 2, ns)
+    rng = np.random.default_rng(A + ns)
+    S = 300
+    pos = np.stack([rng.uniform(-3e-3, 3e-3, S), np.zeros(S), rng.uniform(1e-3, 20e-3, S)]).astype(np.float32)
+    amp = rng.standard_normal(S).astype(np.float32)
+    tx = list(np.radians(np.linspace(-6.0, 6.0, A))) if A > 1 else [0.0]
+    rf = host(fq.fq_simulate_rf(p, tx, [0.0] * A, dev(pos[None]), dev(amp), 1))
+    want = oracle.simulate_rf(p, tx, [0.0] * A, pos, amp)
+    assert rel_l2(rf[0], want) <= RF_TOL
+
+
 def test_rf_quantum_extremes():
     """The 4-element kernel picks each record's integer quantum from an upper
     bound of the sum of |taps| per sample, so the int32 records cannot wrap:
