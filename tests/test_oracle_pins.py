@@ -272,12 +272,46 @@ def test_das_psf_peak_at_scatterer():
     assert abs(fx - 20) < 0.5 and abs(fz - 20) < 0.5
 
 
+def _das_rows_by_hand(p, th, g):
+    """The paper's per-transmit DAS matrices (Alg. 3 steps 2.2.1-2.2.2)
+    built in the test from the definition: for every pixel and every
+    element in the receive aperture, the two linear-interpolation weights at
+    u = tau fs times the phase rotation e^{+i 2 pi f0 tau}.  Returns one
+    dict {(row, col): value} per transmit."""
+    ex = elem_x(p)
+    xs = g.x0 + np.arange(g.nx) * g.dx
+    zs = g.z0 + np.arange(g.nz) * g.dz
+    mats = []
+    for t in th:
+        ent = {}
+        origin = np.min(ex * math.sin(t))
+        for iz, z in enumerate(zs):
+            for ix, x in enumerate(xs):
+                pidx = iz * g.nx + ix
+                half = np.float32(z) * np.float32(0.5 / g.fnumber)
+                for m in range(p.nx):
+                    if abs(np.float32(x) - np.float32(ex[m])) > half:
+                        continue
+                    tau = (x * math.sin(t) + z * math.cos(t) - origin + math.hypot(x - ex[m], z)) / p.c
+                    u = tau * p.fs
+                    i = math.floor(u)
+                    ph = u - i
+                    if i < 0 or i + 1 >= p.n_samples:
+                        continue
+                    rot = np.exp(2j * math.pi * p.f0 * tau)
+                    ent[(pidx, m * p.n_samples + i)] = (1 - ph) * rot
+                    ent[(pidx, m * p.n_samples + i + 1)] = ph * rot
+        mats.append(ent)
+    return mats
+
+
 def test_das_equals_explicit_das_matrix():
     """The paper precomputes one sparse DAS matrix per transmit and applies
     it to the vectorised IQ of every frame (Sec. 2.4.1, Alg. 3 steps
-    2.2.1-2.4).  The oracle's explicit matrices, applied with a library
-    sparse product, reproduce its direct DAS sum; and a hand-built row
-    from the definition matches the stored one."""
+    2.2.1-2.4).  Matrices built in the test from the definition, applied
+    with a library sparse product and averaged over transmits, reproduce
+    the oracle's direct DAS sum; and the oracle's own explicit matrices
+    equal the hand-built ones entry by entry."""
     import scipy.sparse as sp
     th = np.radians([-4.0, 3.0])
     p = probe(nx=12, pitch=0.3e-3, f0=5e6, fs=20e6, ns=512)
@@ -287,35 +321,100 @@ def test_das_equals_explicit_das_matrix():
     g = W.Grid(7, 1, 9, -1.5e-3, 0.0, 4e-3, 0.5e-3, 0.0, 0.7e-3, 1.0)
     iq_ch = oracle.rf2iq(p, rf)
     direct = oracle.das(p, th, np.zeros(2), iq_ch, g)
-    row_ptr, col, val = oracle.das_matrix(p, th, np.zeros(2), g)
     P = g.nz * g.nx
+    hand = _das_rows_by_hand(p, th, g)
     out = np.zeros((P, F), complex)
-    for a in range(2):
-        lo, hi = row_ptr[a * P], row_ptr[(a + 1) * P]
-        Mtx = sp.csr_matrix((val[lo:hi], col[lo:hi], row_ptr[a * P:(a + 1) * P + 1] - lo),
-                            shape=(P, p.nx * p.n_samples))
+    for a, ent in enumerate(hand):
+        rows = [k[0] for k in ent]
+        cols = [k[1] for k in ent]
+        Mtx = sp.csr_matrix((list(ent.values()), (rows, cols)), shape=(P, p.nx * p.n_samples))
         for f in range(F):
             out[:, f] += Mtx @ iq_ch[f, a].reshape(-1)
-    out /= 2
+    out /= len(th)
     assert np.abs(out - direct).max() <= 1e-12 * np.abs(direct).max()
-    # one row by hand: transmit 1, pixel (ix 3, iz 6)
-    ex = elem_x(p)
-    t, x, z = th[1], g.x0 + 3 * g.dx, g.z0 + 6 * g.dz
-    origin = np.min(ex * math.sin(t))
-    want = {}
-    for m in range(p.nx):
-        if abs(np.float32(x) - np.float32(ex[m])) > np.float32(z) * np.float32(0.5 / g.fnumber):
-            continue
-        tau = (x * math.sin(t) + z * math.cos(t) - origin + math.hypot(x - ex[m], z)) / p.c
-        i = math.floor(tau * p.fs)
-        ph = tau * p.fs - i
-        rot = np.exp(2j * math.pi * p.f0 * tau)
-        want[m * p.n_samples + i] = (1 - ph) * rot
-        want[m * p.n_samples + i + 1] = ph * rot
-    r = 1 * P + 6 * g.nx + 3
-    got = dict(zip(col[row_ptr[r]:row_ptr[r + 1]], val[row_ptr[r]:row_ptr[r + 1]]))
-    assert got.keys() == want.keys()
-    assert max(abs(got[k] - want[k]) for k in want) <= 1e-12
+    # the oracle's stored matrices: same entries, same values, every row
+    row_ptr, col, val = oracle.das_matrix(p, th, np.zeros(2), g)
+    for a, ent in enumerate(hand):
+        got = {}
+        for pidx in range(P):
+            r = a * P + pidx
+            for k in range(row_ptr[r], row_ptr[r + 1]):
+                got[(pidx, int(col[k]))] = val[k]
+        assert got.keys() == ent.keys()
+        assert max(abs(got[k] - ent[k]) for k in ent) <= 1e-12
+
+
+def _pulse(t, f0, T):
+    return np.where(np.abs(t) < 0.5 * T, 0.5 * (1 + np.cos(2 * np.pi * t / T)) * np.cos(2 * np.pi * f0 * t), 0.0)
+
+
+def _lowpass_taps(f0, fs):
+    """rf2iq's filter from its stated definition: Hann-windowed ideal
+    low-pass with cutoff f0, J = 2 round(fs/f0), unit DC gain."""
+    J = 2 * round(fs / f0)
+    j = np.arange(-J, J + 1)
+    h = 2 * f0 / fs * np.sinc(2 * f0 / fs * j) * 0.5 * (1 + np.cos(np.pi * j / (J + 1)))
+    return h / h.sum()
+
+
+@pytest.mark.parametrize("ny", [1, 3])
+def test_das_psf_peak_value_closed_form(ny):
+    """Peak value of the compounded image of one scatterer (T2).  At the
+    scatterer the DAS delay equals the echo's time of flight, so each
+    (transmit, element) term is the echo amplitude A_{a,m} times the
+    demodulated pulse h^(s) = 2 sum_j h_j p(s - j/fs) e^{-i 2 pi f0 (s - j/fs)}
+    linearly interpolated at s = 0 between the samples s = -phi/fs and
+    (1 - phi)/fs; the image value is (1/A) sum_a sum_m w_m of those terms
+    (Sec. 2.4.1, Alg. 3 steps 2.3-2.4, with the echo model of App. D).
+    Pins the absolute scale of rf2iq + DAS: a dropped 1/A, factor 2 or tap
+    normalisation moves the peak."""
+    p = probe(nx=10, ny=ny, pitch=0.3e-3, f0=5e6, fs=20e6, ns=1024)
+    th_x = np.radians([-4.0, 0.0, 6.0])
+    th_y = np.radians([0.0, 2.0, -3.0]) if ny > 1 else np.zeros(3)
+    pos = np.array([[0.35e-3], [0.2e-3 if ny > 1 else 0.0], [9.1e-3]], np.float32)
+    xs, ys, zs = (float(v) for v in pos[:, 0])
+    R = np.array([1.7], np.float32)
+    rf = oracle.simulate_rf(p, th_x, th_y, pos, R)[None].astype(np.float32)
+    g = W.Grid(1, 1, 1, xs, ys, zs, 1e-4, 1e-4, 1e-4, 1.0)
+    got = oracle.beamform(p, th_x, th_y, rf, g)[0, 0]
+
+    ex = (np.arange(p.nx) - 0.5 * (p.nx - 1)) * p.pitch_x
+    ey = (np.arange(ny) - 0.5 * (ny - 1)) * p.pitch_y
+    h = _lowpass_taps(p.f0, p.fs)
+    J = (len(h) - 1) // 2
+    jj = np.arange(-J, J + 1)
+    T = p.n_cycles / p.f0
+    k0 = 2 * math.pi * p.f0 / p.c
+
+    def hhat(s):
+        tt = s - jj / p.fs
+        return 2 * np.sum(h * _pulse(tt, p.f0, T) * np.exp(-2j * math.pi * p.f0 * tt))
+
+    half = np.float32(zs) * np.float32(0.5 / g.fnumber)
+    want = 0.0
+    for a in range(3):
+        sx, sy = math.sin(th_x[a]), math.sin(th_y[a])
+        u = np.array([sx, sy, math.sqrt(1 - sx * sx - sy * sy)])
+        origin = min(u[0] * x + u[1] * y for x in ex for y in ey)
+        for iy in range(ny):
+            for ix in range(p.nx):
+                if abs(np.float32(xs) - np.float32(ex[ix])) > half:
+                    continue
+                if ny > 1 and abs(np.float32(ys) - np.float32(ey[iy])) > half:
+                    continue
+                dx, dy = xs - ex[ix], ys - ey[iy]
+                r = math.sqrt(dx * dx + dy * dy + zs * zs)
+                path = u @ np.array([xs, ys, zs]) - origin + r
+                D = np.sinc(k0 * 0.5 * p.width_x * dx / r / math.pi)
+                if ny > 1:
+                    D *= np.sinc(k0 * 0.5 * p.width_y * dy / r / math.pi)
+                amp = float(R[0]) * D * math.exp(-alpha_np(p) * p.f0 * 1e-6 * path) / r
+                uu = path / p.c * p.fs
+                phi = uu - math.floor(uu)
+                want += amp * ((1 - phi) * hhat(-phi / p.fs) + phi * hhat((1 - phi) / p.fs))
+    want /= 3
+    assert abs(want) > 0
+    assert abs(got - want) <= 1e-6 * abs(want), (got, want)
 
 
 def test_das_mirror_symmetry():
