@@ -54,6 +54,8 @@ def lib():
             L.or_num_threads.restype = _i
             L.or_simulate_rf.argtypes = [_i, _i, _d, _d, _d, _d, _d, _d, _d, _d, _i, _i, _i, _p, _p,
                                          _i64, _p, _p, _i, _p]
+            L.or_simulate_rf_lines.argtypes = [_i, _i, _d, _d, _d, _d, _d, _d, _d, _d, _i, _i, _p, _p, _i, _p,
+                                               _i64, _p, _p, _p]
             L.or_rf2iq_taps.argtypes = [_d, _d, _p]
             L.or_rf2iq_taps.restype = _i
             L.or_rf2iq.argtypes = [_d, _d, _i, _i64, _p, _p]
@@ -109,6 +111,23 @@ def simulate_rf(probe, tilt_x, tilt_y, pos, amp, rf=None, accumulate=False):
                          probe.width_y, probe.f0, probe.fs, probe.c, probe.alpha_db_cm_mhz,
                          probe.n_cycles, probe.n_samples, A, _ptr(tilt_x), _ptr(tilt_y),
                          amp.shape[0], _ptr(pos), _ptr(amp), int(bool(accumulate)), _ptr(rf))
+    return rf
+
+
+def simulate_rf_lines(probe, tilt_x, tilt_y, lines, pos, amp):
+    """RF [n_lines][Ns] float64 of the listed lines a * M + m of simulate_rf."""
+    tilt_x = np.ascontiguousarray(tilt_x, np.float64)
+    tilt_y = np.ascontiguousarray(tilt_y, np.float64)
+    lines = np.ascontiguousarray(lines, np.int32)
+    pos = np.ascontiguousarray(pos, np.float32)
+    amp = np.ascontiguousarray(amp, np.float32)
+    M = probe.nx * probe.ny
+    assert lines.min() >= 0 and lines.max() < tilt_x.shape[0] * M
+    rf = np.zeros((lines.shape[0], probe.n_samples), np.float64)
+    lib().or_simulate_rf_lines(probe.nx, probe.ny, probe.pitch_x, probe.pitch_y, probe.width_x, probe.width_y,
+                               probe.f0, probe.fs, probe.c, probe.alpha_db_cm_mhz, probe.n_cycles,
+                               probe.n_samples, _ptr(tilt_x), _ptr(tilt_y), lines.shape[0], _ptr(lines),
+                               amp.shape[0], _ptr(pos), _ptr(amp), _ptr(rf))
     return rf
 
 

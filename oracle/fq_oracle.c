@@ -100,47 +100,74 @@ static double pulse(double t, double f0, double T)
  * Pinned by: single-scatterer closed form (T1), superposition (T3),
  * attenuation ratio, mirror symmetry (T11).
  * ---------------------------------------------------------------------- */
+/* one RF line (transmit a, element m) of the sum above, added to line[Ns] */
+static void rf_line(int nx, int ny, double px, double py, double wx, double wy, double f0, double fs, double c,
+                    double alpha_db_cm_mhz, int n_cycles, int ns, double tilt_x, double tilt_y, int m, int64_t S,
+                    const float *pos, const float *amp, double *line)
+{
+    const double T = (double)n_cycles / f0;
+    const double k0 = 2.0 * OR_PI * f0 / c;
+    const double alpha_np = alpha_db_cm_mhz * 100.0 / (20.0 / log(10.0)); /* Np / (m MHz) */
+    const double f0_mhz = f0 * 1e-6;
+    const float *X = pos, *Y = pos + S, *Z = pos + 2 * S;
+    double u[3];
+    pw_dir(tilt_x, tilt_y, u);
+    double origin = pw_origin(u, nx, ny, px, py);
+    double ex, ey;
+    element_pos(m, nx, ny, px, py, &ex, &ey);
+    for (int64_t s = 0; s < S; ++s) {
+        double x = X[s], y = Y[s], z = Z[s];
+        double dx = x - ex, dy = y - ey, dz = z;
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r == 0.0) continue;
+        double path_tx = u[0] * x + u[1] * y + u[2] * z - origin;
+        double path = path_tx + r;
+        double tau = path / c;
+        double D = sinc_unnorm(k0 * 0.5 * wx * dx / r);
+        if (ny > 1) D *= sinc_unnorm(k0 * 0.5 * wy * dy / r);
+        double A = (double)amp[s] * D * exp(-alpha_np * f0_mhz * path) / r;
+        int64_t kmin = (int64_t)ceil((tau - 0.5 * T) * fs);
+        int64_t kmax = (int64_t)floor((tau + 0.5 * T) * fs);
+        if (kmin < 0) kmin = 0;
+        if (kmax > ns - 1) kmax = ns - 1;
+        for (int64_t k = kmin; k <= kmax; ++k)
+            line[k] += A * pulse((double)k / fs - tau, f0, T);
+    }
+}
+
 void or_simulate_rf(int nx, int ny, double px, double py, double wx, double wy,
                     double f0, double fs, double c, double alpha_db_cm_mhz, int n_cycles, int ns,
                     int n_ang, const double *tilt_x, const double *tilt_y,
                     int64_t S, const float *pos, const float *amp, int accumulate, double *rf)
 {
     const int M = nx * ny;
-    const double T = (double)n_cycles / f0;
-    const double k0 = 2.0 * OR_PI * f0 / c;
-    const double alpha_np = alpha_db_cm_mhz * 100.0 / (20.0 / log(10.0)); /* Np / (m MHz) */
-    const double f0_mhz = f0 * 1e-6;
-    const float *X = pos, *Y = pos + S, *Z = pos + 2 * S;
-
     #pragma omp parallel for schedule(dynamic, 1)
     for (int am = 0; am < n_ang * M; ++am) {
         int a = am / M, m = am % M;
-        double u[3];
-        pw_dir(tilt_x[a], tilt_y[a], u);
-        double origin = pw_origin(u, nx, ny, px, py);
-        double ex, ey;
-        element_pos(m, nx, ny, px, py, &ex, &ey);
         double *line = rf + (int64_t)am * ns;
         if (!accumulate)
             for (int k = 0; k < ns; ++k) line[k] = 0.0;
-        for (int64_t s = 0; s < S; ++s) {
-            double x = X[s], y = Y[s], z = Z[s];
-            double dx = x - ex, dy = y - ey, dz = z;
-            double r = sqrt(dx * dx + dy * dy + dz * dz);
-            if (r == 0.0) continue;
-            double path_tx = u[0] * x + u[1] * y + u[2] * z - origin;
-            double path = path_tx + r;
-            double tau = path / c;
-            double D = sinc_unnorm(k0 * 0.5 * wx * dx / r);
-            if (ny > 1) D *= sinc_unnorm(k0 * 0.5 * wy * dy / r);
-            double A = (double)amp[s] * D * exp(-alpha_np * f0_mhz * path) / r;
-            int64_t kmin = (int64_t)ceil((tau - 0.5 * T) * fs);
-            int64_t kmax = (int64_t)floor((tau + 0.5 * T) * fs);
-            if (kmin < 0) kmin = 0;
-            if (kmax > ns - 1) kmax = ns - 1;
-            for (int64_t k = kmin; k <= kmax; ++k)
-                line[k] += A * pulse((double)k / fs - tau, f0, T);
-        }
+        rf_line(nx, ny, px, py, wx, wy, f0, fs, c, alpha_db_cm_mhz, n_cycles, ns, tilt_x[a], tilt_y[a], m, S,
+                pos, amp, line);
+    }
+}
+
+/* The same sum for a list of lines only: rf[i] (double [n_lines][Ns]) is
+ * line lines[i] = a * M + m of or_simulate_rf (overwritten).  For sampled
+ * checks of workloads whose full RF is too large for this oracle. */
+void or_simulate_rf_lines(int nx, int ny, double px, double py, double wx, double wy,
+                          double f0, double fs, double c, double alpha_db_cm_mhz, int n_cycles, int ns,
+                          const double *tilt_x, const double *tilt_y, int n_lines, const int32_t *lines,
+                          int64_t S, const float *pos, const float *amp, double *rf)
+{
+    const int M = nx * ny;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n_lines; ++i) {
+        int a = lines[i] / M, m = lines[i] % M;
+        double *line = rf + (int64_t)i * ns;
+        for (int k = 0; k < ns; ++k) line[k] = 0.0;
+        rf_line(nx, ny, px, py, wx, wy, f0, fs, c, alpha_db_cm_mhz, n_cycles, ns, tilt_x[a], tilt_y[a], m, S,
+                pos, amp, line);
     }
 }
 
