@@ -54,8 +54,11 @@ typedef enum fq_status {
 
 typedef enum fq_dtype {
     FQ_F32 = 0,  /* IEEE binary32 */
-    FQ_BF16 = 1, /* bfloat16 storage, FP32 arithmetic */
-    FQ_F16 = 2   /* binary16 storage, FP32 arithmetic */
+    FQ_BF16 = 1, /* bfloat16 storage, FP32 arithmetic (8 significant bits) */
+    FQ_F16 = 2   /* binary16 storage, FP32 arithmetic (11 significant bits);
+                    magnitudes above 65504 are stored as +-65504.  Accepted
+                    for RF (fq_simulate_rf, fq_rf2iq input) and channel IQ
+                    (fq_rf2iq output, fq_das / fq_beamform_das ch_dtype). */
 } fq_dtype;
 
 typedef enum fq_gram_mode {
@@ -370,8 +373,8 @@ fq_status fq_bin_scatterers(const float *z, int64_t S, double z0, double dz, int
  *   pos     device float [n_frames][3][S]
  *   amp     device float [S]
  *   rf_base device float [A][M][Ns] or NULL
- *   rf      device [n_frames][A][M][Ns] of out_dtype (FQ_F32 or FQ_BF16),
- *           4-byte aligned
+ *   rf      device [n_frames][A][M][Ns] of out_dtype (FQ_F32, FQ_BF16 or
+ *           FQ_F16), 4-byte aligned
  * Delays use float-float (~48-bit) arithmetic.  Taps are accumulated in
  * fixed point, so results are bit-reproducible.  For probes whose rows hold
  * whole groups of 4 elements (two-cycle pulse of 8-9 taps, elements up to
@@ -384,7 +387,7 @@ fq_status fq_bin_scatterers(const float *z, int64_t S, double z0, double dz, int
  * scatterers closer than ~8 um to an element centre (far inside the
  * element's near field, outside the model) saturate.
  * Errors: FQ_ERR_INVALID_ARG, FQ_ERR_SHAPE (Ns > 8192, n_angles outside
- * [1, FQ_MAX_ANGLES], M > 65536), FQ_ERR_UNSUPPORTED (out_dtype FQ_F16). */
+ * [1, FQ_MAX_ANGLES], M > 65536), FQ_ERR_UNSUPPORTED (another out_dtype). */
 fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, const float *pos,
                          const float *amp, int64_t S, int32_t n_frames, const float *rf_base,
                          int32_t out_dtype, void *rf, void *stream);
@@ -397,8 +400,9 @@ fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, const float *po
  * exp(-i 2 pi f0 (k-j) / fs), h = Hann-windowed ideal low-pass with cutoff
  * f0, J = 2 round(fs/f0), w_j = (1 + cos(pi j / (J+1))) / 2, normalised to
  * sum 1; RF outside [0, Ns) is 0.
- *   rf      device [n_frames][n_lines][Ns] of rf_dtype (FQ_F32 / FQ_BF16)
- *   iq_ch   device complex [n_lines][Ns][F_pad] of iq_dtype, frames
+ *   rf      device [n_frames][n_lines][Ns] of rf_dtype (FQ_F32 / FQ_BF16 / FQ_F16)
+ *   iq_ch   device complex [n_lines][Ns][F_pad] of iq_dtype (the same
+ *           three), frames
  *           innermost, F_pad = fq_frame_pad(n_frames); padded frames are 0.
  * n_lines = A * M.  J <= 32. */
 int32_t fq_frame_pad(int32_t n_frames);
@@ -414,9 +418,10 @@ fq_status fq_rf2iq(const fq_probe *probe, int32_t n_lines, int32_t n_frames, con
  * decided in binary32 on the coordinates rounded to float.
  * Delays are computed once per (pixel, angle, element) and shared by all
  * frames (the paper's precomputed-DAS-matrix idea, without the matrix).
- *   iq_ch  device complex [A*M][Ns][F_pad] of ch_dtype (fq_rf2iq layout)
+ *   iq_ch  device complex [A*M][Ns][F_pad] of ch_dtype (fq_rf2iq layout;
+ *          FQ_F32, FQ_BF16 or FQ_F16)
  *   iq     device complex [P][n_frames] of iq_dtype (Casorati, frames
- *          contiguous), 8-byte aligned.
+ *          contiguous; FQ_F32 or FQ_BF16), 8-byte aligned.
  * FP32 accumulation, float-float delays. */
 fq_status fq_das(const fq_probe *probe, const fq_tx *tx, const void *iq_ch, int32_t ch_dtype,
                  int32_t n_frames, const fq_grid *grid, int32_t iq_dtype, void *iq, void *stream);

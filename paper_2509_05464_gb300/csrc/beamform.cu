@@ -209,6 +209,7 @@ struct StreamShape {
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
 template <typename InT, typename OutT>
 __global__ void __launch_bounds__(256, 3) rf2iq_stream_kernel(const Rf2iqParams p, const InT *__restrict__ rf,
@@ -338,12 +339,11 @@ fq_status run_rf2iq(const fq_probe *probe, int L, int F, const void *rf, int rf_
     Rf2iqParams p;
     FQ_REQUIRE(make_rf2iq_params(probe, L, F, p), FQ_ERR_SHAPE, "fq_rf2iq: 2 round(fs/f0) must be <= %d",
                kMaxHalfTaps);
-    if (rf_dtype == FQ_F32 && iq_dtype == FQ_F32) return launch_rf2iq<float, float>(p, rf, iq, st);
-    if (rf_dtype == FQ_F32 && iq_dtype == FQ_BF16) return launch_rf2iq<float, __nv_bfloat16>(p, rf, iq, st);
-    if (rf_dtype == FQ_BF16 && iq_dtype == FQ_F32) return launch_rf2iq<__nv_bfloat16, float>(p, rf, iq, st);
-    if (rf_dtype == FQ_BF16 && iq_dtype == FQ_BF16)
-        return launch_rf2iq<__nv_bfloat16, __nv_bfloat16>(p, rf, iq, st);
-    return fqi::set_error(FQ_ERR_UNSUPPORTED, "fq_rf2iq: dtypes must be FQ_F32 or FQ_BF16");
+    return fqi::with_storage(rf_dtype, "fq_rf2iq (rf)", [&](auto *in) {
+        return fqi::with_storage(iq_dtype, "fq_rf2iq (iq)", [&](auto *out) {
+            return launch_rf2iq<fqi::storage_t<decltype(in)>, fqi::storage_t<decltype(out)>>(p, rf, iq, st);
+        });
+    });
 }
 
 // -------------------------------------------------------------------- DAS --
@@ -364,9 +364,10 @@ constexpr int kDasTPP = fqb::kDasThreadsPerPixel;  // threads per pixel
 
 // The N frames of one channel at the interpolated sample i + phi:
 // v = v(i) + phi (v(i + 1) - v(i)).  FP32 channel data interpolate in FP32;
-// BF16 channel data interpolate as packed bf16x2 (re, im) pairs and are
-// widened once afterwards, which keeps the ALU work per frame at the FP32
-// count (the widening of both samples would add four instructions per frame).
+// BF16 and FP16 channel data interpolate as packed bf16x2 / half2 (re, im)
+// pairs and are widened once afterwards, which keeps the ALU work per frame
+// at the FP32 count (the widening of both samples would add four
+// instructions per frame).
 template <int N, typename ChT>
 struct InterpFrames;
 template <>
@@ -383,11 +384,34 @@ struct InterpFrames<4, __nv_bfloat16> {
     }
 };
 
-// The same as packed (re, im) pairs: FP32 channel data are loaded as 64-bit
-// (re, im) words and interpolated with f32x2 instructions (2 per frame
-// instead of 4).
+template <>
+struct InterpFrames<4, __half> {
+    static __device__ __forceinline__ void run(const __half *b0, int64_t stride, float phi, float2 (&v)[4])
+    {
+        const uint4 t0 = __ldg(reinterpret_cast<const uint4 *>(b0));
+        const uint4 t1 = __ldg(reinterpret_cast<const uint4 *>(b0 + stride));
+        const __half2 *a = reinterpret_cast<const __half2 *>(&t0);
+        const __half2 *b = reinterpret_cast<const __half2 *>(&t1);
+        const __half2 ph = __float2half2_rn(phi);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = __half22float2(__hfma2(ph, __hsub2(b[k], a[k]), a[k]));
+    }
+};
+
+// The same as packed (re, im) pairs.  16-bit channel data (BF16 or FP16)
+// interpolate as packed 16-bit pairs and are widened afterwards; FP32
+// channel data are loaded as 64-bit (re, im) words and interpolated with
+// f32x2 instructions (2 per frame instead of 4).
 template <int N, typename ChT>
-struct InterpFramesF2;
+struct InterpFramesF2 {
+    static __device__ __forceinline__ void run(const ChT *b0, int64_t stride, fqi::f2 PHI, fqi::f2 (&v)[N])
+    {
+        float2 w[N];
+        InterpFrames<N, ChT>::run(b0, stride, fqi::f2_lo(PHI), w);
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = fqi::f2_make(w[k].x, w[k].y);
+    }
+};
 template <int N>
 struct InterpFramesF2<N, float> {
     static __device__ __forceinline__ void run(const float *b0, int64_t stride, fqi::f2 PHI, fqi::f2 (&v)[N])
@@ -400,16 +424,6 @@ struct InterpFramesF2<N, float> {
             v[2 * i] = fqi::f2_fma(PHI, fqi::f2_sub(fqi::f2{b.x}, fqi::f2{a.x}), fqi::f2{a.x});
             v[2 * i + 1] = fqi::f2_fma(PHI, fqi::f2_sub(fqi::f2{b.y}, fqi::f2{a.y}), fqi::f2{a.y});
         }
-    }
-};
-template <int N>
-struct InterpFramesF2<N, __nv_bfloat16> {
-    static __device__ __forceinline__ void run(const __nv_bfloat16 *b0, int64_t stride, fqi::f2 PHI, fqi::f2 (&v)[N])
-    {
-        float2 w[N];
-        InterpFrames<N, __nv_bfloat16>::run(b0, stride, fqi::f2_lo(PHI), w);
-#pragma unroll
-        for (int k = 0; k < N; ++k) v[k] = fqi::f2_make(w[k].x, w[k].y);
     }
 };
 
@@ -616,11 +630,12 @@ fq_status run_das(const fq_probe *probe, const fq_tx *tx, const void *ch, int ch
     FQ_REQUIRE(g->fnumber > 0.0, FQ_ERR_INVALID_ARG, "fq_das: fnumber must be > 0");
     DasParams p;
     make_das_params(probe, tx, F, g, p);
-    if (ch_dtype == FQ_F32 && iq_dtype == FQ_F32) return launch_das<float, float>(p, ch, iq, st);
-    if (ch_dtype == FQ_F32 && iq_dtype == FQ_BF16) return launch_das<float, __nv_bfloat16>(p, ch, iq, st);
-    if (ch_dtype == FQ_BF16 && iq_dtype == FQ_F32) return launch_das<__nv_bfloat16, float>(p, ch, iq, st);
-    if (ch_dtype == FQ_BF16 && iq_dtype == FQ_BF16) return launch_das<__nv_bfloat16, __nv_bfloat16>(p, ch, iq, st);
-    return fqi::set_error(FQ_ERR_UNSUPPORTED, "fq_das: dtypes must be FQ_F32 or FQ_BF16");
+    FQ_REQUIRE(iq_dtype == FQ_F32 || iq_dtype == FQ_BF16, FQ_ERR_UNSUPPORTED,
+               "fq_das: the Casorati dtype must be FQ_F32 or FQ_BF16");
+    return fqi::with_storage(ch_dtype, "fq_das (channel IQ)", [&](auto *chp) {
+        using ChT = fqi::storage_t<decltype(chp)>;
+        return iq_dtype == FQ_F32 ? launch_das<ChT, float>(p, ch, iq, st) : launch_das<ChT, __nv_bfloat16>(p, ch, iq, st);
+    });
 }
 
 size_t elem_size(int dtype) { return dtype == FQ_F32 ? 4 : 2; }

@@ -13,7 +13,10 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "../../include/fq.h"
 
@@ -211,6 +214,15 @@ __device__ __forceinline__ float2 load_f2(const __nv_bfloat16 *p, int64_t i)
 __device__ __forceinline__ float load_f(const __nv_bfloat16 *p, int64_t i) { return __bfloat162float(p[i]); }
 __device__ __forceinline__ void store_f(float *p, int64_t i, float v) { p[i] = v; }
 __device__ __forceinline__ void store_f(__nv_bfloat16 *p, int64_t i, float v) { p[i] = __float2bfloat16_rn(v); }
+// binary16 storage: values beyond its largest finite magnitude (65504) are
+// stored as +-65504 instead of overflowing to infinity
+__device__ __forceinline__ float clamp_f16(float v) { return fminf(fmaxf(v, -65504.0f), 65504.0f); }
+__device__ __forceinline__ float load_f(const __half *p, int64_t i) { return __half2float(p[i]); }
+__device__ __forceinline__ float2 load_f2(const __half *p, int64_t i)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(p + i));
+}
+__device__ __forceinline__ void store_f(__half *p, int64_t i, float v) { p[i] = __float2half_rn(clamp_f16(v)); }
 
 // complex element c of an interleaved array
 __device__ __forceinline__ float2 load_c(const float *p, int64_t c)
@@ -230,6 +242,30 @@ __device__ __forceinline__ void store_c(__nv_bfloat16 *p, int64_t c, float2 v)
 {
     reinterpret_cast<__nv_bfloat162 *>(p)[c] = __float22bfloat162_rn(v);
 }
+__device__ __forceinline__ float2 load_c(const __half *p, int64_t c)
+{
+    return __half22float2(reinterpret_cast<const __half2 *>(p)[c]);
+}
+__device__ __forceinline__ void store_c(__half *p, int64_t c, float2 v)
+{
+    reinterpret_cast<__half2 *>(p)[c] = __floats2half2_rn(clamp_f16(v.x), clamp_f16(v.y));
+}
+
+// Calls fn(T *) with a null pointer of the storage type of `dtype` (float,
+// __nv_bfloat16 or __half) and returns its status; any other dtype is
+// FQ_ERR_UNSUPPORTED with a message naming `who`.
+template <typename Fn>
+inline fq_status with_storage(int dtype, const char *who, Fn &&fn)
+{
+    switch (dtype) {
+    case FQ_F32: return fn(static_cast<float *>(nullptr));
+    case FQ_BF16: return fn(static_cast<__nv_bfloat16 *>(nullptr));
+    case FQ_F16: return fn(static_cast<__half *>(nullptr));
+    default: return set_error(FQ_ERR_UNSUPPORTED, "%s: dtype %d is not FQ_F32, FQ_BF16 or FQ_F16", who, dtype);
+    }
+}
+template <typename P>
+using storage_t = std::remove_pointer_t<P>;
 
 // ---------------------------------------------------------- parameters --
 // Per-angle plane-wave constants: direction and time origin, as float-float.

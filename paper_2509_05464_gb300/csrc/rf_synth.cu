@@ -1422,16 +1422,17 @@ extern "C" fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, cons
                "fq_simulate_rf: n_samples must be in [1, 8192]");
     FQ_REQUIRE(probe->f0 > 0 && probe->fs > 0 && probe->c > 0 && probe->n_cycles >= 1, FQ_ERR_INVALID_ARG,
                "fq_simulate_rf: f0, fs, c, n_cycles must be positive");
-    FQ_REQUIRE(out_dtype == FQ_F32 || out_dtype == FQ_BF16, FQ_ERR_UNSUPPORTED,
-               "fq_simulate_rf: out_dtype must be FQ_F32 or FQ_BF16");
+    FQ_REQUIRE(out_dtype == FQ_F32 || out_dtype == FQ_BF16 || out_dtype == FQ_F16, FQ_ERR_UNSUPPORTED,
+               "fq_simulate_rf: out_dtype must be FQ_F32, FQ_BF16 or FQ_F16");
     FQ_REQUIRE(fqi::aligned(rf, 4), FQ_ERR_ALIGN, "fq_simulate_rf: rf must be 4-byte aligned");
 
     RfParams p;
     fq_status bs = make_rf_params(probe, tx, S, p);
     if (bs) return bs;
     cudaStream_t st = (cudaStream_t)stream;
-    if (out_dtype == FQ_F32) return dispatch_rf(p, n_frames, pos, amp, rf_base, (float *)rf, st);
-    return dispatch_rf(p, n_frames, pos, amp, rf_base, (__nv_bfloat16 *)rf, st);
+    return fqi::with_storage(out_dtype, "fq_simulate_rf", [&](auto *out) {
+        return dispatch_rf(p, n_frames, pos, amp, rf_base, (fqi::storage_t<decltype(out)> *)rf, st);
+    });
 }
 
 namespace fqi {

@@ -215,6 +215,11 @@ def _dt(t: torch.Tensor) -> int:
     raise TypeError(f"unsupported dtype {t.dtype}")
 
 
+def _code(dtype) -> int:
+    """torch dtype -> fq_dtype code."""
+    return {torch.float32: FQ_F32, torch.bfloat16: FQ_BF16, torch.float16: FQ_F16}[dtype]
+
+
 def _tdt(code: int):
     return {FQ_F32: torch.float32, FQ_BF16: torch.bfloat16, FQ_F16: torch.float16}[code]
 
@@ -500,7 +505,7 @@ def fq_beamform_das_workspace_size(probe, tilt_x, tilt_y, n_frames, ch_dtype=tor
     pr = make_probe(probe)
     th = _TxHolder(tilt_x, tilt_y)
     n = _SZ(0)
-    code = FQ_F32 if ch_dtype == torch.float32 else FQ_BF16
+    code = _code(ch_dtype)
     _check(lib().fq_beamform_das_workspace_size(C.byref(pr), C.byref(th.st), int(n_frames), code, C.byref(n)))
     return n.value
 
@@ -516,7 +521,7 @@ def fq_beamform_das(probe, tilt_x, tilt_y, rf, n_frames, grid, ch_dtype=torch.fl
     pr = make_probe(probe)
     th = _TxHolder(tilt_x, tilt_y)
     gr = make_grid(grid)
-    code = FQ_F32 if ch_dtype == torch.float32 else FQ_BF16
+    code = _code(ch_dtype)
     _check(lib().fq_beamform_das(C.byref(pr), C.byref(th.st), _ptr(rf), _dt(rf), int(n_frames), C.byref(gr), code,
                                  _dt(iq), _ptr(iq), _ptr(ws), ws.numel(), _stream(stream)))
     return iq

@@ -48,7 +48,8 @@ def test_argument_validation_without_gpu(libfq):
     tx = fq.Tx(1, tx_arr, tx_arr)
     assert libfq.fq_simulate_rf(C.byref(p), C.byref(tx), None, None, 0, 1, None, 0, C.c_void_p(16), None) == 2
     p.n_samples = 1024
-    assert libfq.fq_simulate_rf(C.byref(p), C.byref(tx), None, None, 0, 1, None, 2, C.c_void_p(16), None) == 8
+    # a dtype code outside fq_dtype
+    assert libfq.fq_simulate_rf(C.byref(p), C.byref(tx), None, None, 0, 1, None, 7, C.c_void_p(16), None) == 8
     assert libfq.fq_simulate_rf(C.byref(p), C.byref(tx), None, None, 0, 1, None, 0, C.c_void_p(2), None) == 3
     n = C.c_size_t(0)
     assert libfq.fq_clutter_svd_workspace_size(65536, 200, 0, C.byref(n)) == 0 and n.value > 0
