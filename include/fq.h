@@ -509,8 +509,11 @@ fq_status fq_clutter_svd(const void *iq, int32_t dtype, int64_t P, int32_t F, in
  *   - Every call uses the same array and leaves its contents behind: calls
  *     whose work overlaps on the GPU (unordered streams, or several host
  *     threads) race with each other and give wrong results.
- *   - The eigen-solver convergence flag is kept in the array and is not
- *     reported by this call.
+ *   - The device-side status word (eigen-solver convergence) is kept in
+ *     the array: fq_clutter_status(NULL, stream) reads and clears it, as
+ *     for the workspace of fq_clutter_svd.
+ *   - The cached address is looked up again when the device's current
+ *     context has changed (for instance after cudaDeviceReset).
  * Arguments and results are those of fq_clutter_svd with gram_mode
  * FQ_GRAM_F32 (iq_f, pd, eigvals, k_used nullable; everything stays on the
  * device). */
@@ -526,8 +529,9 @@ fq_status fq_power_doppler(const void *iq_f, int32_t dtype, int64_t P, int32_t F
 /* Device-side status word of the calls that decide on the device
  * (eigen-solver convergence, a timed-out tensor-core wait).  Reads and
  * clears the flag the last fq_hermitian_eig / fq_clutter_svd (or
- * tensor-core fq_casorati_gram) on this workspace wrote; synchronises
- * `stream`. */
+ * tensor-core fq_casorati_gram) on this workspace wrote; workspace NULL
+ * reads the built-in array of fq_clutter_svd_noalloc on the current device.
+ * Synchronises `stream`. */
 fq_status fq_clutter_status(void *workspace, void *stream);
 
 /* Test hook (the paper has no counterpart).  FQ_DEBUG_SKIP_TC_LOADS = 1

@@ -12,6 +12,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>  // driver types only: the two driver calls are fetched at run time
+
 #include "batch.cuh"
 #include "fq_internal.cuh"
 
@@ -909,24 +911,57 @@ ClutterLayout layout_capped(int64_t P, int F, int max_chunks)
     return L;
 }
 
-// Device address of the scratch array on the current device, looked up
-// once per device (with that device current) and cached.
+// Unique ID of the calling thread's current CUDA context (0 if none), from
+// the driver's cuCtxGetCurrent / cuCtxGetId, fetched once through the
+// runtime so that the library needs no link to the driver library.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetId)f;
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device.  It is looked
+// up (with that device current) the first time and again whenever the
+// device's current context has changed since (a device reset destroys the
+// context that the cached address belongs to), and cached otherwise.
 fq_status noalloc_scratch(char **out)
 {
     constexpr int kMaxDevices = 64;
     static void *addr[kMaxDevices] = {};
+    static unsigned long long ctx_id[kMaxDevices] = {};
     static std::mutex mu;
     int dev = 0;
     fq_status s = fqi::cuda_check(cudaGetDevice(&dev), "fq_clutter_svd_noalloc: cudaGetDevice");
     if (s) return s;
     FQ_REQUIRE(dev >= 0 && dev < kMaxDevices, FQ_ERR_UNSUPPORTED, "fq_clutter_svd_noalloc: device ordinal %d", dev);
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    const unsigned long long id = current_context_id();
+    if (!addr[dev] || id == 0 || id != ctx_id[dev]) {
         void *p = nullptr;
         s = fqi::cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch),
                             "fq_clutter_svd_noalloc: cudaGetSymbolAddress");
         if (s) return s;
         addr[dev] = p;
+        ctx_id[dev] = current_context_id();  // the lookup makes the device's context current if it was not
     }
     *out = (char *)addr[dev];
     return FQ_OK;
@@ -1077,7 +1112,12 @@ fq_status fq_power_doppler(const void *iq_f, int32_t dtype, int64_t P, int32_t F
 
 fq_status fq_clutter_status(void *workspace, void *stream)
 {
-    FQ_REQUIRE(workspace, FQ_ERR_INVALID_ARG, "fq_clutter_status: null workspace");
+    if (!workspace) {  // the built-in array of fq_clutter_svd_noalloc on the current device
+        char *ws = nullptr;
+        fq_status s = noalloc_scratch(&ws);
+        if (s) return s;
+        workspace = ws;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     int flag = 0;
     fq_status s = fqi::cuda_check(cudaMemcpyAsync(&flag, workspace, sizeof(int), cudaMemcpyDeviceToHost, st),
