@@ -66,7 +66,7 @@ struct fq_batch {
     std::vector<Wave> waves;
     int rf_tune = 3, das_threads = 128;  // RF register budget (see fq_tile_choice), DAS CTA size
     bool rf_quad = true;  // every member's rows hold whole element quads
-    int ns_max = 0, J_max = 0, M_max = 0;
+    int ns_max = 0, J_max = 0, M_max = 0, A_max = 0;
     size_t rf_smem = 0;  // dynamic shared memory of the RF stage kernel
     size_t off_counters = 0, off_status = 0, off_ens = 0, off_params = 0, off_queues = 0, off_scratch = 0, total = 0;
     std::vector<unsigned char> params;  // host image of the parameter blocks
@@ -126,7 +126,9 @@ void item_grids(fq_batch *b, EnsHost &h)
     h.items[ST_RF] = h.gx[ST_RF] * rf_groups * h.F;
     h.gx[ST_RF2IQ] = cdiv(h.ns, kIqTile); h.gy[ST_RF2IQ] = h.L;
     h.items[ST_RF2IQ] = h.gx[ST_RF2IQ] * h.L * (h.Fp / kFrameChunkB);
-    h.gx[ST_DAS] = cdiv(h.P, b->das_threads / kDasThreadsPerPixel); h.gy[ST_DAS] = h.Fp / kFrameChunkB;
+    // DAS tiles: das_threads / kDasThreadsPerPixel voxels along x of one (y, z) row each
+    h.gx[ST_DAS] = cdiv(h.d.grid.nx, b->das_threads / kDasThreadsPerPixel) * h.d.grid.ny * h.d.grid.nz;
+    h.gy[ST_DAS] = h.Fp / kFrameChunkB;
     h.items[ST_DAS] = h.gx[ST_DAS] * h.gy[ST_DAS];
     const int nt = cdiv(h.F, 32);
     h.gx[ST_GRAM] = nt * (nt + 1) / 2; h.gy[ST_GRAM] = h.n_chunks; h.items[ST_GRAM] = h.gx[ST_GRAM] * h.n_chunks;
@@ -283,7 +285,7 @@ fq_status launch_stage(fq_batch *b, char *arena, int w, int s, cudaStream_t st)
     case fqb::ST_RF: return fqi::batched_rf(ens, q, q.total, b->rf_dtype, b->rf_smem, b->rf_tune, b->rf_quad, st);
     case fqb::ST_RF2IQ: return fqi::batched_rf2iq(ens, q, q.total, b->rf_dtype, b->ch_dtype, b->J_max, st);
     case fqb::ST_DAS:
-        return fqi::batched_das(ens, q, q.total, b->ch_dtype, b->iq_dtype, b->M_max, b->das_threads, st);
+        return fqi::batched_das(ens, q, q.total, b->ch_dtype, b->iq_dtype, b->M_max, b->A_max, b->ns_max, b->das_threads, st);
     case fqb::ST_GRAM: return fqi::batched_gram(ens, q, q.total, b->iq_dtype, st);
     case fqb::ST_GRAM_REDUCE: return fqi::batched_gram_reduce(ens, q, q.total, st);
     case fqb::ST_EIG:
@@ -394,7 +396,7 @@ fq_status fq_batch_plan(const fq_ensemble_desc *ens, int32_t n, int32_t rf_dtype
         h.par_seg = po; fqi::build_seg_table(&d.flow, pb + po); po += seg_b;
         h.par_mot = po; fqi::build_motion(&d.motion, pb + po); po += mot_b;
         h.par_rf = po;
-        s = fqi::build_rf_params(&d.probe, &d.tx, d.S, pb + po);
+        s = fqi::build_rf_params(&d.probe, &d.tx, d.S, rf_dtype, pb + po);
         if (!s && !fqi::rf_ntap_ok(pb + po))
             s = fqi::set_error(FQ_ERR_UNSUPPORTED, "batch: ensemble %d: the batched RF kernel needs 8 <= n_cycles fs / f0 < 9", i);
         po += rf_b;
@@ -413,6 +415,7 @@ fq_status fq_batch_plan(const fq_ensemble_desc *ens, int32_t n, int32_t rf_dtype
         b->ns_max = std::max(b->ns_max, h.ns);
         b->J_max = std::max(b->J_max, h.J);
         b->M_max = std::max(b->M_max, h.M);
+        b->A_max = std::max(b->A_max, h.A);
     }
     for (int i = 0; i < n; ++i)
         b->rf_quad = b->rf_quad && fqi::use_rf_quad(b->e[i].d.probe.nx) && fqi::rf_quad_ok(b->params.data() + b->e[i].par_rf);

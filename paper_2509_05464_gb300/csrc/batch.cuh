@@ -154,7 +154,7 @@ fq_status batched_rf(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items
 fq_status batched_rf2iq(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int rf_dtype, int ch_dtype,
                         int J_max, cudaStream_t st);
 fq_status batched_das(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int ch_dtype, int iq_dtype,
-                      int M_max, int threads, cudaStream_t st);
+                      int M_max, int A_max, int ns_max, int threads, cudaStream_t st);
 fq_status batched_gram(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int iq_dtype, cudaStream_t st);
 fq_status batched_gram_reduce(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, cudaStream_t st);
 fq_status batched_eig(const fqb::EnsDev *ens, const int *members, int n, cudaStream_t st);
@@ -168,7 +168,7 @@ size_t motion_bytes();
 void build_seg_table(const fq_flow *flow, void *out);
 void build_motion(const fq_motion *m, void *out);
 size_t rf_params_bytes();
-fq_status build_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, void *out);
+fq_status build_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, int out_dtype, void *out);
 int rf_ntap_ok(const void *rf_params);  // the packed-pair pulse kernel applies
 bool use_rf_quad(int nx);               // the quad-element RF kernel applies to this probe
 bool rf_quad_ok(const void *rf_params);  // ... and to these sizes (records fit in shared memory)

@@ -12,11 +12,14 @@
 // Precision: delays, interpolation index and carrier phase are float-float;
 // the aperture decision is binary32 on coordinates rounded from IEEE double;
 // accumulation is FP32.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "batch.cuh"
 #include "fq_internal.cuh"
+#include "rf_poly.cuh"
 
 namespace {
 
@@ -356,6 +359,8 @@ struct DasParams {
     double x0, y0, z0, dx, dy, dz;
     float half_per_z;   // 1 / (2 f#)
     float inv_A;
+    int rot_tab;        // carrier phase from a per-sample table (see das_smem_bytes)
+    float pi_f0_fs;     // pi f0 / fs
     fqi::AngleFF ang[FQ_MAX_ANGLES];
 };
 
@@ -427,41 +432,108 @@ struct InterpFramesF2<N, float> {
     }
 };
 
-// One tile with TPP threads per pixel (TPP = 4 or 8): pixels
-// bx * blockDim.x / TPP .., frames 16 by .. 16 by + 15.  Thread (pixel, part
-// q) accumulates frames FPT q .. FPT q + FPT - 1, FPT = 16 / TPP.  Elements
-// go in groups of TPP: the threads of a pixel evaluate the float-float delays
-// of TPP different elements, share them by shuffles within the group, and
-// each reads its slice of the two interpolation samples, so that a warp
-// load covers 32 / TPP whole rows instead of 32 partial ones.  `etab` is the
-// dynamic shared memory (6 M floats).
+// (sin x, cos x) for |x| <= 0.8 from the fitted polynomials of rf_poly.cuh
+// (binary32 evaluation error below 6e-8)
+__device__ __forceinline__ void das_sincos_poly(float x, float &s, float &c)
+{
+    using namespace fqpoly;
+    const float t = x * x;
+    s = x * fmaf(fmaf(fmaf(kSinPoly3, t, kSinPoly2), t, kSinPoly1), t, kSinPoly0);
+    c = fmaf(fmaf(fmaf(fmaf(kCosPoly4, t, kCosPoly3), t, kCosPoly2), t, kCosPoly1), t, kCosPoly0);
+}
+
+// Tiles and their order.  A CTA of W = blockDim.x / TPP pixel columns
+// takes W consecutive voxels along x of one (y, z) row, and CTAs are
+// numbered x-block fastest, then y, then z: the CTAs resident at one time
+// cover a thin slab of depths over the whole lateral extent.  A channel
+// line is then needed only over the band of samples that the slab's
+// delays reach (for the 3D workload about a tenth of the record), which
+// stays in L2 while the slab is beamformed, instead of every sample of
+// every line (ordering by x, then z, then y made every resident set span
+// all depths: the 3D DAS read its channel data from DRAM ~50 times).
+__host__ __device__ inline int64_t das_ctas(int gx, int gy, int gz, int W)
+{
+    return (int64_t)((gx + W - 1) / W) * gy * gz;
+}
+
+// Dynamic shared memory of a DAS tile of T threads (W = T / TPP pixels):
+// element abscissae per column and ordinates per row (3 floats each, nx + ny
+// <= M + 1), each pixel's transmit path per angle (A W float pairs) and the
+// per-sample carrier table (rot_ns float pairs).
+// Offsets in floats, each a multiple of 4 (16 bytes), so that the float2
+// tables stay aligned.
+__host__ __device__ inline int das_off_ptx(int M) { return (3 * (M + 1) + 3) & ~3; }
+__host__ __device__ inline int das_off_acc(int M, int A, int W) { return das_off_ptx(M) + ((2 * A * W + 3) & ~3); }
+__host__ __device__ inline int das_off_rot(int M, int A, int W) { return das_off_acc(M, A, W); }
+// rot_ns: samples of the per-sample carrier table (0 = no table)
+__host__ __device__ inline size_t das_smem_bytes(int M, int A, int T, int TPP, int rot_ns)
+{
+    const int W = T / TPP;
+    return sizeof(float) * (size_t)das_off_rot(M, A, W) + sizeof(float2) * (size_t)rot_ns;
+}
+// The carrier phase e^{i 2 pi f0 tau} = e^{i 2 pi (f0/fs) i} e^{i 2 pi (f0/fs) phi}
+// (u = tau fs = i + phi) comes from a per-sample table and a short
+// polynomial when the table fits (ns <= kRotTabMax) and the second angle's
+// half stays inside the polynomial's range (pi f0 / fs <= 0.8, i.e. at least
+// ~3.93 samples per carrier period: every workload here samples at ~4 f0).
+constexpr int kRotTabMax = 2048;
+inline bool das_rot_tab(const fq_probe *probe)
+{
+    return probe->n_samples <= kRotTabMax && M_PI * probe->f0 / probe->fs <= (double)fqpoly::kTapXMax;
+}
+
+// One tile with TPP threads per pixel: W pixels along x, frames 16 by ..
+// 16 by + 15.  Thread (pixel, part q) accumulates frames FPT q .. FPT q +
+// FPT - 1, FPT = 16 / TPP.  The pixels of a CTA share y and z, so the rows
+// of a matrix probe inside the receive aperture are the same for all of
+// them; a warp walks those rows and, in each, the columns that the
+// aperture of any of its pixels can reach, in groups of TPP elements.  The
+// threads of a pixel evaluate the float-float receive distances of TPP
+// different elements once and reuse them for every transmit (the transmit
+// paths of the pixel sit in shared memory); per transmit they form the
+// delays, share them by shuffles within the group, and each reads its slice
+// of the two interpolation samples, so that a warp load covers 32 / TPP
+// whole rows.  Sums over transmits and elements are in that order (element
+// outer, transmit inner).  `etab` is the dynamic shared memory
+// (das_smem_bytes).
 template <int TPP, typename ChT, typename OutT>
-__device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, const ChT *__restrict__ ch,
+__device__ __forceinline__ void das_tile4(const DasParams &p, int64_t bx, int by, const ChT *__restrict__ ch,
                                           OutT *__restrict__ iq, float *etab)
 {
     constexpr int FPT = kFrameChunk / TPP;
-    const int M = p.pr.M;
-    float *exf = etab, *exh = etab + M, *exl = etab + 2 * M;
-    float *eyf = etab + 3 * M, *eyh = etab + 4 * M, *eyl = etab + 5 * M;
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        int ix = m % p.pr.nx, iy = m / p.pr.nx;
-        double ex = __dmul_rn(__dsub_rn((double)ix, __dmul_rn(0.5, (double)(p.pr.nx - 1))), p.pitch_x);
-        double ey = __dmul_rn(__dsub_rn((double)iy, __dmul_rn(0.5, (double)(p.pr.ny - 1))), p.pitch_y);
-        fqi::df2 sx = fqi::split_double(ex), sy = fqi::split_double(ey);
-        exf[m] = (float)ex; exh[m] = sx.hi; exl[m] = sx.lo;
-        eyf[m] = (float)ey; eyh[m] = sy.hi; eyl[m] = sy.lo;
+    const int M = p.pr.M, nxe = p.pr.nx, nye = p.pr.ny;
+    const int W = blockDim.x / TPP;
+    // element m = row * nx + column sits at (x[column], y[row]): the probe is
+    // separable, so the tables hold one abscissa per column and one ordinate
+    // per row (binary32, and the float pair hi + lo)
+    float *exf = etab, *exh = etab + nxe, *exl = etab + 2 * nxe;
+    float *eyf = etab + 3 * nxe, *eyh = eyf + nye, *eyl = eyf + 2 * nye;
+    float2 *ptx_s = reinterpret_cast<float2 *>(etab + das_off_ptx(M));       // [A][W] transmit path (hi, lo)
+    float2 *rot_s = reinterpret_cast<float2 *>(etab + das_off_rot(M, p.A, W));  // [ns] carrier table
+    for (int c = threadIdx.x; c < nxe + nye; c += blockDim.x) {
+        const bool isx = c < nxe;
+        const int i = isx ? c : c - nxe, n = isx ? nxe : nye;
+        const double e = __dmul_rn(__dsub_rn((double)i, __dmul_rn(0.5, (double)(n - 1))), isx ? p.pitch_x : p.pitch_y);
+        const fqi::df2 sp = fqi::split_double(e);
+        if (isx) {
+            exf[i] = (float)e; exh[i] = sp.hi; exl[i] = sp.lo;
+        } else {
+            eyf[i] = (float)e; eyh[i] = sp.hi; eyl[i] = sp.lo;
+        }
     }
-    __syncthreads();
 
     const int q = threadIdx.x % TPP;  // frame part, and element slot within a group of TPP
-    const int64_t pix = (int64_t)bx * (blockDim.x / TPP) + (threadIdx.x / TPP);
+    const int col = threadIdx.x / TPP;
+    const int nxb = (p.gx + W - 1) / W;
+    const int xb = (int)(bx % nxb);
+    const int64_t t = bx / nxb;
+    const int iy = (int)(t % p.gy);
+    const int iz = (int)(t / p.gy);
+    const int ix = xb * W + col;
+    const bool live = ix < p.gx && iz < p.gz;
+    const int64_t pix = ((int64_t)iy * p.gz + iz) * p.gx + ix;
     const int fbase = by * kFrameChunk;
-    const bool live = pix < p.P;
-    const int64_t pp = live ? pix : 0;
-    const int ix = (int)(pp % p.gx);
-    const int iz = (int)((pp / p.gx) % p.gz);
-    const int iy = (int)(pp / ((int64_t)p.gx * p.gz));
-    const double xd = __dadd_rn(p.x0, __dmul_rn((double)ix, p.dx));
+    const double xd = __dadd_rn(p.x0, __dmul_rn((double)(live ? ix : 0), p.dx));
     const double yd = __dadd_rn(p.y0, __dmul_rn((double)iy, p.dy));
     const double zd = __dadd_rn(p.z0, __dmul_rn((double)iz, p.dz));
     const float xf = (float)xd, yf = (float)yd, zf = (float)zd;
@@ -469,88 +541,162 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int bx, int by, co
     const ff X = {xs.hi, xs.lo}, Y = {ys.hi, ys.lo}, Z = {zs.hi, zs.lo};
     const ff zz = fqi::ff_sqr(Z);
     const float half = __fmul_rn(zf, p.half_per_z);
-    const bool matrix = p.pr.ny > 1;
+    const bool matrix = nye > 1;
     const ff fs_c = fqi::ff_load(p.pr.fs_over_c);
     const ff f0_fs = fqi::ff_load(p.pr.f0_over_fs);
     const int ns = p.pr.ns;
     const int64_t row_stride = (int64_t)p.Fp * 2;  // scalars per channel sample (all frames)
+    const int64_t line_stride = (int64_t)ns * row_stride;
 
+    // the carrier table: rot[n] = e^{i 2 pi frac(n f0 / fs)}
+    if (p.rot_tab) {
+        for (int n = threadIdx.x; n < ns; n += blockDim.x) {
+            float sn, cs;
+            sincospif(2.0f * fqi::ff_frac(fqi::ff_mul(f0_fs, ff{(float)n, 0.0f})), &sn, &cs);
+            rot_s[n] = make_float2(cs, sn);
+        }
+    }
+    // this pixel's transmit path u_a . r - origin per angle (float-float)
+    if (q == 0) {
+        for (int a = 0; a < p.A; ++a) {
+            const fqi::AngleFF an = p.ang[a];
+            ff ptx = fqi::ff_add(fqi::ff_mul(fqi::ff_load(an.ux), X), fqi::ff_mul(fqi::ff_load(an.uy), Y));
+            ptx = fqi::ff_add(ptx, fqi::ff_mul(fqi::ff_load(an.uz), Z));
+            ptx = fqi::ff_add(ptx, fqi::ff_neg(fqi::ff_load(an.origin)));
+            ptx_s[a * W + col] = make_float2(ptx.hi, ptx.lo);
+        }
+    }
+    __syncthreads();
+
+    // element rows inside the aperture (the same for every pixel of the CTA:
+    // they share y and z), decided in binary32 like every element below
+    int row_lo = 0, row_hi = nye - 1;
+    if (matrix) {
+        row_lo = nye;
+        row_hi = -1;
+        for (int r = 0; r < nye; ++r) {
+            if (fabsf(__fsub_rn(yf, eyf[r])) <= half) {
+                row_lo = min(row_lo, r);
+                row_hi = r;
+            }
+        }
+    }
+    // columns the aperture of any pixel of the warp can reach: an estimate
+    // one column wider on each side (the per-element test below decides)
+    int c_lo = nxe, c_hi = -1;
+    if (live) {
+        if (nxe > 1 && p.pitch_x > 0.0) {
+            const float c0f = 0.5f * (float)(nxe - 1);
+            const float ip = (float)(1.0 / p.pitch_x);
+            const float lo = fminf(fmaxf(floorf((xf - half) * ip + c0f), -2.0f), (float)nxe + 1.0f);
+            const float hi = fminf(fmaxf(ceilf((xf + half) * ip + c0f), -2.0f), (float)nxe + 1.0f);
+            c_lo = max(0, (int)lo - 1);
+            c_hi = min(nxe - 1, (int)hi + 1);
+        } else {
+            c_lo = 0;
+            c_hi = nxe - 1;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c_lo = min(c_lo, __shfl_xor_sync(0xffffffffu, c_lo, o));
+        c_hi = max(c_hi, __shfl_xor_sync(0xffffffffu, c_hi, o));
+    }
+
+    // sum of v cos and sum of v sin per frame, as (re, im) pairs: the rotated
+    // sum is (C.re - S.im, C.im + S.re)
     // sum of v cos and sum of v sin per frame, as (re, im) pairs: the rotated
     // sum is (C.re - S.im, C.im + S.re)
     fqi::f2 accC[FPT], accS[FPT];
 #pragma unroll
     for (int k = 0; k < FPT; ++k) accC[k] = accS[k] = fqi::f2_dup(0.0f);
+    const ChT *chp = ch + (fbase + FPT * q) * 2;
 
-    for (int a = 0; a < p.A; ++a) {
-        const fqi::AngleFF an = p.ang[a];
-        ff ptx = fqi::ff_add(fqi::ff_mul(fqi::ff_load(an.ux), X), fqi::ff_mul(fqi::ff_load(an.uy), Y));
-        ptx = fqi::ff_add(ptx, fqi::ff_mul(fqi::ff_load(an.uz), Z));
-        ptx = fqi::ff_add(ptx, fqi::ff_neg(fqi::ff_load(an.origin)));
-        const ChT *cha = ch + (int64_t)a * M * ns * row_stride + (fbase + FPT * q) * 2;
-        for (int m0 = 0; m0 < M; m0 += TPP) {
+    for (int r = row_lo; r <= row_hi; ++r) {
+        for (int g0 = c_lo; g0 <= c_hi; g0 += TPP) {
             // this thread's element of the group
-            const int m = m0 + q;
-            bool on = live && m < M;
-            const int mm = on ? m : 0;
-            on = on && fabsf(__fsub_rn(xf, exf[mm])) <= half;
-            if (matrix) on = on && fabsf(__fsub_rn(yf, eyf[mm])) <= half;
+            const int cq = g0 + q;
+            const int cc = min(cq, nxe - 1);
+            const bool on = live && cq <= c_hi && fabsf(__fsub_rn(xf, exf[cc])) <= half;
             if (!__any_sync(0xffffffffu, on)) continue;
-            int i = 0;
-            float phi = 0.0f, sn = 0.0f, cs = 1.0f;
+            ff rm = {0.0f, 0.0f};
             if (on) {
-                ff dxx = fqi::ff_add(X, ff{-exh[mm], -exl[mm]});
+                ff dxx = fqi::ff_add(X, ff{-exh[cc], -exl[cc]});
                 ff r2 = fqi::ff_add(fqi::ff_sqr(dxx), zz);
                 if (matrix || yf != 0.0f) {
-                    ff dyy = fqi::ff_add(Y, ff{-eyh[mm], -eyl[mm]});
+                    ff dyy = fqi::ff_add(Y, ff{-eyh[r], -eyl[r]});
                     r2 = fqi::ff_add(r2, fqi::ff_sqr(dyy));
                 }
-                const ff path = fqi::ff_add(ptx, fqi::ff_sqrt(r2));
-                const ff u = fqi::ff_mul(path, fs_c);
-                fqi::ff_floor_frac(u, i, phi);
-                if (i < 0 || i + 1 >= ns) {
-                    on = false;
-                } else {
-                    const float cyc = fqi::ff_frac(fqi::ff_mul(u, f0_fs));
-                    sincospif(2.0f * cyc, &sn, &cs);
-                }
+                rm = fqi::ff_sqrt(r2);
             }
-            // the group's four elements in turn (values shared within the 4 lanes of a pixel)
-            const int ion = on ? i : -1;  // the sample index, or -1 for an element outside the aperture
+            for (int a = 0; a < p.A; ++a) {
+                int i = 0;
+                float phi = 0.0f, sn = 0.0f, cs = 1.0f;
+                bool ok = on;
+                if (on) {
+                    const float2 pt = ptx_s[a * W + col];
+                    const ff path = fqi::ff_add(ff{pt.x, pt.y}, rm);
+                    const ff u = fqi::ff_mul(path, fs_c);
+                    fqi::ff_floor_frac(u, i, phi);
+                    if (i < 0 || i + 1 >= ns) {
+                        ok = false;
+                    } else if (p.rot_tab) {
+                        // e^{i 2 pi (f0/fs) phi} as the square of its half angle's
+                        // polynomial sine and cosine, times the table entry of i
+                        float sh, ch;
+                        das_sincos_poly(p.pi_f0_fs * phi, sh, ch);
+                        const float ce = (ch - sh) * (ch + sh), se = 2.0f * sh * ch;
+                        const float2 t = rot_s[i];
+                        cs = t.x * ce - t.y * se;
+                        sn = t.x * se + t.y * ce;
+                    } else {
+                        const float cyc = fqi::ff_frac(fqi::ff_mul(u, f0_fs));
+                        sincospif(2.0f * cyc, &sn, &cs);
+                    }
+                }
+                // the group's elements in turn (values shared within the TPP lanes of a pixel)
+                // the channel row (element, sample) within this angle's lines, or
+                // -1 for no contribution (M ns < 2^28: it fits an int)
+                const int ion = ok ? (r * nxe + cq) * ns + i : -1;
+                const ChT *cha = chp + (int64_t)a * M * line_stride;
 #pragma unroll
-            for (int j = 0; j < TPP; ++j) {
-                const int ij = __shfl_sync(0xffffffffu, ion, j, TPP);
-                const float phj = __shfl_sync(0xffffffffu, phi, j, TPP);
-                const float snj = __shfl_sync(0xffffffffu, sn, j, TPP);
-                const float csj = __shfl_sync(0xffffffffu, cs, j, TPP);
-                if (ij < 0) continue;
-                const ChT *b0 = cha + ((int64_t)(m0 + j) * ns + ij) * row_stride;
-                fqi::f2 v[FPT];
-                InterpFramesF2<FPT, ChT>::run(b0, row_stride, fqi::f2_dup(phj), v);
-                const fqi::f2 CS = fqi::f2_dup(csj), SN = fqi::f2_dup(snj);
+                for (int j = 0; j < TPP; ++j) {
+                    const int ij = __shfl_sync(0xffffffffu, ion, j, TPP);
+                    const float phj = __shfl_sync(0xffffffffu, phi, j, TPP);
+                    const float snj = __shfl_sync(0xffffffffu, sn, j, TPP);
+                    const float csj = __shfl_sync(0xffffffffu, cs, j, TPP);
+                    if (ij < 0) continue;
+                    const ChT *b0 = cha + (uint64_t)(unsigned)ij * (uint64_t)row_stride;
+                    fqi::f2 v[FPT];
+                    InterpFramesF2<FPT, ChT>::run(b0, row_stride, fqi::f2_dup(phj), v);
+                    const fqi::f2 CS = fqi::f2_dup(csj), SN = fqi::f2_dup(snj);
 #pragma unroll
-                for (int k = 0; k < FPT; ++k) {
-                    accC[k] = fqi::f2_fma(v[k], CS, accC[k]);
-                    accS[k] = fqi::f2_fma(v[k], SN, accS[k]);
+                    for (int k = 0; k < FPT; ++k) {
+                        accC[k] = fqi::f2_fma(v[k], CS, accC[k]);
+                        accS[k] = fqi::f2_fma(v[k], SN, accS[k]);
+                    }
                 }
             }
         }
     }
-    if (!live) return;
     const int f0 = fbase + FPT * q;
+    if (live) {
 #pragma unroll
-    for (int k = 0; k < FPT; ++k) {
-        float cr, ci, sr, si;
-        fqi::f2_split(accC[k], cr, ci);
-        fqi::f2_split(accS[k], sr, si);
-        if (f0 + k < p.F) fqi::store_c(iq, pix * p.F + f0 + k, make_float2((cr - si) * p.inv_A, (ci + sr) * p.inv_A));
+        for (int k = 0; k < FPT; ++k) {
+            float cr, ci, sr, si;
+            fqi::f2_split(accC[k], cr, ci);
+            fqi::f2_split(accS[k], sr, si);
+            if (f0 + k < p.F)
+                fqi::store_c(iq, pix * p.F + f0 + k, make_float2((cr - si) * p.inv_A, (ci + sr) * p.inv_A));
+        }
     }
+    __syncthreads();  // a persistent CTA's next tile rewrites the shared tables
 }
 
 
-template <typename ChT, typename OutT, int NT>
-__global__ void __launch_bounds__(NT) das_kernel(const DasParams p, const ChT *__restrict__ ch, OutT *__restrict__ iq)
+template <typename ChT, typename OutT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) das_kernel(const DasParams p, const ChT *__restrict__ ch, OutT *__restrict__ iq)
 {
-    extern __shared__ float etab[];  // [6][M]: x as float, x hi, x lo, y float, y hi, y lo
+    extern __shared__ __align__(16) float etab[];  // das_smem_bytes: element tables, transmit paths, running sums
     das_tile4<kDasTPP, ChT, OutT>(p, blockIdx.x, blockIdx.y, ch, iq, etab);
 }
 
@@ -559,7 +705,7 @@ constexpr int kDasParamBytes = (sizeof(DasParams) + 15) & ~15;
 template <typename ChT, typename OutT, int NT>
 __global__ void __launch_bounds__(NT) das_batched_kernel(const fqb::EnsDev *__restrict__ ens, const fqb::StageQueue q)
 {
-    extern __shared__ float etab[];
+    extern __shared__ __align__(16) float etab[];
     __shared__ __align__(16) unsigned char s_par[kDasParamBytes];
     __shared__ int s_buf[2];
     int cur = -1;
@@ -592,15 +738,21 @@ fq_status check_probe_tx(const fq_probe *probe, const fq_tx *tx, const char *who
 template <typename ChT, typename OutT>
 fq_status launch_das(const DasParams &p, const void *ch, void *iq, cudaStream_t st)
 {
-    size_t smem = sizeof(float) * 6 * (size_t)p.pr.M;
-    auto kern = das_kernel<ChT, OutT, kDasThreads>;
+    size_t smem = das_smem_bytes(p.pr.M, p.A, kDasThreads, kDasTPP, p.rot_tab ? p.pr.ns : 0);
+    // resident CTAs per SM the register budget targets: 8 (64 registers per
+    // thread) or 4 (up to 128); FQ_DAS_MINB=4 selects the latter for tuning
+    static int minb = -1;
+    if (minb < 0) {
+        const char *env = std::getenv("FQ_DAS_MINB");
+        minb = (env && env[0] == '4') ? 4 : 8;
+    }
+    auto kern = minb == 4 ? das_kernel<ChT, OutT, kDasThreads, 4> : das_kernel<ChT, OutT, kDasThreads, 8>;
     if (smem > 48 * 1024) {
         fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                            (int)smem), "fq_das: smem attribute");
         if (s) return s;
     }
-    const int px_per_cta = kDasThreads / kDasTPP;
-    dim3 grid((unsigned)((p.P + px_per_cta - 1) / px_per_cta), p.Fp / kFrameChunk);
+    dim3 grid((unsigned)das_ctas(p.gx, p.gy, p.gz, kDasThreads / kDasTPP), p.Fp / kFrameChunk);
     kern<<<grid, kDasThreads, smem, st>>>(p, (const ChT *)ch, (OutT *)iq);
     return fqi::launch_check("fq_das");
 }
@@ -620,6 +772,8 @@ void make_das_params(const fq_probe *probe, const fq_tx *tx, int F, const fq_gri
     p.dx = g->dx; p.dy = g->dy; p.dz = g->dz;
     p.half_per_z = (float)(0.5 / g->fnumber);
     p.inv_A = 1.0f / (float)p.A;
+    p.rot_tab = das_rot_tab(probe) ? 1 : 0;
+    p.pi_f0_fs = (float)(M_PI * probe->f0 / probe->fs);
     fqi::make_angles_ff(probe, tx, p.ang);
 }
 
@@ -748,9 +902,10 @@ fq_status batched_rf2iq(const fqb::EnsDev *ens, const fqb::StageQueue &q, int it
 }
 
 template <typename ChT, typename OutT, int NT>
-fq_status launch_das_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int M_max, cudaStream_t st)
+fq_status launch_das_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int M_max, int A_max,
+                             int ns_max, cudaStream_t st)
 {
-    const size_t smem = sizeof(float) * 6 * (size_t)M_max;
+    const size_t smem = das_smem_bytes(M_max, A_max, NT, kDasTPP, std::min(ns_max, kRotTabMax));
     auto kern = das_batched_kernel<ChT, OutT, NT>;
     fq_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "batched DAS: smem attribute");
@@ -761,21 +916,24 @@ fq_status launch_das_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, i
 }
 
 template <typename ChT, typename OutT>
-fq_status das_by_threads(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int M_max, int threads,
-                         cudaStream_t st)
+fq_status das_by_threads(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int M_max, int A_max,
+                         int ns_max, int threads, cudaStream_t st)
 {
-    if (threads == 64) return launch_das_batched<ChT, OutT, 64>(ens, q, items, M_max, st);
-    if (threads == 256) return launch_das_batched<ChT, OutT, 256>(ens, q, items, M_max, st);
-    return launch_das_batched<ChT, OutT, 128>(ens, q, items, M_max, st);
+    if (threads == 64) return launch_das_batched<ChT, OutT, 64>(ens, q, items, M_max, A_max, ns_max, st);
+    if (threads == 256) return launch_das_batched<ChT, OutT, 256>(ens, q, items, M_max, A_max, ns_max, st);
+    return launch_das_batched<ChT, OutT, 128>(ens, q, items, M_max, A_max, ns_max, st);
 }
 
 fq_status batched_das(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int ch_dtype, int iq_dtype,
-                      int M_max, int threads, cudaStream_t st)
+                      int M_max, int A_max, int ns_max, int threads, cudaStream_t st)
 {
-    if (ch_dtype == FQ_F32 && iq_dtype == FQ_F32) return das_by_threads<float, float>(ens, q, items, M_max, threads, st);
-    if (ch_dtype == FQ_F32) return das_by_threads<float, __nv_bfloat16>(ens, q, items, M_max, threads, st);
-    if (iq_dtype == FQ_F32) return das_by_threads<__nv_bfloat16, float>(ens, q, items, M_max, threads, st);
-    return das_by_threads<__nv_bfloat16, __nv_bfloat16>(ens, q, items, M_max, threads, st);
+    if (ch_dtype == FQ_F32 && iq_dtype == FQ_F32)
+        return das_by_threads<float, float>(ens, q, items, M_max, A_max, ns_max, threads, st);
+    if (ch_dtype == FQ_F32)
+        return das_by_threads<float, __nv_bfloat16>(ens, q, items, M_max, A_max, ns_max, threads, st);
+    if (iq_dtype == FQ_F32)
+        return das_by_threads<__nv_bfloat16, float>(ens, q, items, M_max, A_max, ns_max, threads, st);
+    return das_by_threads<__nv_bfloat16, __nv_bfloat16>(ens, q, items, M_max, A_max, ns_max, threads, st);
 }
 
 }  // namespace fqi

@@ -70,8 +70,13 @@ struct RfParams {
     // factor by which an echo's taps may exceed |amp| |D| / r (attenuation
     // gain before t = 0, binary32 rounding)
     int ag, n_ag, win;
+    // quad kernel: scatterer groups, each accumulated into the records with
+    // its own quantum and added to the FP32 output in turn (1 for 16-bit
+    // outputs, whose storage rounding is far coarser than the records')
+    int n_sg;
     float bound_margin;
     float dbx_far;      // the directivity bound at its largest argument, k0 width_x / 2
+    float dc_corr;      // quad kernel, FP32 outputs: added to tap 4 of every echo, times its amplitude
     fqi::AngleFF ang[FQ_MAX_ANGLES];
 };
 
@@ -790,7 +795,11 @@ __device__ __forceinline__ void cheb_step(f2 &C0, f2 &C1, f2 &N0, f2 &N1, f2 T, 
 
 // One tile: elements 4 bx .. 4 bx + 3, angles ag * p.ag .. (of the group),
 // frame f.  `tile` is the dynamic shared memory (p.ag * 4 * Ns ints).
-template <int NT, typename OutT>
+// Delays: float-float (~48 bits) for FP32 outputs; for 16-bit outputs the
+// binary32 delay (error ~1e-4 sample, a carrier-phase error ~2e-4 rad, below
+// the BF16 / FP16 storage rounding of 2^-9 / 2^-11) saves the error-free
+// transforms of the receive distance and the transmit path.
+template <int NT, typename OutT, bool FFD = (sizeof(OutT) == 4)>
 __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, int f, const float *__restrict__ pos,
                                              const float *__restrict__ amp, const float *__restrict__ rf_base,
                                              OutT *__restrict__ rf, int *tile, QuadShared &sh)
@@ -835,11 +844,6 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
 
     // the previous item of a persistent CTA may still read the tile
     __syncthreads();
-    for (int i = threadIdx.x; i < na * 2 * (ns + 2 * p.win); i += NT) tile[i] = 0;
-    if ((int)threadIdx.x < nrec) {
-        sh.wmax[threadIdx.x] = 0u;
-        sh.bmax[threadIdx.x] = 0u;
-    }
     if ((int)threadIdx.x <= na) {  // [0].w = fs / c; [1 + al] = the transmit direction and origin x fs / c
         const float K = p.pr.fs_over_c.hi;
         float4 g = make_float4(0.0f, 0.0f, 0.0f, K);
@@ -851,11 +855,26 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
         }
         sh.angK[threadIdx.x] = g;
     }
+
+    // Scatterer groups [sb, se): the rounding error of a record grows with
+    // the number of scatterers that share its quantum (the quantum follows
+    // the sum of |taps|, which grows linearly, while the echo grows as its
+    // square root), so FP32 outputs of large media take several groups,
+    // each with its own quanta, summed into the output in FP32.
+    for (int sg = 0; sg < p.n_sg; ++sg) {
+    const int64_t sb = S * sg / p.n_sg, se = S * (sg + 1) / p.n_sg, Sg = se - sb;
+    const bool with_base = rf_base != nullptr && sg == 0;
+    __syncthreads();  // the previous group's store still reads the tile
+    for (int i = threadIdx.x; i < na * 2 * (ns + 2 * p.win); i += NT) tile[i] = 0;
+    if ((int)threadIdx.x < nrec) {
+        sh.wmax[threadIdx.x] = 0u;
+        sh.bmax[threadIdx.x] = 0u;
+    }
     __syncthreads();
 
     // ---- pass 0: the largest possible tap, and the largest |base| per record
     float bm = 0.0f;
-    for (int64_t s = threadIdx.x; s < S; s += NT) {
+    for (int64_t s = sb + threadIdx.x; s < se; s += NT) {
         const float R = amp[s];
         if (R == 0.0f) continue;
         const float x = X[s], y = Y[s], z = Z[s];
@@ -864,7 +883,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, z * z));
         bm = fmaxf(bm, fabsf(R) * fminf(rsqrtf(r2), kInvRCap));
     }
-    if (rf_base) {
+    if (with_base) {
         for (int rec = 0; rec < nrec; ++rec) {
             const int al = rec >> 2, e = rec & 3;
             if (e >= ne) continue;
@@ -888,21 +907,21 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
     const int wstride = ns + 2 * win;
     const float margin = p.bound_margin;
     // units: the sum over every scatterer stays below 2^30 and one bound below 2^21
-    const float unit = fminf(1073741824.0f / ((float)S * bm * 1.0078125f), kUnitMax / (bm * 1.0078125f));
+    const float unit = fminf(1073741824.0f / ((float)Sg * bm * 1.0078125f), kUnitMax / (bm * 1.0078125f));
     unsigned *bins = reinterpret_cast<unsigned *>(tile);
     if (bm > 0.0f) {
         const float K = sh.angK[0].w;
         const float hpK0 = 0.5f * (exf[1] - exf[0]) * K, hpK1 = 0.5f * (exf[3] - exf[2]) * K;
         float nR = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;  // one scatterer ahead
-        if ((int64_t)threadIdx.x < S) {
-            nR = amp[threadIdx.x];
-            nx = X[threadIdx.x];
-            ny = Y[threadIdx.x];
-            nz = Z[threadIdx.x];
+        if (sb + threadIdx.x < se) {
+            nR = amp[sb + threadIdx.x];
+            nx = X[sb + threadIdx.x];
+            ny = Y[sb + threadIdx.x];
+            nz = Z[sb + threadIdx.x];
         }
-        for (int64_t s = threadIdx.x; s < S; s += NT) {
+        for (int64_t s = sb + threadIdx.x; s < se; s += NT) {
             const float R = nR, x = nx, y = ny, z = nz;
-            if (s + NT < S) {
+            if (s + NT < se) {
                 nR = amp[s + NT];
                 nx = X[s + NT];
                 ny = Y[s + NT];
@@ -965,7 +984,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
         const int rec = threadIdx.x;
         const float B = bm > 0.0f ? (float)sh.wmax[rec >> 1] / unit : 0.0f;  // bound of sum |taps| (amplitude units)
         const float den = B * margin + __uint_as_float(sh.bmax[rec]) * 1.0009765625f;
-        float iq = (kTwo31 - (0.5f * (float)S + 64.0f)) / den;
+        float iq = (kTwo31 - (0.5f * (float)Sg + 64.0f)) / den;
         if (!(iq > 0.0f && iq < 1e30f)) iq = 1.0f;
         sh.invq[rec] = iq;
         sh.q[rec] = 1.0f / iq;
@@ -975,7 +994,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
         const int rec = i / ns, k = i - rec * ns;
         const int e = rec & 3;
         int v = 0;
-        if (rf_base && e < ne)
+        if (with_base && e < ne)
             v = __float2int_rn(rf_base[((int64_t)(a0 + (rec >> 2)) * M + m0 + e) * ns + k] * sh.invq[rec]);
         tile[i] = v;
     }
@@ -983,60 +1002,80 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
 
     // ---- pass 2: the taps
     const float Kh = p.pr.fs_over_c.hi, Kl = p.pr.fs_over_c.lo;
+    const float att_l2K = p.att_l2 / Kh;  // per sample of delay
     const float theta = p.theta, theta2 = p.theta2, jmin_f = p.jmin_f, att_l2 = p.att_l2;
     const int kfast = ns - 9;  // records k .. k + 8 inside [0, ns): 0 <= k <= kfast
     const float thc0 = p.tab_h[0][0], ths0 = p.tab_h[0][1], thc1 = p.tab_h[1][0], ths1 = p.tab_h[1][1];
     const f2 COSH = fqi::f2_dup(p.cos_h), SINH = fqi::f2_dup(p.sin_h), TWOCOS = fqi::f2_dup(p.two_cos_h);
     const f2 NCOSH = fqi::f2_dup(-p.cos_h), NSINH = fqi::f2_dup(-p.sin_h), NTWOCOS = fqi::f2_dup(-p.two_cos_h);
     const f2 NHALF = fqi::f2_dup(-0.5f);
+    const f2 DCC = fqi::f2_dup(p.dc_corr);
 
     // the next scatterer's inputs are loaded one iteration ahead
     float nR = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
-    if (bm > 0.0f && (int64_t)threadIdx.x < S) {
-        nR = amp[threadIdx.x];
-        nx = X[threadIdx.x];
-        ny = Y[threadIdx.x];
-        nz = Z[threadIdx.x];
+    if (bm > 0.0f && sb + threadIdx.x < se) {
+        nR = amp[sb + threadIdx.x];
+        nx = X[sb + threadIdx.x];
+        ny = Y[sb + threadIdx.x];
+        nz = Z[sb + threadIdx.x];
     }
-    for (int64_t s = threadIdx.x; bm > 0.0f && s < S; s += NT) {
+    for (int64_t s = sb + threadIdx.x; bm > 0.0f && s < se; s += NT) {
         const float R = nR, x = nx, y = ny, z = nz;
-        if (s + NT < S) {
+        if (s + NT < se) {
             nR = amp[s + NT];
             nx = X[s + NT];
             ny = Y[s + NT];
             nz = Z[s + NT];
         }
         if (R == 0.0f) continue;
-        const ff zz = fqi::ff_two_prod(z, z);
         const bool use_y = matrix || y != 0.0f;
-        // ---- receive side, element 0: float-float distance
-        const float dxh = __fsub_rn(x, ex0.hi);
-        const float bb = __fsub_rn(dxh, x);
-        const float dxl = __fsub_rn(__fadd_rn(__fsub_rn(x, __fsub_rn(dxh, bb)), __fsub_rn(-ex0.hi, bb)), ex0.lo);
-        const float p2 = __fmul_rn(dxh, dxh);
-        float lo = __fmaf_rn(2.0f * dxh, dxl, __fmaf_rn(dxh, dxh, -p2));
-        ff r2 = fqi::ff_two_sum(p2, zz.hi);
-        lo = __fadd_rn(lo, zz.lo);
-        float dyh = 0.0f, q2 = 0.0f;
-        if (use_y) {
-            dyh = __fsub_rn(y, ey.hi);
-            const float cc = __fsub_rn(dyh, y);
-            const float dyl = __fsub_rn(__fadd_rn(__fsub_rn(y, __fsub_rn(dyh, cc)), __fsub_rn(-ey.hi, cc)), ey.lo);
-            q2 = __fmul_rn(dyh, dyh);
-            lo = __fadd_rn(lo, __fmaf_rn(2.0f * dyh, dyl, __fmaf_rn(dyh, dyh, -q2)));
-            ff t2 = fqi::ff_two_sum(r2.hi, q2);
-            r2.hi = t2.hi;
-            lo = __fadd_rn(lo, t2.lo);
+        float dxh, dyh = 0.0f, q2 = 0.0f, zzh, rs0, r0, rl;
+        bool pos0;
+        if constexpr (FFD) {
+            const ff zz = fqi::ff_two_prod(z, z);
+            zzh = zz.hi;
+            // ---- receive side, element 0: float-float distance
+            dxh = __fsub_rn(x, ex0.hi);
+            const float bb = __fsub_rn(dxh, x);
+            const float dxl = __fsub_rn(__fadd_rn(__fsub_rn(x, __fsub_rn(dxh, bb)), __fsub_rn(-ex0.hi, bb)), ex0.lo);
+            const float p2 = __fmul_rn(dxh, dxh);
+            float lo = __fmaf_rn(2.0f * dxh, dxl, __fmaf_rn(dxh, dxh, -p2));
+            ff r2 = fqi::ff_two_sum(p2, zz.hi);
+            lo = __fadd_rn(lo, zz.lo);
+            if (use_y) {
+                dyh = __fsub_rn(y, ey.hi);
+                const float cc = __fsub_rn(dyh, y);
+                const float dyl = __fsub_rn(__fadd_rn(__fsub_rn(y, __fsub_rn(dyh, cc)), __fsub_rn(-ey.hi, cc)), ey.lo);
+                q2 = __fmul_rn(dyh, dyh);
+                lo = __fadd_rn(lo, __fmaf_rn(2.0f * dyh, dyl, __fmaf_rn(dyh, dyh, -q2)));
+                ff t2 = fqi::ff_two_sum(r2.hi, q2);
+                r2.hi = t2.hi;
+                lo = __fadd_rn(lo, t2.lo);
+            }
+            lo = __fadd_rn(lo, r2.lo);
+            r2 = fqi::ff_fast_two_sum(r2.hi, lo);
+            pos0 = r2.hi > 0.0f;
+            rs0 = pos0 ? rsqrtf(r2.hi) : 0.0f;
+            r0 = __fmul_rn(r2.hi, rs0);
+            rl = pos0 ? __fmul_rn(__fadd_rn(__fmaf_rn(-r0, r0, r2.hi), r2.lo), 0.5f * rs0) : 0.0f;
+        } else {
+            // ---- receive side, element 0: binary32 distance with one Newton correction
+            zzh = z * z;
+            dxh = x - exf[0];
+            if (use_y) {
+                dyh = y - eyf;
+                q2 = dyh * dyh;
+            }
+            const float r2h = fmaf(dxh, dxh, zzh + q2);
+            pos0 = r2h > 0.0f;
+            rs0 = pos0 ? rsqrtf(r2h) : 0.0f;
+            r0 = r2h * rs0;
+            rl = pos0 ? fmaf(-r0, r0, r2h) * (0.5f * rs0) : 0.0f;
         }
-        lo = __fadd_rn(lo, r2.lo);
-        r2 = fqi::ff_fast_two_sum(r2.hi, lo);
-        const bool pos0 = r2.hi > 0.0f;
-        const float rs0 = pos0 ? rsqrtf(r2.hi) : 0.0f;
-        const float r0 = __fmul_rn(r2.hi, rs0);
-        const float rl = pos0 ? __fmul_rn(__fadd_rn(__fmaf_rn(-r0, r0, r2.hi), r2.lo), 0.5f * rs0) : 0.0f;
         // ---- receive side, every element: delay offset, directivity, R D / r
-        const float zy2 = __fadd_rn(zz.hi, q2);  // z^2 (+ dy^2), binary32
+        const float zy2 = __fadd_rn(zzh, q2);  // z^2 (+ dy^2), binary32
         const float r0f = r0 + rl;
+        const float r0K = FFD ? 0.0f : r0f * Kh;
         float dxa[E], rsa[E], dee[E];
         bool liv[E];
 #pragma unroll
@@ -1076,18 +1115,27 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
         RD2[1] = fqi::f2_mul(RD2[1], fqi::f2_make(ex2_approx(att_l2 * dee[2]), ex2_approx(att_l2 * dee[3])));
         const f2 DE2[2] = {fqi::f2_make(0.0f, dee[1]), fqi::f2_make(dee[2], dee[3])};
         for (int al = 0; al < na; ++al) {
-            const float4 g0 = sh.angFF[2 * al], g1 = sh.angFF[2 * al + 1];
-            const ff ptx = fqi::ff_dot3_minus({g0.x, g0.y}, {g0.z, g0.w}, {g1.x, g1.y}, {g1.z, g1.w}, x, y, z);
-            ff path = fqi::ff_two_sum(ptx.hi, r0);
-            path.lo = __fadd_rn(path.lo, __fadd_rn(ptx.lo, rl));
-            const float uh = __fmul_rn(path.hi, Kh);
-            const float ul = __fmaf_rn(path.hi, Kl, __fmaf_rn(path.lo, Kh, __fmaf_rn(path.hi, Kh, -uh)));
-            float fl0 = floorf(uh);
-            float fr0 = __fadd_rn(__fsub_rn(uh, fl0), ul);
-            {
+            float fl0, fr0, path_hi;
+            if constexpr (FFD) {
+                const float4 g0 = sh.angFF[2 * al], g1 = sh.angFF[2 * al + 1];
+                const ff ptx = fqi::ff_dot3_minus({g0.x, g0.y}, {g0.z, g0.w}, {g1.x, g1.y}, {g1.z, g1.w}, x, y, z);
+                ff path = fqi::ff_two_sum(ptx.hi, r0);
+                path.lo = __fadd_rn(path.lo, __fadd_rn(ptx.lo, rl));
+                const float uh = __fmul_rn(path.hi, Kh);
+                const float ul = __fmaf_rn(path.hi, Kl, __fmaf_rn(path.lo, Kh, __fmaf_rn(path.hi, Kh, -uh)));
+                fl0 = floorf(uh);
+                fr0 = __fadd_rn(__fsub_rn(uh, fl0), ul);
                 const float c = floorf(fr0);
                 fr0 -= c;
                 fl0 += c;
+                path_hi = path.hi;
+            } else {
+                // binary32: (u . r - origin) fs / c + r fs / c in samples
+                const float4 g = sh.angK[al + 1];
+                const float u = r0K + fmaf(g.x, x, fmaf(g.y, y, fmaf(g.z, z, g.w)));
+                fl0 = floorf(u);
+                fr0 = u - fl0;
+                path_hi = u;  // the attenuation exponent takes samples here
             }
             // per element pair (0, 1), (2, 3), two lanes of packed f32x2 (element
             // 0's offset from itself is 0); FRND, MUFU, conversions and
@@ -1095,7 +1143,7 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
             const ulonglong2 iqv = *reinterpret_cast<const ulonglong2 *>(&sh.invq[al * E]);
             const f2 IQ2[2] = {f2{iqv.x}, f2{iqv.y}};
             const f2 FR0 = fqi::f2_dup(fr0), FL0 = fqi::f2_dup(fl0);
-            const f2 ATT0 = fqi::f2_dup(ex2_approx(att_l2 * path.hi));
+            const f2 ATT0 = fqi::f2_dup(ex2_approx((FFD ? att_l2 : att_l2K) * path_hi));
             f2 A2[2], CH2[2], SH2[2];
             int ke[E];
             bool ine[E], nine[E];
@@ -1155,8 +1203,15 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
                 const int q2i = liv[2] ? ke[2] : 0, q3 = liv[3] ? ke[3] : 0;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    add_tap2(r0p, r1p, q0 + j, q1 + j, tap2n(A01, nhA01, Ca0));
-                    add_tap2(r2p, r3p, q2i + j, q3 + j, tap2n(A23, nhA23, Cb0));
+                    f2 ta = tap2n(A01, nhA01, Ca0), tb = tap2n(A23, nhA23, Cb0);
+                    if constexpr (FFD) {
+                        if (j == 4) {  // the mean error of the recurrence's taps, taken out (see pulse_dc_bias)
+                            ta = fqi::f2_fma(DCC, A01, ta);
+                            tb = fqi::f2_fma(DCC, A23, tb);
+                        }
+                    }
+                    add_tap2(r0p, r1p, q0 + j, q1 + j, ta);
+                    add_tap2(r2p, r3p, q2i + j, q3 + j, tb);
                     cheb_step(Ca0, Ca1, Na0, Na1, TWOCOS, NTWOCOS);
                     cheb_step(Cb0, Cb1, Nb0, Nb1, TWOCOS, NTWOCOS);
                 }
@@ -1191,8 +1246,10 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
         const int e = rec & 3;
         if (e >= ne) continue;
         OutT *out = rf + (((int64_t)f * p.A + a0 + (rec >> 2)) * M + m0 + e) * ns;
-        fqi::store_f(out, k, (float)tile[i] * sh.q[rec]);
+        const float v = (float)tile[i] * sh.q[rec];
+        fqi::store_f(out, k, sg == 0 ? v : fqi::load_f(out, k) + v);  // this CTA owns these samples
     }
+    }  // scatterer groups
 }
 
 template <int NT, int MINB, typename OutT>
@@ -1341,6 +1398,68 @@ fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *a
     }
 }
 
+// The quad kernel's pulse taps come from a binary32 Chebyshev recurrence
+// started at the first tap; its rounded constants (the recurrence factor
+// 2 cos w, the table entries e^{i w j}) give every echo the same small error
+// pattern, whose sum over the taps (the echo's DC content) does not average
+// out: ~-2.3e-7 of the echo amplitude for the two-cycle pulse at ~4 samples
+// per carrier period.  rf2iq passes DC to baseband at -f0 with about half
+// gain, and delay-and-sum adds that component coherently over every
+// (transmit, element) term of a voxel while the echoes themselves add with
+// random phases, so it grew to ~1.2e-5 of the beamformed image of the 3D
+// workload.  This host routine runs the same binary32 operations lane by
+// lane (the kernel's f32x2 instructions round each lane like these scalar
+// ones) over 4096 fractional delays spread uniformly over [0, 1), against
+// the pulse evaluated in double, and returns the mean error per unit
+// amplitude; the kernel subtracts it at one tap of every echo (FP32
+// outputs).
+float pulse_dc_bias(const RfParams &p, double f0, double fs, int n_cycles)
+{
+    using namespace fqpoly;
+    const double hw = n_cycles * fs / (2.0 * f0);
+    const double wh = 2.0 * M_PI * f0 / (n_cycles * fs), wc = 2.0 * M_PI * f0 / fs;
+    const int N = 4096;
+    double err = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const float fr = ((float)i + 0.5f) / (float)N;
+        const bool lo = fr <= p.theta;
+        const int jlo = p.jmin + (lo ? 0 : 1);
+        const bool nine = lo || fr >= p.theta2;
+        const float x = p.w_h * fr;
+        const float t = x * x;
+        float ps = std::fmaf(kSinPoly3, t, kSinPoly2);
+        ps = std::fmaf(ps, t, kSinPoly1);
+        ps = std::fmaf(ps, t, kSinPoly0);
+        const float sf = x * ps;
+        float pc = std::fmaf(kCosPoly4, t, kCosPoly3);
+        pc = std::fmaf(pc, t, kCosPoly2);
+        pc = std::fmaf(pc, t, kCosPoly1);
+        const float cf = std::fmaf(pc, t, kCosPoly0);
+        const float tc = lo ? p.tab_h[0][0] : p.tab_h[1][0], ts = lo ? p.tab_h[0][1] : p.tab_h[1][1];
+        const float ntc = -tc;
+        const float sfts = sf * ts, ntcsf = ntc * sf;
+        const float ch = std::fmaf(cf, tc, sfts);
+        const float sh = std::fmaf(ts, cf, ntcsf);
+        const float shns = sh * -p.sin_h, shs = sh * p.sin_h;
+        float c0 = ch, c1 = std::fmaf(ch, p.cos_h, shns);
+        float n0 = -ch, n1 = std::fmaf(ch, -p.cos_h, shs);
+        const float nhA = -0.5f;
+        for (int j = 0; j < (nine ? 9 : 8); ++j) {
+            const float tap = std::fmaf(std::fmaf(std::fmaf(1.0f, c0, 1.0f), c0, nhA), c0, nhA);
+            const double tt = (double)(jlo + j) - (double)fr;
+            const double ex = std::fabs(tt) < hw ? 0.5 * (1.0 + std::cos(wh * tt)) * std::cos(wc * tt) : 0.0;
+            err += (double)tap - ex;
+            const float c2 = std::fmaf(p.two_cos_h, c1, n0);
+            const float n2 = std::fmaf(-p.two_cos_h, c1, c0);
+            c0 = c1;
+            c1 = c2;
+            n0 = n1;
+            n1 = n2;
+        }
+    }
+    return (float)(err / N);
+}
+
 fq_status make_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, RfParams &p)
 {
     std::memset(&p, 0, sizeof p);
@@ -1401,7 +1520,33 @@ fq_status make_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, RfPa
         p.dbx_far = (float)((1.0 - t / 6.0 + t * t / 120.0) * (1.0 + 1e-6));
     }
     p.bound_margin = (float)(std::exp((double)p.att * (hw + 1.0) / (probe->fs / probe->c)) * (1.0 + 1.0 / 128.0));
+    p.n_sg = 1;
+    p.dc_corr = p.two_cycle ? -pulse_dc_bias(p, probe->f0, probe->fs, probe->n_cycles) : 0.0f;
     return FQ_OK;
+}
+
+// Scatterer groups of the quad kernel for an output type.  A record's
+// relative rounding error grows about linearly with the scatterers that
+// share its quanta (the quantum follows the sum of |taps| in a window, the
+// echo its square root), and with the number of them whose echoes overlap a
+// sample: a matrix probe over a volume puts far more scatterers into each
+// delay shell than a linear probe over a plane (measured: 1.9e-6 for 20k
+// and 4e-5 for 500k scatterers in the 3D workload's 15 mm cube, 8.7e-7 for
+// 100k in the 2D one).  FP32 records therefore take groups of at most 65536
+// scatterers for matrix probes and 262144 for linear ones (each group adds
+// a pass of bounds and a read-modify-write of the records, measured ~0.4%
+// per group on the 3D workload); 16-bit outputs keep one group (their
+// storage rounding is far coarser).
+void set_scatter_groups(RfParams &p, int out_dtype)
+{
+    // FQ_RF_SCAT_GROUP (tuning, read once): the group size, 0 = one group
+    static const int64_t forced = [] {
+        const char *env = std::getenv("FQ_RF_SCAT_GROUP");
+        return env ? std::max<int64_t>(0, std::atoll(env)) : (int64_t)-1;
+    }();
+    int64_t g = p.pr.ny > 1 ? 65536 : 262144;
+    if (forced >= 0) g = forced ? forced : INT64_MAX;
+    p.n_sg = (out_dtype == FQ_F32 && p.S > g) ? (int)((p.S + g - 1) / g) : 1;
 }
 
 }  // namespace
@@ -1429,6 +1574,7 @@ extern "C" fq_status fq_simulate_rf(const fq_probe *probe, const fq_tx *tx, cons
     RfParams p;
     fq_status bs = make_rf_params(probe, tx, S, p);
     if (bs) return bs;
+    set_scatter_groups(p, out_dtype);
     cudaStream_t st = (cudaStream_t)stream;
     return fqi::with_storage(out_dtype, "fq_simulate_rf", [&](auto *out) {
         return dispatch_rf(p, n_frames, pos, amp, rf_base, (fqi::storage_t<decltype(out)> *)rf, st);
@@ -1439,10 +1585,14 @@ namespace fqi {
 
 size_t rf_params_bytes() { return kRfParamBytes; }
 
-fq_status build_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, void *out)
+fq_status build_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, int out_dtype, void *out)
 {
     std::memset(out, 0, kRfParamBytes);
-    return make_rf_params(probe, tx, S, *reinterpret_cast<RfParams *>(out));
+    RfParams &p = *reinterpret_cast<RfParams *>(out);
+    fq_status s = make_rf_params(probe, tx, S, p);
+    if (s) return s;
+    set_scatter_groups(p, out_dtype);
+    return FQ_OK;
 }
 
 // The quad kernel serves probes whose rows hold whole quads (unless

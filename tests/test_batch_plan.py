@@ -41,7 +41,9 @@ def expected_items(w, das_threads=128):
     nt = cd(w.n_frames, 32)
     return {"classify": cd(w.S, 2048), "advect": cd(w.S, 2048) * w.n_frames,
             "rf": cd(w.M, 4) * rf_angle_groups(w.A, w.Ns) * w.n_frames, "rf2iq": cd(w.Ns, 128) * L * (Fp // 16),
-            "das": cd(w.P, das_threads // 4) * (Fp // 16), "gram_reduce": cd(w.n_frames ** 2, 256), "eig": 1,
+            # DAS tiles: das_threads / 4 voxels along x of one (y, z) row, per 16-frame chunk
+            "das": cd(w.grid.nx, das_threads // 4) * w.grid.ny * w.grid.nz * (Fp // 16),
+            "gram_reduce": cd(w.n_frames ** 2, 256), "eig": 1,
             "project": cd(w.P, 64), "gram_pairs": nt * (nt + 1) // 2}
 
 
