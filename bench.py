@@ -1,17 +1,22 @@
 """Benchmark of the uPDI hot path on GB300.
 
-One step = the whole path over one ensemble of the 2D compounded workload
-(128-element linear array, 5 plane waves, 2048 samples, 100k scatterers,
-200 frames, 256x256 pixels): vessel membership -> advection -> RF synthesis
--> rf2iq + DAS compounding -> SVD clutter filter -> power Doppler.
+One step = the whole path over one ensemble: vessel membership -> advection
+-> RF synthesis -> rf2iq -> DAS compounding -> SVD clutter filter -> power
+Doppler.  The default workload is the 3D volumetric one (32x32 matrix
+array, 9 plane-wave tilts, 1536 samples, 500k scatterers in a vessel tree,
+100 frames, 128^3 voxels, RF and channel IQ stored in BF16 with FP32
+arithmetic); `--workload c2` runs the 2D compounded one (128-element linear
+array, 5 plane waves, 2048 samples, 100k scatterers, 200 frames, 256x256
+pixels, FP32).
 
 Prints one JSON line.  `value` is channel-samples/s of the whole step
 (F * A * M * Ns / step time), summed over ranks; `e2e` is the same metric
 through the public API with the scatterer inputs copied from pinned host
 memory and the power Doppler image copied back inside the timed region.
-`roofline` covers the dominant kernel (RF synthesis, FP32-ALU bound).
+`roofline` covers the dominant kernel (RF synthesis, FP32-ALU bound) and
+`roofline_das` the DAS kernel.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c3|c2|...]
 """
 from __future__ import annotations
 
@@ -32,15 +37,26 @@ sys.path.insert(0, ROOT)
 METRIC = "channel-samples/s + DAS voxel-angle/s per GB300, % roofline, err vs FP64"
 UNIT = "channel-samples/s"
 # FP32 work of the model per (scatterer, element, transmit) pair, counted
-# from its plain definition: 17 for geometry and amplitude,
-# 10 per pulse tap, 2 * n_cycles * fs / (2 f0) taps on average.
+# from its plain definition: 17 for geometry and amplitude (22 for matrix
+# arrays, whose directivity has a second sinc factor), 10 per pulse tap,
+# n_cycles * fs / f0 taps on average.
 GEOM_FLOP_PER_PAIR = 17.0
+GEOM_FLOP_MATRIX_EXTRA = 5.0
 FLOP_PER_TAP = 10.0
-# DRAM bytes (read + write) of one full-size C2 RF launch, from one ncu
-# capture of rf_synth_quad_kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum); None once the kernel changes until it is
-# captured again.
-RF_TRAFFIC_BYTES = None
+# FP32 work of DAS per active (voxel, transmit, element) triple: 14 per
+# frame (linear interpolation 6, phase rotation 6, accumulation 2) and 20
+# for the delay and phase shared by all frames (differences, squares, root,
+# transmit path, scale to samples, floor, phase, sine and cosine).
+DAS_FLOP_PER_FRAME = 14.0
+DAS_FLOP_PER_TRIPLE = 20.0
+# DRAM bytes (read + write) of one full-size RF launch per workload, from
+# ncu captures of rf_synth_quad_kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); a workload is absent (traffic null) once the
+# kernel changes until it is captured again.
+RF_TRAFFIC_BYTES = {
+    # 3D volumetric, 100 frames, BF16 RF: 702,794,240 read + 2,824,532,992 written
+    "c3": 702_794_240 + 2_824_532_992,
+}
 
 
 def peaks():
@@ -151,6 +167,61 @@ def sum_over_ranks(x: float) -> float:
     return float(t.item())
 
 
+# ------------------------------------------------------------ workloads --
+# single-ensemble workloads: storage of the RF, the channel IQ and the
+# Casorati matrix (arithmetic is FP32 throughout)
+STEP_WORKLOADS = {
+    "c3": {"rf": "bfloat16", "ch": "bfloat16", "iq": "float32", "dtype": "bf16"},
+    "c2": {"rf": "float32", "ch": "float32", "iq": "float32", "dtype": "f32"},
+}
+
+
+def make_workload(name, seed_offset=0, n_frames=0):
+    from paper_2509_05464_gb300 import workload as W
+    if name == "c3":
+        return W.config3(seed=3 + seed_offset, n_frames=n_frames or 100)
+    return W.config2(seed=2 + seed_offset, n_frames=n_frames or 200)
+
+
+def reduced_workload(name, w):
+    """A seeded subset of the workload that the oracle runs through the whole
+    path in seconds (for the error of each storage variant)."""
+    from paper_2509_05464_gb300 import workload as W
+    if name == "c3":
+        return W.shrink(W.config3(seed=3, n_frames=16), max_scat=20_000, grid_div=4)
+    import dataclasses
+    return dataclasses.replace(w, n_frames=6, k_cut=min(w.k_cut, 5))
+
+
+def das_active_triples(w) -> int:
+    """(voxel, transmit, element) triples inside the receive aperture, decided
+    as the kernels decide it (binary32 |x_p - x_m| <= z_p / (2 f#), and in y
+    for matrix arrays); delays outside the record are not excluded."""
+    p, g = w.probe, w.grid
+    ex = ((np.arange(p.nx) - 0.5 * (p.nx - 1)) * p.pitch_x).astype(np.float32)
+    ey = ((np.arange(p.ny) - 0.5 * (p.ny - 1)) * p.pitch_y).astype(np.float32)
+    xs = (g.x0 + np.arange(g.nx) * g.dx).astype(np.float32)
+    ys = (g.y0 + np.arange(g.ny) * g.dy).astype(np.float32)
+    zs = (g.z0 + np.arange(g.nz) * g.dz).astype(np.float32)
+    half = zs * np.float32(0.5 / g.fnumber)
+    cx = (np.abs(xs[None, :, None] - ex[None, None, :]) <= half[:, None, None]).sum(-1).astype(np.int64)
+    if p.ny > 1:
+        cy = (np.abs(ys[None, :, None] - ey[None, None, :]) <= half[:, None, None]).sum(-1).astype(np.int64)
+    else:
+        cy = np.ones((g.nz, g.ny), np.int64)
+    return int(w.A * (cx.sum(1) * cy.sum(1)).sum())
+
+
+def rf_flop(w) -> float:
+    p = w.probe
+    geom = GEOM_FLOP_PER_PAIR + (GEOM_FLOP_MATRIX_EXTRA if p.ny > 1 else 0.0)
+    return float(w.n_frames) * w.A * w.M * w.S * (geom + FLOP_PER_TAP * p.n_cycles * p.fs / p.f0)
+
+
+def das_flop(w, triples) -> float:
+    return float(triples) * (DAS_FLOP_PER_FRAME * w.n_frames + DAS_FLOP_PER_TRIPLE)
+
+
 # ---------------------------------------------------------------- oracle --
 def oracle_run(w, n_frames):
     """The oracle through the whole path on the first n_frames frames:
@@ -163,17 +234,78 @@ def oracle_run(w, n_frames):
     return time.perf_counter() - t0, r
 
 
-def oracle_step(w, n_frames):
-    return oracle_run(w, n_frames)[0]
-
-
-def cpu_baseline(w, n_frames=6):
+def oracle_sample_3d(w, n_lines=64, block=32, p_svd=16384):
+    """The oracle on bounded subsets of a 3D ensemble, each stage timed and
+    extrapolated linearly by its exact work count to the whole step:
+    membership once; advection of one frame (x F); RF of n_lines (transmit,
+    element) lines of frame 0 with every scatterer (x A M F / n_lines);
+    rf2iq of those lines; DAS of a block^3 voxel sub-grid at 1 and 9 frames
+    (cost a + b F fitted, x P / block^3); the SVD filter of a p_svd x F
+    stand-in Casorati matrix (x P / p_svd).  Returns (seconds per step,
+    description)."""
     import oracle
-    dt, r = oracle_run(w, n_frames)
+    from paper_2509_05464_gb300 import workload as W
+    st, mt = W.segment_table(w), W.motion_table(w.motion)
+    F, A, M, Ns, P = w.n_frames, w.A, w.M, w.Ns, w.P
+    t = {}
+    c = time.perf_counter()
+    _, amp = oracle.classify(w.p0, w.seg, st, len(w.segments), w.amp)
+    t["classify"] = time.perf_counter() - c
+    c = time.perf_counter()
+    pos = oracle.advect(w.p0, w.seg, w.flow, st, mt, 0.0)
+    t["advect"] = (time.perf_counter() - c) * F
+    a_mid = A // 2
+    lines = a_mid * M + np.arange(n_lines)
+    c = time.perf_counter()
+    rf = oracle.simulate_rf_lines(w.probe, w.tilt_x, w.tilt_y, lines, pos, amp).astype(np.float32)
+    t["rf"] = (time.perf_counter() - c) * A * M * F / n_lines
+    c = time.perf_counter()
+    iq = oracle.rf2iq(w.probe, rf)
+    t["rf2iq"] = (time.perf_counter() - c) * A * M * F / n_lines
+    g = w.grid
+    off = [(n - block) // 2 for n in (g.nx, g.ny, g.nz)]
+    sub = W.Grid(block, block if g.ny > 1 else 1, block, g.x0 + off[0] * g.dx, g.y0 + off[1] * g.dy,
+                 g.z0 + off[2] * g.dz, g.dx, g.dy, g.dz, g.fnumber)
+    ch = np.resize(iq, (A * M, Ns))  # the computed lines stand in for every channel (timing only)
+    dt = []
+    for nf in (1, 9):
+        chf = np.broadcast_to(ch.reshape(1, A, M, Ns), (nf, A, M, Ns)).copy()
+        c = time.perf_counter()
+        oracle.das(w.probe, w.tilt_x, w.tilt_y, chf, sub)
+        dt.append(time.perf_counter() - c)
+    b = max(dt[1] - dt[0], 0.0) / 8
+    a0 = max(dt[0] - b, 0.0)
+    t["das"] = (a0 + b * F) * P / sub.n_pixels
+    rng = np.random.default_rng(0)
+    S = rng.standard_normal((p_svd, F)) + 1j * rng.standard_normal((p_svd, F))
+    c = time.perf_counter()
+    oracle.svd_filter(S, w.k_cut, w.energy_thresh)
+    t["svd_pd"] = (time.perf_counter() - c) * P / p_svd
+    total = sum(t.values())
+    desc = (f"FP64 oracle on bounded subsets, each stage extrapolated linearly by its work count: membership "
+            f"of all {w.S} scatterers, advection of 1 of {F} frames, RF of {n_lines} of {A * M} (transmit, "
+            f"element) lines of frame 0 with every scatterer, rf2iq of those lines, DAS of a {block}^3 voxel "
+            f"block at 1 and 9 frames (a + b F fit), the SVD filter of a {p_svd} x {F} random stand-in; "
+            f"measured {sum(dt) + t['classify']:.1f} s of stages; extrapolated stage seconds "
+            + json.dumps({k: round(v, 1) for k, v in t.items()}))
+    return total, desc
+
+
+def cpu_baseline(name, w):
+    """The oracle as it stands on the host cores: (cpu_baseline dict, oracle
+    results of the reduced workload or None)."""
+    import oracle
+    if name == "c3":
+        sec, desc = oracle_sample_3d(w)
+        cs = w.n_frames * w.A * w.M * w.Ns
+        return {"value": cs / sec, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                "sample": desc}
+    n_frames = 6
+    dt, _ = oracle_run(w, n_frames)
     cs = n_frames * w.A * w.M * w.Ns
     return {"value": cs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"whole path (advect, membership, RF, rf2iq, DAS, SVD filter, PD) on the first {n_frames} "
-                      f"of {w.n_frames} frames of the same workload, FP64, {dt:.1f} s"}, r
+                      f"of {w.n_frames} frames of the same workload, FP64, {dt:.1f} s"}
 
 
 def rel_l2(a, b):
@@ -182,84 +314,118 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-# Precision variants of the path: (name, RF storage, channel IQ, Casorati, Gram)
+# Storage variants of the path: (name, RF, channel IQ, Casorati, Gram)
 VARIANTS = [("f32", "float32", "float32", "float32", "f32"),
+            ("f16", "float16", "float16", "float32", "f32"),
+            ("bf16", "bfloat16", "bfloat16", "float32", "f32"),
             ("f32+tf32_gram", "float32", "float32", "float32", "tf32"),
-            ("f32+bf16_gram", "float32", "float32", "float32", "bf16"),
-            ("bf16", "bfloat16", "bfloat16", "bfloat16", "bf16")]
+            ("bf16_all", "bfloat16", "bfloat16", "bfloat16", "bf16")]
 
 
-def precision_variants(w, ref, n_ref, steps, warmup):
-    """Each variant on the full workload (device-timed step) and its error vs
-    the FP64 oracle: RF and Casorati IQ on the first n_ref frames of the full
-    run, PD of an n_ref-frame ensemble of the same workload."""
-    import dataclasses
+def variant_kwargs(rf_t, ch_t, iq_t, gm):
+    import torch
+    from paper_2509_05464_gb300 import fq
+    gmode = {"f32": fq.FQ_GRAM_F32, "tf32": fq.FQ_GRAM_TF32, "bf16": fq.FQ_GRAM_BF16}
+    return dict(rf_dtype=getattr(torch, rf_t), ch_dtype=getattr(torch, ch_t), iq_dtype=getattr(torch, iq_t),
+                gram_mode=gmode[gm])
+
+
+STAGES = ("classify", "advect", "simulate", "rf2iq", "das", "clutter")
+
+
+def time_steps(pl, steps, flush=None):
+    """Device time of `steps` whole steps on the current stream, with events
+    between the stages: (mean ms per step, mean ms per stage)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        if flush is not None:
+            flush.zero_()  # L2 flush outside the timed events
+        ev[i][0].record(stream)
+        for j, name in enumerate(STAGES):
+            getattr(pl, name)()
+            ev[i][j + 1].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [e[0].elapsed_time(e[-1]) for e in ev]
+    stage_ms = {name: sum(e[j].elapsed_time(e[j + 1]) for e in ev) / steps for j, name in enumerate(STAGES)}
+    return sum(step_ms) / steps, stage_ms
+
+
+def variant_errors(w_small, ref, kw):
+    """Errors of one storage variant against the FP64 oracle on the reduced
+    workload: RF, Casorati IQ and PD relative L2."""
+    from paper_2509_05464_gb300 import fq
+    from paper_2509_05464_gb300.pipeline import Pipeline
+    ps = Pipeline(w_small, **kw)
+    ps.upload()
+    ps.step()
+    fq.fq_clutter_status(ps.ws_svd)
+    pd = ps.download().numpy().copy()
+    rf = ps.rf.float().cpu().numpy()
+    iq = ps.iq.float().cpu().numpy()
+    del ps
+    S_ref = ref["S"]
+    return {"rf_rel_l2": rel_l2(rf, ref["rf"]),
+            "iq_rel_l2": rel_l2(np.stack([iq[..., 0], iq[..., 1]]), np.stack([S_ref.real, S_ref.imag])),
+            "pd_rel_l2": rel_l2(pd, ref["pd"])}
+
+
+def precision_variants(w, w_small, ref, steps, warmup):
+    """Each storage variant on the full workload (device-timed steps) and its
+    error against the FP64 oracle on the reduced workload."""
     import torch
     from paper_2509_05464_gb300 import fq
     from paper_2509_05464_gb300.pipeline import Pipeline
-    gmode = {"f32": fq.FQ_GRAM_F32, "tf32": fq.FQ_GRAM_TF32, "bf16": fq.FQ_GRAM_BF16}
-    w_small = dataclasses.replace(w, n_frames=n_ref, k_cut=min(w.k_cut, n_ref - 1))
-    S_ref = ref["S"]
     out = []
-    stream = torch.cuda.current_stream()
     for name, rf_t, ch_t, iq_t, gm in VARIANTS:
-        kw = dict(rf_dtype=getattr(torch, rf_t), ch_dtype=getattr(torch, ch_t), iq_dtype=getattr(torch, iq_t),
-                  gram_mode=gmode[gm])
+        kw = variant_kwargs(rf_t, ch_t, iq_t, gm)
         pl = Pipeline(w, **kw)
         pl.upload()
         for _ in range(warmup):
             pl.step()
-        names = ("classify", "advect", "simulate", "beamform", "clutter")
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(steps)]
-        torch.cuda.synchronize()
-        for i in range(steps):
-            ev[i][0].record(stream)
-            for j, nm in enumerate(names):
-                getattr(pl, nm)()
-                ev[i][j + 1].record(stream)
-        torch.cuda.synchronize()
+        ms, stage = time_steps(pl, steps)
         fq.fq_clutter_status(pl.ws_svd)
-        ms = sum(e[0].elapsed_time(e[-1]) for e in ev) / steps
-        stage = {nm: sum(e[j].elapsed_time(e[j + 1]) for e in ev) / steps for j, nm in enumerate(names)}
-        rf = pl.rf[:n_ref].float().cpu().numpy()
-        iq = pl.iq[:, :n_ref].float().cpu().numpy()
-        iq_c = iq[..., 0] + 1j * iq[..., 1]
         del pl
-        ps = Pipeline(w_small, **kw)
-        ps.upload()
-        ps.step()
-        fq.fq_clutter_status(ps.ws_svd)
-        pd = ps.download().numpy().copy()
-        del ps
+        torch.cuda.empty_cache()
+        err = variant_errors(w_small, ref, kw) if ref is not None else None
         out.append({"variant": name, "rf": rf_t, "channel_iq": ch_t, "casorati": iq_t, "gram": gm,
-                    "ms_per_step": ms, "stage_ms": stage,
-                    "err_vs_fp64": {"rf_rel_l2": rel_l2(rf, ref["rf"]),
-                                    "iq_rel_l2": rel_l2(np.stack([iq_c.real, iq_c.imag]),
-                                                        np.stack([S_ref.real, S_ref.imag])),
-                                    "pd_rel_l2": rel_l2(pd, ref["pd"])}})
+                    "steps": steps, "ms_per_step": ms, "stage_ms": stage, "err_vs_fp64": err})
         torch.cuda.empty_cache()
     return out
 
 
 def run_reference(args, rank, world):
-    from paper_2509_05464_gb300 import workload as W
+    """The FP64 oracle on the host cores, each step a bounded sample of the
+    workload extrapolated to the whole step (3D) or the whole path on the
+    first 2 frames (2D)."""
     import oracle
     if rank != 0:
         return
-    w = W.config2(seed=2)
-    nf = 2
+    name = args.workload if args.workload in STEP_WORKLOADS else "c3"
+    w = make_workload(name, 0, args.frames)
+    if name == "c3":
+        def one():
+            return oracle_sample_3d(w, n_lines=32, block=24, p_svd=8192)
+        cs = w.n_frames * w.A * w.M * w.Ns
+    else:
+        nf = 2
+
+        def one():
+            return oracle_run(w, nf)[0], f"each step: the whole path on the first {nf} of {w.n_frames} frames"
+        cs = nf * w.A * w.M * w.Ns
     for _ in range(args.warmup):
-        oracle_step(w, nf)
-    times = [oracle_step(w, nf) for _ in range(args.steps)]
-    t = sum(times) / len(times)
-    cs = nf * w.A * w.M * w.Ns
+        one()
+    res = [one() for _ in range(args.steps)]
+    t = sum(r[0] for r in res) / len(res)
     v = cs / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "sample_frames": nf},
+            "config": {"workload": w.name},
             "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": oracle.num_threads(),
-                             "sample": f"each step: the whole path on the first {nf} of {w.n_frames} frames"},
+                             "sample": res[-1][1]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -268,16 +434,19 @@ def run_reference(args, rank, world):
 def run_ours(args, rank, world, local):
     import torch
     from paper_2509_05464_gb300 import fq
-    from paper_2509_05464_gb300 import workload as W
     from paper_2509_05464_gb300.pipeline import Pipeline
 
     torch.cuda.set_device(local)
     fq.lib()
-    w = W.config2(seed=2 + rank, n_frames=args.frames)  # an independent ensemble per rank (weak scaling)
+    name = args.workload
+    spec = STEP_WORKLOADS[name]
+    w = make_workload(name, rank, args.frames)  # an independent ensemble per rank (weak scaling)
     if args.scatterers or args.grid_div:  # reduced cases for profiler captures only
+        from paper_2509_05464_gb300 import workload as W
         w = W.shrink(w, max_scat=args.scatterers or None, grid_div=args.grid_div or None)
-    gram_mode = {"f32": fq.FQ_GRAM_F32, "tf32": fq.FQ_GRAM_TF32, "bf16": fq.FQ_GRAM_BF16}[args.gram]
-    pl = Pipeline(w, gram_mode=gram_mode)
+    gram = args.gram or "f32"
+    kw = variant_kwargs(spec["rf"], spec["ch"], spec["iq"], gram)
+    pl = Pipeline(w, **kw)
     pl.upload()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -289,23 +458,11 @@ def run_ours(args, rank, world, local):
 
     clk = ClockSampler(local)
     clk.start()
-    stages = ("classify", "advect", "simulate", "beamform", "clutter")
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
     barrier()
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.zero_()  # L2 flush outside the timed events
-        ev[i][0].record(stream)
-        for j, name in enumerate(stages):
-            getattr(pl, name)()
-            ev[i][j + 1].record(stream)
-    torch.cuda.synchronize()
+    ms_local, stage_ms = time_steps(pl, args.steps, flush)
     barrier()
     clocks = clk.stop()
-    step_ms = [e[0].elapsed_time(e[-1]) for e in ev]
-    stage_ms = {name: sum(e[j].elapsed_time(e[j + 1]) for e in ev) / args.steps for j, name in enumerate(stages)}
-    ms = max_over_ranks(sum(step_ms) / len(step_ms))
-    rf_avg = stage_ms["simulate"]
+    ms = max_over_ranks(ms_local)
 
     # end to end through the public API (pinned host in, PD out)
     e2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -326,38 +483,69 @@ def run_ours(args, rank, world, local):
     pk, src = peaks()
     sm_for_peak = float(pk.get("sm_max_mhz", 2070.0))
     peak = fp32_alu_peak_tflops(sm_for_peak)
+    peak_src = (f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
+                f"({src} max clock)")
     p = w.probe
-    taps = p.n_cycles * p.fs / p.f0  # 2 * half-width
-    pairs = w.n_frames * w.A * w.M * w.S
-    flop = pairs * (GEOM_FLOP_PER_PAIR + FLOP_PER_TAP * taps)
-    achieved = flop / (rf_avg * 1e-3) / 1e12
-    cpu, ref = cpu_baseline(w) if args.cpu_baseline else (None, None)
-    variants = None
-    if ref is not None and args.variants:
+    taps = p.n_cycles * p.fs / p.f0
+    pairs = float(w.n_frames) * w.A * w.M * w.S
+    flop = rf_flop(w)
+    rf_ms = stage_ms["simulate"]
+    achieved = flop / (rf_ms * 1e-3) / 1e12
+    triples = das_active_triples(w)
+    dflop = das_flop(w, triples)
+    das_ms = stage_ms["das"]
+    d_ach = dflop / (das_ms * 1e-3) / 1e12
+    full = args.frames == 0 and not (args.scatterers or args.grid_div)
+    traffic = RF_TRAFFIC_BYTES.get(name) if full else None
+    cpu = None
+    if args.cpu_baseline:
+        cpu = cpu_baseline(name, w)
+    variants, err = None, None
+    if args.variants:
+        import oracle
+        from paper_2509_05464_gb300 import workload as W
+        w_small = reduced_workload(name, w)
+        st, mt = W.segment_table(w_small), W.motion_table(w_small.motion)
+        t0 = time.perf_counter()
+        ref = oracle.pipeline(w_small, st, mt)
+        ref_s = time.perf_counter() - t0
         del pl, flush
         torch.cuda.empty_cache()
-        variants = precision_variants(w, ref, 6, steps=3, warmup=2)
+        vsteps = args.variant_steps or (4 if name == "c3" else 20)
+        variants = precision_variants(w, w_small, ref, steps=vsteps, warmup=2)
+        err = next(v["err_vs_fp64"] for v in variants
+                   if (v["rf"], v["channel_iq"], v["casorati"], v["gram"]) == (spec["rf"], spec["ch"], spec["iq"], gram))
+        err = dict(err, reduced_workload=w_small.name, oracle_s=round(ref_s, 1))
+    stor = f"RF {spec['rf']}, channel IQ {spec['ch']}, Casorati {spec['iq']}, Gram {gram}, FP32 arithmetic"
     line = {
         "metric": METRIC, "value": total_cs / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic",
         "config": {"workload": w.name, "frames": w.n_frames, "angles": w.A, "elements": w.M, "samples": w.Ns,
-                   "scatterers": w.S, "pixels": w.P, "gram": args.gram,
+                   "scatterers": w.S, "voxels": w.P, "storage": stor,
                    "parallelism": f"independent ensemble per GPU x{world}",
                    "l2": "256 MiB buffer rewritten between timed steps, outside the timed events"},
         "das_voxel_angle_per_s": total_va / (ms * 1e-3),
+        "das_voxel_angle_per_s_das_kernel": total_va / (das_ms * 1e-3),
         "stage_ms": stage_ms,
         "roofline": {"bound": "alu", "kernel": "rf_synth_quad_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": RF_TRAFFIC_BYTES if w.n_frames == 200 and w.S == 100_000 else None,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
-                                    f"({src} max clock)",
-                     "work": f"{GEOM_FLOP_PER_PAIR:.0f} + {FLOP_PER_TAP:.0f} x {taps:.3f} taps FLOP per pair, "
-                             f"{pairs:.3e} pairs"},
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_src,
+                     "work": f"{flop / pairs:.2f} FLOP per (scatterer, element, transmit, frame) pair "
+                             f"({taps:.3f} taps), {pairs:.3e} pairs"},
+        "roofline_das": {"bound": "alu", "kernel": "das_kernel", "achieved": d_ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": d_ach / peak, "traffic": None, "peak_source": peak_src,
+                         "work": f"{DAS_FLOP_PER_FRAME:.0f} FLOP per frame + {DAS_FLOP_PER_TRIPLE:.0f} per active "
+                                 f"(voxel, transmit, element) triple, {triples:.4e} triples x {w.n_frames} frames",
+                         "hbm_gbs_algorithmic": (w.A * w.M * w.Ns * fq.frame_pad(w.n_frames) * 2
+                                                 * torch.empty((), dtype=kw["ch_dtype"]).element_size()
+                                                 + w.P * w.n_frames * 2
+                                                 * torch.empty((), dtype=kw["iq_dtype"]).element_size())
+                                                / (das_ms * 1e-3) / 1e9},
         "cpu_baseline": cpu,
         "e2e": {"value": total_cs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
                 "d2h_bytes_per_step": d2h_bytes, "ms_per_step": e2e_ms},
-        "err_vs_fp64": variants[0]["err_vs_fp64"] if variants else None,
+        "err_vs_fp64": err,
         "precision_variants": variants,
         "gpu_launches": n_launches * args.steps,
         "clocks": clocks,
@@ -609,7 +797,7 @@ def run_field(args, rank, world, local):
 
     torch.cuda.set_device(local)
     fq.lib()
-    fw = W.field_c2(seed=2 + rank, n_frames=args.frames)
+    fw = W.field_c2(seed=2 + rank, n_frames=args.frames or 200)
     h_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (fw.p0, fw.seg, fw.v)]
     p0, seg, v = (t.to("cuda") for t in h_in)
     pos = torch.empty((fw.n_frames, 3, fw.S), dtype=torch.float32, device="cuda")
@@ -715,7 +903,7 @@ def run_post(args, rank, world, local):
 
     torch.cuda.set_device(local)
     fq.lib()
-    w = W.config2(seed=2 + rank, n_frames=args.frames)
+    w = W.config2(seed=2 + rank, n_frames=args.frames or 200)
     pl = Pipeline(w)
     pl.upload()
     pl.step()
@@ -816,7 +1004,7 @@ def run_das_matrix(args, rank, world, local):
 
     torch.cuda.set_device(local)
     fq.lib()
-    w = W.config2(seed=2 + rank, n_frames=args.frames)
+    w = W.config2(seed=2 + rank, n_frames=args.frames or 200)
     pl = Pipeline(w)
     pl.upload()
     pl.classify()
@@ -899,7 +1087,7 @@ def run_rf_freq(args, rank, world, local):
 
     torch.cuda.set_device(local)
     fq.lib()
-    F = args.frames if args.frames != 200 else 2
+    F = args.frames or 2
     w = W.config2(seed=2 + rank, n_frames=F)
     pl = Pipeline(w)
     pl.upload()
@@ -985,7 +1173,7 @@ def run_gram(args, rank, world, local):
 
     torch.cuda.set_device(local)
     fq.lib()
-    P, F = 96 ** 3, args.frames if args.frames != 200 else 400
+    P, F = 96 ** 3, args.frames or 400
     g = torch.Generator(device="cuda").manual_seed(5 + rank)
     S = torch.randn((P, F, 2), generator=g, device="cuda")
     stream = torch.cuda.current_stream()
@@ -1051,11 +1239,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the precision variants (each is checked against the oracle)")
-    ap.add_argument("--frames", type=int, default=200, help="ensemble length (200 = the benchmark workload)")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="ensemble length (0 = the workload's own: 100 for c3, 200 for c2)")
+    ap.add_argument("--variant-steps", type=int, default=0,
+                    help="timed steps per storage variant (0 = 4 for c3, 20 for c2)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
-    ap.add_argument("--workload", choices=["c2", "c4", "c5", "field", "post", "dasmatrix", "rffreq", "gram"], default="c2",
-                    help="c2: one 200-frame 2D ensemble (default); c4: the 64-ensemble uneven batch; "
+    ap.add_argument("--workload", choices=["c3", "c2", "c4", "c5", "field", "post", "dasmatrix", "rffreq", "gram"],
+                    default="c3",
+                    help="c3: one 100-frame 3D volumetric ensemble (default); c2: one 200-frame 2D ensemble; "
+                         "c4: the 64-ensemble uneven batch; "
                          "c5: the learned clutter filter; field: advection in a gridded velocity field; "
                          "post: display compression, MIPs and image quality; dasmatrix: the paper's "
                          "explicit DAS matrices against the fused DAS; rffreq: RF synthesis in the frequency "
@@ -1069,7 +1262,7 @@ def main():
     ap.add_argument("--arena-gb", type=int, default=64, help="c4: arena budget in GiB (waves beyond it)")
     ap.add_argument("--no-sequential", dest="sequential", action="store_false",
                     help="c4: skip the one-by-one comparison run")
-    ap.add_argument("--gram", choices=["f32", "tf32", "bf16"], default="f32",
+    ap.add_argument("--gram", choices=["f32", "tf32", "bf16"], default="",
                     help="Casorati Gram arithmetic: FP32 CUDA cores or TF32 / BF16 tensor cores")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)

@@ -104,6 +104,24 @@ class Pipeline:
         fq.fq_beamform_das(w.probe, w.tilt_x, w.tilt_y, self.rf, w.n_frames, w.grid, self.ch_dtype,
                            self.iq_dtype, iq=self.iq, ws=self.ws_das)
 
+    def channel_iq(self):
+        """The channel IQ [A M][Ns][F_pad][2] that beamform() keeps in its workspace."""
+        w = self.w
+        Fp = fq.frame_pad(w.n_frames)
+        n = w.A * w.M * w.Ns * Fp * 2
+        es = torch.empty((), dtype=self.ch_dtype).element_size()
+        return self.ws_das[:n * es].view(self.ch_dtype).view(w.A * w.M, w.Ns, Fp, 2)
+
+    def rf2iq(self):
+        """First half of beamform(): rf2iq into the channel IQ."""
+        w = self.w
+        fq.fq_rf2iq(w.probe, w.A * w.M, w.n_frames, self.rf, iq_ch=self.channel_iq())
+
+    def das(self):
+        """Second half of beamform(): DAS compounding of the channel IQ."""
+        w = self.w
+        fq.fq_das(w.probe, w.tilt_x, w.tilt_y, self.channel_iq(), w.n_frames, w.grid, iq=self.iq)
+
     def clutter(self):
         w = self.w
         fq.fq_clutter_svd(self.iq, w.k_cut, w.energy_thresh, self.gram_mode, want_iq_f=self.iq_f is not None,
