@@ -56,6 +56,8 @@ def lib():
                                          _i64, _p, _p, _i, _p]
             L.or_simulate_rf_lines.argtypes = [_i, _i, _d, _d, _d, _d, _d, _d, _d, _d, _i, _i, _p, _p, _i, _p,
                                                _i64, _p, _p, _p]
+            L.or_simulate_rf_pfield.argtypes = [_i, _i, _d, _d, _d, _d, _d, _d, _d, _d, _i, _i, _i, _i, _p, _p,
+                                                _p, _i, _i64, _p, _p, _p]
             L.or_rf2iq_taps.argtypes = [_d, _d, _p]
             L.or_rf2iq_taps.restype = _i
             L.or_rf2iq.argtypes = [_d, _d, _i, _i64, _p, _p]
@@ -146,6 +148,27 @@ def simulate_rf_freq(probe, tilt_x, tilt_y, pos, amp, n_fft=None):
                               probe.f0, probe.fs, probe.c, probe.alpha_db_cm_mhz, probe.n_cycles,
                               probe.n_samples, N, A, _ptr(tilt_x), _ptr(tilt_y), amp.shape[0], _ptr(pos),
                               _ptr(amp), _ptr(rf))
+    return rf
+
+
+def simulate_rf_pfield(probe, tilt_x, tilt_y, apod, pos, amp, n_sub=1, n_fft=None):
+    """Frequency-domain RF [A][M][Ns] float64 with the per-element transmit
+    sum of Eq. 1 (transmit weights apod [M], plane-wave steering delays) and
+    n_sub sub-elements per element along x (Eq. 2); n_fft defaults to 2 Ns."""
+    tilt_x = np.ascontiguousarray(tilt_x, np.float64)
+    tilt_y = np.ascontiguousarray(tilt_y, np.float64)
+    apod = np.ascontiguousarray(apod, np.float64)
+    pos = np.ascontiguousarray(pos, np.float32)
+    amp = np.ascontiguousarray(amp, np.float32)
+    A = tilt_x.shape[0]
+    M = probe.nx * probe.ny
+    assert apod.shape == (M,) and n_sub >= 1
+    N = 2 * probe.n_samples if n_fft is None else int(n_fft)
+    rf = np.zeros((A, M, probe.n_samples), np.float64)
+    lib().or_simulate_rf_pfield(probe.nx, probe.ny, probe.pitch_x, probe.pitch_y, probe.width_x, probe.width_y,
+                                probe.f0, probe.fs, probe.c, probe.alpha_db_cm_mhz, probe.n_cycles,
+                                probe.n_samples, N, A, _ptr(tilt_x), _ptr(tilt_y), _ptr(apod), int(n_sub),
+                                amp.shape[0], _ptr(pos), _ptr(amp), _ptr(rf))
     return rf
 
 

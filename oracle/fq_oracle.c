@@ -926,3 +926,134 @@ void or_simulate_rf_freq(int nx, int ny, double px, double py, double wx, double
     }
     free(Sw);
 }
+
+/* ------------------------------------------------------------------------
+ * RF synthesis with the transmit sum of Eq. 1 and the sub-elements of
+ * Eq. 2 (App. D), per frequency like or_simulate_rf_freq (Alg. 2 step 2.6):
+ * every element e of the probe transmits with weight W_e (the transmit
+ * aperture weighting) and the plane-wave steering delay
+ *   dtau_{a,e} = (u_a . e - min_e' u_a . e') / c,
+ * each element is split into v sub-elements along x (Eq. 2: the element's
+ * pressure is the coherent sum over its sub-elements), and a sub-element q
+ * radiates to or receives from a scatterer at distance d the Green's function
+ *   g_q(f) = D_q(f) exp(-alpha f d) e^{-i 2 pi f d / c} / d,
+ *   D_q(f) = sinc(k (w_x / 2v) (x_s - x_q) / d) [* sinc(k (w_y / 2) (y_s - y_q) / d)],
+ *   sub-element centres x_q = x_e + (mu - (v - 1)/2) w_x / v, y_q = y_e.
+ *   T_{a,s}(f) = sum_e W_e e^{-i 2 pi f dtau_{a,e}} (1/v) sum_mu g_{e mu}(f)
+ *   G_{m,s}(f) = (1/v) sum_mu g_{m mu}(f)
+ *   RF_{a,m}[n] = df sum_{j < N/2} w_j Re{ S(f_j) sum_s R_s T_{a,s}(f_j) G_{m,s}(f_j) e^{i 2 pi f_j n / fs} }
+ * with f_j, df, w_j, S(f) as in or_simulate_rf_freq; elevation focusing
+ * delta(Y, r, k) = 1 (unfocused elements).  apod: double [M] transmit
+ * weights; rf: double [A][M][Ns].  Pinned by: the discrete spectrum of a
+ * single-element transmit and receive (closed form), superposition over
+ * transmit weights, the far-field limit of the sub-element sum, and the
+ * arrival time of a steered full-aperture transmit on the array axis.
+ * ---------------------------------------------------------------------- */
+static void or_green(double x, double y, double z, double qx, double qy, double bx, double by, int matrix,
+                     double f, double c, double alpha_np, double *re, double *im)
+{
+    double dx = x - qx, dy = y - qy;
+    double d = sqrt(dx * dx + dy * dy + z * z);
+    double k = 2.0 * OR_PI * f / c;
+    double D = sinc_unnorm(k * bx * dx / d);
+    if (matrix) D *= sinc_unnorm(k * by * dy / d);
+    double a = D * exp(-alpha_np * f * 1e-6 * d) / d;
+    *re = a * cos(-k * d);
+    *im = a * sin(-k * d);
+}
+
+void or_simulate_rf_pfield(int nx, int ny, double px, double py, double wx, double wy,
+                           double f0, double fs, double c, double alpha_db_cm_mhz, int n_cycles, int ns,
+                           int n_fft, int n_ang, const double *tilt_x, const double *tilt_y, const double *apod,
+                           int n_sub, int64_t S, const float *pos, const float *amp, double *rf)
+{
+    const int M = nx * ny;
+    const int v = n_sub;
+    const int matrix = ny > 1;
+    const double T = (double)n_cycles / f0;
+    const double alpha_np = alpha_db_cm_mhz * 100.0 / (20.0 / log(10.0)); /* Np / (m MHz) */
+    const double df = fs / (double)n_fft;
+    const int J = n_fft / 2;
+    const double bx = 0.5 * wx / v, by = 0.5 * wy;
+    const float *X = pos, *Y = pos + S, *Z = pos + 2 * S;
+    double *Sw = (double *)malloc(sizeof(double) * J);
+    for (int j = 0; j < J; ++j) Sw[j] = pulse_spectrum(j * df, f0, T);
+    double *Tre = (double *)malloc(sizeof(double) * (size_t)(S > 0 ? S : 1) * J);
+    double *Tim = (double *)malloc(sizeof(double) * (size_t)(S > 0 ? S : 1) * J);
+
+    for (int a = 0; a < n_ang; ++a) {
+        double u[3];
+        pw_dir(tilt_x[a], tilt_y[a], u);
+        double origin = pw_origin(u, nx, ny, px, py);
+        /* transmit field at every scatterer and frequency */
+        #pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t s = 0; s < S; ++s) {
+            double x = X[s], y = Y[s], z = Z[s];
+            for (int j = 0; j < J; ++j) {
+                double f = j * df, tr = 0.0, ti = 0.0;
+                for (int e = 0; e < M; ++e) {
+                    if (apod[e] == 0.0) continue;
+                    double ex, ey;
+                    element_pos(e, nx, ny, px, py, &ex, &ey);
+                    double dtau = (u[0] * ex + u[1] * ey - origin) / c;
+                    double sr = 0.0, si = 0.0;
+                    for (int mu = 0; mu < v; ++mu) {
+                        double qx = ex + ((double)mu - 0.5 * (v - 1)) * wx / v;
+                        double gr, gi;
+                        or_green(x, y, z, qx, ey, bx, by, matrix, f, c, alpha_np, &gr, &gi);
+                        sr += gr;
+                        si += gi;
+                    }
+                    double w = apod[e] / v;
+                    double ph = -2.0 * OR_PI * f * dtau;
+                    double cr = cos(ph), ci = sin(ph);
+                    tr += w * (sr * cr - si * ci);
+                    ti += w * (sr * ci + si * cr);
+                }
+                Tre[s * J + j] = tr;
+                Tim[s * J + j] = ti;
+            }
+        }
+        /* receive per element, then the inverse transform */
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int m = 0; m < M; ++m) {
+            double ex, ey;
+            element_pos(m, nx, ny, px, py, &ex, &ey);
+            double *Pre = (double *)calloc(J, sizeof(double)), *Pim = (double *)calloc(J, sizeof(double));
+            for (int64_t s = 0; s < S; ++s) {
+                double x = X[s], y = Y[s], z = Z[s];
+                double R = (double)amp[s];
+                for (int j = 0; j < J; ++j) {
+                    double f = j * df, gr = 0.0, gi = 0.0;
+                    for (int mu = 0; mu < v; ++mu) {
+                        double qx = ex + ((double)mu - 0.5 * (v - 1)) * wx / v;
+                        double hr, hi;
+                        or_green(x, y, z, qx, ey, bx, by, matrix, f, c, alpha_np, &hr, &hi);
+                        gr += hr;
+                        gi += hi;
+                    }
+                    gr /= v;
+                    gi /= v;
+                    double tr = Tre[s * J + j], ti = Tim[s * J + j];
+                    Pre[j] += R * (tr * gr - ti * gi);
+                    Pim[j] += R * (tr * gi + ti * gr);
+                }
+            }
+            double *line = rf + ((int64_t)a * M + m) * ns;
+            for (int n = 0; n < ns; ++n) {
+                double t = n / fs, acc = 0.0;
+                for (int j = 0; j < J; ++j) {
+                    double w = j == 0 ? 1.0 : 2.0;
+                    double ph = 2.0 * OR_PI * j * df * t;
+                    acc += w * Sw[j] * (Pre[j] * cos(ph) - Pim[j] * sin(ph));
+                }
+                line[n] = df * acc;
+            }
+            free(Pre);
+            free(Pim);
+        }
+    }
+    free(Tre);
+    free(Tim);
+    free(Sw);
+}
