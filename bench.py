@@ -69,9 +69,12 @@ def peaks():
 
 
 def fp32_alu_peak_tflops(sm_mhz):
-    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2 (packed f32x2 FMA issues
-    # two lanes' worth per instruction on sm_103a) x clock
-    return 152 * 128 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock.  The packed f32x2
+    # FMA (two lanes per instruction) does not raise this: `--workload
+    # alupeak` measures 76.9 TFLOP/s with scalar FFMA and 79.3 with f32x2 at
+    # 2070 MHz, i.e. a packed instruction occupies the FMA pipe for two
+    # cycles; it saves issue slots, not pipe time.
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -234,7 +237,7 @@ def oracle_run(w, n_frames):
     return time.perf_counter() - t0, r
 
 
-def oracle_sample_3d(w, n_lines=64, block=32, p_svd=16384):
+def oracle_sample_3d(w, n_lines=192, block=40, p_svd=65536):
     """The oracle on bounded subsets of a 3D ensemble, each stage timed and
     extrapolated linearly by its exact work count to the whole step:
     membership once; advection of one frame (x F); RF of n_lines (transmit,
@@ -248,6 +251,7 @@ def oracle_sample_3d(w, n_lines=64, block=32, p_svd=16384):
     st, mt = W.segment_table(w), W.motion_table(w.motion)
     F, A, M, Ns, P = w.n_frames, w.A, w.M, w.Ns, w.P
     t = {}
+    t_start = time.perf_counter()
     c = time.perf_counter()
     _, amp = oracle.classify(w.p0, w.seg, st, len(w.segments), w.amp)
     t["classify"] = time.perf_counter() - c
@@ -281,12 +285,13 @@ def oracle_sample_3d(w, n_lines=64, block=32, p_svd=16384):
     c = time.perf_counter()
     oracle.svd_filter(S, w.k_cut, w.energy_thresh)
     t["svd_pd"] = (time.perf_counter() - c) * P / p_svd
+    measured = time.perf_counter() - t_start
     total = sum(t.values())
     desc = (f"FP64 oracle on bounded subsets, each stage extrapolated linearly by its work count: membership "
             f"of all {w.S} scatterers, advection of 1 of {F} frames, RF of {n_lines} of {A * M} (transmit, "
             f"element) lines of frame 0 with every scatterer, rf2iq of those lines, DAS of a {block}^3 voxel "
             f"block at 1 and 9 frames (a + b F fit), the SVD filter of a {p_svd} x {F} random stand-in; "
-            f"measured {sum(dt) + t['classify']:.1f} s of stages; extrapolated stage seconds "
+            f"{measured:.1f} s measured; extrapolated stage seconds "
             + json.dumps({k: round(v, 1) for k, v in t.items()}))
     return total, desc
 
@@ -483,7 +488,7 @@ def run_ours(args, rank, world, local):
     pk, src = peaks()
     sm_for_peak = float(pk.get("sm_max_mhz", 2070.0))
     peak = fp32_alu_peak_tflops(sm_for_peak)
-    peak_src = (f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
+    peak_src = (f"152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_for_peak:.0f} MHz "
                 f"({src} max clock)")
     p = w.probe
     taps = p.n_cycles * p.fs / p.f0
@@ -668,7 +673,7 @@ def run_batched(args, rank, world, local):
         "batched_speedup_vs_sequential": (seq_ms / ms_step) if args.sequential else None,
         "roofline": {"bound": "alu", "kernel": "rf_quad_batched_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_for_peak:.0f} MHz "
                                     f"({src} max clock)",
                      "work": f"{GEOM_FLOP_PER_PAIR:.0f} + {FLOP_PER_TAP:.0f} x {taps:.3f} taps FLOP per pair, "
                              f"{pairs:.3e} pairs"},
@@ -877,7 +882,7 @@ def run_field(args, rank, world, local):
                    "frac_over_2_ulps": float((ulps > 2).any(axis=(0, 1)).mean())},
         "roofline": {"bound": "alu", "kernel": "advect_field_kernel", "achieved": ach, "peak": peak,
                      "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x {sm_for_peak:.0f} MHz "
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_for_peak:.0f} MHz "
                                     f"({src} max clock)",
                      "work": f"{FIELD_FLOP_PER_STEP} FLOP per RK4 step, {steps:.3e} steps"},
         "cpu_baseline": cpu,
@@ -1136,6 +1141,24 @@ def run_rf_freq(args, rank, world, local):
     got = sub[0].cpu().numpy()
     err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
     td_vs_fd = float(torch.linalg.norm(rf_f - rf_t) / torch.linalg.norm(rf_t))
+    # Eq. 1's transmit sum over all 128 elements and Eq. 2's sub-elements
+    # (2 per element), on the first 10000 scatterers of frame 0, every
+    # transmit; parity against the oracle on 200 of them, transmit 2
+    n_tx = 10_000
+    ptx = torch.from_numpy(np.ascontiguousarray(pos[0, :, :n_tx].cpu().numpy())[None]).cuda()
+    atx = torch.from_numpy(np.ascontiguousarray(amp[:n_tx].cpu().numpy())).cuda()
+    rf_p = torch.empty((1, w.A, w.M, w.Ns), dtype=torch.float32, device="cuda")
+    pf_ms = timed(lambda: fq.fq_simulate_rf_pfield(w.probe, w.tilt_x, w.tilt_y, ptx, atx, 1, n_sub=2, n_fft=n_fft,
+                                                   rf=rf_p), 1)
+    n_ps = 200
+    sub_p = fq.fq_simulate_rf_pfield(w.probe, w.tilt_x[2:3], w.tilt_y[2:3], ptx[:, :, :n_ps].contiguous(),
+                                     atx[:n_ps].contiguous(), 1, n_sub=2, n_fft=n_fft)
+    t0 = time.perf_counter()
+    want_p = oracle.simulate_rf_pfield(w.probe, w.tilt_x[2:3], w.tilt_y[2:3], np.ones(w.M),
+                                       ptx[0, :, :n_ps].cpu().numpy(), atx[:n_ps].cpu().numpy(), n_sub=2,
+                                       n_fft=n_fft)
+    oracle_p_s = time.perf_counter() - t0
+    err_p = float(np.linalg.norm(sub_p[0].cpu().numpy() - want_p) / np.linalg.norm(want_p))
     pk, src = peaks()
     peak = fp32_alu_peak_tflops(float(pk.get("sm_max_mhz", 2070.0)))
     terms = F * w.A * w.M * w.S * (n_fft // 2)
@@ -1151,9 +1174,15 @@ def run_rf_freq(args, rank, world, local):
                         "rel_l2_freq_vs_time": td_vs_fd},
         "parity": {"sample": f"first {ns_s} scatterers of frame 0, transmit 2, every element",
                    "rel_l2_vs_oracle": err, "oracle_s": oracle_s},
+        "transmit_sum": {"what": "Eq. 1 transmit sum over all 128 elements (uniform weights, steering delays) and "
+                                 "2 sub-elements per element (Eq. 2)",
+                         "sample": f"first {n_tx} scatterers of frame 0, every transmit and element",
+                         "ms": pf_ms, "channel_samples_per_s": w.A * w.M * w.Ns / (pf_ms * 1e-3),
+                         "parity": {"sample": f"first {n_ps} scatterers, transmit 2", "rel_l2_vs_oracle": err_p,
+                                    "oracle_s": oracle_p_s}},
         "roofline": {"bound": "alu", "kernel": "spectrum_kernel", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                      "frac": ach / peak, "traffic": None,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x 2 (f32x2) x max clock ({src})",
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 (FMA) x max clock ({src})",
                      "work": f"22 FLOP per (scatterer, element, transmit, frame, bin) term, {terms:.3e} terms"},
         "cpu_baseline": None,
         "e2e": None,
@@ -1222,6 +1251,52 @@ def run_gram(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ FP32 ALU probe --
+def run_alu_probe(args, rank, world, local):
+    """Measured FP32 throughput, scalar FFMA and packed f32x2 FMA: the
+    evidence behind the ALU roof (152 SMs x 128 lanes x 2 FLOP x clock)
+    that the RF and DAS lines divide by."""
+    import torch
+    from paper_2509_05464_gb300 import fq
+    torch.cuda.set_device(local)
+    fq.lib()
+    sink = torch.zeros(256, device="cuda")
+    stream = torch.cuda.current_stream()
+    blocks, iters = 152 * 8 * 8, 4096
+    out = {}
+    clk = ClockSampler(local)
+    clk.start()
+    for packed in (0, 1):
+        for _ in range(max(1, args.warmup)):
+            fq.fq_alu_probe(packed, blocks, iters, sink)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            fq.fq_alu_probe(packed, blocks, iters, sink)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        flop = blocks * 256.0 * iters * 8 * 2 * (2 if packed else 1)
+        out["f32x2" if packed else "scalar"] = {"ms": ms, "tflops": flop / (ms * 1e-3) / 1e12}
+    clocks = clk.stop()
+    if rank != 0:
+        return
+    pk, src = peaks()
+    smax = float(pk.get("sm_max_mhz", 2070.0))
+    line = {"metric": "FP32 FMA throughput (TFLOP/s), scalar and packed f32x2", "value": out["f32x2"]["tflops"],
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["f32x2"]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{blocks} CTAs x 256 threads x {iters} rounds x 8 independent FMA chains"},
+            "probe": out,
+            "derived_peak_tflops": {"unit_count": fp32_alu_peak_tflops(smax),
+                                    "clock_mhz": smax, "clock_source": src},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": 2 * (args.steps + max(1, args.warmup)),
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def b_arena_gb(ms, args):
     from paper_2509_05464_gb300 import fq
     b = fq.Batch(ms, plan_only=True, max_arena_bytes=args.arena_gb << 30)
@@ -1245,7 +1320,8 @@ def main():
                     help="timed steps per storage variant (0 = 4 for c3, 20 for c2)")
     ap.add_argument("--scatterers", type=int, default=0, help="profiling only: keep this many scatterers")
     ap.add_argument("--grid-div", type=int, default=0, help="profiling only: divide the pixel grid per axis")
-    ap.add_argument("--workload", choices=["c3", "c2", "c4", "c5", "field", "post", "dasmatrix", "rffreq", "gram"],
+    ap.add_argument("--workload", choices=["c3", "c2", "c4", "c5", "field", "post", "dasmatrix", "rffreq", "gram",
+                                           "alupeak"],
                     default="c3",
                     help="c3: one 100-frame 3D volumetric ensemble (default); c2: one 200-frame 2D ensemble; "
                          "c4: the 64-ensemble uneven batch; "
@@ -1283,6 +1359,8 @@ def main():
         run_rf_freq(args, rank, world, local)
     elif args.workload == "gram":
         run_gram(args, rank, world, local)
+    elif args.workload == "alupeak":
+        run_alu_probe(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     import torch.distributed as dist

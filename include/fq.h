@@ -246,6 +246,32 @@ fq_status fq_simulate_rf_freq(const fq_probe *probe, const fq_tx *tx, const floa
                               int64_t S, int32_t n_frames, int32_t n_fft, int32_t out_dtype, void *rf,
                               void *workspace, size_t workspace_bytes, void *stream);
 
+/* Eq. 1 with its transmit sum over elements and Eq. 2's sub-elements (App.
+ * D; Alg. 2 steps 2.2 and 2.6), per frequency like fq_simulate_rf_freq:
+ *   RF[f][a][m][n] = df sum_j w_j Re{ S(f_j) sum_s R_s T_{a,s}(f_j) G_{m,s}(f_j) e^{i 2 pi f_j n / fs} }
+ *   T_{a,s}(f) = sum_e W_e e^{-i 2 pi f dtau_{a,e}} (1/v) sum_{mu < v} g_{e mu,s}(f)   (transmit)
+ *   G_{m,s}(f) = (1/v) sum_{mu < v} g_{m mu,s}(f)                                       (receive)
+ *   g_{q,s}(f) = D_q(f) exp(-alpha f d) e^{-i 2 pi f d / c} / d,  d = |r_s - q|,
+ *   D_q(f) = sinc(k (width_x / 2v) (x_s - x_q) / d) [* sinc(k (width_y / 2) (y_s - y_q) / d)],
+ *   dtau_{a,e} = (u_a . e - min_e' u_a . e') / c  (plane-wave steering delays),
+ *   sub-element centres x_q = x_e + (mu - (v - 1)/2) width_x / v, y_q = y_e.
+ * S(f), w_j, df, f_j as for fq_simulate_rf_freq; elevation focusing is
+ * not modelled (unfocused elements).
+ *   apod    host double [M] transmit weights W_e, or NULL (all 1)
+ *   n_sub   sub-elements per element v, 1 .. 8 (M v <= 4096)
+ *   pos     device float [n_frames][3][S], amp device float [S]
+ *   rf      device [n_frames][A][M][n_samples] of out_dtype (FQ_F32 or FQ_BF16)
+ *   workspace device, 256-byte aligned, fq_simulate_rf_pfield_workspace_size
+ *           bytes (the spectra, one transmit field [S][N/2] complex, tables).
+ * The call synchronises `stream` once after uploading its host tables.
+ * Errors: FQ_ERR_INVALID_ARG, FQ_ERR_SHAPE (n_fft, M v), FQ_ERR_UNSUPPORTED
+ * (out_dtype), FQ_ERR_WORKSPACE, FQ_ERR_ALIGN. */
+fq_status fq_simulate_rf_pfield_workspace_size(const fq_probe *probe, const fq_tx *tx, int64_t S, int32_t n_frames,
+                                               int32_t n_fft, int32_t n_sub, size_t *bytes);
+fq_status fq_simulate_rf_pfield(const fq_probe *probe, const fq_tx *tx, const double *apod, int32_t n_sub,
+                                const float *pos, const float *amp, int64_t S, int32_t n_frames, int32_t n_fft,
+                                int32_t out_dtype, void *rf, void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* the paper's explicit DAS-matrix route (Sec. 2.4.1, Alg. 3)           */
 /* ------------------------------------------------------------------ */
@@ -541,6 +567,16 @@ fq_status fq_clutter_status(void *workspace, void *stream);
  * operation.  For testing the timeout path only. */
 enum { FQ_DEBUG_SKIP_TC_LOADS = 1 };
 fq_status fq_debug_set(int32_t what, int32_t value);
+
+/* Throughput probe of the FP32 pipes (the paper has no counterpart): the
+ * denominator of the ALU rooflines the RF and DAS kernels are reported
+ * against.  `blocks` CTAs of 256 threads each run `iters` rounds of 8
+ * independent fused multiply-adds, scalar (packed = 0) or as packed f32x2
+ * instructions that issue two lanes' FMAs at once (packed = 1): 2 FLOP per
+ * lane and FMA, i.e. blocks x 256 x iters x 8 x 2 (x 2 when packed) FLOP.
+ * The caller times the launch on `stream` (CUDA events).  sink: device float
+ * [256], written only to keep the chains from being optimised away. */
+fq_status fq_alu_probe(int32_t packed, int32_t blocks, int32_t iters, float *sink, void *stream);
 
 /* sizeof of the ABI's structs as this library was compiled, for bindings
  * that check their own layouts: 0 fq_probe, 1 fq_tx, 2 fq_grid,

@@ -158,10 +158,13 @@ __device__ __forceinline__ ff ff_dot3_minus(df2 ux, df2 uy, df2 uz, df2 o, float
 
 // ------------------------------------------------------ packed FP32 x 2 --
 // Blackwell executes add / sub / mul / fma on a pair of binary32 values held
-// in one 64-bit register (f32x2) as a single instruction at twice the
-// scalar FP32 rate (measured 153 vs 75 TFLOP/s on GB300).  Both lanes round
-// to nearest exactly like the scalar _rn forms, so the float-float error-free
-// transforms carry over unchanged.
+// in one 64-bit register (f32x2) as a single instruction.  On GB300 it does
+// not raise the FP32 rate (a throughput probe, fq_alu_probe, measured 79.3
+// TFLOP/s packed against 76.9 scalar: a packed instruction holds the FMA
+// pipe for two cycles) but it halves the issue slots of paired arithmetic,
+// which is what the issue-bound kernels here are short of.  Both lanes round
+// to nearest exactly like the scalar _rn forms, so the float-float
+// error-free transforms carry over unchanged.
 struct f2 { unsigned long long v; };
 
 __device__ __forceinline__ f2 f2_make(float a, float b)

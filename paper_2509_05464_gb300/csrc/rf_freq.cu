@@ -297,3 +297,380 @@ extern "C" fq_status fq_simulate_rf_freq(const fq_probe *probe, const fq_tx *tx,
     }
     return fqi::launch_check("fq_simulate_rf_freq");
 }
+
+// ---------------------------------------------------------------------------
+// Eq. 1 with its transmit sum over elements and Eq. 2's sub-elements (App.
+// D; Alg. 2 steps 2.2, 2.6): every element e transmits with weight W_e and
+// the plane-wave steering delay dtau_{a,e} = (u_a . e - min u_a . e') / c;
+// every element is v sub-elements along x; a sub-element q at distance d
+// contributes g_q(f) = D_q(f) exp(-alpha f d) e^{-i 2 pi f d / c} / d, with
+// the sub-element's directivity (half-width w_x / 2v in x, w_y / 2 in y).
+//   T_{a,s}(f) = sum_e W_e e^{-i 2 pi f dtau_{a,e}} (1/v) sum_mu g_{e mu}(f)
+//   P_{a,m}(f) = sum_s R_s T_{a,s}(f) (1/v) sum_mu g_{m mu}(f)
+// Per (frame, transmit): tx_field_kernel writes T for every scatterer and
+// frequency bin into the workspace (one CTA per 4 scatterers, one thread per
+// 16 bins, the (element, sub-element) terms of a scatterer first evaluated
+// into shared memory: float-float cycles per bin of c dtau + d, the
+// attenuation exponent, weight / d and the directivity steps); then
+// pfield_spectrum_kernel (one CTA per receive element) multiplies each
+// scatterer's transmit field by its receive sub-element sum, with the same
+// per-bin recurrences and float-pair accumulation as spectrum_kernel; the
+// inverse transform is ifft_kernel.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kTxScat = 4;  // scatterers per CTA of tx_field_kernel
+
+struct PfieldParams {
+    FreqParams fp;
+    int v;              // sub-elements per element
+    float bkx_sub;      // b_sub k_1 per unit sin(theta): (width_x / 2v) 2 pi df / c
+};
+
+// The 16 bins j0 .. j0 + 15 of one term sum_t amp_t e^{-i 2 pi j cyc_t}
+// exp(-atn_t j) sinc(j bx_t) [sinc(j by_t)] added to acc (binary32), with the
+// anchors at j0 from accurate functions and recurrences over the bins.
+__device__ __forceinline__ void bins_term(float ch, float cl, float atn, float rr, float bx, float by, bool matrix,
+                                          int j0, float (&acc)[kBinsPerThread][2])
+{
+    const ff cyc = {ch, cl};
+    float sn, cs, ws, wc;
+    sincospif(-2.0f * fqi::ff_frac(fqi::ff_mul_f(cyc, (float)j0)), &sn, &cs);
+    sincospif(-2.0f * fqi::ff_frac(cyc), &ws, &wc);
+    float zr = cs, zi = sn;
+    float att = expf(-atn * (float)j0);
+    const float q = expf(-atn);
+    float sbx, cbx, sx0, cx0;
+    sincosf(bx, &sbx, &cbx);
+    sincosf(bx * (float)j0, &sx0, &cx0);
+    float sx_prev = fmaf(sx0, cbx, -cx0 * sbx), sx = sx0;
+    const float tcx = 2.0f * cbx;
+    float sy_prev = 0.0f, sy = 0.0f, tcy = 0.0f;
+    if (matrix) {
+        float sby, cby, sy0, cy0;
+        sincosf(by, &sby, &cby);
+        sincosf(by * (float)j0, &sy0, &cy0);
+        sy_prev = fmaf(sy0, cby, -cy0 * sby);
+        sy = sy0;
+        tcy = 2.0f * cby;
+    }
+#pragma unroll
+    for (int b = 0; b < kBinsPerThread; ++b) {
+        const float jj = (float)(j0 + b);
+        const float xb = jj * bx;
+        float D = (xb == 0.0f) ? 1.0f : __fdividef(sx, xb);
+        if (matrix) {
+            const float yb = jj * by;
+            D *= (yb == 0.0f) ? 1.0f : __fdividef(sy, yb);
+            const float syn = fmaf(tcy, sy, -sy_prev);
+            sy_prev = sy;
+            sy = syn;
+        }
+        const float A = rr * att * D;
+        acc[b][0] = fmaf(A, zr, acc[b][0]);
+        acc[b][1] = fmaf(A, zi, acc[b][1]);
+        const float nzr = fmaf(zr, wc, -zi * ws), nzi = fmaf(zr, ws, zi * wc);
+        zr = nzr;
+        zi = nzi;
+        att *= q;
+        const float sxn = fmaf(tcx, sx, -sx_prev);
+        sx_prev = sx;
+        sx = sxn;
+    }
+}
+
+// sub-element q's term for a scatterer at (x, y, z): float-float distance
+// d, then (cycles per bin of path + d, attenuation exponent per bin, weight
+// / d, directivity steps)
+__device__ __forceinline__ void sub_term(const PfieldParams &p, float x, float y, float z, float4 qpos, ff path0,
+                                         float w, float *out6)
+{
+    const bool matrix = p.fp.pr.ny > 1;
+    const ff dx = fqi::ff_add(ff{x, 0.0f}, ff{-qpos.x, -qpos.y});
+    ff r2 = fqi::ff_add(fqi::ff_sqr(dx), fqi::ff_two_prod(z, z));
+    ff dy = ff{0.0f, 0.0f};
+    if (matrix || y != 0.0f) {
+        dy = fqi::ff_add(ff{y, 0.0f}, ff{-qpos.z, -qpos.w});
+        r2 = fqi::ff_add(r2, fqi::ff_sqr(dy));
+    }
+    const bool ok = r2.hi > 0.0f && w != 0.0f;
+    const ff d = ok ? fqi::ff_sqrt(r2) : ff{1.0f, 0.0f};
+    const ff cyc = fqi::ff_mul(fqi::ff_add(path0, d), fqi::ff_load(p.fp.dfc));
+    const float rinv = 1.0f / d.hi;
+    out6[0] = cyc.hi;
+    out6[1] = cyc.lo;
+    out6[2] = p.fp.atn_per_m * d.hi;
+    out6[3] = ok ? w * rinv : 0.0f;
+    out6[4] = p.bkx_sub * (dx.hi * rinv);
+    out6[5] = matrix ? p.fp.bky * (dy.hi * rinv) : 0.0f;
+}
+
+__global__ void __launch_bounds__(kChunk) tx_field_kernel(const PfieldParams p, int f, int a,
+                                                          const float *__restrict__ pos, const float4 *__restrict__ subpos,
+                                                          const float2 *__restrict__ steer, const float *__restrict__ apod,
+                                                          float2 *__restrict__ T)
+{
+    extern __shared__ float ent[];  // [n_ent][6]
+    const int M = p.fp.pr.M, v = p.v, n_ent = M * v;
+    const int64_t S = p.fp.S;
+    const float *X = pos + (int64_t)f * 3 * S, *Y = X + S, *Z = Y + S;
+    const bool matrix = p.fp.pr.ny > 1;
+    const int j0 = threadIdx.x * kBinsPerThread;
+    const bool live = j0 < p.fp.J;
+    for (int si = 0; si < kTxScat; ++si) {
+        const int64_t s = (int64_t)blockIdx.x * kTxScat + si;
+        if (s >= S) break;
+        const float x = X[s], y = Y[s], z = Z[s];
+        __syncthreads();
+        for (int t = threadIdx.x; t < n_ent; t += blockDim.x) {
+            const int e = t / v;
+            const float2 st = steer[(int64_t)a * M + e];
+            sub_term(p, x, y, z, subpos[t], ff{st.x, st.y}, apod[e] / (float)v, ent + 6 * t);
+        }
+        __syncthreads();
+        if (!live) continue;
+        float acc[kBinsPerThread][2];
+#pragma unroll
+        for (int b = 0; b < kBinsPerThread; ++b) acc[b][0] = acc[b][1] = 0.0f;
+        for (int t = 0; t < n_ent; ++t) {
+            const float *q = ent + 6 * t;
+            if (q[3] == 0.0f) continue;
+            bins_term(q[0], q[1], q[2], q[3], q[4], q[5], matrix, j0, acc);
+        }
+        float2 *o = T + s * p.fp.J;
+#pragma unroll
+        for (int b = 0; b < kBinsPerThread; ++b)
+            if (j0 + b < p.fp.J) o[j0 + b] = make_float2(acc[b][0], acc[b][1]);
+    }
+}
+
+__global__ void __launch_bounds__(kChunk) pfield_spectrum_kernel(const PfieldParams p, int f, int a,
+                                                                 const float *__restrict__ pos,
+                                                                 const float *__restrict__ amp,
+                                                                 const float4 *__restrict__ subpos,
+                                                                 const float2 *__restrict__ T,
+                                                                 float2 *__restrict__ spec)
+{
+    constexpr int kCh = 64;  // scatterers per chunk
+    __shared__ float ent[kCh * 8 * 6];  // [scatterer][sub-element < 8][6]
+    const int m = blockIdx.x;
+    const int M = p.fp.pr.M, v = p.v;
+    const int64_t S = p.fp.S;
+    const float *X = pos + (int64_t)f * 3 * S, *Y = X + S, *Z = Y + S;
+    const bool matrix = p.fp.pr.ny > 1;
+    const int j0 = threadIdx.x * kBinsPerThread;
+    const bool live = j0 < p.fp.J;
+    float accH[kBinsPerThread][2], accL[kBinsPerThread][2];
+#pragma unroll
+    for (int b = 0; b < kBinsPerThread; ++b) accH[b][0] = accH[b][1] = accL[b][0] = accL[b][1] = 0.0f;
+    for (int64_t c0 = 0; c0 < S; c0 += kCh) {
+        const int n = (int)min((int64_t)kCh, S - c0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < n * v; t += blockDim.x) {
+            const int64_t s = c0 + t / v;
+            const int mu = t % v;
+            sub_term(p, X[s], Y[s], Z[s], subpos[(int64_t)m * v + mu], ff{0.0f, 0.0f}, amp[s] / (float)v,
+                     ent + 6 * ((t / v) * 8 + mu));
+        }
+        __syncthreads();
+        if (!live) continue;
+        float fa[kBinsPerThread][2];
+#pragma unroll
+        for (int b = 0; b < kBinsPerThread; ++b) fa[b][0] = fa[b][1] = 0.0f;
+        for (int t = 0; t < n; ++t) {
+            float g[kBinsPerThread][2];
+#pragma unroll
+            for (int b = 0; b < kBinsPerThread; ++b) g[b][0] = g[b][1] = 0.0f;
+            bool any = false;
+            for (int mu = 0; mu < v; ++mu) {
+                const float *q = ent + 6 * (t * 8 + mu);
+                if (q[3] == 0.0f) continue;
+                any = true;
+                bins_term(q[0], q[1], q[2], q[3], q[4], q[5], matrix, j0, g);
+            }
+            if (!any) continue;
+            const float2 *Ts = T + (c0 + t) * p.fp.J + j0;
+#pragma unroll
+            for (int b = 0; b < kBinsPerThread; ++b) {
+                const float2 tv = j0 + b < p.fp.J ? Ts[b] : make_float2(0.0f, 0.0f);
+                fa[b][0] = fmaf(tv.x, g[b][0], fmaf(-tv.y, g[b][1], fa[b][0]));
+                fa[b][1] = fmaf(tv.x, g[b][1], fmaf(tv.y, g[b][0], fa[b][1]));
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kBinsPerThread; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float h = accH[b][c], d = fa[b][c];
+                const float s = h + d, bb = s - h;
+                const float e = (h - (s - bb)) + (d - bb);
+                const float l = accL[b][c] + e;
+                accH[b][c] = s + l;
+                accL[b][c] = l - (accH[b][c] - s);
+            }
+    }
+    if (!live) return;
+    float2 *out = spec + (((int64_t)f * p.fp.A + a) * M + m) * p.fp.J;
+#pragma unroll
+    for (int b = 0; b < kBinsPerThread; ++b)
+        if (j0 + b < p.fp.J) out[j0 + b] = make_float2(accH[b][0] + accL[b][0], accH[b][1] + accL[b][1]);
+}
+
+constexpr int kMaxSub = 8;
+
+struct PfieldLayout {
+    size_t spec, wS, T, subpos, steer, apod, total;
+};
+
+PfieldLayout pfield_layout(const fq_probe *probe, const fq_tx *tx, int64_t S, int F, int N, int v)
+{
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t M = (size_t)probe->nx * probe->ny, J = N / 2;
+    PfieldLayout L;
+    size_t o = 0;
+    L.spec = o; o += al((size_t)F * tx->n_angles * M * J * sizeof(float2));
+    L.wS = o; o += al(J * sizeof(float));
+    L.T = o; o += al((size_t)(S > 0 ? S : 1) * J * sizeof(float2));
+    L.subpos = o; o += al(M * v * sizeof(float4));
+    L.steer = o; o += al((size_t)tx->n_angles * M * sizeof(float2));
+    L.apod = o; o += al(M * sizeof(float));
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+extern "C" fq_status fq_simulate_rf_pfield_workspace_size(const fq_probe *probe, const fq_tx *tx, int64_t S,
+                                                          int32_t n_frames, int32_t n_fft, int32_t n_sub,
+                                                          size_t *bytes)
+{
+    FQ_REQUIRE(probe && tx && bytes && S >= 0 && n_frames >= 1 && pow2(n_fft) && n_sub >= 1 && n_sub <= kMaxSub,
+               FQ_ERR_INVALID_ARG, "fq_simulate_rf_pfield_workspace_size: bad arguments");
+    *bytes = pfield_layout(probe, tx, S, n_frames, n_fft, n_sub).total;
+    return FQ_OK;
+}
+
+extern "C" fq_status fq_simulate_rf_pfield(const fq_probe *probe, const fq_tx *tx, const double *apod, int32_t n_sub,
+                                           const float *pos, const float *amp, int64_t S, int32_t n_frames,
+                                           int32_t n_fft, int32_t out_dtype, void *rf, void *workspace,
+                                           size_t workspace_bytes, void *stream)
+{
+    FQ_REQUIRE(probe && tx && rf && workspace, FQ_ERR_INVALID_ARG, "fq_simulate_rf_pfield: null argument");
+    FQ_REQUIRE(S >= 0 && n_frames >= 1 && (S == 0 || (pos && amp)), FQ_ERR_INVALID_ARG,
+               "fq_simulate_rf_pfield: bad scatterer arguments");
+    FQ_REQUIRE(n_sub >= 1 && n_sub <= kMaxSub, FQ_ERR_INVALID_ARG, "fq_simulate_rf_pfield: n_sub must be in [1, %d]",
+               kMaxSub);
+    FQ_REQUIRE(tx->n_angles >= 1 && tx->n_angles <= FQ_MAX_ANGLES && tx->tilt_x && tx->tilt_y, FQ_ERR_SHAPE,
+               "fq_simulate_rf_pfield: n_angles must be in [1, %d]", FQ_MAX_ANGLES);
+    const int M = probe->nx * probe->ny;
+    FQ_REQUIRE(probe->nx >= 1 && probe->ny >= 1 && M * n_sub <= 4096 && probe->n_samples >= 2, FQ_ERR_SHAPE,
+               "fq_simulate_rf_pfield: elements x sub-elements must be at most 4096");
+    FQ_REQUIRE(pow2(n_fft) && n_fft >= probe->n_samples && n_fft <= kMaxFft, FQ_ERR_SHAPE,
+               "fq_simulate_rf_pfield: n_fft must be a power of two in [n_samples, %d]", kMaxFft);
+    FQ_REQUIRE(out_dtype == FQ_F32 || out_dtype == FQ_BF16, FQ_ERR_UNSUPPORTED,
+               "fq_simulate_rf_pfield: out_dtype must be FQ_F32 or FQ_BF16");
+    const PfieldLayout L = pfield_layout(probe, tx, S, n_frames, n_fft, n_sub);
+    FQ_REQUIRE(workspace_bytes >= L.total, FQ_ERR_WORKSPACE, "fq_simulate_rf_pfield: workspace needs %zu bytes",
+               L.total);
+    FQ_REQUIRE(fqi::aligned(workspace, 256), FQ_ERR_ALIGN, "fq_simulate_rf_pfield: workspace not 256-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = static_cast<char *>(workspace);
+    PfieldParams p;
+    std::memset(&p, 0, sizeof p);
+    fqi::make_probe_ff(probe, p.fp.pr);
+    p.fp.A = tx->n_angles;
+    p.fp.N = n_fft;
+    p.fp.J = n_fft / 2;
+    p.fp.S = S;
+    const double df = probe->fs / n_fft;
+    p.fp.dfc = fqi::split_double(df / probe->c);
+    p.fp.atn_per_m = (float)(probe->alpha_db_cm_mhz * 100.0 / (20.0 / std::log(10.0)) * 1e-6 * df);
+    p.fp.bky = (float)(0.5 * probe->width_y * 2.0 * M_PI * df / probe->c);
+    p.bkx_sub = (float)(0.5 * probe->width_x / n_sub * 2.0 * M_PI * df / probe->c);
+    p.v = n_sub;
+    // host tables: spectral weights, sub-element centres, steering paths c dtau, weights
+    std::vector<float> h(p.fp.J);
+    const double T = probe->n_cycles / probe->f0;
+    for (int j = 0; j < p.fp.J; ++j) h[j] = (float)(df * (j == 0 ? 1.0 : 2.0) * pulse_spectrum(j * df, probe->f0, T));
+    std::vector<float4> sub((size_t)M * n_sub);
+    std::vector<float2> steer((size_t)tx->n_angles * M);
+    std::vector<float> w(M);
+    for (int e = 0; e < M; ++e) {
+        const int ix = e % probe->nx, iy = e / probe->nx;
+        const double ex = ((double)ix - 0.5 * (probe->nx - 1)) * probe->pitch_x;
+        const double ey = ((double)iy - 0.5 * (probe->ny - 1)) * probe->pitch_y;
+        for (int mu = 0; mu < n_sub; ++mu) {
+            const double qx = ex + ((double)mu - 0.5 * (n_sub - 1)) * probe->width_x / n_sub;
+            const fqi::df2 a = fqi::split_double(qx), b = fqi::split_double(ey);
+            sub[(size_t)e * n_sub + mu] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
+        w[e] = apod ? (float)apod[e] : 1.0f;
+    }
+    for (int a = 0; a < tx->n_angles; ++a) {
+        const double ux = std::sin(tx->tilt_x[a]), uy = std::sin(tx->tilt_y[a]);
+        double best = 1e300;
+        for (int e = 0; e < M; ++e) {
+            const double ex = ((double)(e % probe->nx) - 0.5 * (probe->nx - 1)) * probe->pitch_x;
+            const double ey = ((double)(e / probe->nx) - 0.5 * (probe->ny - 1)) * probe->pitch_y;
+            best = std::min(best, ux * ex + uy * ey);
+        }
+        for (int e = 0; e < M; ++e) {
+            const double ex = ((double)(e % probe->nx) - 0.5 * (probe->nx - 1)) * probe->pitch_x;
+            const double ey = ((double)(e / probe->nx) - 0.5 * (probe->ny - 1)) * probe->pitch_y;
+            const fqi::df2 d = fqi::split_double(ux * ex + uy * ey - best);
+            steer[(size_t)a * M + e] = make_float2(d.hi, d.lo);
+        }
+    }
+    float2 *spec = reinterpret_cast<float2 *>(ws + L.spec);
+    float *wS = reinterpret_cast<float *>(ws + L.wS);
+    float2 *Tf = reinterpret_cast<float2 *>(ws + L.T);
+    float4 *dsub = reinterpret_cast<float4 *>(ws + L.subpos);
+    float2 *dsteer = reinterpret_cast<float2 *>(ws + L.steer);
+    float *dapod = reinterpret_cast<float *>(ws + L.apod);
+    fq_status s = fqi::cuda_check(cudaMemcpyAsync(wS, h.data(), sizeof(float) * p.fp.J, cudaMemcpyHostToDevice, st),
+                                  "fq_simulate_rf_pfield: weights");
+    if (!s) s = fqi::cuda_check(cudaMemcpyAsync(dsub, sub.data(), sizeof(float4) * sub.size(), cudaMemcpyHostToDevice, st),
+                                "fq_simulate_rf_pfield: sub-elements");
+    if (!s) s = fqi::cuda_check(cudaMemcpyAsync(dsteer, steer.data(), sizeof(float2) * steer.size(),
+                                                cudaMemcpyHostToDevice, st), "fq_simulate_rf_pfield: steering");
+    if (!s) s = fqi::cuda_check(cudaMemcpyAsync(dapod, w.data(), sizeof(float) * M, cudaMemcpyHostToDevice, st),
+                                "fq_simulate_rf_pfield: weights");
+    if (!s) s = fqi::cuda_check(cudaStreamSynchronize(st), "fq_simulate_rf_pfield: tables");  // host vectors end here
+    if (s) return s;
+    const int threads = ((p.fp.J + kBinsPerThread - 1) / kBinsPerThread + 31) / 32 * 32;
+    FQ_REQUIRE(threads <= kChunk, FQ_ERR_SHAPE, "fq_simulate_rf_pfield: too many bins");
+    const size_t tx_smem = sizeof(float) * 6 * (size_t)M * n_sub;
+    s = fqi::cuda_check(cudaFuncSetAttribute(tx_field_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tx_smem),
+                        "fq_simulate_rf_pfield: smem");
+    if (s) return s;
+    for (int f = 0; f < n_frames; ++f)
+        for (int a = 0; a < tx->n_angles; ++a) {
+            if (S > 0) {
+                tx_field_kernel<<<(unsigned)((S + kTxScat - 1) / kTxScat), threads, tx_smem, st>>>(p, f, a, pos, dsub,
+                                                                                                     dsteer, dapod, Tf);
+                s = fqi::launch_check("fq_simulate_rf_pfield: transmit field");
+                if (s) return s;
+            }
+            pfield_spectrum_kernel<<<(unsigned)M, threads, 0, st>>>(p, f, a, pos, amp, dsub, Tf, spec);
+            s = fqi::launch_check("fq_simulate_rf_pfield: spectrum");
+            if (s) return s;
+        }
+    int logN = 0;
+    while ((1 << logN) < n_fft) ++logN;
+    const size_t smem = sizeof(float2) * (size_t)n_fft;
+    const unsigned lines = (unsigned)((int64_t)n_frames * p.fp.A * M);
+    if (out_dtype == FQ_F32) {
+        s = fqi::cuda_check(cudaFuncSetAttribute(ifft_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem), "fq_simulate_rf_pfield: smem");
+        if (s) return s;
+        ifft_kernel<float><<<lines, 512, smem, st>>>(spec, wS, p.fp.J, n_fft, logN, probe->n_samples, (float *)rf);
+    } else {
+        s = fqi::cuda_check(cudaFuncSetAttribute(ifft_kernel<__nv_bfloat16>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                            "fq_simulate_rf_pfield: smem");
+        if (s) return s;
+        ifft_kernel<__nv_bfloat16><<<lines, 512, smem, st>>>(spec, wS, p.fp.J, n_fft, logN, probe->n_samples,
+                                                             (__nv_bfloat16 *)rf);
+    }
+    return fqi::launch_check("fq_simulate_rf_pfield");
+}

@@ -122,6 +122,11 @@ def lib():
             "fq_post_workspace_size": [_I32, _I32, C.POINTER(_SZ)],
             "fq_das_matrix_workspace_size": [C.POINTER(Tx), C.POINTER(Grid), C.POINTER(_SZ)],
             "fq_simulate_rf_freq_workspace_size": [C.POINTER(Probe), C.POINTER(Tx), _I32, _I32, C.POINTER(_SZ)],
+            "fq_alu_probe": [_I32, _I32, _I32, _P, _P],
+            "fq_simulate_rf_pfield_workspace_size": [C.POINTER(Probe), C.POINTER(Tx), _I64, _I32, _I32, _I32,
+                                                     C.POINTER(_SZ)],
+            "fq_simulate_rf_pfield": [C.POINTER(Probe), C.POINTER(Tx), _P, _I32, _P, _P, _I64, _I32, _I32, _I32, _P,
+                                      _P, _SZ, _P],
             "fq_simulate_rf_freq": [C.POINTER(Probe), C.POINTER(Tx), _P, _P, _I64, _I32, _I32, _I32, _P, _P, _SZ,
                                     _P],
             "fq_das_matrix_count": [C.POINTER(Probe), C.POINTER(Tx), C.POINTER(Grid), _P, _P, _SZ, _P],
@@ -344,6 +349,42 @@ def fq_simulate_rf_freq(probe, tilt_x, tilt_y, pos, amp, n_frames, n_fft=None, o
     _check(lib().fq_simulate_rf_freq(C.byref(pr), C.byref(th.st), _ptr(pos), _ptr(amp), S, int(n_frames), int(n_fft),
                                      _dt(rf), _ptr(rf), _ptr(ws), ws.numel(), _stream(stream)))
     return rf
+
+
+def fq_simulate_rf_pfield(probe, tilt_x, tilt_y, pos, amp, n_frames, apod=None, n_sub=1, n_fft=None,
+                          out_dtype=torch.float32, rf=None, ws=None, stream=None):
+    """RF [n_frames][A][M][Ns] by Eq. 1 per frequency with the transmit sum
+    over elements (weights apod [M], host; None = all 1) and n_sub
+    sub-elements per element (Eq. 2); n_fft defaults to the power of two
+    >= 2 Ns."""
+    S = amp.shape[0]
+    A = len(tilt_x)
+    M = probe.nx * probe.ny
+    if n_fft is None:
+        n_fft = 1
+        while n_fft < 2 * probe.n_samples:
+            n_fft *= 2
+    if rf is None:
+        rf = torch.empty((n_frames, A, M, probe.n_samples), dtype=out_dtype, device=amp.device)
+    pr = make_probe(probe)
+    th = _TxHolder(tilt_x, tilt_y)
+    w = None
+    if apod is not None:
+        w = np.ascontiguousarray(apod, np.float64)
+        assert w.shape == (M,)
+    if ws is None:
+        n = _SZ(0)
+        _check(lib().fq_simulate_rf_pfield_workspace_size(C.byref(pr), C.byref(th.st), S, int(n_frames), int(n_fft),
+                                                          int(n_sub), C.byref(n)))
+        ws = workspace(n.value, amp.device)
+    _check(lib().fq_simulate_rf_pfield(C.byref(pr), C.byref(th.st), None if w is None else w.ctypes.data_as(C.c_void_p),
+                                       int(n_sub), _ptr(pos), _ptr(amp), S, int(n_frames), int(n_fft), _dt(rf),
+                                       _ptr(rf), _ptr(ws), ws.numel(), _stream(stream)))
+    return rf
+
+
+def fq_alu_probe(packed, blocks, iters, sink, stream=None):
+    _check(lib().fq_alu_probe(int(packed), int(blocks), int(iters), _ptr(sink), _stream(stream)))
 
 
 # ------------------------------------------- the paper's DAS-matrix route --
