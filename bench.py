@@ -237,7 +237,7 @@ def oracle_run(w, n_frames):
     return time.perf_counter() - t0, r
 
 
-def oracle_sample_3d(w, n_lines=192, block=40, p_svd=65536):
+def oracle_sample_3d(w, n_lines=64, block=32, p_svd=16384):
     """The oracle on bounded subsets of a 3D ensemble, each stage timed and
     extrapolated linearly by its exact work count to the whole step:
     membership once; advection of one frame (x F); RF of n_lines (transmit,
