@@ -3,19 +3,21 @@
 //
 // Layout: rf2iq writes the channel IQ frames-innermost, [A*M][Ns][F_pad]
 // complex, so that the DAS kernel, which computes each (pixel, transmit,
-// element) delay once and applies it to a chunk of FC frames, reads the two
-// interpolation samples of all FC frames as contiguous 128-byte vectors.
-// This is the paper's "delay matrix computed once, reused by every frame"
-// idea (Alg. 3 steps 2.2-2.3) without materialising the sparse matrix: the
-// delays live in registers for the duration of a frame chunk.
+// element) delay once and applies it to a chunk of 16 frames, reads the two
+// interpolation samples of those frames as contiguous 16-byte vectors.
+// Alg. 3 (steps 2.2-2.3) builds each transmit's delays once and applies
+// them to every frame through a stored sparse matrix; here the delays live
+// in registers for the duration of a frame chunk instead.
 //
 // Precision: delays, interpolation index and carrier phase are float-float;
 // the aperture decision is binary32 on coordinates rounded from IEEE double;
+// FP32 channel data interpolate in FP32, 16-bit data in their own precision;
 // accumulation is FP32.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "batch.cuh"
 #include "fq_internal.cuh"
@@ -26,7 +28,7 @@ namespace {
 using fqi::ff;
 
 constexpr int kMaxHalfTaps = 32;
-constexpr int kFrameChunk = 16;  // frames per DAS thread and per rf2iq CTA (F_pad multiple)
+constexpr int kFrameChunk = 16;  // frames per DAS tile and per rf2iq CTA (F_pad multiple)
 
 // ------------------------------------------------------------------ rf2iq --
 struct Rf2iqParams {
@@ -367,71 +369,6 @@ struct DasParams {
 constexpr int kDasThreads = 128;
 constexpr int kDasTPP = fqb::kDasThreadsPerPixel;  // threads per pixel
 
-// The N frames of one channel at the interpolated sample i + phi:
-// v = v(i) + phi (v(i + 1) - v(i)).  FP32 channel data interpolate in FP32;
-// BF16 and FP16 channel data interpolate as packed bf16x2 / half2 (re, im)
-// pairs and are widened once afterwards, which keeps the ALU work per frame
-// at the FP32 count (the widening of both samples would add four
-// instructions per frame).
-template <int N, typename ChT>
-struct InterpFrames;
-template <>
-struct InterpFrames<4, __nv_bfloat16> {
-    static __device__ __forceinline__ void run(const __nv_bfloat16 *b0, int64_t stride, float phi, float2 (&v)[4])
-    {
-        const uint4 t0 = __ldg(reinterpret_cast<const uint4 *>(b0));
-        const uint4 t1 = __ldg(reinterpret_cast<const uint4 *>(b0 + stride));
-        const __nv_bfloat162 *a = reinterpret_cast<const __nv_bfloat162 *>(&t0);
-        const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&t1);
-        const __nv_bfloat162 ph = __float2bfloat162_rn(phi);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = __bfloat1622float2(__hfma2(ph, __hsub2(b[k], a[k]), a[k]));
-    }
-};
-
-template <>
-struct InterpFrames<4, __half> {
-    static __device__ __forceinline__ void run(const __half *b0, int64_t stride, float phi, float2 (&v)[4])
-    {
-        const uint4 t0 = __ldg(reinterpret_cast<const uint4 *>(b0));
-        const uint4 t1 = __ldg(reinterpret_cast<const uint4 *>(b0 + stride));
-        const __half2 *a = reinterpret_cast<const __half2 *>(&t0);
-        const __half2 *b = reinterpret_cast<const __half2 *>(&t1);
-        const __half2 ph = __float2half2_rn(phi);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = __half22float2(__hfma2(ph, __hsub2(b[k], a[k]), a[k]));
-    }
-};
-
-// The same as packed (re, im) pairs.  16-bit channel data (BF16 or FP16)
-// interpolate as packed 16-bit pairs and are widened afterwards; FP32
-// channel data are loaded as 64-bit (re, im) words and interpolated with
-// f32x2 instructions (2 per frame instead of 4).
-template <int N, typename ChT>
-struct InterpFramesF2 {
-    static __device__ __forceinline__ void run(const ChT *b0, int64_t stride, fqi::f2 PHI, fqi::f2 (&v)[N])
-    {
-        float2 w[N];
-        InterpFrames<N, ChT>::run(b0, stride, fqi::f2_lo(PHI), w);
-#pragma unroll
-        for (int k = 0; k < N; ++k) v[k] = fqi::f2_make(w[k].x, w[k].y);
-    }
-};
-template <int N>
-struct InterpFramesF2<N, float> {
-    static __device__ __forceinline__ void run(const float *b0, int64_t stride, fqi::f2 PHI, fqi::f2 (&v)[N])
-    {
-        const ulonglong2 *q0 = reinterpret_cast<const ulonglong2 *>(b0);
-        const ulonglong2 *q1 = reinterpret_cast<const ulonglong2 *>(b0 + stride);
-#pragma unroll
-        for (int i = 0; i < N / 2; ++i) {
-            const ulonglong2 a = __ldg(q0 + i), b = __ldg(q1 + i);
-            v[2 * i] = fqi::f2_fma(PHI, fqi::f2_sub(fqi::f2{b.x}, fqi::f2{a.x}), fqi::f2{a.x});
-            v[2 * i + 1] = fqi::f2_fma(PHI, fqi::f2_sub(fqi::f2{b.y}, fqi::f2{a.y}), fqi::f2{a.y});
-        }
-    }
-};
-
 // (sin x, cos x) for |x| <= 0.8 from the fitted polynomials of rf_poly.cuh
 // (binary32 evaluation error below 6e-8)
 __device__ __forceinline__ void das_sincos_poly(float x, float &s, float &c)
@@ -482,34 +419,201 @@ inline bool das_rot_tab(const fq_probe *probe)
     return probe->n_samples <= kRotTabMax && M_PI * probe->f0 / probe->fs <= (double)fqpoly::kTapXMax;
 }
 
-// One tile with TPP threads per pixel: W pixels along x, frames 16 by ..
-// 16 by + 15.  Thread (pixel, part q) accumulates frames FPT q .. FPT q +
-// FPT - 1, FPT = 16 / TPP.  The pixels of a CTA share y and z, so the rows
-// of a matrix probe inside the receive aperture are the same for all of
-// them; a warp walks those rows and, in each, the columns that the
-// aperture of any of its pixels can reach, in groups of TPP elements.  The
-// threads of a pixel evaluate the float-float receive distances of TPP
-// different elements once and reuse them for every transmit (the transmit
-// paths of the pixel sit in shared memory); per transmit they form the
-// delays, share them by shuffles within the group, and each reads its slice
-// of the two interpolation samples, so that a warp load covers 32 / TPP
-// whole rows.  Sums over transmits and elements are in that order (element
-// outer, transmit inner).  `etab` is the dynamic shared memory
-// (das_smem_bytes).
-template <int TPP, typename ChT, typename OutT>
-__device__ __forceinline__ void das_tile4(const DasParams &p, int64_t bx, int by, const ChT *__restrict__ ch,
-                                          OutT *__restrict__ iq, float *etab)
+// Running sums of one thread's FPT frames of the chunk, read as FPT / FL
+// 16-byte groups of FL frames (FL = 4 for 16-bit data, 2 for FP32) GS groups
+// apart, interpolated at i + phi and rotated by (cs, sn).
+//
+// SepAcc (FP32 data): the interpolation in f32x2 on (re, im) pairs, then sum
+// v cos and sum v sin per frame (rotated at the end: (C.re - S.im,
+// C.im + S.re)), two f32x2 operations per frame each.
+template <int FPT, int GS>
+struct SepAcc {
+    fqi::f2 C[FPT], S[FPT];
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int k = 0; k < FPT; ++k) C[k] = S[k] = fqi::f2_dup(0.0f);
+    }
+    __device__ __forceinline__ void add(const float *b0, int64_t stride, float phi, float cs, float sn)
+    {
+        const ulonglong2 *q0 = reinterpret_cast<const ulonglong2 *>(b0);
+        const ulonglong2 *q1 = reinterpret_cast<const ulonglong2 *>(b0 + stride);
+        ulonglong2 t0[FPT / 2], t1[FPT / 2];
+#pragma unroll
+        for (int g = 0; g < FPT / 2; ++g) {
+            t0[g] = __ldg(q0 + g * GS);
+            t1[g] = __ldg(q1 + g * GS);
+        }
+        const fqi::f2 PHI = fqi::f2_dup(phi), CS = fqi::f2_dup(cs), SN = fqi::f2_dup(sn);
+#pragma unroll
+        for (int g = 0; g < FPT / 2; ++g) {
+            const fqi::f2 v0 = fqi::f2_fma(PHI, fqi::f2_sub(fqi::f2{t1[g].x}, fqi::f2{t0[g].x}), fqi::f2{t0[g].x});
+            const fqi::f2 v1 = fqi::f2_fma(PHI, fqi::f2_sub(fqi::f2{t1[g].y}, fqi::f2{t0[g].y}), fqi::f2{t0[g].y});
+            C[2 * g] = fqi::f2_fma(v0, CS, C[2 * g]);
+            S[2 * g] = fqi::f2_fma(v0, SN, S[2 * g]);
+            C[2 * g + 1] = fqi::f2_fma(v1, CS, C[2 * g + 1]);
+            S[2 * g + 1] = fqi::f2_fma(v1, SN, S[2 * g + 1]);
+        }
+    }
+    __device__ __forceinline__ void add_xor(int o)
+    {
+#pragma unroll
+        for (int k = 0; k < FPT; ++k) {
+            float c0, c1, s0, s1;
+            fqi::f2_split(C[k], c0, c1);
+            fqi::f2_split(S[k], s0, s1);
+            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            C[k] = fqi::f2_make(c0, c1);
+            S[k] = fqi::f2_make(s0, s1);
+        }
+    }
+    __device__ __forceinline__ float2 get(int k) const
+    {
+        float cr, ci, sr, si;
+        fqi::f2_split(C[k], cr, ci);
+        fqi::f2_split(S[k], sr, si);
+        return make_float2(cr - si, ci + sr);
+    }
+};
+
+// the real parts (lo) and imaginary parts (hi) of two packed 16-bit (re, im)
+// words as binary32 pairs
+__device__ __forceinline__ void widen_pair(uint32_t a, uint32_t b, fqi::f2 &re, fqi::f2 &im, __nv_bfloat16 *)
 {
-    constexpr int FPT = kFrameChunk / TPP;
+    asm("{ .reg .b32 r0, r1, i0, i1;\n\t shl.b32 r0, %2, 16;\n\t shl.b32 r1, %3, 16;\n\t"
+        " and.b32 i0, %2, 0xffff0000;\n\t and.b32 i1, %3, 0xffff0000;\n\t"
+        " mov.b64 %0, {r0, r1};\n\t mov.b64 %1, {i0, i1}; }"
+        : "=l"(re.v), "=l"(im.v) : "r"(a), "r"(b));
+}
+__device__ __forceinline__ void widen_pair(uint32_t a, uint32_t b, fqi::f2 &re, fqi::f2 &im, __half *)
+{
+    const float2 x = __half22float2(*reinterpret_cast<const __half2 *>(&a));
+    const float2 y = __half22float2(*reinterpret_cast<const __half2 *>(&b));
+    re = fqi::f2_make(x.x, y.x);
+    im = fqi::f2_make(x.y, y.y);
+}
+
+// RotAcc (BF16 / FP16 data): the interpolation as packed 16-bit (re, im)
+// pairs (phi rounded to the storage type, as the storage itself), then the
+// rotated sums of two frames per pair of registers, (re_k, re_k+1) and
+// (im_k, im_k+1): four f32x2 operations per two frames, and half the
+// registers of SepAcc's form.
+template <int FPT, int GS, typename H>
+struct RotAcc {
+    using H2 = typename std::conditional<std::is_same<H, __half>::value, __half2, __nv_bfloat162>::type;
+    fqi::f2 R[FPT / 2], I[FPT / 2];
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int m = 0; m < FPT / 2; ++m) R[m] = I[m] = fqi::f2_dup(0.0f);
+    }
+    __device__ __forceinline__ void add(const H *b0, int64_t stride, float phi, float cs, float sn)
+    {
+        const uint4 *q0 = reinterpret_cast<const uint4 *>(b0);
+        const uint4 *q1 = reinterpret_cast<const uint4 *>(b0 + stride);
+        uint4 t0[FPT / 4], t1[FPT / 4];
+#pragma unroll
+        for (int g = 0; g < FPT / 4; ++g) {
+            t0[g] = __ldg(q0 + g * GS);
+            t1[g] = __ldg(q1 + g * GS);
+        }
+        H2 ph;
+        if constexpr (std::is_same<H, __half>::value) ph = __float2half2_rn(phi);
+        else ph = __float2bfloat162_rn(phi);
+        const fqi::f2 CS = fqi::f2_dup(cs), SN = fqi::f2_dup(sn), NSN = fqi::f2_dup(-sn);
+#pragma unroll
+        for (int g = 0; g < FPT / 4; ++g) {
+            const H2 *a = reinterpret_cast<const H2 *>(&t0[g]);
+            const H2 *b = reinterpret_cast<const H2 *>(&t1[g]);
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const H2 x = __hfma2(ph, __hsub2(b[k], a[k]), a[k]);
+                w[k] = *reinterpret_cast<const uint32_t *>(&x);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                fqi::f2 RE, IM;
+                widen_pair(w[2 * h], w[2 * h + 1], RE, IM, (H *)nullptr);
+                const int m = 2 * g + h;
+                R[m] = fqi::f2_fma(RE, CS, R[m]);
+                R[m] = fqi::f2_fma(IM, NSN, R[m]);
+                I[m] = fqi::f2_fma(RE, SN, I[m]);
+                I[m] = fqi::f2_fma(IM, CS, I[m]);
+            }
+        }
+    }
+    __device__ __forceinline__ void add_xor(int o)
+    {
+#pragma unroll
+        for (int m = 0; m < FPT / 2; ++m) {
+            float r0, r1, i0, i1;
+            fqi::f2_split(R[m], r0, r1);
+            fqi::f2_split(I[m], i0, i1);
+            r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+            r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+            i0 += __shfl_xor_sync(0xffffffffu, i0, o);
+            i1 += __shfl_xor_sync(0xffffffffu, i1, o);
+            R[m] = fqi::f2_make(r0, r1);
+            I[m] = fqi::f2_make(i0, i1);
+        }
+    }
+    __device__ __forceinline__ float2 get(int k) const
+    {
+        float r0, r1, i0, i1;
+        fqi::f2_split(R[k / 2], r0, r1);
+        fqi::f2_split(I[k / 2], i0, i1);
+        return (k & 1) ? make_float2(r1, i1) : make_float2(r0, i0);
+    }
+};
+
+// One DAS tile.  A CTA of W = blockDim.x / TPP pixel columns (TPP = 4
+// threads per pixel) takes W consecutive voxels along x of one (y, z) row,
+// frames 16 by .. 16 by + 15 (das_ctas gives the order of the CTAs).  The
+// pixels of a CTA share y and z, so the rows of a matrix probe inside the
+// receive aperture are the same for all of them; a warp walks those rows
+// and, in each, the columns that the aperture of any of its pixels can
+// reach, in groups of TPP elements.  The TPP threads of a pixel are ES
+// element slots x FS frame slots (TPP = ES FS).  Each thread evaluates the
+// float-float receive distance of one element of a group (g0 + sub) once
+// for every transmit (the transmit paths of the pixel sit in shared memory)
+// and, per transmit, its delay and carrier rotation; thread (qe, qf) then
+// takes the group's elements qe, qe + ES, .. (their delays shared by
+// shuffles) over its FPT = 16 / FS frames.  The frame slots interleave by
+// 16-byte groups of FL frames (thread qf takes frames FL (g FS + qf) ..
+// + FL - 1), so that one load instruction of a pixel's FS threads reads FS
+// adjacent groups.  The ES partial sums of a pixel's frames are added by
+// shuffles at the end.  Sums: element groups in order (rows, then columns),
+// transmits, the slot's elements in order, then the ES slots pairwise.
+// Slots per channel type (3D workload, 128^3 voxels, 100 frames): 16-bit
+// channels take ES = FS = 2 (8 frames per delay and thread, RotAcc): 783 ms
+// against 1031 ms with 4 frames per thread (ES = 1, FS = 4); FP32 channels
+// take ES = 1, FS = 4: with 8 frames of FP32 per thread the 2D workload's
+// DAS measured 7.0 ms against 5.0.  `etab` is the dynamic shared memory
+// (das_smem_bytes).
+template <typename ChT>
+struct DasSlots {
+    static constexpr int ES = sizeof(ChT) == 2 ? 2 : 1;
+    static constexpr int FS = kDasTPP / ES;
+};
+
+template <typename ChT, typename OutT>
+__device__ __forceinline__ void das_tile(const DasParams &p, int64_t bx, int by, const ChT *__restrict__ ch,
+                                            OutT *__restrict__ iq, float *etab)
+{
+    constexpr int ES = DasSlots<ChT>::ES, FS = DasSlots<ChT>::FS, TPP = kDasTPP;
+    constexpr int FPT = kFrameChunk / FS;
+    constexpr int FL = 8 / (int)sizeof(ChT);  // frames per 16 bytes
+    static_assert(ES * FS == TPP && (ES & (ES - 1)) == 0 && FPT % FL == 0, "slots");
     const int M = p.pr.M, nxe = p.pr.nx, nye = p.pr.ny;
     const int W = blockDim.x / TPP;
-    // element m = row * nx + column sits at (x[column], y[row]): the probe is
-    // separable, so the tables hold one abscissa per column and one ordinate
-    // per row (binary32, and the float pair hi + lo)
     float *exf = etab, *exh = etab + nxe, *exl = etab + 2 * nxe;
     float *eyf = etab + 3 * nxe, *eyh = eyf + nye, *eyl = eyf + 2 * nye;
-    float2 *ptx_s = reinterpret_cast<float2 *>(etab + das_off_ptx(M));       // [A][W] transmit path (hi, lo)
-    float2 *rot_s = reinterpret_cast<float2 *>(etab + das_off_rot(M, p.A, W));  // [ns] carrier table
+    float2 *ptx_s = reinterpret_cast<float2 *>(etab + das_off_ptx(M));
+    float2 *rot_s = reinterpret_cast<float2 *>(etab + das_off_rot(M, p.A, W));
     for (int c = threadIdx.x; c < nxe + nye; c += blockDim.x) {
         const bool isx = c < nxe;
         const int i = isx ? c : c - nxe, n = isx ? nxe : nye;
@@ -522,7 +626,8 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int64_t bx, int by
         }
     }
 
-    const int q = threadIdx.x % TPP;  // frame part, and element slot within a group of TPP
+    const int sub = threadIdx.x % TPP;  // the element of a group whose delay this thread evaluates
+    const int qe = sub % ES, qf = sub / ES;
     const int col = threadIdx.x / TPP;
     const int nxb = (p.gx + W - 1) / W;
     const int xb = (int)(bx % nxb);
@@ -545,10 +650,9 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int64_t bx, int by
     const ff fs_c = fqi::ff_load(p.pr.fs_over_c);
     const ff f0_fs = fqi::ff_load(p.pr.f0_over_fs);
     const int ns = p.pr.ns;
-    const int64_t row_stride = (int64_t)p.Fp * 2;  // scalars per channel sample (all frames)
+    const int64_t row_stride = (int64_t)p.Fp * 2;
     const int64_t line_stride = (int64_t)ns * row_stride;
 
-    // the carrier table: rot[n] = e^{i 2 pi frac(n f0 / fs)}
     if (p.rot_tab) {
         for (int n = threadIdx.x; n < ns; n += blockDim.x) {
             float sn, cs;
@@ -556,8 +660,7 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int64_t bx, int by
             rot_s[n] = make_float2(cs, sn);
         }
     }
-    // this pixel's transmit path u_a . r - origin per angle (float-float)
-    if (q == 0) {
+    if (sub == 0) {
         for (int a = 0; a < p.A; ++a) {
             const fqi::AngleFF an = p.ang[a];
             ff ptx = fqi::ff_add(fqi::ff_mul(fqi::ff_load(an.ux), X), fqi::ff_mul(fqi::ff_load(an.uy), Y));
@@ -568,8 +671,6 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int64_t bx, int by
     }
     __syncthreads();
 
-    // element rows inside the aperture (the same for every pixel of the CTA:
-    // they share y and z), decided in binary32 like every element below
     int row_lo = 0, row_hi = nye - 1;
     if (matrix) {
         row_lo = nye;
@@ -581,8 +682,6 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int64_t bx, int by
             }
         }
     }
-    // columns the aperture of any pixel of the warp can reach: an estimate
-    // one column wider on each side (the per-element test below decides)
     int c_lo = nxe, c_hi = -1;
     if (live) {
         if (nxe > 1 && p.pitch_x > 0.0) {
@@ -602,19 +701,15 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int64_t bx, int by
         c_hi = max(c_hi, __shfl_xor_sync(0xffffffffu, c_hi, o));
     }
 
-    // sum of v cos and sum of v sin per frame, as (re, im) pairs: the rotated
-    // sum is (C.re - S.im, C.im + S.re)
-    // sum of v cos and sum of v sin per frame, as (re, im) pairs: the rotated
-    // sum is (C.re - S.im, C.im + S.re)
-    fqi::f2 accC[FPT], accS[FPT];
-#pragma unroll
-    for (int k = 0; k < FPT; ++k) accC[k] = accS[k] = fqi::f2_dup(0.0f);
-    const ChT *chp = ch + (fbase + FPT * q) * 2;
+    using Acc = typename std::conditional<sizeof(ChT) == 2, RotAcc<FPT, FS, ChT>, SepAcc<FPT, FS>>::type;
+    Acc acc;
+    acc.init();
+    const ChT *chp = ch + (fbase + FL * qf) * 2;
+    const int lane0 = (threadIdx.x & 31) - sub;  // the pixel's first lane
 
     for (int r = row_lo; r <= row_hi; ++r) {
         for (int g0 = c_lo; g0 <= c_hi; g0 += TPP) {
-            // this thread's element of the group
-            const int cq = g0 + q;
+            const int cq = g0 + sub;
             const int cc = min(cq, nxe - 1);
             const bool on = live && cq <= c_hi && fabsf(__fsub_rn(xf, exf[cc])) <= half;
             if (!__any_sync(0xffffffffu, on)) continue;
@@ -640,8 +735,6 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int64_t bx, int by
                     if (i < 0 || i + 1 >= ns) {
                         ok = false;
                     } else if (p.rot_tab) {
-                        // e^{i 2 pi (f0/fs) phi} as the square of its half angle's
-                        // polynomial sine and cosine, times the table entry of i
                         float sh, ch;
                         das_sincos_poly(p.pi_f0_fs * phi, sh, ch);
                         const float ce = (ch - sh) * (ch + sh), se = 2.0f * sh * ch;
@@ -653,51 +746,44 @@ __device__ __forceinline__ void das_tile4(const DasParams &p, int64_t bx, int by
                         sincospif(2.0f * cyc, &sn, &cs);
                     }
                 }
-                // the group's elements in turn (values shared within the TPP lanes of a pixel)
-                // the channel row (element, sample) within this angle's lines, or
-                // -1 for no contribution (M ns < 2^28: it fits an int)
                 const int ion = ok ? (r * nxe + cq) * ns + i : -1;
                 const ChT *cha = chp + (int64_t)a * M * line_stride;
 #pragma unroll
-                for (int j = 0; j < TPP; ++j) {
-                    const int ij = __shfl_sync(0xffffffffu, ion, j, TPP);
-                    const float phj = __shfl_sync(0xffffffffu, phi, j, TPP);
-                    const float snj = __shfl_sync(0xffffffffu, sn, j, TPP);
-                    const float csj = __shfl_sync(0xffffffffu, cs, j, TPP);
+                for (int tq = 0; tq < FS; ++tq) {
+                    const int j = qe + ES * tq;  // the group's element this thread sums now
+                    const int src = lane0 + j;
+                    const int ij = __shfl_sync(0xffffffffu, ion, src);
+                    const float phj = __shfl_sync(0xffffffffu, phi, src);
+                    const float snj = __shfl_sync(0xffffffffu, sn, src);
+                    const float csj = __shfl_sync(0xffffffffu, cs, src);
                     if (ij < 0) continue;
-                    const ChT *b0 = cha + (uint64_t)(unsigned)ij * (uint64_t)row_stride;
-                    fqi::f2 v[FPT];
-                    InterpFramesF2<FPT, ChT>::run(b0, row_stride, fqi::f2_dup(phj), v);
-                    const fqi::f2 CS = fqi::f2_dup(csj), SN = fqi::f2_dup(snj);
-#pragma unroll
-                    for (int k = 0; k < FPT; ++k) {
-                        accC[k] = fqi::f2_fma(v[k], CS, accC[k]);
-                        accS[k] = fqi::f2_fma(v[k], SN, accS[k]);
-                    }
+                    acc.add(cha + (uint64_t)(unsigned)ij * (uint64_t)row_stride, row_stride, phj, csj, snj);
                 }
             }
         }
     }
-    const int f0 = fbase + FPT * q;
+    // the ES slots' partial sums (lanes sub = qe + ES qf: the slots of one
+    // frame slice are ES consecutive lanes)
+#pragma unroll
+    for (int o = 1; o < ES; o <<= 1) acc.add_xor(o);
     if (live) {
 #pragma unroll
         for (int k = 0; k < FPT; ++k) {
-            float cr, ci, sr, si;
-            fqi::f2_split(accC[k], cr, ci);
-            fqi::f2_split(accS[k], sr, si);
-            if (f0 + k < p.F)
-                fqi::store_c(iq, pix * p.F + f0 + k, make_float2((cr - si) * p.inv_A, (ci + sr) * p.inv_A));
+            if (k % ES != qe) continue;  // every slot holds the sum: each stores a share
+            const int fk = fbase + FL * ((k / FL) * FS + qf) + k % FL;
+            const float2 v = acc.get(k);
+            if (fk < p.F) fqi::store_c(iq, pix * p.F + fk, make_float2(v.x * p.inv_A, v.y * p.inv_A));
         }
     }
-    __syncthreads();  // a persistent CTA's next tile rewrites the shared tables
+    __syncthreads();
 }
 
 
 template <typename ChT, typename OutT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) das_kernel(const DasParams p, const ChT *__restrict__ ch, OutT *__restrict__ iq)
 {
-    extern __shared__ __align__(16) float etab[];  // das_smem_bytes: element tables, transmit paths, running sums
-    das_tile4<kDasTPP, ChT, OutT>(p, blockIdx.x, blockIdx.y, ch, iq, etab);
+    extern __shared__ __align__(16) float etab[];  // das_smem_bytes: element tables, transmit paths, carrier table
+    das_tile<ChT, OutT>(p, blockIdx.x, blockIdx.y, ch, iq, etab);
 }
 
 constexpr int kDasParamBytes = (sizeof(DasParams) + 15) & ~15;
@@ -717,7 +803,7 @@ __global__ void __launch_bounds__(NT) das_batched_kernel(const fqb::EnsDev *__re
             cur = it.e;
             __syncthreads();
         }
-        das_tile4<kDasTPP, ChT, OutT>(*reinterpret_cast<const DasParams *>(s_par), it.x, it.y, (const ChT *)e.ch,
+        das_tile<ChT, OutT>(*reinterpret_cast<const DasParams *>(s_par), it.x, it.y, (const ChT *)e.ch,
                             (OutT *)e.iq, etab);
     }
 }
