@@ -126,9 +126,12 @@ void item_grids(fq_batch *b, EnsHost &h)
     h.items[ST_RF] = h.gx[ST_RF] * rf_groups * h.F;
     h.gx[ST_RF2IQ] = cdiv(h.ns, kIqTile); h.gy[ST_RF2IQ] = h.L;
     h.items[ST_RF2IQ] = h.gx[ST_RF2IQ] * h.L * (h.Fp / kFrameChunkB);
-    // DAS tiles: das_threads / kDasThreadsPerPixel voxels along x of one (y, z) row each
-    h.gx[ST_DAS] = cdiv(h.d.grid.nx, b->das_threads / kDasThreadsPerPixel) * h.d.grid.ny * h.d.grid.nz;
-    h.gy[ST_DAS] = h.Fp / kFrameChunkB;
+    // DAS tiles: voxels along x of one (y, z) row, das_threads / 4 of them and
+    // 16 frames for FP32 channel data, das_threads / 32 (one warp each) and
+    // 128 frames for 16-bit channel data
+    const bool das_w = b->ch_dtype != FQ_F32;
+    h.gx[ST_DAS] = cdiv(h.d.grid.nx, b->das_threads / (das_w ? 32 : kDasThreadsPerPixel)) * h.d.grid.ny * h.d.grid.nz;
+    h.gy[ST_DAS] = das_w ? cdiv(h.Fp, kDasWarpFramesB) : h.Fp / kFrameChunkB;
     h.items[ST_DAS] = h.gx[ST_DAS] * h.gy[ST_DAS];
     const int nt = cdiv(h.F, 32);
     h.gx[ST_GRAM] = nt * (nt + 1) / 2; h.gy[ST_GRAM] = h.n_chunks; h.items[ST_GRAM] = h.gx[ST_GRAM] * h.n_chunks;

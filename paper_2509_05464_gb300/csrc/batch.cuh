@@ -20,7 +20,8 @@ constexpr int kItemPix = 64;      // pixels per projection item (8 warps x 8)
 constexpr int kRfItemElems = 2;   // receive elements per RF item (the paired kernel; 4 for the quad kernel)
 constexpr int kIqTile = 128;      // rf2iq output samples per item
 constexpr int kFrameChunkB = 16;  // frames per rf2iq / DAS item
-constexpr int kDasThreadsPerPixel = 4;  // 8 measured slower on the 2D benchmark (more shuffles)
+constexpr int kDasThreadsPerPixel = 4;  // FP32 channel data (8 measured slower on the 2D benchmark)
+constexpr int kDasWarpFramesB = 128;     // frames per DAS item of 16-bit channel data (one warp per voxel)
 
 enum Stage {
     ST_CLASSIFY = 0,

@@ -455,21 +455,6 @@ struct SepAcc {
             S[2 * g + 1] = fqi::f2_fma(v1, SN, S[2 * g + 1]);
         }
     }
-    __device__ __forceinline__ void add_xor(int o)
-    {
-#pragma unroll
-        for (int k = 0; k < FPT; ++k) {
-            float c0, c1, s0, s1;
-            fqi::f2_split(C[k], c0, c1);
-            fqi::f2_split(S[k], s0, s1);
-            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
-            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
-            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            C[k] = fqi::f2_make(c0, c1);
-            S[k] = fqi::f2_make(s0, s1);
-        }
-    }
     __device__ __forceinline__ float2 get(int k) const
     {
         float cr, ci, sr, si;
@@ -546,21 +531,6 @@ struct RotAcc {
             }
         }
     }
-    __device__ __forceinline__ void add_xor(int o)
-    {
-#pragma unroll
-        for (int m = 0; m < FPT / 2; ++m) {
-            float r0, r1, i0, i1;
-            fqi::f2_split(R[m], r0, r1);
-            fqi::f2_split(I[m], i0, i1);
-            r0 += __shfl_xor_sync(0xffffffffu, r0, o);
-            r1 += __shfl_xor_sync(0xffffffffu, r1, o);
-            i0 += __shfl_xor_sync(0xffffffffu, i0, o);
-            i1 += __shfl_xor_sync(0xffffffffu, i1, o);
-            R[m] = fqi::f2_make(r0, r1);
-            I[m] = fqi::f2_make(i0, i1);
-        }
-    }
     __device__ __forceinline__ float2 get(int k) const
     {
         float r0, r1, i0, i1;
@@ -570,44 +540,34 @@ struct RotAcc {
     }
 };
 
-// One DAS tile.  A CTA of W = blockDim.x / TPP pixel columns (TPP = 4
-// threads per pixel) takes W consecutive voxels along x of one (y, z) row,
-// frames 16 by .. 16 by + 15 (das_ctas gives the order of the CTAs).  The
-// pixels of a CTA share y and z, so the rows of a matrix probe inside the
-// receive aperture are the same for all of them; a warp walks those rows
-// and, in each, the columns that the aperture of any of its pixels can
-// reach, in groups of TPP elements.  The TPP threads of a pixel are ES
-// element slots x FS frame slots (TPP = ES FS).  Each thread evaluates the
-// float-float receive distance of one element of a group (g0 + sub) once
-// for every transmit (the transmit paths of the pixel sit in shared memory)
-// and, per transmit, its delay and carrier rotation; thread (qe, qf) then
-// takes the group's elements qe, qe + ES, .. (their delays shared by
-// shuffles) over its FPT = 16 / FS frames.  The frame slots interleave by
-// 16-byte groups of FL frames (thread qf takes frames FL (g FS + qf) ..
-// + FL - 1), so that one load instruction of a pixel's FS threads reads FS
-// adjacent groups.  The ES partial sums of a pixel's frames are added by
-// shuffles at the end.  Sums: element groups in order (rows, then columns),
-// transmits, the slot's elements in order, then the ES slots pairwise.
-// Slots per channel type (3D workload, 128^3 voxels, 100 frames): 16-bit
-// channels take ES = FS = 2 (8 frames per delay and thread, RotAcc): 783 ms
-// against 1031 ms with 4 frames per thread (ES = 1, FS = 4); FP32 channels
-// take ES = 1, FS = 4: with 8 frames of FP32 per thread the 2D workload's
-// DAS measured 7.0 ms against 5.0.  `etab` is the dynamic shared memory
+// One DAS tile of FP32 channel data.  A CTA of W = blockDim.x / 4 pixel
+// columns (four threads per pixel) takes W consecutive voxels along x of one
+// (y, z) row, frames 16 by .. 16 by + 15 (das_ctas gives the order of the
+// CTAs).  The pixels of a CTA share y and z, so the rows of a matrix probe
+// inside the receive aperture are the same for all of them; a warp walks
+// those rows and, in each, the columns that the aperture of any of its
+// pixels can reach, in groups of four elements.  Each thread of a pixel
+// evaluates the float-float receive distance of one element of a group
+// (g0 + sub) once for every transmit (the transmit paths of the pixel sit in
+// shared memory) and, per transmit, its delay and carrier rotation; the
+// four threads then take every element of the group (delays shared by
+// shuffles), thread q over frames 2 (4 g + q) .. + 1 for g = 0, 1 (16-byte
+// groups interleaved, so that a load instruction of a pixel's threads reads
+// 64 adjacent bytes).  Sums: element groups in order (rows, then columns),
+// transmits, the group's elements in order.  With 8 frames of FP32 per
+// thread (two threads per element) the 2D workload's DAS measured 7.0 ms
+// against 5.0 ms, and one warp per pixel (as das_tile_w) 5.4 ms: the 16-byte
+// groups of FP32 data hold two frames, and the extra frames per delay do
+// not pay for the wider loads.  `etab` is the dynamic shared memory
 // (das_smem_bytes).
-template <typename ChT>
-struct DasSlots {
-    static constexpr int ES = sizeof(ChT) == 2 ? 2 : 1;
-    static constexpr int FS = kDasTPP / ES;
-};
-
 template <typename ChT, typename OutT>
 __device__ __forceinline__ void das_tile(const DasParams &p, int64_t bx, int by, const ChT *__restrict__ ch,
                                             OutT *__restrict__ iq, float *etab)
 {
-    constexpr int ES = DasSlots<ChT>::ES, FS = DasSlots<ChT>::FS, TPP = kDasTPP;
+    static_assert(sizeof(ChT) == 4, "das_tile takes FP32 channel data");
+    constexpr int TPP = kDasTPP, FS = kDasTPP;  // four threads per pixel, each a frame slot
     constexpr int FPT = kFrameChunk / FS;
-    constexpr int FL = 8 / (int)sizeof(ChT);  // frames per 16 bytes
-    static_assert(ES * FS == TPP && (ES & (ES - 1)) == 0 && FPT % FL == 0, "slots");
+    constexpr int FL = 2;  // FP32 frames per 16 bytes
     const int M = p.pr.M, nxe = p.pr.nx, nye = p.pr.ny;
     const int W = blockDim.x / TPP;
     float *exf = etab, *exh = etab + nxe, *exl = etab + 2 * nxe;
@@ -626,8 +586,7 @@ __device__ __forceinline__ void das_tile(const DasParams &p, int64_t bx, int by,
         }
     }
 
-    const int sub = threadIdx.x % TPP;  // the element of a group whose delay this thread evaluates
-    const int qe = sub % ES, qf = sub / ES;
+    const int sub = threadIdx.x % TPP;  // the element of a group whose delay this thread evaluates, and the frame slot
     const int col = threadIdx.x / TPP;
     const int nxb = (p.gx + W - 1) / W;
     const int xb = (int)(bx % nxb);
@@ -701,10 +660,9 @@ __device__ __forceinline__ void das_tile(const DasParams &p, int64_t bx, int by,
         c_hi = max(c_hi, __shfl_xor_sync(0xffffffffu, c_hi, o));
     }
 
-    using Acc = typename std::conditional<sizeof(ChT) == 2, RotAcc<FPT, FS, ChT>, SepAcc<FPT, FS>>::type;
-    Acc acc;
+    SepAcc<FPT, FS> acc;
     acc.init();
-    const ChT *chp = ch + (fbase + FL * qf) * 2;
+    const ChT *chp = ch + (fbase + FL * sub) * 2;
     const int lane0 = (threadIdx.x & 31) - sub;  // the pixel's first lane
 
     for (int r = row_lo; r <= row_hi; ++r) {
@@ -749,8 +707,7 @@ __device__ __forceinline__ void das_tile(const DasParams &p, int64_t bx, int by,
                 const int ion = ok ? (r * nxe + cq) * ns + i : -1;
                 const ChT *cha = chp + (int64_t)a * M * line_stride;
 #pragma unroll
-                for (int tq = 0; tq < FS; ++tq) {
-                    const int j = qe + ES * tq;  // the group's element this thread sums now
+                for (int j = 0; j < TPP; ++j) {  // the group's elements in turn
                     const int src = lane0 + j;
                     const int ij = __shfl_sync(0xffffffffu, ion, src);
                     const float phj = __shfl_sync(0xffffffffu, phi, src);
@@ -762,15 +719,10 @@ __device__ __forceinline__ void das_tile(const DasParams &p, int64_t bx, int by,
             }
         }
     }
-    // the ES slots' partial sums (lanes sub = qe + ES qf: the slots of one
-    // frame slice are ES consecutive lanes)
-#pragma unroll
-    for (int o = 1; o < ES; o <<= 1) acc.add_xor(o);
     if (live) {
 #pragma unroll
         for (int k = 0; k < FPT; ++k) {
-            if (k % ES != qe) continue;  // every slot holds the sum: each stores a share
-            const int fk = fbase + FL * ((k / FL) * FS + qf) + k % FL;
+            const int fk = fbase + FL * ((k / FL) * FS + sub) + k % FL;
             const float2 v = acc.get(k);
             if (fk < p.F) fqi::store_c(iq, pix * p.F + fk, make_float2(v.x * p.inv_A, v.y * p.inv_A));
         }
@@ -778,6 +730,211 @@ __device__ __forceinline__ void das_tile(const DasParams &p, int64_t bx, int by,
     __syncthreads();
 }
 
+
+// ---- one warp per pixel (16-bit channel data) ---------------------------
+// A CTA of NW = blockDim.x / 32 warps takes NW consecutive voxels along x of
+// one (y, z) row (das_ctas with W = NW), frames 128 by .. 128 by + 127:
+// lane l sums frames 128 by + 4 l .. + 3, so that a load instruction reads
+// one element's samples of 128 consecutive frames (512 bytes of 16-bit data,
+// 1024 of FP32).  Per group of 32 columns of an aperture row, lane l
+// evaluates column g0 + l's receive distance once and, per transmit, its
+// delay and carrier rotation into the warp's slot table; then the warp walks
+// the group's elements with an echo in the record, each read back from the
+// table by every lane (a broadcast), so the loop has no divergence.  Lanes
+// whose frames lie beyond the padded count idle (F = 100: 28 of 32 lanes
+// work).  3D workload (128^3 voxels, 100 frames, BF16 channels): 690 ms
+// against 783 ms for four threads per pixel with two element and two frame
+// slots (8 frames per delay and thread, the first of these kernels to
+// share a delay over more than 4 frames) and 1031 ms for four threads per
+// pixel over 4 frames each; loading two elements before summing either
+// measured 684 ms (BF16) but 793 ms (FP16, 64 registers) and is not used.
+constexpr int kDasWarpFrames = 128;
+
+__host__ __device__ inline int das_w_off_slot(int M, int A, int NW) { return das_off_ptx(M) + ((2 * A * NW + 3) & ~3); }
+__host__ __device__ inline int das_w_off_rot(int M, int A, int NW) { return das_w_off_slot(M, A, NW) + 4 * 32 * NW; }
+__host__ __device__ inline size_t das_w_smem_bytes(int M, int A, int NW, int rot_ns)
+{
+    return sizeof(float) * (size_t)das_w_off_rot(M, A, NW) + sizeof(float2) * (size_t)rot_ns;
+}
+
+template <typename ChT, typename OutT>
+__device__ __forceinline__ void das_tile_w(const DasParams &p, int64_t bx, int by, const ChT *__restrict__ ch,
+                                           OutT *__restrict__ iq, float *etab)
+{
+    const int M = p.pr.M, nxe = p.pr.nx, nye = p.pr.ny;
+    const int NW = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float *exf = etab, *exh = etab + nxe, *exl = etab + 2 * nxe;
+    float *eyf = etab + 3 * nxe, *eyh = eyf + nye, *eyl = eyf + 2 * nye;
+    float2 *ptx_s = reinterpret_cast<float2 *>(etab + das_off_ptx(M));                      // [A][NW]
+    float4 *slot = reinterpret_cast<float4 *>(etab + das_w_off_slot(M, p.A, NW)) + 32 * wid;  // [32] this warp's
+    float2 *rot_s = reinterpret_cast<float2 *>(etab + das_w_off_rot(M, p.A, NW));             // [ns]
+    for (int c = threadIdx.x; c < nxe + nye; c += blockDim.x) {
+        const bool isx = c < nxe;
+        const int i = isx ? c : c - nxe, n = isx ? nxe : nye;
+        const double e = __dmul_rn(__dsub_rn((double)i, __dmul_rn(0.5, (double)(n - 1))), isx ? p.pitch_x : p.pitch_y);
+        const fqi::df2 sp = fqi::split_double(e);
+        if (isx) {
+            exf[i] = (float)e; exh[i] = sp.hi; exl[i] = sp.lo;
+        } else {
+            eyf[i] = (float)e; eyh[i] = sp.hi; eyl[i] = sp.lo;
+        }
+    }
+    const int nxb = (p.gx + NW - 1) / NW;
+    const int xb = (int)(bx % nxb);
+    const int64_t t = bx / nxb;
+    const int iy = (int)(t % p.gy);
+    const int iz = (int)(t / p.gy);
+    const int ix = xb * NW + wid;
+    const bool live = ix < p.gx && iz < p.gz;  // warp-uniform
+    const int64_t pix = ((int64_t)iy * p.gz + iz) * p.gx + ix;
+    const int f0 = by * kDasWarpFrames + 4 * lane;  // this lane's first frame
+    const bool fon = f0 < p.Fp;
+    const double xd = __dadd_rn(p.x0, __dmul_rn((double)(live ? ix : 0), p.dx));
+    const double yd = __dadd_rn(p.y0, __dmul_rn((double)iy, p.dy));
+    const double zd = __dadd_rn(p.z0, __dmul_rn((double)iz, p.dz));
+    const float xf = (float)xd, yf = (float)yd, zf = (float)zd;
+    const fqi::df2 xs = fqi::split_double(xd), ys = fqi::split_double(yd), zs = fqi::split_double(zd);
+    const ff X = {xs.hi, xs.lo}, Y = {ys.hi, ys.lo}, Z = {zs.hi, zs.lo};
+    const ff zz = fqi::ff_sqr(Z);
+    const float half = __fmul_rn(zf, p.half_per_z);
+    const bool matrix = nye > 1;
+    const ff fs_c = fqi::ff_load(p.pr.fs_over_c);
+    const ff f0_fs = fqi::ff_load(p.pr.f0_over_fs);
+    const int ns = p.pr.ns;
+    const int64_t row_stride = (int64_t)p.Fp * 2;
+    const int64_t line_stride = (int64_t)ns * row_stride;
+
+    if (p.rot_tab) {
+        for (int n = threadIdx.x; n < ns; n += blockDim.x) {
+            float sn, cs;
+            sincospif(2.0f * fqi::ff_frac(fqi::ff_mul(f0_fs, ff{(float)n, 0.0f})), &sn, &cs);
+            rot_s[n] = make_float2(cs, sn);
+        }
+    }
+    for (int a = lane; a < p.A; a += 32) {
+        const fqi::AngleFF an = p.ang[a];
+        ff ptx = fqi::ff_add(fqi::ff_mul(fqi::ff_load(an.ux), X), fqi::ff_mul(fqi::ff_load(an.uy), Y));
+        ptx = fqi::ff_add(ptx, fqi::ff_mul(fqi::ff_load(an.uz), Z));
+        ptx = fqi::ff_add(ptx, fqi::ff_neg(fqi::ff_load(an.origin)));
+        ptx_s[a * NW + wid] = make_float2(ptx.hi, ptx.lo);
+    }
+    __syncthreads();
+
+    int row_lo = 0, row_hi = nye - 1;
+    if (matrix) {
+        row_lo = nye;
+        row_hi = -1;
+        for (int r = 0; r < nye; ++r) {
+            if (fabsf(__fsub_rn(yf, eyf[r])) <= half) {
+                row_lo = min(row_lo, r);
+                row_hi = r;
+            }
+        }
+    }
+    // columns the pixel's aperture can reach: an estimate one column wider on
+    // each side (the per-element test below decides)
+    int c_lo = nxe, c_hi = -1;
+    if (live) {
+        if (nxe > 1 && p.pitch_x > 0.0) {
+            const float c0f = 0.5f * (float)(nxe - 1);
+            const float ip = (float)(1.0 / p.pitch_x);
+            const float lo = fminf(fmaxf(floorf((xf - half) * ip + c0f), -2.0f), (float)nxe + 1.0f);
+            const float hi = fminf(fmaxf(ceilf((xf + half) * ip + c0f), -2.0f), (float)nxe + 1.0f);
+            c_lo = max(0, (int)lo - 1);
+            c_hi = min(nxe - 1, (int)hi + 1);
+        } else {
+            c_lo = 0;
+            c_hi = nxe - 1;
+        }
+    }
+
+    static_assert(sizeof(ChT) == 2, "das_tile_w takes 16-bit channel data");
+    RotAcc<4, 1, ChT> acc;
+    acc.init();
+    const ChT *chp = ch + (int64_t)(fon ? f0 : 0) * 2;
+
+    for (int r = row_lo; r <= row_hi; ++r) {
+        for (int g0 = c_lo; g0 <= c_hi; g0 += 32) {
+            const int cq = g0 + lane;
+            const int cc = min(cq, nxe - 1);
+            const bool on = cq <= c_hi && fabsf(__fsub_rn(xf, exf[cc])) <= half;
+            if (!__any_sync(0xffffffffu, on)) continue;
+            ff rm = {0.0f, 0.0f};
+            if (on) {
+                ff dxx = fqi::ff_add(X, ff{-exh[cc], -exl[cc]});
+                ff r2 = fqi::ff_add(fqi::ff_sqr(dxx), zz);
+                if (matrix || yf != 0.0f) {
+                    ff dyy = fqi::ff_add(Y, ff{-eyh[r], -eyl[r]});
+                    r2 = fqi::ff_add(r2, fqi::ff_sqr(dyy));
+                }
+                rm = fqi::ff_sqrt(r2);
+            }
+            for (int a = 0; a < p.A; ++a) {
+                int i = 0;
+                float phi = 0.0f, sn = 0.0f, cs = 1.0f;
+                bool ok = on;
+                if (on) {
+                    const float2 pt = ptx_s[a * NW + wid];
+                    const ff path = fqi::ff_add(ff{pt.x, pt.y}, rm);
+                    const ff u = fqi::ff_mul(path, fs_c);
+                    fqi::ff_floor_frac(u, i, phi);
+                    if (i < 0 || i + 1 >= ns) {
+                        ok = false;
+                    } else if (p.rot_tab) {
+                        float sh, ch;
+                        das_sincos_poly(p.pi_f0_fs * phi, sh, ch);
+                        const float ce = (ch - sh) * (ch + sh), se = 2.0f * sh * ch;
+                        const float2 t = rot_s[i];
+                        cs = t.x * ce - t.y * se;
+                        sn = t.x * se + t.y * ce;
+                    } else {
+                        const float cyc = fqi::ff_frac(fqi::ff_mul(u, f0_fs));
+                        sincospif(2.0f * cyc, &sn, &cs);
+                    }
+                }
+                // the channel row (element, sample) within this angle's lines
+                // (M ns < 2^28: it fits an int)
+                slot[lane] = make_float4(__int_as_float(ok ? (r * nxe + cq) * ns + i : 0), phi, cs, sn);
+                __syncwarp();
+                unsigned m = __ballot_sync(0xffffffffu, ok);
+                const ChT *cha = chp + (int64_t)a * M * line_stride;
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    const float4 d = slot[j];
+                    if (fon)
+                        acc.add(cha + (uint64_t)(unsigned)__float_as_int(d.x) * (uint64_t)row_stride, row_stride,
+                                d.y, d.z, d.w);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    if (live && fon) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 v = acc.get(k);
+            if (f0 + k < p.F) fqi::store_c(iq, pix * p.F + f0 + k, make_float2(v.x * p.inv_A, v.y * p.inv_A));
+        }
+    }
+    __syncthreads();  // a persistent CTA's next tile rewrites the shared tables
+}
+
+// Launch bounds give the thread count alone: for 256-thread CTAs of 16-bit
+// data ptxas then settles at 40 registers (a few spilled values), which ran
+// the 3D workload's DAS in 690 ms; minimum-block bounds that allow 42 to 48
+// registers without spills measured 795-799 ms, 70 registers 1089 ms, and
+// 128- or 512-thread CTAs 865 and 897 ms.
+constexpr int kDasWarpThreads = 256;
+static_assert(kDasWarpFrames == fqb::kDasWarpFramesB, "batched item shapes");
+
+template <typename ChT, typename OutT, int NT>
+__global__ void __launch_bounds__(NT) das_w_kernel(const DasParams p, const ChT *__restrict__ ch, OutT *__restrict__ iq)
+{
+    extern __shared__ __align__(16) float etab[];  // das_w_smem_bytes
+    das_tile_w<ChT, OutT>(p, blockIdx.x, blockIdx.y, ch, iq, etab);
+}
 
 template <typename ChT, typename OutT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) das_kernel(const DasParams p, const ChT *__restrict__ ch, OutT *__restrict__ iq)
@@ -803,8 +960,12 @@ __global__ void __launch_bounds__(NT) das_batched_kernel(const fqb::EnsDev *__re
             cur = it.e;
             __syncthreads();
         }
-        das_tile<ChT, OutT>(*reinterpret_cast<const DasParams *>(s_par), it.x, it.y, (const ChT *)e.ch,
-                            (OutT *)e.iq, etab);
+        if constexpr (sizeof(ChT) == 2)
+            das_tile_w<ChT, OutT>(*reinterpret_cast<const DasParams *>(s_par), it.x, it.y, (const ChT *)e.ch,
+                                  (OutT *)e.iq, etab);
+        else
+            das_tile<ChT, OutT>(*reinterpret_cast<const DasParams *>(s_par), it.x, it.y, (const ChT *)e.ch,
+                                (OutT *)e.iq, etab);
     }
 }
 
@@ -824,23 +985,38 @@ fq_status check_probe_tx(const fq_probe *probe, const fq_tx *tx, const char *who
 template <typename ChT, typename OutT>
 fq_status launch_das(const DasParams &p, const void *ch, void *iq, cudaStream_t st)
 {
-    size_t smem = das_smem_bytes(p.pr.M, p.A, kDasThreads, kDasTPP, p.rot_tab ? p.pr.ns : 0);
-    // resident CTAs per SM the register budget targets: 8 (64 registers per
-    // thread) or 4 (up to 128); FQ_DAS_MINB=4 selects the latter for tuning
-    static int minb = -1;
-    if (minb < 0) {
-        const char *env = std::getenv("FQ_DAS_MINB");
-        minb = (env && env[0] == '4') ? 4 : 8;
+    if constexpr (sizeof(ChT) == 2) {
+        constexpr int NW = kDasWarpThreads / 32;
+        const size_t smem = das_w_smem_bytes(p.pr.M, p.A, NW, p.rot_tab ? p.pr.ns : 0);
+        auto kern = das_w_kernel<ChT, OutT, kDasWarpThreads>;
+        if (smem > 48 * 1024) {
+            fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                               (int)smem), "fq_das: smem attribute");
+            if (s) return s;
+        }
+        dim3 grid((unsigned)das_ctas(p.gx, p.gy, p.gz, NW), (p.Fp + kDasWarpFrames - 1) / kDasWarpFrames);
+        kern<<<grid, kDasWarpThreads, smem, st>>>(p, (const ChT *)ch, (OutT *)iq);
+        return fqi::launch_check("fq_das");
+    } else {
+        size_t smem = das_smem_bytes(p.pr.M, p.A, kDasThreads, kDasTPP, p.rot_tab ? p.pr.ns : 0);
+        // resident CTAs per SM the register budget targets: 8 (64 registers
+        // per thread) or 4 (up to 128); FQ_DAS_MINB=4 selects the latter for
+        // tuning
+        static int minb = -1;
+        if (minb < 0) {
+            const char *env = std::getenv("FQ_DAS_MINB");
+            minb = (env && env[0] == '4') ? 4 : 8;
+        }
+        auto kern = minb == 4 ? das_kernel<ChT, OutT, kDasThreads, 4> : das_kernel<ChT, OutT, kDasThreads, 8>;
+        if (smem > 48 * 1024) {
+            fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                               (int)smem), "fq_das: smem attribute");
+            if (s) return s;
+        }
+        dim3 grid((unsigned)das_ctas(p.gx, p.gy, p.gz, kDasThreads / kDasTPP), p.Fp / kFrameChunk);
+        kern<<<grid, kDasThreads, smem, st>>>(p, (const ChT *)ch, (OutT *)iq);
+        return fqi::launch_check("fq_das");
     }
-    auto kern = minb == 4 ? das_kernel<ChT, OutT, kDasThreads, 4> : das_kernel<ChT, OutT, kDasThreads, 8>;
-    if (smem > 48 * 1024) {
-        fq_status s = fqi::cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                           (int)smem), "fq_das: smem attribute");
-        if (s) return s;
-    }
-    dim3 grid((unsigned)das_ctas(p.gx, p.gy, p.gz, kDasThreads / kDasTPP), p.Fp / kFrameChunk);
-    kern<<<grid, kDasThreads, smem, st>>>(p, (const ChT *)ch, (OutT *)iq);
-    return fqi::launch_check("fq_das");
 }
 
 void make_das_params(const fq_probe *probe, const fq_tx *tx, int F, const fq_grid *g, DasParams &p)
@@ -991,7 +1167,9 @@ template <typename ChT, typename OutT, int NT>
 fq_status launch_das_batched(const fqb::EnsDev *ens, const fqb::StageQueue &q, int items, int M_max, int A_max,
                              int ns_max, cudaStream_t st)
 {
-    const size_t smem = das_smem_bytes(M_max, A_max, NT, kDasTPP, std::min(ns_max, kRotTabMax));
+    const int rot = std::min(ns_max, kRotTabMax);
+    const size_t smem = sizeof(ChT) == 2 ? das_w_smem_bytes(M_max, A_max, NT / 32, rot)
+                                         : das_smem_bytes(M_max, A_max, NT, kDasTPP, rot);
     auto kern = das_batched_kernel<ChT, OutT, NT>;
     fq_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                              "batched DAS: smem attribute");
