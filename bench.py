@@ -538,7 +538,9 @@ def run_ours(args, rank, world, local):
                      "peak_source": peak_src,
                      "work": f"{flop / pairs:.2f} FLOP per (scatterer, element, transmit, frame) pair "
                              f"({taps:.3f} taps), {pairs:.3e} pairs"},
-        "roofline_das": {"bound": "alu", "kernel": "das_kernel", "achieved": d_ach, "peak": peak,
+        "roofline_das": {"bound": "alu",
+                         "kernel": "das_kernel" if kw["ch_dtype"] == torch.float32 else "das_w_kernel",
+                         "achieved": d_ach, "peak": peak,
                          "unit": "TFLOP/s", "frac": d_ach / peak, "traffic": None, "peak_source": peak_src,
                          "work": f"{DAS_FLOP_PER_FRAME:.0f} FLOP per frame + {DAS_FLOP_PER_TRIPLE:.0f} per active "
                                  f"(voxel, transmit, element) triple, {triples:.4e} triples x {w.n_frames} frames",
