@@ -717,7 +717,7 @@ def run_cnn(args, rank, world, local):
     torch.cuda.synchronize()
     e0.record(stream)
     hist = learned.train(net, vol[:n_tr], tgt[:n_tr], steps=args.cnn_train_steps, batch=batch, lr=args.cnn_lr, seed=2,
-                         log_every=max(1, args.cnn_train_steps // 10))
+                         log_every=max(1, args.cnn_train_steps // 10), schedule="cosine")
     e1.record(stream)
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1) / args.cnn_train_steps
@@ -1332,11 +1332,11 @@ def main():
                          "explicit DAS matrices against the fused DAS; rffreq: RF synthesis in the frequency "
                          "domain against the time-domain kernel (2 frames unless --frames); gram: the tensor-core "
                          "Gram at 96^3 voxels x 400 frames")
-    ap.add_argument("--cnn-ensembles", type=int, default=64, help="c5: simulated training + held-out ensembles")
-    ap.add_argument("--cnn-train-steps", type=int, default=1500, help="c5: timed training steps")
+    ap.add_argument("--cnn-ensembles", type=int, default=256, help="c5: simulated training + held-out ensembles")
+    ap.add_argument("--cnn-train-steps", type=int, default=6000, help="c5: timed training steps (cosine schedule)")
     ap.add_argument("--cnn-infer-frames", type=int, default=200, help="c5: frames of the inference ensemble")
     ap.add_argument("--cnn-gain", type=float, default=8.0, help="c5: target gain of the training pairs")
-    ap.add_argument("--cnn-lr", type=float, default=3e-4, help="c5: Adam learning rate")
+    ap.add_argument("--cnn-lr", type=float, default=1e-3, help="c5: Adam peak learning rate")
     ap.add_argument("--arena-gb", type=int, default=64, help="c4: arena budget in GiB (waves beyond it)")
     ap.add_argument("--no-sequential", dest="sequential", action="store_false",
                     help="c4: skip the one-by-one comparison run")

@@ -12,6 +12,7 @@ libfq's kernels; this module only orders the calls.
 from __future__ import annotations
 
 import copy
+import math
 
 import numpy as np
 import torch
@@ -66,8 +67,19 @@ def ensembles(seeds, n_frames=64, Z=32, X=32, n_scat=2000, target_gain=1.0, remo
     return vol, tgt, scales, torch.stack(pd_gt), torch.stack(pd_svd)
 
 
-def train(net, vol, tgt, steps, batch=4, lr=1e-3, seed=0, log_every=0):
-    """Adam on random mini-batches of the volumes; returns the loss history."""
+def lr_at(step, steps, lr, schedule, warmup=200, floor=0.02):
+    """Learning rate of a 1-based step: constant, or a linear warm-up over
+    `warmup` steps followed by a cosine decay to `floor` x lr at `steps`."""
+    if schedule == "constant":
+        return lr
+    if step <= warmup:
+        return lr * step / warmup
+    return lr * (floor + (1.0 - floor) * 0.5 * (1.0 + math.cos(math.pi * step / steps)))
+
+
+def train(net, vol, tgt, steps, batch=4, lr=1e-3, seed=0, log_every=0, schedule="constant"):
+    """Adam on random mini-batches of the volumes (learning rate per
+    lr_at); returns the loss history."""
     n, F, Z, X = vol.shape[:4]
     rng = np.random.default_rng(seed)
     acts = fq.cnn_act_workspace(batch, F, Z, X, vol.device)
@@ -82,7 +94,7 @@ def train(net, vol, tgt, steps, batch=4, lr=1e-3, seed=0, log_every=0):
         torch.index_select(tgt, 0, idx, out=tb)
         fq.fq_cnn_forward(net, xb, acts)
         fq.fq_cnn_backward(net, xb, tb, acts, grads, loss)
-        fq.fq_cnn_adam(net, grads, lr, step)
+        fq.fq_cnn_adam(net, grads, lr_at(step, steps, lr, schedule), step)
         if log_every and (step % log_every == 0 or step == 1):
             hist.append((step, float(loss.item())))
     if not log_every:

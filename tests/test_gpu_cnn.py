@@ -152,3 +152,24 @@ def test_training_reduces_loss_and_beats_the_unfiltered_ensemble():
     e_cnn = learned.rel_l2(pd_cnn, pd_gt[held])
     e_raw = learned.rel_l2(raw, pd_gt[held])
     assert np.isfinite(e_cnn) and e_cnn < e_raw
+
+
+def test_trained_filter_beats_the_svd_filter_on_held_out_ensembles():
+    """The learned filter trained on 240 simulated C1-like ensembles (64
+    frames, 32 x 32 pixels, tissue motion; 6000 Adam steps of 4 volumes,
+    warm-up then cosine decay from 1e-3) against the SVD filter with k = 2
+    on 16 held-out ensembles: the relative L2 error of power Doppler
+    against the blood-only ground truth is lower for the network (about
+    0.47 against 0.50; the training is deterministic: the same seeds give
+    the same weights)."""
+    seeds = list(range(10000, 10256))
+    vol, tgt, scales, pd_gt, pd_svd = learned.ensembles(seeds, target_gain=8.0)
+    n_tr = 240
+    net = fq.CNN(0)
+    learned.train(net, vol[:n_tr], tgt[:n_tr], steps=6000, batch=4, lr=1e-3, seed=2, schedule="cosine")
+    assert int(net.status.item()) == 0
+    held = slice(n_tr, len(seeds))
+    pd_cnn = learned.predict_pd(net, vol[held], scales[n_tr:], 8.0)
+    e_cnn = learned.rel_l2(pd_cnn, pd_gt[held])
+    e_svd = learned.rel_l2(pd_svd[held], pd_gt[held])
+    assert np.isfinite(e_cnn) and e_cnn < 0.97 * e_svd, (e_cnn, e_svd)
