@@ -709,18 +709,17 @@ def run_cnn(args, rank, world, local):
     gen_s = time.perf_counter() - t0
     n_tr = n_ens - n_test
     F, Z, X = vol.shape[1:4]
-    net = fq.CNN(0)
     batch = 4
-    learned.train(net, vol[:n_tr], tgt[:n_tr], steps=max(1, args.warmup), batch=batch, lr=args.cnn_lr, seed=1)
+    learned.train(fq.CNN(0), vol[:n_tr], tgt[:n_tr], steps=max(1, args.warmup), batch=batch, lr=args.cnn_lr, seed=1)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    hist = learned.train(net, vol[:n_tr], tgt[:n_tr], steps=args.cnn_train_steps, batch=batch, lr=args.cnn_lr, seed=2,
-                         log_every=max(1, args.cnn_train_steps // 10), schedule="cosine")
+    net, init, hist, tries = learned.fit(vol[:n_tr], tgt[:n_tr], steps=args.cnn_train_steps, batch=batch,
+                                         lr=args.cnn_lr, seed=2, log_every=max(1, args.cnn_train_steps // 10))
     e1.record(stream)
     torch.cuda.synchronize()
-    train_ms = e0.elapsed_time(e1) / args.cnn_train_steps
+    train_ms = e0.elapsed_time(e1) / (args.cnn_train_steps * len(tries))
     held = slice(n_tr, n_ens)
     pd_cnn = learned.predict_pd(net, vol[held], scales[n_tr:], args.cnn_gain)
     inv = torch.tensor([1.0 / (s * s) for s in scales[n_tr:]], device=vol.device)[:, None]
@@ -772,7 +771,9 @@ def run_cnn(args, rank, world, local):
         "config": {"workload": f"C5 learned filter: inference on {Fi} x {Zi} x {Xi} (C2 ensemble); training on "
                                f"{n_tr} C1-like 64 x 32 x 32 ensembles, batch {batch}",
                    "train_ms_per_step": train_ms, "train_voxels_per_s": batch * F * Z * X / (train_ms * 1e-3),
-                   "train_loss": hist, "data_generation_s": gen_s,
+                   "train_loss": hist, "train_attempts": [{"init": t[0], "first_loss": t[1], "last_loss": t[2]}
+                                                           for t in tries],
+                   "data_generation_s": gen_s,
                    "l2": "inference working set (activations 0.84 GB per layer) far above L2"},
         "quality": quality,
         "roofline": {"bound": "tensor", "kernel": "conv_ring_kernel", "achieved": ach, "peak": peak,

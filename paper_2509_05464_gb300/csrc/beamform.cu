@@ -695,10 +695,11 @@ __device__ __forceinline__ void das_tile(const DasParams &p, int64_t bx, int by,
                     } else if (p.rot_tab) {
                         float sh, ch;
                         das_sincos_poly(p.pi_f0_fs * phi, sh, ch);
-                        const float ce = (ch - sh) * (ch + sh), se = 2.0f * sh * ch;
+                        const float ce = __fmul_rn(__fsub_rn(ch, sh), __fadd_rn(ch, sh));
+                        const float se = __fmul_rn(2.0f * sh, ch);
                         const float2 t = rot_s[i];
-                        cs = t.x * ce - t.y * se;
-                        sn = t.x * se + t.y * ce;
+                        cs = fmaf(t.x, ce, -__fmul_rn(t.y, se));
+                        sn = fmaf(t.x, se, __fmul_rn(t.y, ce));
                     } else {
                         const float cyc = fqi::ff_frac(fqi::ff_mul(u, f0_fs));
                         sincospif(2.0f * cyc, &sn, &cs);
@@ -884,10 +885,11 @@ __device__ __forceinline__ void das_tile_w(const DasParams &p, int64_t bx, int b
                     } else if (p.rot_tab) {
                         float sh, ch;
                         das_sincos_poly(p.pi_f0_fs * phi, sh, ch);
-                        const float ce = (ch - sh) * (ch + sh), se = 2.0f * sh * ch;
+                        const float ce = __fmul_rn(__fsub_rn(ch, sh), __fadd_rn(ch, sh));
+                        const float se = __fmul_rn(2.0f * sh, ch);
                         const float2 t = rot_s[i];
-                        cs = t.x * ce - t.y * se;
-                        sn = t.x * se + t.y * ce;
+                        cs = fmaf(t.x, ce, -__fmul_rn(t.y, se));
+                        sn = fmaf(t.x, se, __fmul_rn(t.y, ce));
                     } else {
                         const float cyc = fqi::ff_frac(fqi::ff_mul(u, f0_fs));
                         sincospif(2.0f * cyc, &sn, &cs);

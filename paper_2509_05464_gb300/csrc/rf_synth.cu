@@ -1059,23 +1059,25 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
             r0 = __fmul_rn(r2.hi, rs0);
             rl = pos0 ? __fmul_rn(__fadd_rn(__fmaf_rn(-r0, r0, r2.hi), r2.lo), 0.5f * rs0) : 0.0f;
         } else {
-            // ---- receive side, element 0: binary32 distance with one Newton correction
-            zzh = z * z;
-            dxh = x - exf[0];
+            // ---- receive side, element 0: binary32 distance with one Newton
+            // correction (explicitly rounded operations: the same results in
+            // every kernel that inlines this tile)
+            zzh = __fmul_rn(z, z);
+            dxh = __fsub_rn(x, exf[0]);
             if (use_y) {
-                dyh = y - eyf;
-                q2 = dyh * dyh;
+                dyh = __fsub_rn(y, eyf);
+                q2 = __fmul_rn(dyh, dyh);
             }
-            const float r2h = fmaf(dxh, dxh, zzh + q2);
+            const float r2h = fmaf(dxh, dxh, __fadd_rn(zzh, q2));
             pos0 = r2h > 0.0f;
             rs0 = pos0 ? rsqrtf(r2h) : 0.0f;
-            r0 = r2h * rs0;
-            rl = pos0 ? fmaf(-r0, r0, r2h) * (0.5f * rs0) : 0.0f;
+            r0 = __fmul_rn(r2h, rs0);
+            rl = pos0 ? __fmul_rn(fmaf(-r0, r0, r2h), __fmul_rn(0.5f, rs0)) : 0.0f;
         }
         // ---- receive side, every element: delay offset, directivity, R D / r
         const float zy2 = __fadd_rn(zzh, q2);  // z^2 (+ dy^2), binary32
-        const float r0f = r0 + rl;
-        const float r0K = FFD ? 0.0f : r0f * Kh;
+        const float r0f = __fadd_rn(r0, rl);
+        const float r0K = FFD ? 0.0f : __fmul_rn(r0f, Kh);
         float dxa[E], rsa[E], dee[E];
         bool liv[E];
 #pragma unroll
@@ -1088,11 +1090,12 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
                 dee[e] = 0.0f;
                 ok = pos0;
             } else {
-                dxe = x - exf[e];
+                dxe = __fsub_rn(x, exf[e]);
                 const float re2 = fmaf(dxe, dxe, zy2);
                 rse = rsqrtf(re2);
-                const float re = re2 * rse;
-                dee[e] = __fdividef(cd[e] * (fmaf(2.0f, x, -csh[e]) - csl[e]), re + r0f);  // r_e - r_0
+                const float re = __fmul_rn(re2, rse);
+                dee[e] = __fdividef(__fmul_rn(cd[e], __fsub_rn(fmaf(2.0f, x, -csh[e]), csl[e])),
+                                    __fadd_rn(re, r0f));  // r_e - r_0
                 ok = re2 > 0.0f;
             }
             dxa[e] = dxe;
@@ -1132,9 +1135,9 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
             } else {
                 // binary32: (u . r - origin) fs / c + r fs / c in samples
                 const float4 g = sh.angK[al + 1];
-                const float u = r0K + fmaf(g.x, x, fmaf(g.y, y, fmaf(g.z, z, g.w)));
+                const float u = __fadd_rn(r0K, fmaf(g.x, x, fmaf(g.y, y, fmaf(g.z, z, g.w))));
                 fl0 = floorf(u);
-                fr0 = u - fl0;
+                fr0 = __fsub_rn(u, fl0);
                 path_hi = u;  // the attenuation exponent takes samples here
             }
             // per element pair (0, 1), (2, 3), two lanes of packed f32x2 (element
@@ -1246,8 +1249,8 @@ __device__ __forceinline__ void rf_quad_tile(const RfParams &p, int bx, int ag, 
         const int e = rec & 3;
         if (e >= ne) continue;
         OutT *out = rf + (((int64_t)f * p.A + a0 + (rec >> 2)) * M + m0 + e) * ns;
-        const float v = (float)tile[i] * sh.q[rec];
-        fqi::store_f(out, k, sg == 0 ? v : fqi::load_f(out, k) + v);  // this CTA owns these samples
+        const float v = __fmul_rn((float)tile[i], sh.q[rec]);
+        fqi::store_f(out, k, sg == 0 ? v : __fadd_rn(fqi::load_f(out, k), v));  // this CTA owns these samples
     }
     }  // scatterer groups
 }

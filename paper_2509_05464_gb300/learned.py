@@ -77,7 +77,7 @@ def lr_at(step, steps, lr, schedule, warmup=200, floor=0.02):
     return lr * (floor + (1.0 - floor) * 0.5 * (1.0 + math.cos(math.pi * step / steps)))
 
 
-def train(net, vol, tgt, steps, batch=4, lr=1e-3, seed=0, log_every=0, schedule="constant"):
+def train(net, vol, tgt, steps, batch=4, lr=1e-3, seed=0, log_every=0, schedule="constant", warmup=200):
     """Adam on random mini-batches of the volumes (learning rate per
     lr_at); returns the loss history."""
     n, F, Z, X = vol.shape[:4]
@@ -94,12 +94,35 @@ def train(net, vol, tgt, steps, batch=4, lr=1e-3, seed=0, log_every=0, schedule=
         torch.index_select(tgt, 0, idx, out=tb)
         fq.fq_cnn_forward(net, xb, acts)
         fq.fq_cnn_backward(net, xb, tb, acts, grads, loss)
-        fq.fq_cnn_adam(net, grads, lr_at(step, steps, lr, schedule), step)
+        fq.fq_cnn_adam(net, grads, lr_at(step, steps, lr, schedule, warmup), step)
         if log_every and (step % log_every == 0 or step == 1):
             hist.append((step, float(loss.item())))
     if not log_every:
         hist.append((steps, float(loss.item())))
     return hist
+
+
+def fit(vol, tgt, steps, batch=4, lr=1e-3, seed=2, schedule="cosine", warmup=200, inits=(0, 1, 2), log_every=0):
+    """Train from the first of `inits` (weight seeds) whose run does not
+    collapse, with the batch order of `seed` + the attempt; returns (net,
+    init seed, loss history, attempts).  A collapse is a run whose hidden
+    ReLUs all go silent early, so the output stays at zero and the loss at
+    the target's power: its mean loss over the last tenth of the steps
+    (sampled every steps / 100) is at least 0.8 of the first step's (the
+    zero-initialised last layer makes the first loss the target power)."""
+    every = max(1, steps // 100)
+    tries = []
+    for a, init in enumerate(inits):
+        net = fq.CNN(init)
+        hist = train(net, vol, tgt, steps, batch=batch, lr=lr, seed=seed + a, schedule=schedule, warmup=warmup,
+                     log_every=every)
+        first = hist[0][1]
+        tail = float(np.mean([l for _, l in hist[-10:]]))
+        tries.append((init, first, tail))
+        if tail < 0.8 * first:
+            break
+    keep = [h for h in hist if not log_every or h[0] % log_every == 0 or h[0] == 1]
+    return net, init, keep, tries
 
 
 def predict_pd(net, vol, scales, target_gain=1.0):

@@ -6,6 +6,7 @@ import ctypes as C
 import math
 
 import pytest
+import torch
 
 from paper_2509_05464_gb300 import build as fqbuild
 from paper_2509_05464_gb300 import fq
@@ -34,15 +35,17 @@ def rf_angle_groups(A, Ns):
     return -(-A // ag)
 
 
-def expected_items(w, das_threads=128):
+def expected_items(w, das_threads=128, ch16=False):
     cd = lambda a, b: -(-a // b)
     Fp = fq.frame_pad(w.n_frames)
     L = w.A * w.M
     nt = cd(w.n_frames, 32)
     return {"classify": cd(w.S, 2048), "advect": cd(w.S, 2048) * w.n_frames,
             "rf": cd(w.M, 4) * rf_angle_groups(w.A, w.Ns) * w.n_frames, "rf2iq": cd(w.Ns, 128) * L * (Fp // 16),
-            # DAS tiles: das_threads / 4 voxels along x of one (y, z) row, per 16-frame chunk
-            "das": cd(w.grid.nx, das_threads // 4) * w.grid.ny * w.grid.nz * (Fp // 16),
+            # DAS tiles: voxels along x of one (y, z) row; FP32 channels das_threads / 4 of them
+            # per 16-frame chunk, 16-bit channels das_threads / 32 (a warp each) per 128 frames
+            "das": (cd(w.grid.nx, das_threads // 32) * w.grid.ny * w.grid.nz * cd(Fp, 128) if ch16 else
+                    cd(w.grid.nx, das_threads // 4) * w.grid.ny * w.grid.nz * (Fp // 16)),
             "gram_reduce": cd(w.n_frames ** 2, 256), "eig": 1,
             "project": cd(w.P, 64), "gram_pairs": nt * (nt + 1) // 2}
 
@@ -56,6 +59,11 @@ def test_item_counts_and_single_wave():
         assert items[st] == sum(expected_items(w)[st] for w in ms), st
     # Gram items = upper tile pairs x pixel chunks (at least one chunk each)
     assert items["gram"] >= sum(expected_items(w)["gram_pairs"] for w in ms)
+    b.close()
+    # BF16 storage: the DAS of 16-bit channel data tiles one warp per voxel
+    b = fq.Batch(ms, dtype=torch.bfloat16, plan_only=True)
+    _, items = b.info()
+    assert items["das"] == sum(expected_items(w, ch16=True)["das"] for w in ms)
     b.close()
 
 
