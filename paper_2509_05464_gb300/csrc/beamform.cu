@@ -742,13 +742,15 @@ __device__ __forceinline__ void das_tile(const DasParams &p, int64_t bx, int by,
 // delay and carrier rotation into the warp's slot table; then the warp walks
 // the group's elements with an echo in the record, each read back from the
 // table by every lane (a broadcast), so the loop has no divergence.  Lanes
-// whose frames lie beyond the padded count idle (F = 100: 28 of 32 lanes
-// work).  3D workload (128^3 voxels, 100 frames, BF16 channels): 690 ms
+// whose frames lie beyond the padded count repeat the last frame group and
+// discard it (F = 100: 28 of 32 lanes carry frames).  3D workload (128^3 voxels, 100 frames, BF16 channels): 662 ms
 // against 783 ms for four threads per pixel with two element and two frame
 // slots (8 frames per delay and thread, the first of these kernels to
 // share a delay over more than 4 frames) and 1031 ms for four threads per
 // pixel over 4 frames each; loading two elements before summing either
-// measured 684 ms (BF16) but 793 ms (FP16, 64 registers) and is not used.
+// (with the earlier per-lane test in the loop: 684 ms against 690 for BF16,
+// 793 against 719 for FP16) and precomputing the broadcast values (778 ms)
+// are not used.
 constexpr int kDasWarpFrames = 128;
 
 __host__ __device__ inline int das_w_off_slot(int M, int A, int NW) { return das_off_ptx(M) + ((2 * A * NW + 3) & ~3); }
@@ -853,7 +855,11 @@ __device__ __forceinline__ void das_tile_w(const DasParams &p, int64_t bx, int b
     static_assert(sizeof(ChT) == 2, "das_tile_w takes 16-bit channel data");
     RotAcc<4, 1, ChT> acc;
     acc.init();
-    const ChT *chp = ch + (int64_t)(fon ? f0 : 0) * 2;
+    // lanes past the padded frame count read the last frame group (their
+    // sums are never stored), so the element loop has no branch: 690 ->
+    // 662 ms on the 3D workload against a test per element
+    const ChT *chp = ch + (int64_t)(fon ? f0 : p.Fp - 4) * 2;
+    const unsigned rs32 = (unsigned)(p.Fp * 2);
 
     for (int r = row_lo; r <= row_hi; ++r) {
         for (int g0 = c_lo; g0 <= c_hi; g0 += 32) {
@@ -905,9 +911,7 @@ __device__ __forceinline__ void das_tile_w(const DasParams &p, int64_t bx, int b
                     const int j = __ffs(m) - 1;
                     m &= m - 1;
                     const float4 d = slot[j];
-                    if (fon)
-                        acc.add(cha + (uint64_t)(unsigned)__float_as_int(d.x) * (uint64_t)row_stride, row_stride,
-                                d.y, d.z, d.w);
+                    acc.add(cha + (uint64_t)(unsigned)__float_as_int(d.x) * rs32, row_stride, d.y, d.z, d.w);
                 }
                 __syncwarp();
             }
@@ -923,11 +927,12 @@ __device__ __forceinline__ void das_tile_w(const DasParams &p, int64_t bx, int b
     __syncthreads();  // a persistent CTA's next tile rewrites the shared tables
 }
 
-// Launch bounds give the thread count alone: for 256-thread CTAs of 16-bit
-// data ptxas then settles at 40 registers (a few spilled values), which ran
-// the 3D workload's DAS in 690 ms; minimum-block bounds that allow 42 to 48
-// registers without spills measured 795-799 ms, 70 registers 1089 ms, and
-// 128- or 512-thread CTAs 865 and 897 ms.
+// Launch bounds give the thread count alone; ptxas picks the register
+// count (48 for the branch-free element loop, 662 ms on the 3D workload; a
+// 6-CTA bound, at most 42, 669 ms).  With the earlier per-lane test in the
+// loop it picked 40 (a few spilled values, 690 ms), where bounds allowing
+// 42-48 registers without spills measured 795-799 ms and 70 registers
+// 1089 ms; 128- or 512-thread CTAs 865 and 897 ms.
 constexpr int kDasWarpThreads = 256;
 static_assert(kDasWarpFrames == fqb::kDasWarpFramesB, "batched item shapes");
 
