@@ -714,8 +714,12 @@ __device__ __forceinline__ void das_tile(const DasParams &p, int64_t bx, int by,
                     const float phj = __shfl_sync(0xffffffffu, phi, src);
                     const float snj = __shfl_sync(0xffffffffu, sn, src);
                     const float csj = __shfl_sync(0xffffffffu, cs, src);
-                    if (ij < 0) continue;
-                    acc.add(cha + (uint64_t)(unsigned)ij * (uint64_t)row_stride, row_stride, phj, csj, snj);
+                    // an element without an echo in the record reads row 0
+                    // with a zero rotation (adds exact zeros): no branch in
+                    // the loop, 5.03 -> 4.57 ms on the 2D workload
+                    const bool use = ij >= 0;
+                    acc.add(cha + (uint64_t)(unsigned)(use ? ij : 0) * (uint64_t)row_stride, row_stride, phj,
+                            use ? csj : 0.0f, use ? snj : 0.0f);
                 }
             }
         }
