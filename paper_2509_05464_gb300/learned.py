@@ -7,7 +7,9 @@ set to 0) are beamformed; the input is the whole-scene IQ divided by its
 RMS, the target the blood-only IQ divided by the same RMS, and the power
 Doppler of the ground truth is the blood-only PD.  Every numeric step
 (simulation, packing, convolutions, loss, gradients, Adam, PD) runs in
-libfq's kernels; this module only orders the calls.
+libfq's kernels; this module orders the calls, sets the learning rate of
+each step and decides restarts from the losses the kernels report
+(`rel_l2`, the error measure of finished results, runs in torch).
 """
 from __future__ import annotations
 
@@ -60,8 +62,7 @@ def ensembles(seeds, n_frames=64, Z=32, X=32, n_scat=2000, target_gain=1.0, remo
         _, _, sc = fq.fq_cnn_from_casorati(iq, n_frames, Z, X, remove_mean, vol=vol[i])
         fq.fq_cnn_from_casorati(iqb, n_frames, Z, X, remove_mean, scale_in=sc, gain=target_gain, target=tgt[i])
         scale = float(sc.item())
-        b = iqb.double()
-        pd_gt.append((b[..., 0] ** 2 + b[..., 1] ** 2).mean(dim=1).float())
+        pd_gt.append(fq.fq_power_doppler(iqb))
         pd_svd.append(pdsvd)
         scales.append(scale)
     return vol, tgt, scales, torch.stack(pd_gt), torch.stack(pd_svd)
