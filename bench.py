@@ -54,8 +54,9 @@ DAS_FLOP_PER_TRIPLE = 20.0
 # dram__bytes_write.sum); a workload is absent (traffic null) once the
 # kernel changes until it is captured again.
 RF_TRAFFIC_BYTES = {
-    # 3D volumetric, 100 frames, BF16 RF: 701,392,896 read + 2,823,366,144 written
-    "c3": 701_392_896 + 2_823_366_144,
+    # 3D volumetric, 100 frames, BF16 RF, all 9 transmits per CTA:
+    # 689,863,936 read + 2,824,233,472 written
+    "c3": 689_863_936 + 2_824_233_472,
 }
 
 

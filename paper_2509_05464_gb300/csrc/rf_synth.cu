@@ -37,12 +37,13 @@ using fqi::ff;
 
 constexpr int kMaxTaps = 64;  // pulse taps per (scatterer, element) pair the kernel supports
 // quad kernel: shared-memory records per CTA (angles x 4 elements x Ns int32)
-// up to this size (the more angles a CTA holds, the more of the receive
-// geometry it shares: on the 2D compounded workload 5 angles per CTA measured
-// 6% faster than 3).  The CTAs that fit per SM by shared memory split 32
-// resident warps (64 registers per thread): on that workload 32 warps ran
-// 9.4% faster than 16 (128 registers), 24 warps 7.8%.
-constexpr size_t kQuadRecordBudget = 200 * 1024;
+// up to kQuadSmemMax (below QuadShared): the more angles a CTA holds, the
+// more of the receive geometry, the scatterer loads and the bound pass it
+// shares (2D compounded workload: 5 angles per CTA 6% faster than 3; 3D
+// workload: all 9 angles, 216 KB of records at 1536 samples, 1686 ms against
+// 1821 ms for groups of 5 and 4).  The CTAs that fit per SM by shared memory
+// split 32 resident warps (64 registers per thread): on the 2D workload 32
+// warps ran 9.4% faster than 16 (128 registers), 24 warps 7.8%.
 inline int quad_ctas_per_sm(size_t smem) { return smem <= 52 * 1024 ? 4 : (smem <= 110 * 1024 ? 2 : 1); }
 
 struct RfParams {
@@ -732,6 +733,11 @@ struct QuadShared {
     float4 angFF[2 * FQ_MAX_ANGLES];   // pass 2: per angle (ux, uy) and (uz, origin) as float pairs
 };
 
+// Largest record (or bound-bin) area of a quad CTA: a block holds at most
+// 227 KB (232,448 bytes) of shared memory on this GPU, less the kernels'
+// static QuadShared and, in the batched kernel, the parameter block.
+constexpr size_t kQuadSmemMax = 232448 - sizeof(QuadShared) - (size_t)kRfParamBytes - 64;
+
 // an upper bound of |sin(u) / u| for |u| <= 5 (the fitted directivity's
 // range): 1 - u^2/6 + u^4/120 bounds sin(u)/u from above for every u (the
 // alternating series), is at least 0.16 on [pi, 5] where |sin(u)/u| < 0.22,
@@ -1375,7 +1381,7 @@ bool rf_fast_ok(const RfParams &p)
 
 // the quad kernel's records fit in shared memory and its rounding slack
 // (half a quantum per scatterer) stays far below the int32 range
-bool quad_ok(const RfParams &p) { return quad_smem(p) <= 200 * 1024 && p.S < (int64_t(1) << 30); }
+bool quad_ok(const RfParams &p) { return quad_smem(p) <= kQuadSmemMax && p.S < (int64_t(1) << 30); }
 
 template <typename OutT>
 fq_status dispatch_rf(const RfParams &p, int F, const float *pos, const float *amp, const float *base,
@@ -1502,13 +1508,13 @@ fq_status make_rf_params(const fq_probe *probe, const fq_tx *tx, int64_t S, RfPa
     p.two_cos_c = (float)(2.0 * std::cos(wc));
     p.two_cycle = probe->n_cycles == 2;
     fqi::make_angles_ff(probe, tx, p.ang);
-    // quad kernel: angle groups as large as the record budget allows, balanced
-    // (FQ_RF_AG_KB, 16-200, overrides the budget in KB for tuning)
+    // quad kernel: angle groups as large as the shared memory allows, balanced
+    // (FQ_RF_AG_KB, at least 16, lowers the budget in KB for tuning)
     const size_t per_angle = 4 * sizeof(int) * (size_t)probe->n_samples;
-    size_t budget = kQuadRecordBudget;
+    size_t budget = kQuadSmemMax;
     if (const char *env = std::getenv("FQ_RF_AG_KB")) {
         const long kb = std::atol(env);
-        if (kb >= 16 && kb <= 200) budget = (size_t)kb * 1024;
+        if (kb >= 16 && (size_t)kb * 1024 <= kQuadSmemMax) budget = (size_t)kb * 1024;
     }
     int ag = (int)std::max<size_t>(1, budget / per_angle);
     ag = std::min(ag, p.A);

@@ -29,9 +29,11 @@ def test_struct_layouts_match_library():
 
 
 def rf_angle_groups(A, Ns):
-    """the quad RF kernel holds as many transmits per CTA as 200 KB of int32
-    records (4 elements x Ns samples each) allow, in balanced groups"""
-    ag = min(max(1, 200 * 1024 // (16 * Ns)), A)
+    """the quad RF kernel holds as many transmits per CTA as its shared
+    memory allows int32 records (4 elements x Ns samples each): 222,816
+    bytes, 227 KB per block less the kernels' static shared memory, in
+    balanced groups"""
+    ag = min(max(1, 222816 // (16 * Ns)), A)
     return -(-A // ag)
 
 
