@@ -19,8 +19,13 @@
  * frequency-domain PFIELD model (Eq. 1).  The paper prints no echo values,
  * and the narrowband time-domain restatement used here differs from Eq. 1
  * by design (ideal plane-wave transmit, single point per element, no
- * elevation focusing); only its internal physics (time of flight, pulse
- * energy, attenuation, directivity, superposition, symmetry) is pinned.
+ * elevation focusing); its internal physics (time of flight, pulse energy,
+ * attenuation, directivity, superposition, symmetry) is pinned, and so is
+ * its agreement with this file's frequency-domain form in the narrowband
+ * limit.  The transmit sum over elements and sub-elements of Eq. 1-2
+ * (or_simulate_rf_pfield) is pinned on its own (single-element spectrum,
+ * superposition over weights, far-field limit, steered arrival time); the
+ * ratio between an ideal unit plane wave and that sum is the free constant.
  */
 #include <math.h>
 #include <stdint.h>
